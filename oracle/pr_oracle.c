@@ -1,0 +1,594 @@
+/*
+ * Plain FP64 CPU oracle for the real-fluid property evaluation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * bench's CPU-baseline / reference arm load this library.  The CUDA library
+ * shares no code, header, table or constant with it: every constant below is
+ * written here on its own, and the species data arrive as arguments.
+ *
+ * What it computes, per cell (T, p, Y_1..Y_N), following the paper's Sec. 2
+ * (Eq. 1 and the text after it) and the published methods that the paper
+ * delegates to Cantera:
+ *   1. mole fractions X_k and mean molar mass;
+ *   2. Peng-Robinson pure-species a_c, b (Eq. 1 constants, taken at their exact
+ *      critical-point values; the printed 0.45724 / 0.07780 are their roundings)
+ *      and the PR-1976 alpha(T, omega);
+ *   3. van der Waals one-fluid mixing a_m = sum_i sum_j X_i X_j (1-k_ij)
+ *      sqrt(a_i a_j), b_m = sum X_i b_i, with first and second T-derivatives,
+ *      as the plain double sum;
+ *   4. all real roots of the PR cubic in Z by bracketing + bisection, the
+ *      physical root being the one with Z > B and least residual Gibbs energy;
+ *   5. density, departure enthalpy and heat capacity on NASA-7 ideal-gas terms;
+ *   6. Chung et al. (1988) dense-fluid viscosity and conductivity with Chung's
+ *      mixture corresponding-states rules (the paper's "modified Chung's
+ *      transport model", Sec. 2);
+ *   7. the inversion T(h, p, Y) by a safeguarded Newton iteration.
+ * Nothing is blocked, fused or factorised beyond these definitions.
+ *
+ * Parity pins (tests, CPU only): Z_c of a pure species at its critical point,
+ * the low-pressure (ideal-gas) limit, cp against the finite-difference dh/dT,
+ * all cubic roots against high-precision polynomial roots and brute-force sign
+ * scans, T(h(T)) = T, mixing invariances, the dilute limit of the Chung
+ * correlations, and the paper's Table 1 kinematic viscosity of LOX.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_R 8.314462618 /* J/(mol K) */
+
+/* Species data, all arrays of length N (nasa_*: N x 7, kij: N x N or NULL). */
+typedef struct {
+    int32_t N;
+    int32_t transport_rule;     /* 0: Chung mixture rules; 1: mole-fraction average of pure-species Chung viscosity */
+    int32_t printed_constants;  /* 1: use the printed 0.45724 / 0.07780 instead of the exact values */
+    int32_t pad;
+    const double *W;            /* g/mol */
+    const double *Tc, *pc, *omega, *Vc; /* K, Pa, -, cm^3/mol */
+    const double *dipole, *kappa;       /* debye, - */
+    const double *nasa_lo, *nasa_hi;    /* N x 7 */
+    const double *T_mid;                /* K */
+    const double *kij;                  /* N x N or NULL (zero) */
+} orc_species;
+
+/* Per-cell diagnostics for the tests. */
+typedef struct {
+    double Wbar;                 /* kg/mol */
+    double am, dam, d2am, bm;    /* mixture a, da/dT, d2a/dT2 (J m^3/mol^2), b (m^3/mol) */
+    double A, B;                 /* dimensionless cubic parameters */
+    double roots[3];             /* all real roots, ascending */
+    int32_t n_roots;             /* number of real roots */
+    int32_t n_phys;              /* roots with Z > B */
+    double Z;                    /* selected root */
+    double gres_gap;             /* |g1 - g2| between the two best physical roots (or +inf) */
+    double cond;                 /* root condition number */
+    double h_ig, cp_ig, cv_ig_molar; /* J/kg, J/(kg K), J/(mol K) */
+    double h_dep, cp_dep;        /* J/mol, J/(mol K) */
+    double dpdT, dpdV;           /* (dp/dT)_V, (dp/dV)_T */
+    double mu_dilute, lambda_dilute; /* Pa s, W/(m K): the y -> 0 limit of the dense forms */
+} orc_diag;
+
+enum { ORC_OK = 0, ORC_NEWTON_MAXIT = 1, ORC_H_OUT_OF_RANGE = 2, ORC_NO_ROOT = 3,
+       ORC_BAD_INPUT = 4, ORC_AMBIGUOUS = 5 };
+
+/* ---------------------------------------------------------------------- */
+/* PR constants from the critical-point condition.  At T = Tc, p = pc the
+ * cubic in Z has a triple root Z_c; matching (Z - Z_c)^3 term by term gives
+ * Z_c = (1 - B_c)/3, A_c = 3 Z_c^2 + 3 B_c^2 + 2 B_c and, for B_c = Omega_b,
+ * 64 x^3 + 6 x^2 + 12 x - 1 = 0.  The root is found by bisection here. */
+static void orc_pr_omegas(int printed, double *Oa, double *Ob)
+{
+    if (printed) { *Oa = 0.45724; *Ob = 0.07780; return; }
+    double lo = 0.0, hi = 0.5;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double f = ((64.0 * mid + 6.0) * mid + 12.0) * mid - 1.0;
+        if (f > 0) hi = mid; else lo = mid;
+    }
+    double b = 0.5 * (lo + hi);
+    double zc = (1.0 - b) / 3.0;
+    *Ob = b;
+    *Oa = 3.0 * zc * zc + 3.0 * b * b + 2.0 * b;
+}
+
+void orc_pr_constants(int printed, double *Oa, double *Ob) { orc_pr_omegas(printed, Oa, Ob); }
+
+/* ---------------------------------------------------------------------- */
+/* Cubic Z^3 + c2 Z^2 + c1 Z + c0 (Eq. 1 written in Z = pV/RT). */
+static double cubic_eval(double c2, double c1, double c0, double z)
+{
+    return ((z + c2) * z + c1) * z + c0;
+}
+
+static double bisect_root(double c2, double c1, double c0, double lo, double hi)
+{
+    double flo = cubic_eval(c2, c1, c0, lo);
+    if (flo == 0.0) return lo;
+    double fhi = cubic_eval(c2, c1, c0, hi);
+    if (fhi == 0.0) return hi;
+    for (int it = 0; it < 2000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double fm = cubic_eval(c2, c1, c0, mid);
+        if (fm == 0.0) return mid;
+        if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; fhi = fm; }
+    }
+    double z = 0.5 * (lo + hi);
+    /* two Newton polish steps, kept only if they reduce |P| */
+    for (int k = 0; k < 2; ++k) {
+        double f = cubic_eval(c2, c1, c0, z);
+        double d = (3.0 * z + 2.0 * c2) * z + c1;
+        if (d == 0.0) break;
+        double zn = z - f / d;
+        if (fabs(cubic_eval(c2, c1, c0, zn)) < fabs(f)) z = zn;
+    }
+    return z;
+}
+
+/* All real roots of Z^3 + c2 Z^2 + c1 Z + c0, ascending.  Returns their count.
+ * The real line is cut at the critical points of the cubic (roots of its
+ * derivative) into monotone pieces; each piece with a sign change holds one
+ * root, found by bisection.  A critical point where the cubic vanishes to
+ * within rounding is a double root and is reported once. */
+int orc_cubic_real_roots(double c2, double c1, double c0, double roots[3])
+{
+    double M = 1.0 + fmax(fabs(c2), fmax(fabs(c1), fabs(c0)));  /* Cauchy bound */
+    double pts[4];
+    int np = 0;
+    pts[np++] = -M;
+    double disc = c2 * c2 - 3.0 * c1;           /* derivative 3z^2 + 2 c2 z + c1 */
+    double crit[2]; int nc = 0;
+    if (disc > 0) {
+        double s = sqrt(disc);
+        crit[0] = (-c2 - s) / 3.0;
+        crit[1] = (-c2 + s) / 3.0;
+        nc = 2;
+        pts[np++] = crit[0];
+        pts[np++] = crit[1];
+    }
+    pts[np++] = M;
+    int n = 0;
+    for (int k = 0; k + 1 < np; ++k) {
+        double a = pts[k], b = pts[k + 1];
+        double fa = cubic_eval(c2, c1, c0, a), fb = cubic_eval(c2, c1, c0, b);
+        if ((fa < 0 && fb > 0) || (fa > 0 && fb < 0)) {
+            roots[n++] = bisect_root(c2, c1, c0, a, b);
+        }
+    }
+    /* touching roots at the critical points */
+    for (int k = 0; k < nc; ++k) {
+        double z = crit[k];
+        double f = cubic_eval(c2, c1, c0, z);
+        double scale = fabs(z * z * z) + fabs(c2 * z * z) + fabs(c1 * z) + fabs(c0);
+        if (fabs(f) <= 8.0 * 2.220446049250313e-16 * scale) {
+            int dup = 0;
+            for (int j = 0; j < n; ++j) if (fabs(roots[j] - z) <= 1e-7 * (1.0 + fabs(z))) dup = 1;
+            if (!dup && n < 3) roots[n++] = z;
+        }
+    }
+    /* ascending */
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (roots[j] < roots[i]) { double t = roots[i]; roots[i] = roots[j]; roots[j] = t; }
+    return n;
+}
+
+/* Residual Gibbs energy g = G_res/(RT) of the PR fluid at root Z. */
+static double pr_gres(double Z, double A, double B)
+{
+    const double s2 = sqrt(2.0);
+    return Z - 1.0 - log(Z - B) - A / (2.0 * s2 * B) * log((Z + (1.0 + s2) * B) / (Z + (1.0 - s2) * B));
+}
+
+double orc_pr_gres(double Z, double A, double B) { return pr_gres(Z, A, B); }
+
+/* ---------------------------------------------------------------------- */
+/* NASA-7 ideal-gas cp/R and h/(RT) of one species (two T ranges; the low set
+ * below T_mid, the high set at and above it; evaluated outside [T_low,
+ * T_high] by extrapolation). */
+static void nasa7(const double *lo, const double *hi, double Tmid, double T, double *cpR, double *hRT, double *dcpR)
+{
+    const double *a = (T < Tmid) ? lo : hi;
+    *cpR = a[0] + a[1] * T + a[2] * T * T + a[3] * T * T * T + a[4] * T * T * T * T;
+    *hRT = a[0] + a[1] * T / 2.0 + a[2] * T * T / 3.0 + a[3] * T * T * T / 4.0 + a[4] * T * T * T * T / 5.0 + a[5] / T;
+    if (dcpR) *dcpR = a[1] + 2.0 * a[2] * T + 3.0 * a[3] * T * T + 4.0 * a[4] * T * T * T;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Chung et al. (1988) coefficient tables: E_i = a + b*omega + c*mu_r^4 + d*kappa
+ * for the viscosity (i = 1..10) and B_i for the conductivity (i = 1..7),
+ * as tabulated in Poling, Prausnitz & O'Connell, Tables 9-6 and 10-3. */
+static const double CHUNG_VISC[10][4] = {
+    {6.324, 50.412, -51.680, 1189.0},
+    {1.210e-3, -1.154e-3, -6.257e-3, 0.03728},
+    {5.283, 254.209, -168.48, 3898.0},
+    {6.623, 38.096, -8.464, 31.42},
+    {19.745, 7.630, -14.354, 31.53},
+    {-1.900, -12.537, 4.985, -18.15},
+    {24.275, 3.450, -11.291, 69.35},
+    {0.7972, 1.117, 0.01235, -4.117},
+    {-0.2382, 0.06770, -0.8163, 4.025},
+    {0.06863, 0.3479, 0.5926, -0.727},
+};
+static const double CHUNG_COND[7][4] = {
+    {2.4166, 0.74824, -0.91858, 121.72},
+    {-0.50924, -1.5094, -49.991, 69.983},
+    {6.6107, 5.6207, 64.760, 27.039},
+    {14.543, -8.9139, -5.6379, 74.344},
+    {0.79274, 0.82019, -0.69369, 6.3173},
+    {-5.8634, 12.801, 9.5893, 65.529},
+    {91.089, 128.11, -54.217, 523.81},
+};
+
+/* Neufeld et al. (1972) reduced collision integral for viscosity, as used by Chung. */
+static double neufeld_omega_v(double Ts)
+{
+    return 1.16145 * pow(Ts, -0.14874) + 0.52487 * exp(-0.77320 * Ts) + 2.16178 * exp(-2.43787 * Ts);
+}
+
+/* Corresponding-states inputs of one Chung evaluation. */
+typedef struct {
+    double Tc, Vc, omega, M, mur4, kappa; /* K, cm^3/mol, -, g/mol, -, - */
+} chung_cs;
+
+/* Chung dense-fluid viscosity [Pa s] and conductivity [W/(m K)] of a fluid
+ * with corresponding-states parameters cs at temperature T, molar density
+ * rho_mol [mol/m^3] and ideal-gas molar cv (for the conductivity). */
+static void chung_dense(const chung_cs *cs, double T, double rho_mol, double cv_molar,
+                        double *mu, double *lam, double *mu0, double *lam0)
+{
+    double Ts = 1.2593 * T / cs->Tc;
+    double Fc = 1.0 - 0.2756 * cs->omega + 0.059035 * cs->mur4 + cs->kappa;
+    double Ov = neufeld_omega_v(Ts);
+    double y = rho_mol * 1e-6 * cs->Vc / 6.0;       /* rho in mol/cm^3 */
+    double G1 = (1.0 - 0.5 * y) / ((1.0 - y) * (1.0 - y) * (1.0 - y));
+    double E[10];
+    for (int i = 0; i < 10; ++i)
+        E[i] = CHUNG_VISC[i][0] + CHUNG_VISC[i][1] * cs->omega + CHUNG_VISC[i][2] * cs->mur4 + CHUNG_VISC[i][3] * cs->kappa;
+    /* (1 - exp(-E4 y))/y, with its limit E4 as y -> 0 */
+    double fy4 = (y > 0) ? -expm1(-E[3] * y) / y : E[3];
+    double G2 = (E[0] * fy4 + E[1] * G1 * exp(E[4] * y) + E[2] * G1) / (E[0] * E[3] + E[1] + E[2]);
+    double etass = E[6] * y * y * G2 * exp(E[7] + E[8] / Ts + E[9] / (Ts * Ts));
+    double etas = sqrt(Ts) / Ov * Fc * (1.0 / G2 + E[5] * y) + etass;
+    double Vc23 = pow(cs->Vc, 2.0 / 3.0);
+    double eta_uP = etas * 36.344 * sqrt(cs->M * cs->Tc) / Vc23;
+    *mu = eta_uP * 1e-7;
+    /* dilute gas viscosity (the y -> 0 limit of the dense form) */
+    double eta0_uP = 40.785 * Fc * sqrt(cs->M * T) / (Vc23 * Ov);
+    double eta0 = eta0_uP * 1e-7;
+    *mu0 = eta0;
+    /* conductivity */
+    double Bc[7];
+    for (int i = 0; i < 7; ++i)
+        Bc[i] = CHUNG_COND[i][0] + CHUNG_COND[i][1] * cs->omega + CHUNG_COND[i][2] * cs->mur4 + CHUNG_COND[i][3] * cs->kappa;
+    double fyb4 = (y > 0) ? -expm1(-Bc[3] * y) / y : Bc[3];
+    double H2 = (Bc[0] * fyb4 + Bc[1] * G1 * exp(Bc[4] * y) + Bc[2] * G1) / (Bc[0] * Bc[3] + Bc[1] + Bc[2]);
+    double Tr = T / cs->Tc;
+    double alpha = cv_molar / ORC_R - 1.5;
+    double beta = 0.7862 - 0.7109 * cs->omega + 1.3168 * cs->omega * cs->omega;
+    double Zp = 2.0 + 10.5 * Tr * Tr;
+    double Psi = 1.0 + alpha * ((0.215 + 0.28288 * alpha - 1.061 * beta + 0.26665 * Zp) /
+                                (0.6366 + beta * Zp + 1.061 * alpha * beta));
+    double Mkg = cs->M * 1e-3;
+    double q = 3.586e-3 * sqrt(cs->Tc / Mkg) / Vc23;
+    *lam = 31.2 * eta0 * Psi / Mkg * (1.0 / H2 + Bc[5] * y) + q * Bc[6] * y * y * sqrt(Tr) * H2;
+    *lam0 = 31.2 * eta0 * Psi / Mkg;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Thermodynamic part of one cell: everything up to h and cp.  Returns the
+ * status (0, 3, 4 or 5).  Output arrays may be NULL except d. */
+static int cell_thermo(const orc_species *sp, double T, double p, const double *Y, ptrdiff_t ystride,
+                       double *X, orc_diag *d)
+{
+    const int N = sp->N;
+    memset(d, 0, sizeof(*d));
+    if (!(T > 0) || !(p > 0) || !isfinite(T) || !isfinite(p)) return ORC_BAD_INPUT;
+    double ysum = 0.0, s = 0.0;
+    for (int k = 0; k < N; ++k) {
+        double y = Y[k * ystride];
+        if (!(y >= 0.0) || !isfinite(y)) return ORC_BAD_INPUT;
+        ysum += y;
+        s += y / (sp->W[k] * 1e-3);
+    }
+    if (fabs(ysum - 1.0) > 1e-6) return ORC_BAD_INPUT;
+    /* 1. mole fractions */
+    for (int k = 0; k < N; ++k) X[k] = (Y[k * ystride] / (sp->W[k] * 1e-3)) / s;
+    double Wbar = 0.0;
+    for (int k = 0; k < N; ++k) Wbar += X[k] * sp->W[k] * 1e-3;
+    d->Wbar = Wbar;
+
+    /* 2. pure-species PR parameters and alpha(T, omega) (PR 1976) */
+    double Oa, Ob;
+    orc_pr_omegas(sp->printed_constants, &Oa, &Ob);
+    double a[64], r[64], dr[64], d2r[64], b[64];
+    for (int k = 0; k < N; ++k) {
+        double Tc = sp->Tc[k], pc = sp->pc[k], w = sp->omega[k];
+        double ac = Oa * ORC_R * ORC_R * Tc * Tc / pc;
+        b[k] = Ob * ORC_R * Tc / pc;
+        double kap = 0.37464 + 1.54226 * w - 0.26992 * w * w;
+        double u = 1.0 + kap * (1.0 - sqrt(T / Tc));
+        a[k] = ac * u * u;                             /* a_k(T) */
+        double sg = (u >= 0.0) ? 1.0 : -1.0;           /* one-sided at u = 0 */
+        r[k] = sqrt(ac) * fabs(u);                     /* sqrt(a_k) */
+        dr[k] = -sg * sqrt(ac) * kap / (2.0 * sqrt(T * Tc));
+        d2r[k] = sg * sqrt(ac) * kap / (4.0 * sqrt(Tc)) * pow(T, -1.5);
+    }
+    /* 3. van der Waals mixing: plain double sums */
+    double am = 0, dam = 0, d2am = 0, bm = 0;
+    for (int i = 0; i < N; ++i) {
+        bm += X[i] * b[i];
+        for (int j = 0; j < N; ++j) {
+            double kk = sp->kij ? (1.0 - sp->kij[i * N + j]) : 1.0;
+            double w2 = X[i] * X[j] * kk;
+            am += w2 * sqrt(a[i] * a[j]);
+            dam += w2 * (dr[i] * r[j] + r[i] * dr[j]);
+            d2am += w2 * (d2r[i] * r[j] + 2.0 * dr[i] * dr[j] + r[i] * d2r[j]);
+        }
+    }
+    d->am = am; d->dam = dam; d->d2am = d2am; d->bm = bm;
+
+    /* 4. cubic and root selection */
+    double RT = ORC_R * T;
+    double A = am * p / (RT * RT), B = bm * p / RT;
+    d->A = A; d->B = B;
+    double c2 = -(1.0 - B), c1 = A - 3.0 * B * B - 2.0 * B, c0 = -(A * B - B * B - B * B * B);
+    d->n_roots = orc_cubic_real_roots(c2, c1, c0, d->roots);
+    double best = NAN, gbest = INFINITY, gsecond = INFINITY;
+    int nphys = 0;
+    for (int k = 0; k < d->n_roots; ++k) {
+        double z = d->roots[k];
+        if (!(z > B)) continue;
+        ++nphys;
+        double g = pr_gres(z, A, B);
+        if (nphys == 1) { best = z; gbest = g; continue; }
+        double gap = fabs(g - gbest);
+        if (g < gbest - 1e-12 || (gap <= 1e-12 && z > best)) {
+            gsecond = gbest; gbest = g; best = z;
+        } else if (g < gsecond) {
+            gsecond = g;
+        }
+    }
+    d->n_phys = nphys;
+    d->gres_gap = (nphys > 1) ? fabs(gsecond - gbest) : INFINITY;
+    if (nphys == 0) return ORC_NO_ROOT;
+    double Z = best;
+    d->Z = Z;
+    {
+        double dP = (3.0 * Z + 2.0 * c2) * Z + c1;
+        double num = fabs(Z * Z * Z) + fabs(c2) * Z * Z + fabs(c1) * fabs(Z) + fabs(c0);
+        d->cond = num / (fabs(Z) * fabs(dP));
+    }
+
+    /* 5. ideal-gas part (NASA-7) */
+    double h_ig = 0, cp_ig = 0;
+    for (int k = 0; k < N; ++k) {
+        double cpR, hRT;
+        nasa7(sp->nasa_lo + 7 * k, sp->nasa_hi + 7 * k, sp->T_mid[k], T, &cpR, &hRT, NULL);
+        double Wk = sp->W[k] * 1e-3;
+        h_ig += Y[k * ystride] * hRT * ORC_R * T / Wk;
+        cp_ig += Y[k * ystride] * cpR * ORC_R / Wk;
+    }
+    d->h_ig = h_ig; d->cp_ig = cp_ig;
+    d->cv_ig_molar = cp_ig * Wbar - ORC_R;
+
+    /* 6. departures from the PR residual Helmholtz energy */
+    const double s2 = sqrt(2.0);
+    double V = Z * RT / p;
+    double L = log((Z + (1.0 + s2) * B) / (Z + (1.0 - s2) * B));
+    double h_dep = RT * (Z - 1.0) + (T * dam - am) / (2.0 * s2 * bm) * L;
+    double cv_dep = T * d2am / (2.0 * s2 * bm) * L;
+    double den = V * V + 2.0 * bm * V - bm * bm;
+    double dpdT = ORC_R / (V - bm) - dam / den;
+    double dpdV = -RT / ((V - bm) * (V - bm)) + 2.0 * am * (V + bm) / (den * den);
+    double cp_dep = cv_dep - T * dpdT * dpdT / dpdV - ORC_R;
+    d->h_dep = h_dep; d->cp_dep = cp_dep; d->dpdT = dpdT; d->dpdV = dpdV;
+    if (nphys > 1 && d->gres_gap < 1e-9) return ORC_AMBIGUOUS;
+    return ORC_OK;
+}
+
+/* Chung transport for a thermodynamic state already evaluated. */
+static void cell_transport(const orc_species *sp, double T, double p, const double *X, const orc_diag *d,
+                           double *mu, double *lam, double *mu0, double *lam0)
+{
+    const int N = sp->N;
+    double rho_mol = p / (d->Z * ORC_R * T);            /* mol/m^3 */
+    if (sp->transport_rule == 1) {
+        /* mole-fraction-averaged pure-species Chung properties */
+        double m = 0, l = 0, m0 = 0, l0 = 0;
+        for (int k = 0; k < N; ++k) {
+            chung_cs cs;
+            cs.Tc = sp->Tc[k]; cs.Vc = sp->Vc[k]; cs.omega = sp->omega[k]; cs.M = sp->W[k];
+            double mur = 131.3 * sp->dipole[k] / sqrt(sp->Vc[k] * sp->Tc[k]);
+            cs.mur4 = mur * mur * mur * mur; cs.kappa = sp->kappa[k];
+            double mk, lk, m0k, l0k;
+            chung_dense(&cs, T, rho_mol, d->cv_ig_molar, &mk, &lk, &m0k, &l0k);
+            m += X[k] * mk; l += X[k] * lk; m0 += X[k] * m0k; l0 += X[k] * l0k;
+        }
+        *mu = m; *lam = l; *mu0 = m0; *lam0 = l0;
+        return;
+    }
+    /* Chung mixing rules: sigma_i = 0.809 Vc^(1/3) [A], eps_i/k = Tc/1.2593,
+     * pair values by geometric/arithmetic/harmonic combining, then
+     * sigma_m^3, (eps/k)_m, M_m, omega_m, mu_m^4, kappa_m as double sums. */
+    double s3 = 0, e_s3 = 0, e_s2_M = 0, w_s3 = 0, mu4_sum = 0, kap = 0;
+    for (int i = 0; i < N; ++i) {
+        double si = 0.809 * cbrt(sp->Vc[i]), ei = sp->Tc[i] / 1.2593;
+        for (int j = 0; j < N; ++j) {
+            double sj = 0.809 * cbrt(sp->Vc[j]), ej = sp->Tc[j] / 1.2593;
+            double sij = sqrt(si * sj), eij = sqrt(ei * ej);
+            double wij = 0.5 * (sp->omega[i] + sp->omega[j]);
+            double Mij = 2.0 * sp->W[i] * sp->W[j] / (sp->W[i] + sp->W[j]);
+            double kij = sqrt(sp->kappa[i] * sp->kappa[j]);
+            double xx = X[i] * X[j];
+            double sij3 = sij * sij * sij;
+            s3 += xx * sij3;
+            e_s3 += xx * eij * sij3;
+            e_s2_M += xx * eij * sij * sij * sqrt(Mij);
+            w_s3 += xx * wij * sij3;
+            mu4_sum += xx * sp->dipole[i] * sp->dipole[i] * sp->dipole[j] * sp->dipole[j] / sij3;
+            kap += xx * kij;
+        }
+    }
+    double sm = cbrt(s3);
+    double em = e_s3 / s3;
+    double Mm_root = e_s2_M / (em * sm * sm);
+    chung_cs cs;
+    cs.M = Mm_root * Mm_root;
+    cs.omega = w_s3 / s3;
+    double mum4 = s3 * mu4_sum;                          /* debye^4 */
+    cs.kappa = kap;
+    cs.Vc = pow(sm / 0.809, 3.0);
+    cs.Tc = 1.2593 * em;
+    double mum = sqrt(sqrt(mum4));
+    double mur = 131.3 * mum / sqrt(cs.Vc * cs.Tc);
+    cs.mur4 = mur * mur * mur * mur;
+    chung_dense(&cs, T, rho_mol, d->cv_ig_molar, mu, lam, mu0, lam0);
+}
+
+/* One cell, all outputs.  out = {rho, Z, h, cp, mu, lambda}. */
+int orc_cell(const orc_species *sp, double T, double p, const double *Y, ptrdiff_t ystride,
+             double out[6], orc_diag *diag)
+{
+    double X[64];
+    orc_diag dl;
+    orc_diag *d = diag ? diag : &dl;
+    int st = cell_thermo(sp, T, p, Y, ystride, X, d);
+    if (st != ORC_OK && st != ORC_AMBIGUOUS) {
+        for (int q = 0; q < 6; ++q) out[q] = NAN;
+        return st;
+    }
+    double Z = d->Z;
+    out[0] = p * d->Wbar / (Z * ORC_R * T);
+    out[1] = Z;
+    out[2] = d->h_ig + d->h_dep / d->Wbar;
+    out[3] = d->cp_ig + d->cp_dep / d->Wbar;
+    double mu0, lam0;
+    cell_transport(sp, T, p, X, d, &out[4], &out[5], &mu0, &lam0);
+    d->mu_dilute = mu0; d->lambda_dilute = lam0;
+    return st;
+}
+
+/* Batch over n cells, SoA: T[n], p[n], Y[N*n] species-major; out[6*n] as
+ * rho, Z, h, cp, mu, lambda blocks of n; status[n] may be NULL.  nthreads <= 0
+ * uses the OpenMP default. */
+void orc_props(const orc_species *sp, int64_t n, const double *T, const double *p, const double *Y,
+               double *out, int32_t *status, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        double o[6];
+        int st = orc_cell(sp, T[i], p[i], Y + i, (ptrdiff_t)n, o, NULL);
+        for (int q = 0; q < 6; ++q) out[q * n + i] = o[q];
+        if (status) status[i] = st;
+    }
+    (void)nthreads;
+}
+
+/* Diagnostics for n cells (serial). */
+void orc_diagnose(const orc_species *sp, int64_t n, const double *T, const double *p, const double *Y,
+                  double *out, int32_t *status, orc_diag *diag)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double o[6];
+        int st = orc_cell(sp, T[i], p[i], Y + i, (ptrdiff_t)n, o, &diag[i]);
+        for (int q = 0; q < 6; ++q) out[q * n + i] = o[q];
+        if (status) status[i] = st;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Inversion T(h*, p, Y): safeguarded Newton on f(T) = h(T) - h*, f' = cp.
+ * Bracket [60, 5000] K.  A Newton step that leaves the current bracket, or
+ * that follows a step which failed to halve |f|, is replaced by bisection.
+ * Stops when |dT| <= 1e-13 T or |f| <= 1e-13 max(|h*|, cp T).  Status 1 after
+ * max_iter iterations; status 2 when h* lies outside [h(60 K), h(5000 K)]
+ * (T clamped to the bracket end) or when the bracket collapses onto a jump of
+ * h(T) (a switch of the physical root) that h* falls inside. */
+static int cell_h(const orc_species *sp, double T, double p, const double *Y, ptrdiff_t ys, double *h, double *cp)
+{
+    double X[64];
+    orc_diag d;
+    int st = cell_thermo(sp, T, p, Y, ys, X, &d);
+    if (st != ORC_OK && st != ORC_AMBIGUOUS) return st;
+    *h = d.h_ig + d.h_dep / d.Wbar;
+    *cp = d.cp_ig + d.cp_dep / d.Wbar;
+    return ORC_OK;
+}
+
+int orc_T_from_h_cell(const orc_species *sp, double hstar, double p, const double *Y, ptrdiff_t ys,
+                      double Tguess, int max_iter, double rtol, double *Tout, int *iters)
+{
+    const double Tlo0 = 60.0, Thi0 = 5000.0;
+    double hlo, cplo, hhi, cphi;
+    *iters = 0;
+    if (!isfinite(hstar) || !isfinite(Tguess)) { *Tout = NAN; return ORC_BAD_INPUT; }
+    int st = cell_h(sp, Tlo0, p, Y, ys, &hlo, &cplo);
+    if (st) { *Tout = NAN; return st; }
+    st = cell_h(sp, Thi0, p, Y, ys, &hhi, &cphi);
+    if (st) { *Tout = NAN; return st; }
+    if (hstar < hlo) { *Tout = Tlo0; return ORC_H_OUT_OF_RANGE; }
+    if (hstar > hhi) { *Tout = Thi0; return ORC_H_OUT_OF_RANGE; }
+    double a = Tlo0, b = Thi0;
+    double T = fmin(fmax(Tguess, a), b);
+    double fprev = INFINITY;
+    for (int it = 1; it <= max_iter; ++it) {
+        double h, cp;
+        st = cell_h(sp, T, p, Y, ys, &h, &cp);
+        *iters = it;
+        if (st) { *Tout = T; return st; }
+        double f = h - hstar;
+        double ftol = rtol * fmax(fabs(hstar), fabs(cp) * T);
+        if (fabs(f) <= ftol) { *Tout = T; return ORC_OK; }
+        if (f < 0) a = T; else b = T;
+        double Tn = T - f / cp;
+        int newton_ok = (cp > 0) && (Tn > a) && (Tn < b) && (fabs(f) <= 0.5 * fabs(fprev));
+        if (!newton_ok) Tn = 0.5 * (a + b);
+        fprev = f;
+        if (fabs(Tn - T) <= rtol * T) {
+            *Tout = Tn;
+            /* converged in T: accept only if h(T) meets h* (no jump inside) */
+            double h2, cp2;
+            if (cell_h(sp, Tn, p, Y, ys, &h2, &cp2)) return ORC_NO_ROOT;
+            if (fabs(h2 - hstar) <= 1e-6 * fmax(fabs(hstar), fabs(cp2) * Tn)) return ORC_OK;
+            return ORC_H_OUT_OF_RANGE;
+        }
+        T = Tn;
+    }
+    *Tout = T;
+    return ORC_NEWTON_MAXIT;
+}
+
+void orc_T_from_h(const orc_species *sp, int64_t n, const double *hstar, const double *p, const double *Y,
+                  const double *Tguess, double *Tout, int32_t *status, int32_t *iters,
+                  int max_iter, double rtol, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        int it = 0;
+        int st = orc_T_from_h_cell(sp, hstar[i], p[i], Y + i, (ptrdiff_t)n, Tguess[i], max_iter, rtol, &Tout[i], &it);
+        if (status) status[i] = st;
+        if (iters) iters[i] = it;
+    }
+    (void)nthreads;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
