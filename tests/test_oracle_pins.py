@@ -425,3 +425,36 @@ def test_pseudo_boiling_shape(orc, species, name):
     assert len(peaks) == 1
     assert np.isfinite(cp).all()
     assert out[0, 0] / out[0, -1] > 5.0   # large density drop across the line
+
+
+def test_chung_dilute_conductivity_monatomic_eucken(orc, species):
+    """For a monatomic gas (cv = 3/2 R, so Chung's alpha = 0 and Psi = 1)
+    the dilute Chung conductivity is the kinetic-theory Eucken value
+    lambda = (15/4) R mu / M; 31.2 / R = 3.7525 agrees with 15/4 to 0.07 %."""
+    k = W.SPECIES.index("H")
+    T = np.array([300.0, 1000.0, 2500.0])
+    Y = np.zeros((9, 3))
+    Y[k] = 1.0
+    _, _, d = orc.diagnose(species, T, np.ones(3), Y)
+    M = species.W[k] * 1e-3
+    for di in d:
+        assert di["cv_ig_molar"] == pytest.approx(1.5 * R, rel=1e-8)
+        assert di["lambda_dilute"] == pytest.approx(3.75 * R * di["mu_dilute"] / M, rel=1e-3)
+
+
+@pytest.mark.parametrize("name", ["O2", "CH4", "CO2", "CO", "H2"])
+def test_chung_dilute_conductivity_between_eucken_forms(orc, species, name):
+    """Polyatomic non-polar gases: Chung's Psi factor places the dilute
+    conductivity between the Eucken (cv + 9/4 R) and modified-Eucken
+    (1.32 cv + 1.77 R) values of lambda M / mu, within 8 %."""
+    k = W.SPECIES.index(name)
+    T = np.array([300.0, 700.0, 1500.0, 2500.0])
+    Y = np.zeros((9, T.size))
+    Y[k] = 1.0
+    _, _, d = orc.diagnose(species, T, np.ones(T.size), Y)
+    M = species.W[k] * 1e-3
+    for di in d:
+        eu = (di["cv_ig_molar"] + 2.25 * R) * di["mu_dilute"] / M
+        meu = (1.32 * di["cv_ig_molar"] + 1.77 * R) * di["mu_dilute"] / M
+        lo, hi = min(eu, meu), max(eu, meu)
+        assert 0.92 * lo <= di["lambda_dilute"] <= 1.08 * hi
