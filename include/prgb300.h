@@ -1,0 +1,131 @@
+/*
+ * prgb300.h -- C ABI of the GB300 real-fluid property library (libprgb300.so).
+ *
+ * Per-cell real-fluid thermophysical properties of a multi-species mixture
+ * (the property evaluation that arxiv 2312.04830 replaces by a DNN, Sec. 4):
+ * Peng-Robinson cubic equation of state (Eq. 1) with van der Waals one-fluid
+ * mixing (Sec. 2, text after Eq. 1), NASA-7 ideal-gas terms, Chung's dense-fluid
+ * viscosity and conductivity (Sec. 2, last paragraph), and the inversion
+ * T(h, p, Y) the solver needs because it advances enthalpy (Sec. 4.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Status: every call returns 0 (PR_OK) or a negative PR_E* code; the
+ *    message of the last failure on the calling thread is pr_last_error().
+ *    Arguments are validated on the host before any launch; a failed call
+ *    launches nothing.  Kernels never trap: per-cell problems are reported in
+ *    the per-cell status array (PR_CELL_*).
+ *  - Memory: all array arguments are DEVICE pointers owned by the caller
+ *    (unless stated otherwise), valid for the duration of the asynchronous
+ *    work.  The library allocates only inside pr_create / surrogate_create /
+ *    serve_create and frees in the matching destroy.
+ *  - Layout: structure of arrays.  Cell arrays have length n.  Mass fractions
+ *    are species-major: Y[k * ldY + i] for species k, cell i (ldY >= n).
+ *  - Precision: PR_FP64 takes and returns double arrays; PR_FP32 and
+ *    PR_MIXED take and return float arrays.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Calls are asynchronous with respect to the host.
+ *  - Units: SI.  T [K], p [Pa], Y [-] (mass fractions, sum 1 within 1e-6; not
+ *    renormalised), rho [kg/m^3], Z [-], h [J/kg] (absolute, formation
+ *    enthalpy included), cp [J/(kg K)], mu [Pa s], lambda [W/(m K)].
+ */
+#ifndef PRGB300_H
+#define PRGB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pr_status;
+
+#define PR_OK            0
+#define PR_EINVAL       -1  /* bad argument (null pointer, size, alignment, range) */
+#define PR_ENOMEM       -2  /* device or host allocation failed */
+#define PR_ECUDA        -3  /* a CUDA runtime call failed */
+#define PR_ETIMEOUT     -4  /* a bounded wait ran out */
+#define PR_ENOTREADY    -5  /* result not available yet */
+#define PR_EUNSUPPORTED -6  /* option not supported by this build */
+
+/* Per-cell status codes written to cell_status arrays. */
+#define PR_CELL_OK          0  /* converged / evaluated */
+#define PR_CELL_MAXIT       1  /* Newton inversion hit max_iter */
+#define PR_CELL_H_RANGE     2  /* h* outside [h(60 K), h(5000 K)] or inside a jump of h(T) */
+#define PR_CELL_NO_ROOT     3  /* cubic has no root with Z > B */
+#define PR_CELL_BAD_INPUT   4  /* non-finite / non-positive T or p, negative Y, |sum Y - 1| > 1e-6 */
+#define PR_CELL_AMBIGUOUS   5  /* two physical roots with |Delta g_res| < 1e-9 (larger Z kept) */
+
+typedef enum { PR_FP64 = 0, PR_FP32 = 1, PR_MIXED = 2 } pr_precision;
+
+/* Flags of pr_species_table.flags */
+#define PR_FLAG_PRINTED_CONSTANTS 1  /* use Eq. 1's printed 0.45724 / 0.07780 instead of the exact
+                                        critical-point values 0.457235529 / 0.077796074 */
+#define PR_FLAG_TRANSPORT_XAVG    2  /* mu, lambda = mole-fraction average of pure-species Chung
+                                        values instead of Chung's mixture rules */
+
+#define PR_MAX_SPECIES 32
+
+/* Species data (HOST pointers, copied by pr_create; the caller keeps ownership).
+ * W [g/mol], Tc [K], pc [Pa], omega [-], Vc [cm^3/mol], dipole [debye],
+ * kappa (Chung association factor) [-], nasa_lo / nasa_hi: NASA-7 a1..a7 of
+ * the low (T < T_mid) and high ranges, row-major [N][7]; T_mid [K];
+ * kij: binary interaction parameters [N][N] row-major, or NULL for all zero. */
+typedef struct {
+    int32_t n_species;   /* 1 .. PR_MAX_SPECIES */
+    int32_t flags;       /* PR_FLAG_* */
+    const double *W, *Tc, *pc, *omega, *Vc, *dipole, *kappa;
+    const double *nasa_lo, *nasa_hi, *T_mid;
+    const double *kij;
+} pr_species_table;
+
+typedef struct pr_ctx pr_ctx;
+
+/* Create a context on the current CUDA device: validates the table, copies
+ * it to the device and derives the per-species constants there (one small
+ * kernel).  Synchronous.  *out receives the handle; PR_EINVAL on a bad table
+ * (n_species out of range, Tc/pc/W/Vc not positive, NaN), PR_ENOMEM/PR_ECUDA on
+ * device failures. */
+pr_status pr_create(const pr_species_table *tbl, pr_ctx **out);
+
+/* Release a context (synchronises the device first).  NULL is a no-op. */
+void pr_destroy(pr_ctx *ctx);
+
+/* Forward properties, one thread per cell (Eq. 1 + mixing + NASA-7 + Chung).
+ *   T, p     [n] inputs; Y [N][ldY] inputs (species-major).
+ *   rho, Z, h, cp, mu, lambda  [n] outputs; any may be NULL to skip it.  When
+ *            both mu and lambda are NULL the transport step is not run.
+ *   cell_status [n] int32 output or NULL.
+ * Cells with status PR_CELL_BAD_INPUT or PR_CELL_NO_ROOT get NaN outputs.
+ * n = 0 is a no-op.  All pointers must be aligned to their element size. */
+pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n,
+                   const void *T, const void *p, const void *Y, int64_t ldY,
+                   void *rho, void *Z, void *h, void *cp, void *mu, void *lambda,
+                   int32_t *cell_status, void *stream);
+
+/* Inversion T(h*, p, Y) by safeguarded Newton on f(T) = h(T) - h*, f' = cp,
+ * inside the bracket [60, 5000] K, starting from T_guess (clipped to the
+ * bracket).  A Newton step that leaves the current bracket, or follows a step
+ * that did not halve |f|, is replaced by bisection.  Converged when
+ * |dT| <= rtol T or |f| <= rtol max(|h*|, cp T).
+ *   hstar, p, T_guess [n]; Y [N][ldY]; T_out [n] output;
+ *   cell_status [n] (required), iters [n] (NULL allowed);
+ *   max_iter in 1..1000; rtol in [1e-15, 1e-2].
+ * Status per cell: PR_CELL_OK, PR_CELL_MAXIT (T_out = last iterate),
+ * PR_CELL_H_RANGE (T_out clamped to the bracket end, or the jump location),
+ * PR_CELL_BAD_INPUT, PR_CELL_NO_ROOT. */
+pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n,
+                      const void *hstar, const void *p, const void *Y, int64_t ldY,
+                      const void *T_guess, void *T_out, int32_t *cell_status, int32_t *iters,
+                      int max_iter, double rtol, void *stream);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *pr_last_error(void);
+
+/* Library version string. */
+const char *pr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRGB300_H */

@@ -1,0 +1,7 @@
+// Instantiation of the property kernels for float arithmetic with a double cubic solve.
+#include "pr_kernels.cuh"
+
+namespace prk {
+PRK_DECLARE(float, double, 9, )
+PRK_DECLARE(float, double, 32, )
+}  // namespace prk

@@ -1,0 +1,56 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "prgb300.h"
+
+namespace prgb {
+
+// Thread-local error message, returned by pr_last_error().
+void set_error(const char *fmt, ...);
+const char *last_error();
+
+#define PR_CUDA_TRY(call)                                                                 \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ::prgb::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return PR_ECUDA;                                                              \
+        }                                                                                 \
+    } while (0)
+
+#define PR_CHECK_ARG(cond, ...)                 \
+    do {                                        \
+        if (!(cond)) {                          \
+            ::prgb::set_error(__VA_ARGS__);     \
+            return PR_EINVAL;                   \
+        }                                       \
+    } while (0)
+
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace prgb
+
+// The context: species data on the device in FP64 and FP32, launch limits.
+struct pr_ctx {
+    int device;
+    int n_species;
+    int ns_pad;          // compiled species bound used for this table (9 or 32)
+    int flags;
+    bool has_kij;
+    int num_sms;
+    void *d_sp64;        // SpeciesRec<double>[ns_pad]
+    void *d_sp32;        // SpeciesRec<float>[ns_pad]
+    double *d_pair64;    // [ns_pad][ns_pad] Chung pair weights
+    float *d_pair32;
+    double *d_kij64;     // [ns_pad][ns_pad] (1 - k_ij), zero padded
+    float *d_kij32;
+    int occ_props[3][2]; // resident blocks per SM: [precision][kij]
+    int occ_newton[3][2];
+};

@@ -1,0 +1,219 @@
+// Kernel templates of the forward-property and inversion paths, and their
+// launchers.  Instantiated per precision in pr_inst_{fp64,fp32,mixed}.cu so
+// that the three precisions compile in parallel.
+//
+// Kernel layout: persistent grid-stride CTAs of 128 threads, one cell per
+// thread per iteration.  Each CTA stages the species records, the Chung pair
+// table and (if any) the (1 - k_ij) matrix into shared memory once, then walks
+// the cells.  Cell arrays are read and written coalesced (SoA, consecutive
+// threads on consecutive cells).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pr_device.cuh"
+
+namespace prk {
+
+constexpr int kBlock = 128;
+
+// --------------------------------------------------------- shared staging
+template <typename Real, int NS, bool KIJ>
+struct Smem {
+    SpeciesRec<Real> sp[NS];
+    Real pair[NS * NS];
+    Real kij[KIJ ? NS * NS : 1];
+};
+
+template <typename Real, int NS, bool KIJ>
+__device__ __forceinline__ void stage(Smem<Real, NS, KIJ> &s, const SpeciesRec<Real> *sp, const Real *pair,
+                                      const Real *kij)
+{
+    const Real *src = reinterpret_cast<const Real *>(sp);
+    Real *dst = reinterpret_cast<Real *>(s.sp);
+    constexpr int nw = NS * sizeof(SpeciesRec<Real>) / sizeof(Real);
+    for (int j = threadIdx.x; j < nw; j += blockDim.x) dst[j] = src[j];
+    for (int j = threadIdx.x; j < NS * NS; j += blockDim.x) s.pair[j] = pair[j];
+    if (KIJ)
+        for (int j = threadIdx.x; j < NS * NS; j += blockDim.x) s.kij[j] = kij[j];
+    __syncthreads();
+}
+
+// ----------------------------------------------------------- props kernel
+template <typename Real>
+struct PropsArgs {
+    int64_t n, ldY;
+    const Real *T, *p, *Y;
+    Real *rho, *Z, *h, *cp, *mu, *lam;
+    int32_t *status;
+    const SpeciesRec<Real> *sp;
+    const Real *pair, *kij;
+    int N, flags;
+};
+
+template <typename Real, typename RZ, int NS, bool KIJ>
+__global__ void __launch_bounds__(kBlock) props_kernel(const PropsArgs<Real> a)
+{
+    __shared__ Smem<Real, NS, KIJ> s;
+    stage<Real, NS, KIJ>(s, a.sp, a.pair, a.kij);
+    const bool want_tr = (a.mu != nullptr) || (a.lam != nullptr);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const Real T = __ldg(a.T + i), p = __ldg(a.p + i);
+        Comp<Real, NS> c;
+        bool ok = load_comp<Real, NS>(c, a.Y, a.ldY, i, a.N, s.sp);
+        ok = ok && (T > Real(0)) && (p > Real(0)) && M<Real>::finite(T) && M<Real>::finite(p);
+        Thermo<Real> th;
+        th.status = kBadInput;
+        Real mu = M<Real>::nan(), lam = M<Real>::nan();
+        if (ok) {
+            thermo<Real, RZ, NS, KIJ>(c, T, p, s.sp, s.kij, th);
+            if (th.status != kNoRoot && want_tr) transport<Real, NS>(c, T, th, s.sp, s.pair, a.flags, mu, lam);
+        }
+        const bool good = ok && th.status != kNoRoot;
+        const Real nanv = M<Real>::nan();
+        if (a.rho) a.rho[i] = good ? p * c.Wbar / (th.Z * Real(kR) * T) : nanv;
+        if (a.Z) a.Z[i] = good ? th.Z : nanv;
+        if (a.h) a.h[i] = good ? th.h : nanv;
+        if (a.cp) a.cp[i] = good ? th.cp : nanv;
+        if (a.mu) a.mu[i] = good ? mu : nanv;
+        if (a.lam) a.lam[i] = good ? lam : nanv;
+        if (a.status) a.status[i] = th.status;
+    }
+}
+
+// ---------------------------------------------------------- Newton kernel
+template <typename Real>
+struct NewtonArgs {
+    int64_t n, ldY;
+    const Real *hstar, *p, *Y, *Tg;
+    Real *Tout;
+    int32_t *status, *iters;
+    const SpeciesRec<Real> *sp;
+    const Real *pair, *kij;
+    int N, flags, max_iter;
+    double rtol;
+};
+
+// h(T) and cp(T) of a cell at fixed p and composition; status 0 or an error.
+template <typename Real, typename RZ, int NS, bool KIJ>
+__device__ __noinline__ int eval_h(const Comp<Real, NS> &c, double T, Real p, const SpeciesRec<Real> *sp,
+                                      const Real *kij, double &h, double &cp)
+{
+    Thermo<Real> th;
+    thermo<Real, RZ, NS, KIJ>(c, (Real)T, p, sp, kij, th);
+    if (th.status == kNoRoot) return kNoRoot;
+    h = (double)th.h;
+    cp = (double)th.cp;
+    return kOk;
+}
+
+template <typename Real, typename RZ, int NS, bool KIJ>
+__global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a)
+{
+    __shared__ Smem<Real, NS, KIJ> s;
+    stage<Real, NS, KIJ>(s, a.sp, a.pair, a.kij);
+    // FP32 thermodynamics resolve h to ~1e-7 of its scale: floor the tolerance
+    const double rtol = (sizeof(Real) == 4) ? fmax(a.rtol, 2e-6) : a.rtol;
+    const double jump_tol = (sizeof(Real) == 4) ? 2e-5 : 1e-6;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const double hs = (double)__ldg(a.hstar + i);
+        const Real p = __ldg(a.p + i);
+        const double Tg = (double)__ldg(a.Tg + i);
+        Comp<Real, NS> c;
+        bool ok = load_comp<Real, NS>(c, a.Y, a.ldY, i, a.N, s.sp);
+        ok = ok && isfinite(hs) && isfinite(Tg) && (p > Real(0)) && M<Real>::finite(p);
+        int st = kBadInput, it = 0;
+        double Tres = nan("");
+        if (ok) {
+            double lo = kTLo, hi = kTHi;
+            bool lo_done = false, hi_done = false;   // endpoint h evaluated (range checked)
+            double T = fmin(fmax(Tg, lo), hi);
+            double fprev = INFINITY;
+            st = kMaxIt;
+            Tres = T;
+#pragma unroll 1
+            for (it = 1; it <= a.max_iter; ++it) {
+                double h, cp;
+                int e = eval_h<Real, RZ, NS, KIJ>(c, T, p, s.sp, s.kij, h, cp);
+                if (e) { st = e; Tres = T; break; }
+                const double f = h - hs;
+                if (fabs(f) <= rtol * fmax(fabs(hs), fabs(cp) * T)) { st = kOk; Tres = T; break; }
+                if (f < 0) lo = T; else hi = T;
+                double Tn = T - f / cp;
+                const bool newton_ok = (cp > 0) && (Tn > lo) && (Tn < hi) && (fabs(f) <= 0.5 * fabs(fprev));
+                if (!newton_ok) Tn = 0.5 * (lo + hi);
+                // the next iterate leans on a bracket end whose h is unknown:
+                // check that h* lies inside the range first
+                if (!newton_ok && ((lo == kTLo && !lo_done) || (hi == kTHi && !hi_done))) {
+                    const bool use_lo = (lo == kTLo && !lo_done);
+                    const double Te = use_lo ? kTLo : kTHi;
+                    double he, cpe;
+                    int e2 = eval_h<Real, RZ, NS, KIJ>(c, Te, p, s.sp, s.kij, he, cpe);
+                    if (e2) { st = e2; Tres = T; break; }
+                    if (use_lo) lo_done = true; else hi_done = true;
+                    if ((use_lo && hs < he) || (!use_lo && hs > he)) { st = kHRange; Tres = Te; break; }
+                }
+                fprev = f;
+                if (fabs(Tn - T) <= rtol * T) {
+                    Tres = Tn;
+                    double h2, cp2;
+                    if (eval_h<Real, RZ, NS, KIJ>(c, Tn, p, s.sp, s.kij, h2, cp2)) { st = kNoRoot; break; }
+                    st = (fabs(h2 - hs) <= jump_tol * fmax(fabs(hs), fabs(cp2) * Tn)) ? kOk : kHRange;
+                    break;
+                }
+                T = Tn;
+                Tres = T;
+            }
+            if (it > a.max_iter) it = a.max_iter;
+        }
+        a.Tout[i] = (Real)Tres;
+        a.status[i] = st;
+        if (a.iters) a.iters[i] = it;
+    }
+}
+
+
+// ------------------------------------------------------------- launchers
+inline int grid_for(int64_t n, int occ, int sms)
+{
+    int64_t need = (n + kBlock - 1) / kBlock;
+    int64_t cap = (int64_t)occ * sms;
+    return (int)(need < cap ? need : cap);
+}
+
+template <typename Real, typename RZ, int NS>
+void launch_props(const PropsArgs<Real> &a, bool kij, int occ, int sms, cudaStream_t st)
+{
+    const int g = grid_for(a.n, occ, sms);
+    if (kij) props_kernel<Real, RZ, NS, true><<<g, kBlock, 0, st>>>(a);
+    else props_kernel<Real, RZ, NS, false><<<g, kBlock, 0, st>>>(a);
+}
+
+template <typename Real, typename RZ, int NS>
+void launch_newton(const NewtonArgs<Real> &a, bool kij, int occ, int sms, cudaStream_t st)
+{
+    const int g = grid_for(a.n, occ, sms);
+    if (kij) newton_kernel<Real, RZ, NS, true><<<g, kBlock, 0, st>>>(a);
+    else newton_kernel<Real, RZ, NS, false><<<g, kBlock, 0, st>>>(a);
+}
+
+// resident CTAs per SM of the four kernels of one (Real, RZ, NS):
+// occ[0..1] props (kij off/on), occ[2..3] Newton (kij off/on)
+template <typename Real, typename RZ, int NS>
+void occupancy(int occ[4])
+{
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], props_kernel<Real, RZ, NS, false>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], props_kernel<Real, RZ, NS, true>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], newton_kernel<Real, RZ, NS, false>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], newton_kernel<Real, RZ, NS, true>, kBlock, 0);
+    for (int k = 0; k < 4; ++k) occ[k] = occ[k] > 0 ? occ[k] : 1;
+}
+
+#define PRK_DECLARE(Real, RZ, NS, EXT)                                                                    \
+    EXT template void launch_props<Real, RZ, NS>(const PropsArgs<Real> &, bool, int, int, cudaStream_t);   \
+    EXT template void launch_newton<Real, RZ, NS>(const NewtonArgs<Real> &, bool, int, int, cudaStream_t); \
+    EXT template void occupancy<Real, RZ, NS>(int *);
+
+}  // namespace prk

@@ -24,3 +24,19 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def prlib():
+    """The CUDA library, built in-tree if needed (nvcc cross-compiles without a GPU)."""
+    from paper_2312_04830_gb300 import binding, build
+    build.build()
+    return binding.lib()
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for tests marked gpu")
+    return torch.device("cuda:0")

@@ -1,0 +1,231 @@
+"""Parity of the CUDA property path with the FP64 oracle (GPU).
+
+Every call goes through the C ABI (ctypes binding).  Inputs come from the
+seeded generators; expected values come from the oracle only.
+"""
+import numpy as np
+import pytest
+
+from paper_2312_04830_gb300 import workloads as W
+
+from .parity import assert_fp64_parity, cond_numbers, error_summary
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(prlib, cuda, species):
+    from paper_2312_04830_gb300 import binding
+    c = binding.PropertyContext(species)
+    yield c
+    c.close()
+
+
+def to_dev(a, dtype, cuda):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=cuda)
+
+
+def run_props(ctx, T, p, Y, cuda, precision="fp64"):
+    import torch
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out, st = ctx.props(to_dev(T, dt, cuda), to_dev(p, dt, cuda), to_dev(Y, dt, cuda), precision=precision)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy(), st.cpu().numpy()
+
+
+def oracle_props(orc, species, T, p, Y, **kw):
+    out, st, d = orc.diagnose(species, T, p, Y, **kw)
+    return out, st, cond_numbers(d)
+
+
+# ------------------------------------------------------------------ FP64
+def test_props_fp64_uniform_cells(ctx, orc, species, cuda):
+    """32^3 independent cells: T ~ U[100, 3500] K, p = 10 MPa +-5 %, Dirichlet Y."""
+    T, p, Y = W.uniform_cells(32768)
+    g, gs = run_props(ctx, T, p, Y, cuda)
+    o, os_, cond = oracle_props(orc, species, T, p, Y)
+    rep = assert_fp64_parity(g, gs, o, os_, T, cond, label="uniform")
+    assert rep["n_ok"] > 32000
+
+
+@pytest.mark.parametrize("n", [1, 31, 127, 128, 129, 1000, 4099])
+def test_props_fp64_ragged_sizes(ctx, orc, species, cuda, n):
+    T, p, Y = W.uniform_cells(n, seed=100 + n)
+    g, gs = run_props(ctx, T, p, Y, cuda)
+    o, os_, cond = oracle_props(orc, species, T, p, Y)
+    assert_fp64_parity(g, gs, o, os_, T, cond, label=f"n={n}")
+
+
+def test_props_empty_is_noop(ctx, cuda):
+    import torch
+    z = torch.empty(0, dtype=torch.float64, device=cuda)
+    out, st = ctx.props(z, z, torch.empty((9, 0), dtype=torch.float64, device=cuda))
+    assert out.shape == (6, 0)
+
+
+def _edge_states(species):
+    Ts, ps, Ys = [], [], []
+    def add(T, p, k=None, Y=None):
+        y = np.zeros(9)
+        if k is not None:
+            y[k] = 1.0
+        else:
+            y[:] = Y
+        Ts.append(T); ps.append(p); Ys.append(y)
+    for k in range(9):
+        add(species.Tc[k], species.pc[k], k)                         # critical point (ill-conditioned)
+        add(species.Tc[k] * 1.001, species.pc[k] * 1.01, k)
+        add(1500.0, 1.0, k)                                          # ideal-gas limit
+        add(3500.0, 10.5e6, k)
+    for name in ("H2O", "CO2"):                                      # subcritical: two physical roots
+        k = W.SPECIES.index(name)
+        for tr in np.linspace(0.55, 0.98, 12):
+            for pr in np.linspace(0.05, 0.9, 12):
+                add(tr * species.Tc[k], pr * species.pc[k], k)
+    zm = np.linspace(0, 1, 41)                                       # flame sheet (LOX at 120 K, CH4 at 300 K)
+    Tf, Yf = W.flame_sheet_state(zm)
+    for i in range(zm.size):
+        add(Tf[i], 10e6, Y=Yf[:, i])
+    # degenerate inputs: status 4 expected
+    add(-5.0, 10e6, 1); add(np.nan, 10e6, 1); add(300.0, 0.0, 1); add(300.0, np.inf, 1)
+    y = np.zeros(9); y[1] = 0.9; add(300.0, 10e6, Y=y)              # sum Y = 0.9
+    y = np.zeros(9); y[1] = 1.1; y[2] = -0.1; add(300.0, 10e6, Y=y)  # negative Y
+    return np.array(Ts), np.array(ps), np.array(Ys).T.copy()
+
+
+def test_props_fp64_edge_cases(ctx, orc, species, cuda):
+    T, p, Y = _edge_states(species)
+    g, gs = run_props(ctx, T, p, Y, cuda)
+    o, os_, cond = oracle_props(orc, species, T, p, Y)
+    rep = assert_fp64_parity(g, gs, o, os_, T, cond, label="edge")
+    assert rep["n_ill"] >= 6          # the critical points
+    assert np.count_nonzero(os_ == 4) == 6
+    assert np.all(gs[os_ == 4] == 4)
+
+
+def test_props_fp64_kij(prlib, orc, cuda):
+    """Non-zero symmetric k_ij: the O(N^2) mixing path."""
+    from paper_2312_04830_gb300 import binding
+    rng = np.random.default_rng(5)
+    k = rng.uniform(-0.05, 0.15, (9, 9))
+    k = 0.5 * (k + k.T)
+    np.fill_diagonal(k, 0.0)
+    sp = W.species_table(kij=k)
+    c = binding.PropertyContext(sp)
+    T, p, Y = W.uniform_cells(8192, seed=41)
+    g, gs = run_props(c, T, p, Y, cuda)
+    o, os_, cond = oracle_props(orc, sp, T, p, Y)
+    assert_fp64_parity(g, gs, o, os_, T, cond, label="kij")
+    c.close()
+
+
+@pytest.mark.parametrize("names", [("O2",), ("CH4", "O2"), tuple(W.SPECIES) + ("O2",),
+                                   tuple(W.SPECIES) + ("CH4", "CO2", "H2O", "H2", "CO", "O2", "O", "H")])
+def test_props_fp64_species_counts(prlib, orc, cuda, names):
+    """1, 2, 10 and 17 species (the 17 a RAMEC-sized table), padded kernels."""
+    from paper_2312_04830_gb300 import binding
+    sp = W.SpeciesTable(names)
+    c = binding.PropertyContext(sp)
+    rng = np.random.default_rng(len(names))
+    n = 3000
+    T = rng.uniform(100, 3500, n)
+    p = 1e7 * rng.uniform(0.95, 1.05, n)
+    Y = rng.dirichlet(np.full(len(names), 0.5), n).T.copy()
+    g, gs = run_props(c, T, p, Y, cuda)
+    o, os_, cond = oracle_props(orc, sp, T, p, Y)
+    assert_fp64_parity(g, gs, o, os_, T, cond, label=f"N={len(names)}")
+    c.close()
+
+
+def test_props_fp64_transport_xavg_and_printed(prlib, orc, species, cuda):
+    from paper_2312_04830_gb300 import binding
+    T, p, Y = W.uniform_cells(4096, seed=61)
+    for kw in ({"transport_xavg": True}, {"printed_constants": True}):
+        c = binding.PropertyContext(species, **kw)
+        g, gs = run_props(c, T, p, Y, cuda)
+        okw = {"transport_rule": 1} if "transport_xavg" in kw else {"printed_constants": True}
+        o, os_, cond = oracle_props(orc, species, T, p, Y, **okw)
+        assert_fp64_parity(g, gs, o, os_, T, cond, label=str(kw))
+        c.close()
+
+
+def test_props_strided_Y_and_output_subsets(ctx, orc, species, cuda):
+    """Y as a slice of a wider array (ldY > n); skipping mu/lambda leaves the
+    thermodynamic outputs bit-identical."""
+    import torch
+    T, p, Y = W.uniform_cells(5000, seed=71)
+    Ywide = np.zeros((9, 6000))
+    Ywide[:, :5000] = Y
+    Yd = torch.as_tensor(Ywide, device=cuda)[:, :5000]
+    Td, pd = torch.as_tensor(T, device=cuda), torch.as_tensor(p, device=cuda)
+    full, st = ctx.props(Td, pd, Yd)
+    thermo, st2 = ctx.props(Td, pd, Yd, outputs=("rho", "Z", "h", "cp"))
+    torch.cuda.synchronize()
+    assert torch.equal(full[:4], thermo[:4])
+    o, os_, cond = oracle_props(orc, species, T, p, Y)
+    assert_fp64_parity(full.cpu().numpy(), st.cpu().numpy(), o, os_, T, cond, label="strided")
+
+
+def test_props_deterministic(ctx, cuda):
+    import torch
+    T, p, Y = W.uniform_cells(20000, seed=81)
+    a, _ = run_props(ctx, T, p, Y, cuda)
+    b, _ = run_props(ctx, T, p, Y, cuda)
+    assert np.array_equal(a, b, equal_nan=True)
+
+
+# ---------------------------------------------------------------- Newton
+def test_T_from_h_fp64(ctx, orc, species, cuda):
+    """T(h*, p, Y) on the uniform cells: h* = h_oracle(T_true), start from a
+    guess within +-5 %; the GPU's T equals the oracle's inversion."""
+    T, p, Y = W.uniform_cells(32768, seed=91)
+    Ttrue = W.newton_targets(T, seed=92)
+    hs, sts = orc.props(species, Ttrue, p, Y)
+    hstar = hs[2]
+    To, sto, ito = orc.T_from_h(species, hstar, p, Y, T)
+    import torch
+    Tg, stg, itg = ctx.T_from_h(to_dev(hstar, torch.float64, cuda), to_dev(p, torch.float64, cuda),
+                                to_dev(Y, torch.float64, cuda), to_dev(T, torch.float64, cuda))
+    Tg, stg, itg = Tg.cpu().numpy(), stg.cpu().numpy(), itg.cpu().numpy()
+    ok = (sto == 0) & (sts == 0)
+    assert ok.sum() > 32000
+    assert np.all(stg[ok] == 0)
+    np.testing.assert_allclose(Tg[ok], To[ok], rtol=1e-10)
+    np.testing.assert_allclose(Tg[ok], Ttrue[ok], rtol=1e-10)
+    assert itg[ok].max() <= 60
+
+
+def test_T_from_h_status_codes(ctx, orc, species, cuda):
+    import torch
+    n = 6
+    Y = np.zeros((9, n)); Y[0] = 1.0
+    p = np.full(n, 10e6)
+    hstar = np.array([-1e9, 1e9, np.nan, 0.0, 1e5, -4e6])
+    Tg = np.array([300.0, 300.0, 300.0, 1e4, 1.0, 500.0])
+    To, sto, _ = orc.T_from_h(species, hstar, p, Y, Tg)
+    d = lambda a: to_dev(a, torch.float64, cuda)
+    T2, st2, _ = ctx.T_from_h(d(hstar), d(p), d(Y), d(Tg))
+    T2, st2 = T2.cpu().numpy(), st2.cpu().numpy()
+    assert list(st2) == list(sto)
+    okm = sto != 4
+    np.testing.assert_allclose(T2[okm], To[okm], rtol=1e-10)
+
+
+# ------------------------------------------------------ reduced precision
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_reduced_precision_error_budget(ctx, orc, species, cuda, precision):
+    """FP32 and mixed paths: error distribution against the FP64 oracle on
+    inputs rounded to FP32 (the oracle sees the same rounded inputs)."""
+    T, p, Y = W.uniform_cells(32768, seed=101)
+    T32, p32 = T.astype(np.float32).astype(np.float64), p.astype(np.float32).astype(np.float64)
+    Y32 = Y.astype(np.float32).astype(np.float64)
+    g, gs = run_props(ctx, T32, p32, Y32, cuda, precision=precision)
+    o, os_, cond = oracle_props(orc, species, T32, p32, Y32)
+    m = (os_ == 0) & (gs == 0) & (cond < 1e4)
+    assert m.sum() > 32000
+    summ = error_summary(g, o, T32, m)
+    print(precision, summ)
+    for name, s in summ.items():
+        assert s["median"] < 1e-5, (name, s)
+        assert s["p99"] < 1e-3, (name, s)
