@@ -5,8 +5,10 @@ FP64 rule (per output, per cell whose oracle status is 0):
   * |h_gpu - h_orc| <= 1e-10 max(|h|, cp T)   (h crosses zero);
   * cells whose root condition number c = sum_k |c_k| |Z|^k / (|Z| |P'(Z)|)
     exceeds 1e4 (near-degenerate cubics: rounding of the coefficients moves
-    the root by ~eps c) instead need |dZ|/Z <= 8 eps c, and the other outputs
-    within 1e-10 + 100 * 8 eps c;
+    the root by ~eps c) instead need |dZ|/Z <= 8 eps c, and rho, h, mu,
+    lambda within 1e-10 + 100 * 8 eps c.  cp is not compared on these cells:
+    it holds 1/(dp/dV)_T, which vanishes at the critical point, so its
+    sensitivity to the root is unbounded there;
   * cells the oracle flags ambiguous (two roots within 1e-9 in g_res) are
     excluded and counted; the GPU must flag them ok or ambiguous.
 """
@@ -56,7 +58,7 @@ def assert_fp64_parity(gpu, gst, orc, ost, T, cond, rtol=1e-10, label=""):
     if np.any(sel):
         tolZ = 8 * EPS * cond[sel]
         assert np.all(err[1, sel] <= np.maximum(tolZ, rtol)), f"{label}: ill-conditioned Z"
-        for q in (0, 2, 3, 4, 5):
+        for q in (0, 2, 4, 5):
             assert np.all(err[q, sel] <= rtol + 100 * tolZ), f"{label}: ill-conditioned {NAMES[q]}"
     return {"n_ok": int(well.sum()), "n_ill": int(sel.sum()), "n_ambiguous": int(amb.sum()), "max_rel": worst}
 
