@@ -118,6 +118,94 @@ pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n,
                       const void *T_guess, void *T_out, int32_t *cell_status, int32_t *iters,
                       int max_iter, double rtol, void *stream);
 
+/* ======================================================================
+ * Surrogate MLP (Sec. 4: the DNN that replaces the property evaluation).
+ * Inputs per cell: [log T, p, Y_1..Y_9] (9 species, the context's order);
+ * outputs: [rho, Z, h, cp, mu, lambda] learned as [log rho, Z, h, log cp,
+ * log mu, log lambda], inputs and outputs standardised with statistics of the
+ * training pool.  Hidden layers use the exact GeLU (Sec. 4.1).  Forward and
+ * backward GEMMs run on the tensor cores (BF16 operands, FP32 accumulation);
+ * master weights and Adam moments are FP32.
+ * ====================================================================== */
+
+typedef struct sg_model sg_model;
+
+typedef struct {
+    int32_t width;          /* hidden width: 128, 256, 512 or 1024 */
+    int32_t hidden_layers;  /* number of hidden layers, 1..8 */
+    int32_t max_batch;      /* largest training batch; multiple of 128 */
+    int32_t infer_chunk;    /* rows per inference chunk; multiple of 128 */
+} sg_config;
+
+#define SG_NORM_FLOATS 56  /* in_mean[11] in_std[11] out_mean[6] out_std[6] hull_lo[11] hull_hi[11] + 2 pad */
+
+/* Create a model bound to `ctx` (which must hold exactly 9 species; it is
+ * used for the Peng-Robinson fallback).  Weights ~ U(-1/sqrt(fan_in),
+ * 1/sqrt(fan_in)) from a counter-based generator seeded by `seed`.  Allocates
+ * every device buffer the model will use; synchronous. */
+pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_model **out);
+void surrogate_destroy(sg_model *m);
+
+/* Number of trainable parameters (W_l [out][in] and b_l [out] per layer). */
+int64_t surrogate_num_params(const sg_model *m);
+
+/* Copy the FP32 master parameters to / from HOST memory in the order
+ * W_1, b_1, ..., W_L+1, b_L+1 (row-major W [out][in]); n must equal
+ * surrogate_num_params.  Synchronous. */
+pr_status surrogate_get_params(const sg_model *m, float *host_dst, int64_t n);
+pr_status surrogate_set_params(sg_model *m, const float *host_src, int64_t n);
+
+/* Normalisation and training hull (SG_NORM_FLOATS floats, HOST memory). */
+pr_status surrogate_get_normalization(const sg_model *m, float *host_dst);
+pr_status surrogate_set_normalization(sg_model *m, const float *host_src);
+
+/* Fit the normalisation and the training hull (per-input [min, max] widened
+ * by 1 % of the range) to a pool of n states.  x: DEVICE [11][ldx] raw inputs
+ * (T, p, Y_1..Y_9); y: DEVICE [6][ldy] raw properties (rho, Z, h, cp, mu,
+ * lambda).  Asynchronous on `stream`. */
+pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, int64_t ldx, const float *y,
+                                      int64_t ldy, void *stream);
+
+/* One training step (Sec. 4.3, with the squared error on the standardised
+ * log / scaled targets, i.e. a relative-MSE loss, and Adam with beta =
+ * (0.9, 0.999), eps = 1e-8): batch rows (a multiple of 128, <= max_batch)
+ * are drawn from the pool x [11][ldx], y [6][ldy] (DEVICE, n_pool rows):
+ * rows 0..batch-1 in order when sample_seed == 0 and n_pool == batch, else
+ * uniformly with replacement by a counter-based hash of (sample_seed, row).
+ * loss_out: DEVICE float receiving the batch loss, or NULL. */
+pr_status surrogate_train_step(sg_model *m, int64_t batch, int64_t n_pool, const float *x, int64_t ldx,
+                               const float *y, int64_t ldy, uint64_t sample_seed, float lr, float *loss_out,
+                               void *stream);
+
+/* Loss and gradients of the first `batch` pool rows without updating the
+ * model.  grad_out: DEVICE [surrogate_num_params] in the get_params order. */
+pr_status surrogate_loss_grad(sg_model *m, int64_t batch, const float *x, int64_t ldx, const float *y, int64_t ldy,
+                              float *loss_out, float *grad_out, void *stream);
+
+/* Inference (FP32 I/O): T, p [n], Y [9][ldY] DEVICE inputs; out [6][ldo]
+ * DEVICE outputs rho, Z, h, cp, mu, lambda.  Cells with any input outside
+ * the training hull are evaluated by the FP64 Peng-Robinson path instead and
+ * flagged in used_fallback [n] (DEVICE uint8, NULL allowed). */
+pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p, const float *Y, int64_t ldY,
+                          float *out, int64_t ldo, uint8_t *used_fallback, void *stream);
+
+/* Synchronise the device and report PR_ETIMEOUT if a tensor-core kernel gave
+ * up waiting on one of its barriers since the last call (the flag is then
+ * cleared). */
+pr_status surrogate_sync_status(sg_model *m);
+
+/* Checkpoint (HOST file): weights, Adam moments, step count, normalisation. */
+pr_status surrogate_save(const sg_model *m, const char *path);
+pr_status surrogate_load(sg_model *m, const char *path);
+
+/* Plain tensor-core GEMM with the kernel the MLP uses: D[M][N] (FP32,
+ * row pitch ldd) = A[M][K] * B[N][K]^T with A, B BF16 K-major (row pitches lda,
+ * ldb elements), FP32 accumulation.  K a positive multiple of 64; N = 16, 64 or
+ * a multiple of 128; any M >= 1.  DEVICE pointers, 16-byte aligned.  err_flag:
+ * DEVICE int set to 1 if a barrier wait inside the kernel ran out. */
+pr_status mlp_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
+                        float *D, int64_t ldd, int *err_flag, void *stream);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *pr_last_error(void);
 

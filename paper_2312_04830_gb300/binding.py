@@ -172,3 +172,164 @@ class PropertyContext:
                                 _ptr(T_out), _ptr(status), _ptr(iters), int(max_iter), float(rtol),
                                 _stream(stream)), "pr_T_from_h")
         return T_out, status, iters
+
+
+# ------------------------------------------------------------------ surrogate
+class _SgConfig(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("hidden_layers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("infer_chunk", ctypes.c_int32)]
+
+
+SG_NORM_FLOATS = 56
+N_IN, N_OUT = 11, 6
+
+
+def _sg_lib():
+    L = lib()
+    if not getattr(L, "_sg_ready", False):
+        vp, i64, i32, f32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_uint64
+        L.surrogate_create.argtypes = [vp, ctypes.POINTER(_SgConfig), u64, ctypes.POINTER(vp)]
+        L.surrogate_create.restype = i32
+        L.surrogate_destroy.argtypes = [vp]
+        L.surrogate_destroy.restype = None
+        L.surrogate_num_params.argtypes = [vp]
+        L.surrogate_num_params.restype = i64
+        for fn in ("surrogate_get_params", "surrogate_set_params"):
+            getattr(L, fn).argtypes = [vp, vp, i64]
+            getattr(L, fn).restype = i32
+        for fn in ("surrogate_get_normalization", "surrogate_set_normalization"):
+            getattr(L, fn).argtypes = [vp, vp]
+            getattr(L, fn).restype = i32
+        L.surrogate_fit_normalization.argtypes = [vp, i64, vp, i64, vp, i64, vp]
+        L.surrogate_fit_normalization.restype = i32
+        L.surrogate_train_step.argtypes = [vp, i64, i64, vp, i64, vp, i64, u64, f32, vp, vp]
+        L.surrogate_train_step.restype = i32
+        L.surrogate_loss_grad.argtypes = [vp, i64, vp, i64, vp, i64, vp, vp, vp]
+        L.surrogate_loss_grad.restype = i32
+        L.surrogate_infer.argtypes = [vp, i64, vp, vp, vp, i64, vp, i64, vp, vp]
+        L.surrogate_infer.restype = i32
+        L.surrogate_sync_status.argtypes = [vp]
+        L.surrogate_sync_status.restype = i32
+        L.surrogate_save.argtypes = [vp, ctypes.c_char_p]
+        L.surrogate_save.restype = i32
+        L.surrogate_load.argtypes = [vp, ctypes.c_char_p]
+        L.surrogate_load.restype = i32
+        L.mlp_gemm_bf16.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp]
+        L.mlp_gemm_bf16.restype = i32
+        L._sg_ready = True
+    return L
+
+
+class Surrogate:
+    """The surrogate MLP bound to a PropertyContext (its PR fallback)."""
+
+    def __init__(self, ctx: PropertyContext, width=512, hidden_layers=4, max_batch=65536, infer_chunk=1 << 20,
+                 seed=1):
+        L = _sg_lib()
+        self.ctx = ctx
+        cfg = _SgConfig(width, hidden_layers, max_batch, infer_chunk)
+        h = ctypes.c_void_p()
+        check(L.surrogate_create(ctx.handle, ctypes.byref(cfg), ctypes.c_uint64(seed), ctypes.byref(h)),
+              "surrogate_create")
+        self.handle = h
+        self.width, self.hidden_layers, self.max_batch = width, hidden_layers, max_batch
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _sg_lib().surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return int(_sg_lib().surrogate_num_params(self.handle))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.num_params, dtype=np.float32)
+        check(_sg_lib().surrogate_get_params(self.handle, a.ctypes.data, a.size), "surrogate_get_params")
+        return a
+
+    def set_params(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        check(_sg_lib().surrogate_set_params(self.handle, a.ctypes.data, a.size), "surrogate_set_params")
+
+    def get_normalization(self) -> np.ndarray:
+        a = np.empty(SG_NORM_FLOATS, dtype=np.float32)
+        check(_sg_lib().surrogate_get_normalization(self.handle, a.ctypes.data), "surrogate_get_normalization")
+        return a
+
+    def set_normalization(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == SG_NORM_FLOATS
+        check(_sg_lib().surrogate_set_normalization(self.handle, a.ctypes.data), "surrogate_set_normalization")
+
+    @staticmethod
+    def _pool(x, y):
+        import torch
+        for nm, t, rows in (("x", x, N_IN), ("y", y, N_OUT)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+                raise PrError(f"{nm} must be a float32 CUDA tensor")
+            if t.dim() != 2 or t.shape[0] != rows or t.stride(1) != 1:
+                raise PrError(f"{nm} must be [{rows}, n] with unit stride along rows")
+        if x.shape[1] != y.shape[1]:
+            raise PrError("x and y must have the same number of rows")
+        return x.shape[1], x.stride(0), y.stride(0)
+
+    def fit_normalization(self, x, y, stream=None):
+        n, ldx, ldy = self._pool(x, y)
+        check(_sg_lib().surrogate_fit_normalization(self.handle, n, _ptr(x), ldx, _ptr(y), ldy, _stream(stream)),
+              "surrogate_fit_normalization")
+
+    def train_step(self, x, y, batch, lr, sample_seed=0, loss_out=None, stream=None):
+        n, ldx, ldy = self._pool(x, y)
+        check(_sg_lib().surrogate_train_step(self.handle, batch, n, _ptr(x), ldx, _ptr(y), ldy,
+                                             ctypes.c_uint64(sample_seed), ctypes.c_float(lr), _ptr(loss_out),
+                                             _stream(stream)), "surrogate_train_step")
+
+    def loss_grad(self, x, y, batch, stream=None):
+        import torch
+        n, ldx, ldy = self._pool(x, y)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        grad = torch.empty(self.num_params, dtype=torch.float32, device=x.device)
+        check(_sg_lib().surrogate_loss_grad(self.handle, batch, _ptr(x), ldx, _ptr(y), ldy, _ptr(loss), _ptr(grad),
+                                            _stream(stream)), "surrogate_loss_grad")
+        return loss, grad
+
+    def infer(self, T, p, Y, out=None, used_fallback=None, stream=None):
+        import torch
+        n, ldY = self.ctx._cells(PR_FP32, T, p, Y)
+        if out is None:
+            out = torch.empty((6, n), dtype=torch.float32, device=T.device)
+        if used_fallback is None:
+            used_fallback = torch.empty(n, dtype=torch.uint8, device=T.device)
+        check(_sg_lib().surrogate_infer(self.handle, n, _ptr(T), _ptr(p), _ptr(Y), ldY, _ptr(out), out.stride(0),
+                                        _ptr(used_fallback), _stream(stream)), "surrogate_infer")
+        return out, used_fallback
+
+    def sync_status(self):
+        check(_sg_lib().surrogate_sync_status(self.handle), "surrogate_sync_status")
+
+    def save(self, path):
+        check(_sg_lib().surrogate_save(self.handle, str(path).encode()), "surrogate_save")
+
+    def load(self, path):
+        check(_sg_lib().surrogate_load(self.handle, str(path).encode()), "surrogate_load")
+
+
+def gemm_bf16(A, B, D=None, err=None, stream=None):
+    """D = A @ B^T on the tensor cores (A [M, K], B [N, K] bfloat16 CUDA tensors)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if D is None:
+        D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    check(_sg_lib().mlp_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(D), D.stride(0),
+                                  _ptr(err), _stream(stream)), "mlp_gemm_bf16")
+    return D, err

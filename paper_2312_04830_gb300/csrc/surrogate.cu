@@ -1,0 +1,898 @@
+// Surrogate MLP (the paper's DNN strategy, Sec. 4): training and inference
+// on the tensor cores, with the FP64 Peng-Robinson path as the fallback for
+// states outside the training hull.
+//
+// Network: 11 inputs [log T, p, Y_1..Y_9] -> H hidden layers of width W with
+// GeLU -> 6 outputs [log rho, Z, h, log cp, log mu, log lambda]; inputs and
+// outputs standardised with statistics of the training pool.  Layer l computes
+// z = W_l h + b_l with BF16 operands and FP32 accumulation (mlp_gemm.cuh);
+// master weights and Adam moments are FP32.
+//
+// Padded layouts (so that every GEMM is a whole number of 128 x BN x 64
+// tiles): inputs K = 11 -> 64, the output layer N = 6 -> 16 (and its weight
+// gradient M = 6 -> 128).  Padding entries are zero and stay zero.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mlp_gemm.cuh"
+#include "pr_device.cuh"
+#include "pr_internal.h"
+#include "surrogate_internal.h"
+
+using namespace mlp;
+using prk::SpeciesRec;
+
+namespace {
+
+constexpr int NIN = 11, NOUT = 6;
+constexpr int KIN = 64;      // padded input width (one 64-wide k-block)
+constexpr int NOP = 16;      // padded output width
+constexpr int MOP = 128;     // padded output rows of the last layer's weight gradient
+constexpr int NSTAT = NIN + NOUT;
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ float uniform01(uint64_t h) { return (float)((h >> 40) * (1.0 / 16777216.0)); }
+
+// Features of one cell from raw inputs: [log T, p, Y_1..Y_9].
+__device__ __forceinline__ void features(const float *x, int64_t ldx, int64_t i, float (&f)[NIN])
+{
+    f[0] = logf(__ldg(x + i));
+    f[1] = __ldg(x + ldx + i);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
+}
+
+// Targets from raw properties: [log rho, Z, h, log cp, log mu, log lambda].
+__device__ __forceinline__ void targets(const float *y, int64_t ldy, int64_t i, float (&q)[NOUT])
+{
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) {
+        const float v = __ldg(y + (int64_t)j * ldy + i);
+        q[j] = (j == 1 || j == 2) ? v : logf(v);
+    }
+}
+
+// ------------------------------------------------------------ init params
+__global__ void init_params_kernel(SgDev d, uint64_t seed)
+{
+    const int64_t total = d.n_master;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        ParamRef r = decode_param(d, e);
+        float v = 0.f;
+        if (r.valid) {
+            const float bound = 1.0f / sqrtf((float)(r.layer == 0 ? NIN : d.width));
+            v = bound * (2.f * uniform01(splitmix64(seed * 0x100000001B3ull + (uint64_t)e)) - 1.f);
+        }
+        d.master[e] = v;
+        d.adam_m[e] = 0.f;
+        d.adam_v[e] = 0.f;
+    }
+}
+
+// BF16 copies of the weights: W [out][in_pad] (forward B operand) and W^T
+// [in][out_pad] (input-gradient B operand).
+__device__ __forceinline__ void write_bf16_copies(const SgDev &d, const ParamRef &r, float v)
+{
+    if (r.bias) return;
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    d.wb[r.layer][(int64_t)r.o * r.in_pad + r.i] = b;
+    if (r.layer > 0) d.wt[r.layer][(int64_t)r.i * r.out_pad_k + r.o] = b;
+}
+
+__global__ void refresh_bf16_kernel(SgDev d)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.n_master; e += (int64_t)gridDim.x * blockDim.x) {
+        ParamRef r = decode_param(d, e);
+        write_bf16_copies(d, r, d.master[e]);
+    }
+}
+
+// ----------------------------------------------------------- normalization
+// Per-block partial sums (FP64) of the 17 features / targets: sum, sum of
+// squares, min, max.
+__global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, const float *y, int64_t ldy, double *part)
+{
+    double s[NSTAT], s2[NSTAT], mn[NSTAT], mx[NSTAT];
+#pragma unroll
+    for (int k = 0; k < NSTAT; ++k) { s[k] = 0; s2[k] = 0; mn[k] = 1e300; mx[k] = -1e300; }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float f[NIN], q[NOUT];
+        features(x, ldx, i, f);
+        targets(y, ldy, i, q);
+#pragma unroll
+        for (int k = 0; k < NSTAT; ++k) {
+            const double v = (k < NIN) ? f[k] : q[k - NIN];
+            s[k] += v; s2[k] += v * v; mn[k] = fmin(mn[k], v); mx[k] = fmax(mx[k], v);
+        }
+    }
+    __shared__ double sh[4][NSTAT][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NSTAT; ++k) {
+        double a = s[k], b = s2[k], c = mn[k], e = mx[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c = fmin(c, __shfl_xor_sync(0xffffffffu, c, o));
+            e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+        }
+        if (lane == 0) { sh[0][k][warp] = a; sh[1][k][warp] = b; sh[2][k][warp] = c; sh[3][k][warp] = e; }
+    }
+    __syncthreads();
+    if (threadIdx.x < NSTAT) {
+        const int k = threadIdx.x;
+        double a = 0, b = 0, c = 1e300, e = -1e300;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sh[0][k][w]; b += sh[1][k][w]; c = fmin(c, sh[2][k][w]); e = fmax(e, sh[3][k][w]);
+        }
+        double *p = part + ((int64_t)blockIdx.x * NSTAT + k) * 4;
+        p[0] = a; p[1] = b; p[2] = c; p[3] = e;
+    }
+}
+
+// Mean, standard deviation and the training hull (min/max widened by 1 % of
+// the range) from the block partials.  norm layout: in_mean[11] in_std[11]
+// out_mean[6] out_std[6] hull_lo[11] hull_hi[11].
+__global__ void norm_final_kernel(int nblocks, int64_t n, const double *part, float *norm)
+{
+    const int k = threadIdx.x;
+    if (k >= NSTAT) return;
+    double a = 0, b = 0, c = 1e300, e = -1e300;
+    for (int blk = 0; blk < nblocks; ++blk) {
+        const double *p = part + ((int64_t)blk * NSTAT + k) * 4;
+        a += p[0]; b += p[1]; c = fmin(c, p[2]); e = fmax(e, p[3]);
+    }
+    const double mean = a / (double)n;
+    double var = b / (double)n - mean * mean;
+    double sd = var > 0 ? sqrt(var) : 0.0;
+    if (!(sd > 1e-12 * fmax(1.0, fabs(mean)))) sd = 1.0;
+    if (k < NIN) {
+        norm[k] = (float)mean;
+        norm[NIN + k] = (float)sd;
+        const double w = 0.01 * (e - c);
+        norm[2 * NIN + 2 * NOUT + k] = (float)(c - w);
+        norm[3 * NIN + 2 * NOUT + k] = (float)(e + w);
+    } else {
+        norm[2 * NIN + (k - NIN)] = (float)mean;
+        norm[2 * NIN + NOUT + (k - NIN)] = (float)sd;
+    }
+}
+
+// ------------------------------------------------------------ prep kernels
+// Training batch: row r takes pool row src (in order when sample_seed == 0 and
+// the pool is the batch, else uniformly at random with replacement).
+__global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const float *x, int64_t ldx, const float *y,
+                                  int64_t ldy, uint64_t sample_seed)
+{
+    const float *nm = d.norm;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < B; r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t src = r;
+        if (sample_seed != 0 || n_pool != B) src = (int64_t)(splitmix64(sample_seed ^ ((uint64_t)r * 0xD1B54A32D192ED03ull)) % (uint64_t)n_pool);
+        float f[NIN], q[NOUT];
+        features(x, ldx, src, f);
+        targets(y, ldy, src, q);
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = (k < NIN) ? (f[k] - nm[k]) / nm[NIN + k] : 0.f;
+        store_row16_bf16(d.x0 + r * KIN, v);
+#pragma unroll
+        for (int k = 0; k < NIN; ++k) d.x0t[(int64_t)k * d.max_batch + r] = __float2bfloat16_rn(v[k]);
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) d.tgt[(int64_t)j * d.max_batch + r] = (q[j] - nm[2 * NIN + j]) / nm[2 * NIN + NOUT + j];
+    }
+}
+
+// Inference chunk: standardised inputs, training-hull test, compaction of the
+// cells outside the hull into `list` (chunk-local indices).
+__global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *T, const float *p, const float *Y,
+                                  int64_t ldY, uint8_t *flags, int32_t *list, unsigned int *count)
+{
+    const float *nm = d.norm;
+    const float *lo = nm + 2 * NIN + 2 * NOUT, *hi = lo + NIN;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < mc; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = r0 + r;
+        float f[NIN];
+        f[0] = logf(__ldg(T + i));
+        f[1] = __ldg(p + i);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(Y + (int64_t)k * ldY + i);
+        bool out = false;
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k < NIN) {
+                out = out || !(f[k] >= lo[k] && f[k] <= hi[k]);
+                v[k] = (f[k] - nm[k]) / nm[NIN + k];
+            } else {
+                v[k] = 0.f;
+            }
+        }
+        store_row16_bf16(d.xi + r * KIN, v);
+        if (flags) flags[i] = out ? 1 : 0;
+        if (out) list[atomicAdd(count, 1u)] = (int32_t)r;
+    }
+}
+
+// ---------------------------------------------------------- PR fallback
+// FP64 Peng-Robinson properties of the listed cells (float inputs/outputs),
+// one thread per listed cell.
+template <int NS, bool KIJ>
+__global__ void __launch_bounds__(128) fallback_kernel(const int32_t *list, const unsigned int *count, int64_t r0,
+                                                       const float *T, const float *p, const float *Y, int64_t ldY,
+                                                       float *out, int64_t ldo, const SpeciesRec<double> *sp,
+                                                       const double *pair, const double *kij, int N, int flags)
+{
+    __shared__ SpeciesRec<double> s_sp[NS];
+    __shared__ double s_pair[NS * NS];
+    __shared__ double s_kij[NS * NS];
+    {
+        const double *src = reinterpret_cast<const double *>(sp);
+        double *dst = reinterpret_cast<double *>(s_sp);
+        for (int j = threadIdx.x; j < (int)(NS * sizeof(SpeciesRec<double>) / 8); j += blockDim.x) dst[j] = src[j];
+        for (int j = threadIdx.x; j < NS * NS; j += blockDim.x) { s_pair[j] = pair[j]; s_kij[j] = kij[j]; }
+    }
+    __syncthreads();
+    const unsigned int n = *count;
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int64_t i = r0 + list[t];
+        const double Tv = (double)__ldg(T + i), pv = (double)__ldg(p + i);
+        prk::Comp<double, NS> c;
+        double ysum = 0, s = 0;
+        bool ok = (Tv > 0) && (pv > 0) && isfinite(Tv) && isfinite(pv);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const double y = (k < N) ? (double)__ldg(Y + (int64_t)k * ldY + i) : 0.0;
+            ok = ok && (y >= 0) && isfinite(y);
+            ysum += y;
+            c.x[k] = y * s_sp[k].inv_W;
+            s += c.x[k];
+        }
+        ok = ok && fabs(ysum - 1.0) <= 1e-6 && s > 0;
+        const double is = 1.0 / s;
+        double bm = 0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) { c.x[k] *= is; bm = fma(c.x[k], s_sp[k].b, bm); }
+        c.Wbar = is;
+        c.bm = bm;
+        float o[6];
+        for (int q = 0; q < 6; ++q) o[q] = __int_as_float(0x7fc00000);
+        if (ok) {
+            prk::Thermo<double> th;
+            prk::thermo<double, double, NS, KIJ>(c, Tv, pv, s_sp, s_kij, th);
+            if (th.status != prk::kNoRoot) {
+                double mu, lam;
+                prk::transport<double, NS>(c, Tv, th, s_sp, s_pair, flags, mu, lam);
+                o[0] = (float)(pv * c.Wbar / (th.Z * prk::kR * Tv));
+                o[1] = (float)th.Z; o[2] = (float)th.h; o[3] = (float)th.cp; o[4] = (float)mu; o[5] = (float)lam;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) out[(int64_t)q * ldo + i] = o[q];
+    }
+}
+
+// ------------------------------------------------------------------- Adam
+__global__ void adam_kernel(SgDev d, float lr, float b1, float b2, float eps, int t, int64_t nct_bias,
+                            int export_only, float *grad_out)
+{
+    const float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.n_master; e += (int64_t)gridDim.x * blockDim.x) {
+        ParamRef r = decode_param(d, e);
+        if (!r.valid) continue;
+        float g = 0.f;
+        if (r.bias) {
+            const float *cs = d.colsum[r.layer];
+            const int ncol = r.out_pad_n;
+            for (int64_t c = 0; c < nct_bias; ++c) g += cs[c * ncol + r.o];
+        } else {
+            const float *pp = d.partial[r.layer];
+            const int64_t plane = (int64_t)d.dw_mpad[r.layer] * r.in_pad;
+            for (int s = 0; s < d.dw_splits[r.layer]; ++s) g += pp[s * plane + (int64_t)r.o * r.in_pad + r.i];
+        }
+        if (export_only) {
+            grad_out[r.flat] = g;
+            continue;
+        }
+        const float m = b1 * d.adam_m[e] + (1.f - b1) * g;
+        const float v = b2 * d.adam_v[e] + (1.f - b2) * g * g;
+        d.adam_m[e] = m;
+        d.adam_v[e] = v;
+        const float w = d.master[e] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+        d.master[e] = w;
+        write_bf16_copies(d, r, w);
+    }
+}
+
+__global__ void loss_final_kernel(const float *part, int64_t nct, float scale, float *loss_out)
+{
+    __shared__ float sh[256];
+    float s = 0.f;
+    for (int64_t c = threadIdx.x; c < nct; c += blockDim.x) s += part[c];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss_out = sh[0] * scale;
+}
+
+__global__ void copy_params_kernel(SgDev d, float *flat, int to_flat)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.n_master; e += (int64_t)gridDim.x * blockDim.x) {
+        ParamRef r = decode_param(d, e);
+        if (!r.valid) continue;
+        if (to_flat) flat[r.flat] = d.master[e];
+        else d.master[e] = flat[r.flat];
+    }
+}
+
+// --------------------------------------------------------- tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// K-major BF16 operand [rows][inner] with row pitch `pitch` elements, loaded
+// in boxes of 64 x box_rows with 128-byte swizzling (out-of-range rows and
+// columns read as zero).
+bool make_map(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, uint64_t pitch, uint32_t box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {pitch * 2};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, int EPI>
+cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &a, int gx, int gy, int gz,
+                        cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Cfg<BN>::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    gemm_kernel<BN, EPI><<<dim3(gx, gy, gz), 192, Cfg<BN>::SMEM, st>>>(ta, tb, a);
+    return cudaGetLastError();
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+GemmArgs base_args(sg_model *m)
+{
+    GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.err = m->d_err;
+    return a;
+}
+
+}  // namespace
+
+// ===================================================== host-side plumbing
+static pr_status build_maps(sg_model *m)
+{
+    SgDev &d = m->dev;
+    const int W = m->width, L = m->hidden;
+    const int64_t B = m->max_batch, C = m->chunk;
+    bool ok = true;
+    // weights (forward B operands)
+    ok = ok && make_map(&m->tm_w[0], d.wb[0], KIN, W, KIN, 128);
+    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_w[l], d.wb[l], W, W, W, 128);
+    ok = ok && make_map(&m->tm_w[L], d.wb[L], W, NOP, W, 16);
+    // transposed weights (input-gradient B operands)
+    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_wt[l], d.wt[l], W, W, W, 128);
+    ok = ok && make_map(&m->tm_wt[L], d.wt[L], KIN, W, KIN, 128);
+    // training activations
+    ok = ok && make_map(&m->tm_x0, d.x0, KIN, B, KIN, 128);
+    ok = ok && make_map(&m->tm_x0t, d.x0t, B, KIN, B, 64);
+    for (int l = 0; l < L; ++l) {
+        ok = ok && make_map(&m->tm_h[l], d.h[l], W, B, W, 128);
+        ok = ok && make_map(&m->tm_ht[l], d.ht[l], B, W, B, 128);
+        ok = ok && make_map(&m->tm_dz[l], d.dz[l], W, B, W, 128);
+        ok = ok && make_map(&m->tm_dzt[l], d.dzt[l], B, W, B, 128);
+    }
+    ok = ok && make_map(&m->tm_dzo, d.dzo, KIN, B, KIN, 128);
+    ok = ok && make_map(&m->tm_dzot, d.dzot, B, MOP, B, 128);
+    // inference
+    ok = ok && make_map(&m->tm_xi, d.xi, KIN, C, KIN, 128);
+    ok = ok && make_map(&m->tm_hi[0], d.hi[0], W, C, W, 128);
+    ok = ok && make_map(&m->tm_hi[1], d.hi[1], W, C, W, 128);
+    if (!ok) {
+        prgb::set_error("surrogate: cuTensorMapEncodeTiled unavailable or failed");
+        return PR_ECUDA;
+    }
+    return PR_OK;
+}
+
+static void free_model(sg_model *m)
+{
+    if (!m) return;
+    for (void *p : m->allocs) cudaFree(p);
+    delete m;
+}
+
+extern "C" {
+
+pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_model **out)
+{
+    PR_CHECK_ARG(ctx && cfg && out, "surrogate_create: null argument");
+    *out = nullptr;
+    PR_CHECK_ARG(ctx->n_species == 9, "surrogate_create: the surrogate takes 9 species, context has %d", ctx->n_species);
+    PR_CHECK_ARG(cfg->width == 512 || cfg->width == 256 || cfg->width == 128 || cfg->width == 1024,
+                 "surrogate_create: width must be 128, 256, 512 or 1024");
+    PR_CHECK_ARG(cfg->hidden_layers >= 1 && cfg->hidden_layers <= SG_MAX_HIDDEN, "surrogate_create: hidden_layers 1..%d",
+                 SG_MAX_HIDDEN);
+    PR_CHECK_ARG(cfg->max_batch >= 128 && cfg->max_batch % 128 == 0 && cfg->max_batch <= (1 << 22),
+                 "surrogate_create: max_batch must be a multiple of 128 in [128, 4194304]");
+    PR_CHECK_ARG(cfg->infer_chunk >= 128 && cfg->infer_chunk % 128 == 0 && cfg->infer_chunk <= (1 << 24),
+                 "surrogate_create: infer_chunk must be a multiple of 128 in [128, 16777216]");
+    sg_model *m = new (std::nothrow) sg_model();
+    if (!m) { prgb::set_error("surrogate_create: host allocation failed"); return PR_ENOMEM; }
+    m->ctx = ctx;
+    m->width = cfg->width;
+    m->hidden = cfg->hidden_layers;
+    m->max_batch = cfg->max_batch;
+    m->chunk = cfg->infer_chunk;
+    m->step = 0;
+    m->norm_blocks = 2 * ctx->num_sms;
+    SgDev &d = m->dev;
+    memset(&d, 0, sizeof(d));
+    d.width = m->width;
+    d.hidden = m->hidden;
+    d.max_batch = m->max_batch;
+    const int W = m->width, L = m->hidden;
+    const int64_t B = m->max_batch, C = m->chunk;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) {
+            m->allocs.push_back(*p);
+            e = cudaMemset(*p, 0, bytes);
+        }
+    };
+    // parameter layout: per layer W [out_pad][in_pad] then b [out_pad]
+    int64_t off = 0, flat = 0;
+    for (int l = 0; l <= L; ++l) {
+        const int in = (l == 0) ? NIN : W, in_pad = (l == 0) ? KIN : W;
+        const int out = (l == L) ? NOUT : W, out_pad = (l == L) ? NOP : W;
+        d.lay[l] = {off, off + (int64_t)out_pad * in_pad, in, in_pad, out, out_pad, flat};
+        off += (int64_t)out_pad * in_pad + out_pad;
+        flat += (int64_t)out * in + out;
+    }
+    d.n_master = off;
+    d.n_flat = flat;
+    alloc((void **)&d.master, off * 4);
+    alloc((void **)&d.adam_m, off * 4);
+    alloc((void **)&d.adam_v, off * 4);
+    for (int l = 0; l <= L; ++l) {
+        alloc((void **)&d.wb[l], (size_t)d.lay[l].out_pad * d.lay[l].in_pad * 2);
+        if (l > 0) {
+            const int out_pad_k = (l == L) ? KIN : W;   // K of the input-gradient GEMM
+            alloc((void **)&d.wt[l], (size_t)d.lay[l].in_pad * out_pad_k * 2);
+        }
+    }
+    alloc((void **)&d.norm, 64 * 4);
+    alloc((void **)&d.x0, B * KIN * 2);
+    alloc((void **)&d.x0t, (int64_t)KIN * B * 2);
+    alloc((void **)&d.tgt, (int64_t)NOUT * B * 4);
+    for (int l = 0; l < L; ++l) {
+        alloc((void **)&d.h[l], B * W * 2);
+        alloc((void **)&d.ht[l], B * W * 2);
+        alloc((void **)&d.g[l], B * W * 2);
+        alloc((void **)&d.dz[l], B * W * 2);
+        alloc((void **)&d.dzt[l], B * W * 2);
+    }
+    alloc((void **)&d.dzo, B * KIN * 2);
+    alloc((void **)&d.dzot, (int64_t)MOP * B * 2);
+    // weight-gradient partials: splits chosen so that tiles x splits ~ SM count
+    const int kb = (int)(B / 64);
+    for (int l = 0; l <= L; ++l) {
+        const int mp = (l == L) ? MOP : W;
+        const int np = d.lay[l].in_pad;
+        const int bn = (np >= 128) ? 128 : 64;
+        const int tiles = (mp / 128) * (np / bn);
+        int splits = ctx->num_sms / tiles;
+        splits = splits < 1 ? 1 : (splits > kb ? kb : splits);
+        const int kps = (kb + splits - 1) / splits;
+        splits = (kb + kps - 1) / kps;
+        d.dw_splits[l] = splits;
+        d.dw_kps[l] = kps;
+        d.dw_mpad[l] = mp;
+        alloc((void **)&d.partial[l], (size_t)splits * mp * np * 4);
+        const int ncol = (l == L) ? NOP : W;
+        alloc((void **)&d.colsum[l], (size_t)(B / 128) * ncol * 4);
+    }
+    alloc((void **)&d.loss_part, (B / 128) * 4);
+    alloc((void **)&m->d_loss, 4);
+    alloc((void **)&m->d_err, 4);
+    alloc((void **)&m->d_normpart, (size_t)m->norm_blocks * NSTAT * 4 * 8);
+    alloc((void **)&d.xi, C * KIN * 2);
+    alloc((void **)&d.hi[0], C * W * 2);
+    alloc((void **)&d.hi[1], C * W * 2);
+    alloc((void **)&m->d_list, C * 4);
+    alloc((void **)&m->d_count, 16);
+    alloc((void **)&m->d_flags, C);
+    if (e == cudaSuccess) {
+        // default normalisation: identity, unbounded hull
+        float nm[64];
+        for (int k = 0; k < 64; ++k) nm[k] = 0.f;
+        for (int k = 0; k < NIN; ++k) { nm[NIN + k] = 1.f; nm[2 * NIN + 2 * NOUT + k] = -3e38f; nm[3 * NIN + 2 * NOUT + k] = 3e38f; }
+        for (int j = 0; j < NOUT; ++j) nm[2 * NIN + NOUT + j] = 1.f;
+        e = cudaMemcpy(d.norm, nm, sizeof(nm), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) {
+        init_params_kernel<<<256, 256>>>(d, seed ? seed : 1);
+        refresh_bf16_kernel<<<256, 256>>>(d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        prgb::set_error("surrogate_create: %s", cudaGetErrorString(e));
+        free_model(m);
+        return e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA;
+    }
+    pr_status s = build_maps(m);
+    if (s) { free_model(m); return s; }
+    *out = m;
+    return PR_OK;
+}
+
+void surrogate_destroy(sg_model *m)
+{
+    if (!m) return;
+    cudaDeviceSynchronize();
+    free_model(m);
+}
+
+int64_t surrogate_num_params(const sg_model *m) { return m ? m->dev.n_flat : -1; }
+
+pr_status surrogate_get_params(const sg_model *m, float *host_dst, int64_t n)
+{
+    PR_CHECK_ARG(m && host_dst && n == m->dev.n_flat, "surrogate_get_params: bad arguments");
+    float *tmp = nullptr;
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    PR_CUDA_TRY(cudaMalloc(&tmp, n * 4));
+    copy_params_kernel<<<256, 256>>>(m->dev, tmp, 1);
+    cudaError_t e = cudaMemcpy(host_dst, tmp, n * 4, cudaMemcpyDeviceToHost);
+    cudaFree(tmp);
+    PR_CUDA_TRY(e);
+    return PR_OK;
+}
+
+pr_status surrogate_set_params(sg_model *m, const float *host_src, int64_t n)
+{
+    PR_CHECK_ARG(m && host_src && n == m->dev.n_flat, "surrogate_set_params: bad arguments");
+    float *tmp = nullptr;
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    PR_CUDA_TRY(cudaMalloc(&tmp, n * 4));
+    cudaError_t e = cudaMemcpy(tmp, host_src, n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        copy_params_kernel<<<256, 256>>>(m->dev, tmp, 0);
+        refresh_bf16_kernel<<<256, 256>>>(m->dev);
+        e = cudaDeviceSynchronize();
+    }
+    cudaFree(tmp);
+    PR_CUDA_TRY(e);
+    return PR_OK;
+}
+
+pr_status surrogate_get_normalization(const sg_model *m, float *host_dst)
+{
+    PR_CHECK_ARG(m && host_dst, "surrogate_get_normalization: null argument");
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    PR_CUDA_TRY(cudaMemcpy(host_dst, m->dev.norm, SG_NORM_FLOATS * 4, cudaMemcpyDeviceToHost));
+    return PR_OK;
+}
+
+pr_status surrogate_set_normalization(sg_model *m, const float *host_src)
+{
+    PR_CHECK_ARG(m && host_src, "surrogate_set_normalization: null argument");
+    for (int k = 0; k < NIN; ++k)
+        PR_CHECK_ARG(host_src[NIN + k] > 0, "surrogate_set_normalization: input std must be > 0");
+    for (int j = 0; j < NOUT; ++j)
+        PR_CHECK_ARG(host_src[2 * NIN + NOUT + j] > 0, "surrogate_set_normalization: output std must be > 0");
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    PR_CUDA_TRY(cudaMemcpy(m->dev.norm, host_src, SG_NORM_FLOATS * 4, cudaMemcpyHostToDevice));
+    return PR_OK;
+}
+
+pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, int64_t ldx, const float *y,
+                                      int64_t ldy, void *stream)
+{
+    PR_CHECK_ARG(m && x && y && n > 0 && ldx >= n && ldy >= n, "surrogate_fit_normalization: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->d_normpart);
+    norm_final_kernel<<<1, 32, 0, st>>>(m->norm_blocks, n, m->d_normpart, m->dev.norm);
+    PR_CUDA_TRY(cudaGetLastError());
+    return PR_OK;
+}
+
+// forward + backward of one batch already prepared in the training buffers
+static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
+{
+    SgDev &d = m->dev;
+    const int W = m->width, L = m->hidden;
+    const int mt = ceil_div(B, 128);
+    cudaError_t e = cudaSuccess;
+    // forward, hidden layers
+    for (int l = 0; l < L; ++l) {
+        GemmArgs a = base_args(m);
+        a.M = (int)B; a.N = W; a.K = (l == 0) ? KIN : W; a.kb_per_split = a.K / 64;
+        a.bias = d.master + d.lay[l].b_off;
+        a.out = d.h[l]; a.ldo = W; a.outT = d.ht[l]; a.ldoT = d.max_batch; a.gd = d.g[l]; a.ldg = W;
+        const CUtensorMap &ta = (l == 0) ? m->tm_x0 : m->tm_h[l - 1];
+        e = launch_gemm<128, kEpiHidden>(ta, m->tm_w[l], a, mt, W / 128, 1, st);
+        if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) { prgb::set_error("forward: %s", cudaGetErrorString(e)); return PR_ECUDA; }
+    // output layer + loss + dz of the output
+    {
+        GemmArgs a = base_args(m);
+        a.M = (int)B; a.N = NOP; a.K = W; a.kb_per_split = W / 64;
+        a.bias = d.master + d.lay[L].b_off;
+        a.target = d.tgt; a.ldt = d.max_batch; a.loss_scale = 2.0f / (float)(B * NOUT);
+        a.out = d.dzo; a.ldo = KIN; a.outT = d.dzot; a.ldoT = d.max_batch;
+        a.colsum = d.colsum[L]; a.loss_part = d.loss_part;
+        e = launch_gemm<16, kEpiOutLoss>(m->tm_h[L - 1], m->tm_w[L], a, mt, 1, 1, st);
+        if (e != cudaSuccess) { prgb::set_error("loss: %s", cudaGetErrorString(e)); return PR_ECUDA; }
+    }
+    // input gradients: dz_{l-1} = (dz_l W_l) * GeLU'(z_{l-1})
+    for (int l = L; l >= 1; --l) {
+        GemmArgs a = base_args(m);
+        a.M = (int)B; a.N = W; a.K = (l == L) ? KIN : W; a.kb_per_split = a.K / 64;
+        a.gd = d.g[l - 1]; a.ldg = W;
+        a.out = d.dz[l - 1]; a.ldo = W; a.outT = d.dzt[l - 1]; a.ldoT = d.max_batch;
+        a.colsum = d.colsum[l - 1];
+        const CUtensorMap &ta = (l == L) ? m->tm_dzo : m->tm_dz[l];
+        e = launch_gemm<128, kEpiDx>(ta, m->tm_wt[l], a, mt, W / 128, 1, st);
+        if (e != cudaSuccess) { prgb::set_error("dx: %s", cudaGetErrorString(e)); return PR_ECUDA; }
+    }
+    // weight gradients: dW_l = dz_l^T h_{l-1}, K = batch, split along K
+    for (int l = 0; l <= L; ++l) {
+        GemmArgs a = base_args(m);
+        const int mp = d.dw_mpad[l], np = d.lay[l].in_pad;
+        a.M = mp; a.Mpad = mp; a.N = np; a.K = (int)B; a.kb_per_split = d.dw_kps[l];
+        a.partial = d.partial[l];
+        const int splits = ceil_div(ceil_div(B, 64), d.dw_kps[l]);
+        const CUtensorMap &ta = (l == L) ? m->tm_dzot : m->tm_dzt[l];
+        const CUtensorMap &tb = (l == 0) ? m->tm_x0t : m->tm_ht[l - 1];
+        if (np >= 128) e = launch_gemm<128, kEpiDw>(ta, tb, a, mp / 128, np / 128, splits, st);
+        else e = launch_gemm<64, kEpiDw>(ta, tb, a, mp / 128, np / 64, splits, st);
+        if (e != cudaSuccess) { prgb::set_error("dw: %s", cudaGetErrorString(e)); return PR_ECUDA; }
+        m->last_splits[l] = splits;
+    }
+    return PR_OK;
+}
+
+static pr_status train_common(sg_model *m, int64_t batch, int64_t n_pool, const float *x, int64_t ldx, const float *y,
+                              int64_t ldy, uint64_t seed, float lr, float *loss_out, float *grad_out, void *stream)
+{
+    PR_CHECK_ARG(m && x && y, "surrogate_train_step: null argument");
+    PR_CHECK_ARG(batch >= 128 && batch % 128 == 0 && batch <= m->max_batch,
+                 "surrogate_train_step: batch must be a multiple of 128 and <= max_batch (%lld)", (long long)m->max_batch);
+    PR_CHECK_ARG(n_pool >= batch && ldx >= n_pool && ldy >= n_pool, "surrogate_train_step: pool sizes");
+    PR_CHECK_ARG(std::isfinite(lr) && lr >= 0.f, "surrogate_train_step: bad lr");
+    cudaStream_t st = (cudaStream_t)stream;
+    SgDev &d = m->dev;
+    const int blocks = ceil_div(batch, 256);
+    prep_train_kernel<<<blocks < 2048 ? blocks : 2048, 256, 0, st>>>(d, batch, n_pool, x, ldx, y, ldy, seed);
+    PR_CUDA_TRY(cudaGetLastError());
+    // the dw GEMMs split K over dw_kps k-blocks: make sure the splits fit the batch
+    for (int l = 0; l <= m->hidden; ++l) d.dw_splits[l] = ceil_div(ceil_div(batch, 64), d.dw_kps[l]);
+    pr_status s = fwd_bwd(m, batch, st);
+    if (s) return s;
+    const int64_t nct = batch / 128;
+    if (grad_out) {
+        adam_kernel<<<512, 256, 0, st>>>(d, 0.f, 0.9f, 0.999f, 1e-8f, 1, nct, 1, grad_out);
+    } else {
+        m->step += 1;
+        adam_kernel<<<512, 256, 0, st>>>(d, lr, 0.9f, 0.999f, 1e-8f, (int)m->step, nct, 0, nullptr);
+    }
+    float *lo = loss_out ? loss_out : m->d_loss;
+    loss_final_kernel<<<1, 256, 0, st>>>(d.loss_part, nct, 1.0f / (float)(batch * NOUT), lo);
+    PR_CUDA_TRY(cudaGetLastError());
+    return PR_OK;
+}
+
+pr_status surrogate_train_step(sg_model *m, int64_t batch, int64_t n_pool, const float *x, int64_t ldx,
+                               const float *y, int64_t ldy, uint64_t sample_seed, float lr, float *loss_out,
+                               void *stream)
+{
+    return train_common(m, batch, n_pool, x, ldx, y, ldy, sample_seed, lr, loss_out, nullptr, stream);
+}
+
+pr_status surrogate_loss_grad(sg_model *m, int64_t batch, const float *x, int64_t ldx, const float *y, int64_t ldy,
+                              float *loss_out, float *grad_out, void *stream)
+{
+    PR_CHECK_ARG(grad_out != nullptr, "surrogate_loss_grad: grad_out is NULL");
+    return train_common(m, batch, batch, x, ldx, y, ldy, 0, 0.f, loss_out, grad_out, stream);
+}
+
+pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p, const float *Y, int64_t ldY,
+                          float *out, int64_t ldo, uint8_t *used_fallback, void *stream)
+{
+    PR_CHECK_ARG(m != nullptr, "surrogate_infer: null model");
+    PR_CHECK_ARG(n >= 0, "surrogate_infer: n < 0");
+    if (n == 0) return PR_OK;
+    PR_CHECK_ARG(T && p && Y && out, "surrogate_infer: null array");
+    PR_CHECK_ARG(ldY >= n && ldo >= n, "surrogate_infer: ldY/ldo < n");
+    PR_CHECK_ARG(prgb::aligned(T, 4) && prgb::aligned(p, 4) && prgb::aligned(Y, 4) && prgb::aligned(out, 4),
+                 "surrogate_infer: misaligned array");
+    cudaStream_t st = (cudaStream_t)stream;
+    SgDev &d = m->dev;
+    pr_ctx *ctx = m->ctx;
+    const int W = m->width, L = m->hidden;
+    for (int64_t r0 = 0; r0 < n; r0 += m->chunk) {
+        const int64_t mc = (n - r0 < m->chunk) ? (n - r0) : m->chunk;
+        const int mt = ceil_div(mc, 128);
+        PR_CUDA_TRY(cudaMemsetAsync(m->d_count, 0, 4, st));
+        const int pb = ceil_div(mc, 256);
+        prep_infer_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, used_fallback, m->d_list,
+                                                                 m->d_count);
+        PR_CUDA_TRY(cudaGetLastError());
+        for (int l = 0; l < L; ++l) {
+            GemmArgs a = base_args(m);
+            a.M = (int)mc; a.N = W; a.K = (l == 0) ? KIN : W; a.kb_per_split = a.K / 64;
+            a.bias = d.master + d.lay[l].b_off;
+            a.out = d.hi[l & 1]; a.ldo = W;
+            const CUtensorMap &ta = (l == 0) ? m->tm_xi : m->tm_hi[(l - 1) & 1];
+            PR_CUDA_TRY((launch_gemm<128, kEpiHidden>(ta, m->tm_w[l], a, mt, W / 128, 1, st)));
+        }
+        {
+            GemmArgs a = base_args(m);
+            a.M = (int)mc; a.N = NOP; a.K = W; a.kb_per_split = W / 64;
+            a.bias = d.master + d.lay[L].b_off;
+            a.out6 = out + r0; a.ld6 = ldo;
+            a.out_mean = d.norm + 2 * NIN; a.out_std = d.norm + 2 * NIN + NOUT;
+            PR_CUDA_TRY((launch_gemm<16, kEpiOutPhys>(m->tm_hi[(L - 1) & 1], m->tm_w[L], a, mt, 1, 1, st)));
+        }
+        // FP64 Peng-Robinson for the cells outside the training hull
+        const int fb = ctx->num_sms * 4;
+        if (ctx->has_kij)
+            fallback_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out, ldo,
+                                                         (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64,
+                                                         ctx->d_kij64, ctx->n_species, ctx->flags);
+        else
+            fallback_kernel<9, false><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out, ldo,
+                                                          (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64,
+                                                          ctx->d_kij64, ctx->n_species, ctx->flags);
+        PR_CUDA_TRY(cudaGetLastError());
+    }
+    return PR_OK;
+}
+
+pr_status surrogate_sync_status(sg_model *m)
+{
+    PR_CHECK_ARG(m != nullptr, "surrogate_sync_status: null model");
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    int err = 0;
+    PR_CUDA_TRY(cudaMemcpy(&err, m->d_err, 4, cudaMemcpyDeviceToHost));
+    if (err) {
+        PR_CUDA_TRY(cudaMemset(m->d_err, 0, 4));
+        prgb::set_error("surrogate: a tensor-core kernel gave up waiting on a barrier (results invalid)");
+        return PR_ETIMEOUT;
+    }
+    return PR_OK;
+}
+
+// Checkpoint: "PRSG" v1 | width hidden step | n_master | master, adam_m, adam_v (FP32) | normalisation.
+pr_status surrogate_save(const sg_model *m, const char *path)
+{
+    PR_CHECK_ARG(m && path, "surrogate_save: null argument");
+    const int64_t n = m->dev.n_master;
+    std::vector<float> buf(3 * n + SG_NORM_FLOATS);
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    PR_CUDA_TRY(cudaMemcpy(buf.data(), m->dev.master, n * 4, cudaMemcpyDeviceToHost));
+    PR_CUDA_TRY(cudaMemcpy(buf.data() + n, m->dev.adam_m, n * 4, cudaMemcpyDeviceToHost));
+    PR_CUDA_TRY(cudaMemcpy(buf.data() + 2 * n, m->dev.adam_v, n * 4, cudaMemcpyDeviceToHost));
+    PR_CUDA_TRY(cudaMemcpy(buf.data() + 3 * n, m->dev.norm, SG_NORM_FLOATS * 4, cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    if (!f) { prgb::set_error("surrogate_save: cannot open %s", path); return PR_EINVAL; }
+    const char magic[4] = {'P', 'R', 'S', 'G'};
+    const int32_t hdr[4] = {1, m->width, m->hidden, 0};
+    const int64_t step = m->step;
+    bool ok = fwrite(magic, 1, 4, f) == 4 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&step, 8, 1, f) == 1 &&
+              fwrite(&n, 8, 1, f) == 1 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) { prgb::set_error("surrogate_save: write failed"); return PR_EINVAL; }
+    return PR_OK;
+}
+
+pr_status surrogate_load(sg_model *m, const char *path)
+{
+    PR_CHECK_ARG(m && path, "surrogate_load: null argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) { prgb::set_error("surrogate_load: cannot open %s", path); return PR_EINVAL; }
+    char magic[4];
+    int32_t hdr[4];
+    int64_t step = 0, n = 0;
+    bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "PRSG", 4) == 0 && fread(hdr, 4, 4, f) == 4 &&
+              fread(&step, 8, 1, f) == 1 && fread(&n, 8, 1, f) == 1;
+    ok = ok && hdr[0] == 1 && hdr[1] == m->width && hdr[2] == m->hidden && n == m->dev.n_master;
+    std::vector<float> buf;
+    if (ok) {
+        buf.resize(3 * n + SG_NORM_FLOATS);
+        ok = fread(buf.data(), 4, buf.size(), f) == buf.size();
+    }
+    fclose(f);
+    if (!ok) { prgb::set_error("surrogate_load: %s is not a checkpoint of this model", path); return PR_EINVAL; }
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    PR_CUDA_TRY(cudaMemcpy(m->dev.master, buf.data(), n * 4, cudaMemcpyHostToDevice));
+    PR_CUDA_TRY(cudaMemcpy(m->dev.adam_m, buf.data() + n, n * 4, cudaMemcpyHostToDevice));
+    PR_CUDA_TRY(cudaMemcpy(m->dev.adam_v, buf.data() + 2 * n, n * 4, cudaMemcpyHostToDevice));
+    PR_CUDA_TRY(cudaMemcpy(m->dev.norm, buf.data() + 3 * n, SG_NORM_FLOATS * 4, cudaMemcpyHostToDevice));
+    refresh_bf16_kernel<<<256, 256>>>(m->dev);
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    m->step = step;
+    return PR_OK;
+}
+
+pr_status mlp_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
+                        float *D, int64_t ldd, int *err_flag, void *stream)
+{
+    PR_CHECK_ARG(A && B && D && err_flag, "mlp_gemm_bf16: null argument");
+    PR_CHECK_ARG(M >= 1 && M <= (1 << 30) && K >= 64 && K % 64 == 0 && K <= (1 << 30),
+                 "mlp_gemm_bf16: need M >= 1 and K a positive multiple of 64");
+    PR_CHECK_ARG(N == 16 || N == 64 || (N % 128 == 0 && N <= 65536), "mlp_gemm_bf16: N must be 16, 64 or a multiple of 128");
+    PR_CHECK_ARG(lda >= K && ldb >= K && ldd >= N && lda % 8 == 0 && ldb % 8 == 0 && ldd % 4 == 0,
+                 "mlp_gemm_bf16: leading dimensions (lda, ldb multiples of 8; ldd of 4)");
+    PR_CHECK_ARG(prgb::aligned(A, 16) && prgb::aligned(B, 16) && prgb::aligned(D, 16), "mlp_gemm_bf16: 16-byte alignment");
+    const int bn = (N == 16) ? 16 : (N == 64 ? 64 : 128);
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, A, K, M, lda, 128) || !make_map(&tb, B, K, N, ldb, bn)) {
+        prgb::set_error("mlp_gemm_bf16: tensor map encoding failed");
+        return PR_ECUDA;
+    }
+    GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.M = (int)M; a.Mpad = (int)M; a.N = (int)ldd; a.K = (int)K; a.kb_per_split = (int)(K / 64);
+    a.partial = D;
+    a.err = err_flag;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int gx = ceil_div(M, 128), gy = (int)(N / bn);
+    cudaError_t e;
+    if (bn == 16) e = launch_gemm<16, kEpiDw>(ta, tb, a, gx, gy, 1, st);
+    else if (bn == 64) e = launch_gemm<64, kEpiDw>(ta, tb, a, gx, gy, 1, st);
+    else e = launch_gemm<128, kEpiDw>(ta, tb, a, gx, gy, 1, st);
+    PR_CUDA_TRY(e);
+    return PR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Internal state of the surrogate MLP (device buffers, parameter layout,
+// tensor maps).  Shared by surrogate.cu and the serving loop.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "pr_internal.h"
+
+#define SG_MAX_HIDDEN 8
+// SG_NORM_FLOATS comes from prgb300.h
+
+// Parameter layout of one layer inside the padded FP32 master array.
+struct LayerLayout {
+    int64_t w_off, b_off;   // offsets of W [out_pad][in_pad] and b [out_pad]
+    int in, in_pad, out, out_pad;
+    int64_t flat_off;       // offset in the unpadded (W [out][in], b [out]) export order
+};
+
+// Everything the kernels need, passed by value.
+struct SgDev {
+    int width, hidden;
+    int64_t max_batch;
+    LayerLayout lay[SG_MAX_HIDDEN + 1];
+    int64_t n_master, n_flat;
+    float *master, *adam_m, *adam_v;
+    __nv_bfloat16 *wb[SG_MAX_HIDDEN + 1];   // W [out_pad][in_pad]
+    __nv_bfloat16 *wt[SG_MAX_HIDDEN + 1];   // W^T [in][K of the input-gradient GEMM]
+    float *norm;                            // SG_NORM_FLOATS
+    // training activations (batch-major X [B][.] and feature-major X^T [.][B])
+    __nv_bfloat16 *x0, *x0t;
+    float *tgt;                             // standardised targets [6][B]
+    __nv_bfloat16 *h[SG_MAX_HIDDEN], *ht[SG_MAX_HIDDEN], *g[SG_MAX_HIDDEN];
+    __nv_bfloat16 *dz[SG_MAX_HIDDEN], *dzt[SG_MAX_HIDDEN];
+    __nv_bfloat16 *dzo, *dzot;              // output-layer dz [B][64] and dz^T [128][B]
+    float *partial[SG_MAX_HIDDEN + 1];      // weight-gradient partials [split][Mpad][in_pad]
+    int dw_splits[SG_MAX_HIDDEN + 1], dw_kps[SG_MAX_HIDDEN + 1], dw_mpad[SG_MAX_HIDDEN + 1];
+    float *colsum[SG_MAX_HIDDEN + 1];       // per-CTA column sums of dz [B/128][out_pad]
+    float *loss_part;                       // [B/128]
+    // inference chunk buffers
+    __nv_bfloat16 *xi, *hi[2];
+};
+
+struct ParamRef {
+    bool valid, bias;
+    int layer, o, i;
+    int in_pad, out_pad_n, out_pad_k;
+    int64_t flat;
+};
+
+__device__ __forceinline__ ParamRef decode_param(const SgDev &d, int64_t e)
+{
+    ParamRef r;
+    int l = 0;
+    while (l < d.hidden && e >= d.lay[l + 1].w_off) ++l;
+    const LayerLayout &L = d.lay[l];
+    r.layer = l;
+    r.in_pad = L.in_pad;
+    r.out_pad_n = L.out_pad;
+    r.out_pad_k = (l == d.hidden) ? 64 : d.width;
+    if (e < L.b_off) {
+        const int64_t k = e - L.w_off;
+        r.bias = false;
+        r.o = (int)(k / L.in_pad);
+        r.i = (int)(k % L.in_pad);
+        r.valid = r.o < L.out && r.i < L.in;
+        r.flat = L.flat_off + (int64_t)r.o * L.in + r.i;
+    } else {
+        r.bias = true;
+        r.o = (int)(e - L.b_off);
+        r.i = 0;
+        r.valid = r.o < L.out;
+        r.flat = L.flat_off + (int64_t)L.out * L.in + r.o;
+    }
+    return r;
+}
+
+struct sg_model {
+    pr_ctx *ctx;
+    int width, hidden;
+    int64_t max_batch, chunk;
+    int64_t step;
+    int norm_blocks;
+    SgDev dev;
+    float *d_loss;
+    int *d_err;
+    double *d_normpart;
+    int32_t *d_list;
+    unsigned int *d_count;
+    uint8_t *d_flags;
+    int last_splits[SG_MAX_HIDDEN + 1];
+    CUtensorMap tm_w[SG_MAX_HIDDEN + 1], tm_wt[SG_MAX_HIDDEN + 1];
+    CUtensorMap tm_x0, tm_x0t, tm_h[SG_MAX_HIDDEN], tm_ht[SG_MAX_HIDDEN], tm_dz[SG_MAX_HIDDEN],
+        tm_dzt[SG_MAX_HIDDEN], tm_dzo, tm_dzot, tm_xi, tm_hi[2];
+    std::vector<void *> allocs;
+};

@@ -1,0 +1,194 @@
+"""Surrogate MLP on the GPU (tensor-core forward, backward, Adam, fallback)
+against the float64 oracle MLP and the FP64 Peng-Robinson oracle.
+
+BF16 operands (8-bit significands) bound the agreement of the tensor-core
+path with the float64 oracle: gradients are compared by per-layer relative
+norm (<= 3e-2) and cosine (>= 0.999), outputs in standardised units.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2312_04830_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(prlib, cuda, species):
+    from paper_2312_04830_gb300 import binding
+    c = binding.PropertyContext(species)
+    yield c
+    c.close()
+
+
+def make_pool(orc, species, n, seed):
+    """Training pool: half uniform cells, half noisy flame-sheet states, with
+    oracle properties as targets (float32)."""
+    T, p, Y = W.training_states(n, seed=seed)
+    props, st = orc.props(species, T, p, Y)
+    ok = st == 0
+    T, p, Y, props = T[ok], p[ok], Y[:, ok], props[:, ok]
+    x = np.vstack([T, p, Y]).astype(np.float32)
+    y = props.astype(np.float32)
+    return x, y
+
+
+def to_dev(a, cuda):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), device=cuda)
+
+
+def unflatten(flat, sizes):
+    params, off = [], 0
+    for fin, fout in zip(sizes[:-1], sizes[1:]):
+        Wm = flat[off:off + fin * fout].reshape(fout, fin).astype(np.float64)
+        off += fin * fout
+        b = flat[off:off + fout].astype(np.float64)
+        off += fout
+        params.append((Wm, b))
+    assert off == flat.size
+    return params
+
+
+def standardise(x, y, norm):
+    f = np.vstack([np.log(x[0].astype(np.float64)), x[1], x[2:]]).T
+    s_in = (f - norm[0:11]) / norm[11:22]
+    q = omlp.output_targets(y.astype(np.float64))
+    s_out = (q - norm[22:28]) / norm[28:34]
+    return s_in, s_out
+
+
+@pytest.mark.parametrize("width,layers,batch", [(128, 2, 256), (512, 4, 1024)])
+def test_gradients_match_oracle(ctx, orc, species, cuda, width, layers, batch):
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=width, hidden_layers=layers, max_batch=batch, infer_chunk=1024, seed=7)
+    x, y = make_pool(orc, species, batch + 64, seed=5)
+    x, y = x[:, :batch], y[:, :batch]
+    xd, yd = to_dev(x, cuda), to_dev(y, cuda)
+    sg.fit_normalization(xd, yd)
+    loss, grad = sg.loss_grad(xd, yd, batch)
+    sg.sync_status()
+    g_gpu = grad.cpu().numpy().astype(np.float64)
+    norm = sg.get_normalization().astype(np.float64)
+    sizes = [11] + [width] * layers + [6]
+    params = unflatten(sg.get_params(), sizes)
+    s_in, s_out = standardise(x, y, norm)
+    yhat, cache = omlp.forward(params, s_in)
+    l_orc = omlp.loss(yhat, s_out)
+    grads = omlp.backward(params, cache, yhat, s_out)
+    assert float(loss.item()) == pytest.approx(l_orc, rel=2e-2)
+    g_orc = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+    off = 0
+    for li, (gW, gb) in enumerate(grads):
+        for name, go in (("W", gW.ravel()), ("b", gb)):
+            gg = g_gpu[off:off + go.size]
+            off += go.size
+            rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
+            cos = float(gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go)))
+            assert rel < 3e-2 and cos > 0.999, (li, name, rel, cos)
+    assert off == g_orc.size
+    sg.close()
+
+
+def test_adam_step_matches_oracle(ctx, orc, species, cuda):
+    """One Adam step from zero moments equals the oracle's update with the
+    GPU's own gradients (isolates the optimiser kernel)."""
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=256, seed=9)
+    x, y = make_pool(orc, species, 400, seed=6)
+    x, y = x[:, :256], y[:, :256]
+    xd, yd = to_dev(x, cuda), to_dev(y, cuda)
+    sg.fit_normalization(xd, yd)
+    p0 = sg.get_params().astype(np.float64)
+    _, grad = sg.loss_grad(xd, yd, 256)
+    g = grad.cpu().numpy().astype(np.float64)
+    sg.train_step(xd, yd, batch=256, lr=1e-3)
+    sg.sync_status()
+    p1 = sg.get_params().astype(np.float64)
+    new = omlp.adam_step([(p0, np.zeros(1))], [(g, np.zeros(1))], {}, lr=1e-3)
+    np.testing.assert_allclose(p1, new[0][0], rtol=1e-5, atol=1e-9)
+
+
+def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
+    """surrogate_infer (tensor cores, chunked, ragged tail) against the float64
+    forward with the same weights, inside the training hull."""
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=1024, seed=11)
+    x, y = make_pool(orc, species, 6000, seed=12)
+    xd, yd = to_dev(x, cuda), to_dev(y, cuda)
+    sg.fit_normalization(xd, yd)
+    n = 2500                    # 3 chunks of 1024, the last one ragged
+    T, p, Y = to_dev(x[0, :n], cuda), to_dev(x[1, :n], cuda), to_dev(x[2:, :n], cuda)
+    out, fb = sg.infer(T, p, Y)
+    sg.sync_status()
+    out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy()
+    assert fb.sum() == 0
+    norm = sg.get_normalization().astype(np.float64)
+    params = unflatten(sg.get_params(), [11, 512, 512, 512, 512, 6])
+    s_in, _ = standardise(x[:, :n], y[:, :n], norm)
+    yhat, _ = omlp.forward(params, s_in)
+    s_gpu = (omlp.output_targets(out) - norm[22:28]) / norm[28:34]
+    err = np.abs(s_gpu - yhat)
+    print("standardised output error: median", np.median(err), "max", err.max())
+    assert np.median(err) < 0.01
+    assert err.max() < 0.1
+    sg.close()
+
+
+def test_fallback_outside_hull_is_pr_fp64(ctx, orc, species, cuda):
+    """Cells outside the training hull take the FP64 Peng-Robinson path: their
+    outputs equal the oracle's (rounded to FP32) and they are flagged."""
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=512, seed=13)
+    x, y = make_pool(orc, species, 4000, seed=14)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    Tin, pin, Yin = W.uniform_cells(700, seed=15)
+    Tin = 300.0 + (Tin - 100.0) * (2800.0 / 3400.0)          # inside the hull in T
+    out_T = np.r_[np.full(150, 4200.0), np.full(150, 60.0)]  # outside: too hot / too cold
+    Tall = np.r_[Tin, out_T]
+    pall = np.r_[pin, np.full(300, 1e7)]
+    Yall = np.hstack([Yin, Yin[:, :300]])
+    perm = np.random.default_rng(0).permutation(Tall.size)
+    Tall, pall, Yall = Tall[perm], pall[perm], Yall[:, perm]
+    x32 = np.vstack([Tall, pall, Yall]).astype(np.float32)
+    out, fb = sg.infer(to_dev(x32[0], cuda), to_dev(x32[1], cuda), to_dev(x32[2:], cuda))
+    sg.sync_status()
+    out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy()
+    outside = (Tall > 4000) | (Tall < 80)
+    assert np.array_equal(fb.astype(bool), outside)
+    o, st = orc.props(species, x32[0].astype(np.float64), x32[1].astype(np.float64), x32[2:].astype(np.float64))
+    m = outside & (st == 0)
+    assert m.sum() > 250
+    np.testing.assert_allclose(out[:, m], o[:, m], rtol=2e-7)
+    sg.close()
+
+
+def test_training_reduces_loss_and_checkpoint_roundtrip(ctx, orc, species, cuda, tmp_path):
+    import torch
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=256, hidden_layers=3, max_batch=4096, infer_chunk=4096, seed=17)
+    x, y = make_pool(orc, species, 40000, seed=18)
+    xd, yd = to_dev(x, cuda), to_dev(y, cuda)
+    sg.fit_normalization(xd, yd)
+    loss = torch.empty(1, dtype=torch.float32, device=cuda)
+    losses = []
+    for step in range(400):
+        sg.train_step(xd, yd, batch=4096, lr=1e-3, sample_seed=1000 + step, loss_out=loss)
+        if step % 50 == 0 or step == 399:
+            losses.append(float(loss.item()))
+    sg.sync_status()
+    print("losses", losses)
+    assert losses[-1] < 0.2 * losses[0]
+    path = tmp_path / "sg.ckpt"
+    sg.save(path)
+    sg2 = binding.Surrogate(ctx, width=256, hidden_layers=3, max_batch=4096, infer_chunk=4096, seed=99)
+    sg2.load(path)
+    T, p, Y = xd[0, :3000].contiguous(), xd[1, :3000].contiguous(), xd[2:, :3000]
+    a, _ = sg.infer(T, p, Y)
+    b, _ = sg2.infer(T, p, Y)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert np.array_equal(sg.get_params(), sg2.get_params())
+    sg.close()
+    sg2.close()
