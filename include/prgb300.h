@@ -162,7 +162,8 @@ pr_status surrogate_set_normalization(sg_model *m, const float *host_src);
 /* Fit the normalisation and the training hull (per-input [min, max] widened
  * by 1 % of the range) to a pool of n states.  x: DEVICE [11][ldx] raw inputs
  * (T, p, Y_1..Y_9); y: DEVICE [6][ldy] raw properties (rho, Z, h, cp, mu,
- * lambda).  Asynchronous on `stream`. */
+ * lambda).  Rows whose features or log-targets are not finite (e.g. a
+ * non-positive property) are left out.  Asynchronous on `stream`. */
 pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, int64_t ldx, const float *y,
                                       int64_t ldy, void *stream);
 
@@ -172,6 +173,7 @@ pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, in
  * are drawn from the pool x [11][ldx], y [6][ldy] (DEVICE, n_pool rows):
  * rows 0..batch-1 in order when sample_seed == 0 and n_pool == batch, else
  * uniformly with replacement by a counter-based hash of (sample_seed, row).
+ * Outputs whose target is not finite contribute neither loss nor gradient.
  * loss_out: DEVICE float receiving the batch loss, or NULL. */
 pr_status surrogate_train_step(sg_model *m, int64_t batch, int64_t n_pool, const float *x, int64_t ldx,
                                const float *y, int64_t ldy, uint64_t sample_seed, float lr, float *loss_out,

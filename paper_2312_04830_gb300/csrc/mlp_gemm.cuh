@@ -26,7 +26,8 @@ constexpr int BK = 64;
 enum Epi : int {
     kEpiHidden = 0,    // h = GeLU(acc + b) -> out; (train) h^T -> outT, GeLU'(acc + b) -> gd
     kEpiOutPhys = 1,   // y = acc + b (n < 6) -> de-standardise -> physical properties out6[6][ld6]
-    kEpiOutLoss = 2,   // y = acc + b; d = y - target; loss += d^2; dz = scale d -> out, outT, colsum
+    kEpiOutLoss = 2,   // y = acc + b; d = y - target (0 where the target is not finite); loss += d^2;
+                       // dz = scale d -> out, outT, colsum
     kEpiDx = 3,        // dz = acc * gd -> out, outT, colsum
     kEpiDw = 4,        // partial[split][m][n] = acc (FP32)
 };
@@ -262,7 +263,10 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CU
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     float d = 0.f;
-                    if (mval && c == 0 && j < 6) d = v[j] + __ldg(a.bias + j) - __ldg(a.target + (int64_t)j * a.ldt + m);
+                    if (mval && c == 0 && j < 6) {
+                        const float t = __ldg(a.target + (int64_t)j * a.ldt + m);
+                        d = isfinite(t) ? v[j] + __ldg(a.bias + j) - t : 0.f;   // non-finite targets are masked
+                    }
                     lsum += d * d;
                     v[j] = a.loss_scale * d;
                 }
@@ -309,6 +313,7 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CU
                 a.loss_part[blockIdx.x] = red[4 * BN] + red[4 * BN + 1] + red[4 * BN + 2] + red[4 * BN + 3];
         }
     }
+    __syncwarp();   // reconverge each warp (role lanes vs idle lanes) before the CTA barrier
     if (fail) atomicExch(a.err, 1);
     umma::tc_fence_before();
     __syncthreads();

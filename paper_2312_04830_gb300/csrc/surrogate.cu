@@ -108,12 +108,18 @@ __global__ void refresh_bf16_kernel(SgDev d)
 __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, const float *y, int64_t ldy, double *part)
 {
     double s[NSTAT], s2[NSTAT], mn[NSTAT], mx[NSTAT];
+    double cnt = 0;
 #pragma unroll
     for (int k = 0; k < NSTAT; ++k) { s[k] = 0; s2[k] = 0; mn[k] = 1e300; mx[k] = -1e300; }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float f[NIN], q[NOUT];
         features(x, ldx, i, f);
         targets(y, ldy, i, q);
+        bool fin = true;
+#pragma unroll
+        for (int k = 0; k < NSTAT; ++k) fin = fin && isfinite((k < NIN) ? f[k] : q[k - NIN]);
+        if (!fin) continue;   // rows with a non-finite feature or target are left out
+        cnt += 1;
 #pragma unroll
         for (int k = 0; k < NSTAT; ++k) {
             const double v = (k < NIN) ? f[k] : q[k - NIN];
@@ -121,7 +127,10 @@ __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, cons
         }
     }
     __shared__ double sh[4][NSTAT][8];
+    __shared__ double shc[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) shc[warp] = cnt;
 #pragma unroll
     for (int k = 0; k < NSTAT; ++k) {
         double a = s[k], b = s2[k], c = mn[k], e = mx[k];
@@ -140,25 +149,32 @@ __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, cons
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             a += sh[0][k][w]; b += sh[1][k][w]; c = fmin(c, sh[2][k][w]); e = fmax(e, sh[3][k][w]);
         }
-        double *p = part + ((int64_t)blockIdx.x * NSTAT + k) * 4;
+        double *p = part + ((int64_t)blockIdx.x * (NSTAT + 1) + k) * 4;
         p[0] = a; p[1] = b; p[2] = c; p[3] = e;
+    }
+    if (threadIdx.x == 0) {
+        double c = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) c += shc[w];
+        part[((int64_t)blockIdx.x * (NSTAT + 1) + NSTAT) * 4] = c;
     }
 }
 
 // Mean, standard deviation and the training hull (min/max widened by 1 % of
 // the range) from the block partials.  norm layout: in_mean[11] in_std[11]
 // out_mean[6] out_std[6] hull_lo[11] hull_hi[11].
-__global__ void norm_final_kernel(int nblocks, int64_t n, const double *part, float *norm)
+__global__ void norm_final_kernel(int nblocks, const double *part, float *norm)
 {
     const int k = threadIdx.x;
     if (k >= NSTAT) return;
-    double a = 0, b = 0, c = 1e300, e = -1e300;
+    double a = 0, b = 0, c = 1e300, e = -1e300, n = 0;
     for (int blk = 0; blk < nblocks; ++blk) {
-        const double *p = part + ((int64_t)blk * NSTAT + k) * 4;
+        const double *p = part + ((int64_t)blk * (NSTAT + 1) + k) * 4;
         a += p[0]; b += p[1]; c = fmin(c, p[2]); e = fmax(e, p[3]);
+        n += part[((int64_t)blk * (NSTAT + 1) + NSTAT) * 4];
     }
-    const double mean = a / (double)n;
-    double var = b / (double)n - mean * mean;
+    if (!(n > 0)) return;   // no valid row: keep the previous normalisation
+    const double mean = a / n;
+    double var = b / n - mean * mean;
     double sd = var > 0 ? sqrt(var) : 0.0;
     if (!(sd > 1e-12 * fmax(1.0, fabs(mean)))) sd = 1.0;
     if (k < NIN) {
@@ -542,7 +558,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     alloc((void **)&d.loss_part, (B / 128) * 4);
     alloc((void **)&m->d_loss, 4);
     alloc((void **)&m->d_err, 4);
-    alloc((void **)&m->d_normpart, (size_t)m->norm_blocks * NSTAT * 4 * 8);
+    alloc((void **)&m->d_normpart, (size_t)m->norm_blocks * (NSTAT + 1) * 4 * 8);
     alloc((void **)&d.xi, C * KIN * 2);
     alloc((void **)&d.hi[0], C * W * 2);
     alloc((void **)&d.hi[1], C * W * 2);
@@ -639,7 +655,7 @@ pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, in
     PR_CHECK_ARG(m && x && y && n > 0 && ldx >= n && ldy >= n, "surrogate_fit_normalization: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->d_normpart);
-    norm_final_kernel<<<1, 32, 0, st>>>(m->norm_blocks, n, m->d_normpart, m->dev.norm);
+    norm_final_kernel<<<1, 32, 0, st>>>(m->norm_blocks, m->d_normpart, m->dev.norm);
     PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
 }
