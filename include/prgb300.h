@@ -208,6 +208,32 @@ pr_status surrogate_load(sg_model *m, const char *path);
 pr_status mlp_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
                         float *D, int64_t ldd, int *err_flag, void *stream);
 
+/* ----------------------------------------------------------------------
+ * Allocation-free fallback evaluation.  The paper has no counterpart: this
+ * entry point exists for host programs that cannot call cudaMalloc (for
+ * example a solver that owns all device memory through its own pool, or one
+ * held to a device-memory budget fixed in advance).
+ *
+ * For every cell i < n with mask[i] != 0, evaluates the FP64 Peng-Robinson
+ * properties from FP32 inputs (the same step surrogate_infer applies to cells
+ * outside the training hull) and writes rho, Z, h, cp, mu, lambda as FP32 to
+ * out[q * ldo + i], q = 0..5; cells with mask[i] == 0 are left untouched.
+ * T, p [n], Y [N][ldY], mask [n] (uint8) and out [6][ldo] are DEVICE pointers
+ * owned by the caller.
+ *
+ * It allocates nothing: the compacted cell list lives in a fixed scratch array
+ * compiled into the library (PR_NOALLOC_MAX_CELLS indices plus a counter,
+ * about 4 MB), which every GPU that loads the library holds until the process
+ * exits.  n > PR_NOALLOC_MAX_CELLS is rejected with PR_EINVAL.  The first call
+ * on each device looks up the scratch array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one scratch array and clears its counter first; calls whose
+ * work overlaps on the GPU (e.g. on two streams at once) race on it.
+ * Asynchronous on `stream`. */
+#define PR_NOALLOC_MAX_CELLS (1 << 20)
+pr_status pr_fallback_props_noalloc(pr_ctx *ctx, int64_t n, const float *T, const float *p, const float *Y,
+                                    int64_t ldY, const uint8_t *mask, float *out, int64_t ldo, void *stream);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *pr_last_error(void);
 
