@@ -6,8 +6,9 @@ One step = one pass of every path over the whole field, inputs resident in HBM:
   newton_fp64  pr_T_from_h, FP64           (T from h* = h(T_true), start at T)
   props_fp32   pr_props,    FP32
   newton_fp32  pr_T_from_h, FP32
-(+ surrogate paths when the library provides them).  `value` counts one
-cell-evaluation per cell per path.
+  surrogate_bf16  surrogate_infer: BF16 tensor-core MLP, FP64 PR fallback
+                  outside the training hull (trained first, untimed)
+`value` counts one cell-evaluation per cell per path.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,7 +35,14 @@ METRIC = "cell-evals/s: PR FP64/FP32 vs BF16 MLP at <=1% rel err; %HBM roofline;
 UNIT = "cell-evals/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor), nominal
+# FP64 (non-tensor) peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 flops per cell of the FP64 kernels, from ncu instruction counts
+# (2 x DFMA + DADD + DMUL per launch / cells) on the 128^3 flame-vortex field
+FP64_FLOPS_PER_CELL = {"props_fp64": 1814.0}
+# surrogate: 2 x (11*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
+def mlp_flops_per_cell(width=512, layers=4, n_in=11, n_out=6):
+    return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
 
 # Algorithmic bytes per cell of each path (N = 9 species): inputs + outputs
 # that the path must move, FP64: T, p, Y[9] in, 6 outputs + int32 status out.
@@ -44,6 +52,7 @@ BYTES_PER_CELL = {
     "newton_fp64": (3 + N_SPECIES) * 8 + 8 + 4 + 4,
     "props_fp32": (2 + N_SPECIES) * 4 + 6 * 4 + 4,
     "newton_fp32": (3 + N_SPECIES) * 4 + 4 + 4 + 4,
+    "surrogate_bf16": (2 + N_SPECIES) * 4 + 6 * 4 + 1,
 }
 
 
@@ -56,6 +65,9 @@ def parse():
     ap.add_argument("--grid", type=int, default=256, help="field edge (cells = grid^3)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sg-pool", type=int, default=1 << 23, help="training states for the surrogate")
+    ap.add_argument("--sg-steps", type=int, default=2000, help="Adam steps of batch 65536")
     return ap.parse_args()
 
 
@@ -136,7 +148,7 @@ def make_field(grid: int):
     return T, p, Y, Ttrue
 
 
-def cpu_baseline(T, p, Y, Ttrue, species, budget_cells_props=1 << 20, budget_cells_newton=1 << 18):
+def cpu_baseline(T, p, Y, Ttrue, species, budget_cells_props=1 << 24, budget_cells_newton=1 << 22):
     """The FP64 oracle, as it stands, on the host cores over a bounded sample
     of the same field: props on the first cells, the inversion on the first
     cells of the perturbed-h workload (h* from the oracle itself)."""
@@ -203,6 +215,33 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- our arm
+def train_surrogate(ctx, dev, args):
+    """Train the surrogate on PR-labelled states (untimed set-up of the
+    inference path; its own throughput and held-out error are reported)."""
+    import torch
+    from paper_2312_04830_gb300 import binding, train as TR
+    t0 = time.perf_counter()
+    x, y = TR.make_pool(ctx, args.sg_pool, 20231207, dev)
+    xh, yh = TR.make_pool(ctx, 1 << 20, 20231208, dev)
+    t_data = time.perf_counter() - t0
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=1 << 20)
+    sg.fit_normalization(x, y)
+    TR.train(sg, x, y, 20, 65536, 1e-3, log_every=0)          # warm-up steps
+    sg.close()
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=1 << 20)
+    sg.fit_normalization(x, y)
+    losses, secs = TR.train(sg, x, y, args.sg_steps, 65536, 1e-3, log_every=max(1, args.sg_steps // 10))
+    sg.sync_status()
+    flops = 3 * mlp_flops_per_cell() * 65536 * args.sg_steps
+    report = {"pool": int(x.shape[1]), "steps": args.sg_steps, "batch": 65536, "seconds": secs,
+              "samples_per_s": 65536 * args.sg_steps / secs, "tflops": flops / secs / 1e12,
+              "epochs": 65536 * args.sg_steps / x.shape[1], "data_seconds": t_data,
+              "loss_first_last": [losses[0][1], losses[-1][1]],
+              "heldout_error_vs_pr_fp64": TR.evaluate(sg, xh, yh)}
+    del x, y, xh, yh
+    return sg, report
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -216,6 +255,7 @@ def run_ours(args):
 
     species = W.species_table()
     ctx = binding.PropertyContext(species)
+    sg, sg_report = (None, None) if args.no_surrogate else train_surrogate(ctx, dev, args)
     T, p, Y, Ttrue = make_field(args.grid)
     n = T.size
 
@@ -228,8 +268,11 @@ def run_ours(args):
     hs64 = hs64[2].clone()
     hs32, _ = ctx.props(Tt32, p32, Y32, precision="fp32", outputs=("h",))
     hs32 = hs32[2].clone()
+    del Tt64, Tt32
     out64 = torch.empty((6, n), dtype=torch.float64, device=dev)
     out32 = torch.empty((6, n), dtype=torch.float32, device=dev)
+    outsg = torch.empty((6, n), dtype=torch.float32, device=dev)
+    fb = torch.empty(n, dtype=torch.uint8, device=dev)
     st = torch.empty(n, dtype=torch.int32, device=dev)
     Tn64, Tn32 = torch.empty_like(T64), torch.empty_like(T32)
     it = torch.empty(n, dtype=torch.int32, device=dev)
@@ -242,10 +285,16 @@ def run_ours(args):
         "props_fp32": lambda: ctx.props(T32, p32, Y32, "fp32", out=out32, status=st),
         "newton_fp32": lambda: ctx.T_from_h(hs32, p32, Y32, T32, "fp32", T_out=Tn32, status=st, iters=it),
     }
-    launches_per_step = len(paths)
+    launches = {nm: 1 for nm in paths}
+    if sg is not None:
+        paths.append("surrogate_bf16")
+        calls["surrogate_bf16"] = lambda: sg.infer(T32, p32, Y32, out=outsg, used_fallback=fb)
+        n_chunks = (n + (1 << 20) - 1) >> 20
+        launches["surrogate_bf16"] = n_chunks * (1 + 5 + 1)     # prep, 5 GEMMs, fallback per chunk
+    launches_per_step = sum(launches.values())
 
     def step(ev=None):
-        for k, name in enumerate(paths):
+        for name in paths:
             if ev is not None:
                 ev[name][0].record(stream)
             calls[name]()
@@ -282,11 +331,12 @@ def run_ours(args):
     per_path_ms = {nm: statistics.mean(e[nm][0].elapsed_time(e[nm][1]) for e in evs) for nm in paths}
     evals = n * len(paths) * args.steps * ws
     value = evals / (elapsed_ms * 1e-3)
+    fb_frac = float(fb.float().mean()) if sg is not None else None
 
     # ----------------------------------------------------------- e2e
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(ctx, T, p, Y, Ttrue, hs64, hs32, dev, stream, max(2, min(args.steps, 4)), ws)
+        e2e = run_e2e(ctx, sg, T, p, Y, hs64, hs32, dev, stream, max(2, min(args.steps, 4)), ws)
 
     if rank != 0:
         if ws > 1:
@@ -294,20 +344,37 @@ def run_ours(args):
         return 0
 
     pk, pk_kind = peaks()
-    dom = max(per_path_ms, key=per_path_ms.get)
+    bf16_peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
     roof_paths = {}
     for nm in paths:
-        gbs = BYTES_PER_CELL[nm] * n / (per_path_ms[nm] * 1e-3) / 1e9
-        roof_paths[nm] = {"ms": per_path_ms[nm], "cell_evals_per_s": n / (per_path_ms[nm] * 1e-3),
-                          "algorithmic_GBps": gbs, "hbm_frac": gbs / pk["hbm_gbs"],
-                          "bytes_per_cell": BYTES_PER_CELL[nm]}
-    dom_gbs = roof_paths[dom]["algorithmic_GBps"]
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": dom_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": dom_gbs / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind}
+        sec = per_path_ms[nm] * 1e-3
+        gbs = BYTES_PER_CELL[nm] * n / sec / 1e9
+        r = {"ms": per_path_ms[nm], "cell_evals_per_s": n / sec, "algorithmic_GBps": gbs,
+             "hbm_frac": gbs / pk["hbm_gbs"], "bytes_per_cell": BYTES_PER_CELL[nm]}
+        if nm in FP64_FLOPS_PER_CELL:
+            tf = FP64_FLOPS_PER_CELL[nm] * n / sec / 1e12
+            r.update({"fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS})
+        if nm == "surrogate_bf16":
+            tf = mlp_flops_per_cell() * n * (1.0 - fb_frac) / sec / 1e12
+            r.update({"tensor_tflops": tf, "tensor_frac": tf / bf16_peak, "fallback_fraction": fb_frac})
+        roof_paths[nm] = r
+    dom = max(per_path_ms, key=per_path_ms.get)
+    d = roof_paths[dom]
+    if "fp64_tflops" in d:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": d["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": d["fp64_frac"], "traffic": None,
+                    "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (unit counts and clock)"}
+    elif "tensor_tflops" in d:
+        roofline = {"bound": "tensor", "kernel": dom, "achieved": d["tensor_tflops"], "peak": bf16_peak,
+                    "unit": "TFLOP/s", "frac": d["tensor_frac"], "traffic": None,
+                    "peak_source": f"{pk_kind} bf16 sustained"}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": d["algorithmic_GBps"], "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "frac": d["hbm_frac"], "traffic": None, "peak_source": pk_kind}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32+bf16", "data": "synthetic",
         "config": {"workload": f"flame-vortex field {args.grid}^3 = {n} cells, N=9 species, p = 10 MPa, "
                                "Burke-Schumann LOX/CH4 flame sheet on a Taylor-Green-distorted slab",
                    "cells": n, "paths": paths, "parallelism": f"replicas x{ws}",
@@ -317,6 +384,8 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    if sg_report is not None:
+        line["surrogate_training"] = sg_report
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
@@ -328,7 +397,7 @@ def run_ours(args):
     return 0
 
 
-def run_e2e(ctx, T, p, Y, Ttrue, hs64, hs32, dev, stream, steps, ws):
+def run_e2e(ctx, sg, T, p, Y, hs64, hs32, dev, stream, steps, ws):
     """Same metric through the C ABI with HOST buffers: per step, pinned-host
     inputs are copied to the device, every path runs, and every output is
     copied back to pinned host memory."""
@@ -343,15 +412,18 @@ def run_e2e(ctx, T, p, Y, Ttrue, hs64, hs32, dev, stream, steps, ws):
     d_in32 = [torch.empty_like(x, device=dev) for x in h_in32]
     o64 = torch.empty((6, n), dtype=torch.float64, device=dev)
     o32 = torch.empty((6, n), dtype=torch.float32, device=dev)
+    osg = torch.empty((6, n), dtype=torch.float32, device=dev)
+    fbd = torch.empty(n, dtype=torch.uint8, device=dev)
     t64, t32 = torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.float32, device=dev)
     sts = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
     it = torch.empty(n, dtype=torch.int32, device=dev)
-    h_out = [torch.empty((6, n), dtype=torch.float64).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory(),
-             torch.empty((6, n), dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory()]
-    h_st = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(4)]
-    d_out = [o64, t64, o32, t32]
+    d_out = [o64, t64, o32, t32] + sts
+    if sg is not None:
+        d_out += [osg, fbd]
+    h_out = [torch.empty_like(x, device="cpu").pin_memory() for x in d_out]
     h2d = sum(x.numel() * x.element_size() for x in h_in64 + h_in32)
-    d2h = sum(x.numel() * x.element_size() for x in h_out + h_st)
+    d2h = sum(x.numel() * x.element_size() for x in h_out)
+    n_paths = 4 + (1 if sg is not None else 0)
 
     def one():
         for h, d in zip(h_in64 + h_in32, d_in64 + d_in32):
@@ -360,7 +432,9 @@ def run_e2e(ctx, T, p, Y, Ttrue, hs64, hs32, dev, stream, steps, ws):
         ctx.T_from_h(d_in64[3], d_in64[1], d_in64[2], d_in64[4], "fp64", T_out=t64, status=sts[1], iters=it)
         ctx.props(d_in32[0], d_in32[1], d_in32[2], "fp32", out=o32, status=sts[2])
         ctx.T_from_h(d_in32[3], d_in32[1], d_in32[2], d_in32[4], "fp32", T_out=t32, status=sts[3], iters=it)
-        for d, h in zip(d_out + sts, h_out + h_st):
+        if sg is not None:
+            sg.infer(d_in32[0], d_in32[1], d_in32[2], out=osg, used_fallback=fbd)
+        for d, h in zip(d_out, h_out):
             h.copy_(d, non_blocking=True)
 
     one()
@@ -378,7 +452,7 @@ def run_e2e(ctx, T, p, Y, Ttrue, hs64, hs32, dev, stream, steps, ws):
         tt = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms = float(tt.item())
-    return {"value": n * 4 * steps * ws / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    return {"value": n * n_paths * steps * ws / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps}
 
 

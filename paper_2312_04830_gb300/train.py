@@ -1,0 +1,128 @@
+"""Train the surrogate on PR-labelled states and measure its error against the PR path.
+
+Workload (the training configuration): a pool of states, half independent
+uniform cells and half noisy flame-sheet states, labelled by the FP64
+Peng-Robinson path (`pr_props`); states with non-physical outcomes dropped
+(the paper's data constraints, Sec. 4.2); batches of 65536 drawn from the pool;
+Adam with a cosine-decayed learning rate; error measured on held-out states
+against the FP64 PR path, the surrogate's judge.
+
+    python -m paper_2312_04830_gb300.train --pool 67108864 --epochs 20 --save sg.ckpt
+
+prints one JSON report.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import binding, workloads as W
+
+OUT_NAMES = ("rho", "Z", "h", "cp", "mu", "lambda")
+
+
+def label_pool(ctx, T, p, Y, device, chunk=1 << 23):
+    """(x [11][n], y [6][n]) float32 device tensors of the physical states,
+    labelled by the FP64 PR path, host arrays passed in pieces of `chunk`."""
+    import torch
+    xs, ys = [], []
+    for a in range(0, T.size, chunk):
+        b = min(T.size, a + chunk)
+        d = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=device)
+        Td, pd, Yd = d(T[a:b]), d(p[a:b]), d(Y[:, a:b])
+        props, st = ctx.props(Td, pd, Yd, precision="fp64")
+        keep = (st == 0) & torch.all(torch.isfinite(props), dim=0) & torch.all(props[[0, 3, 4, 5]] > 0, dim=0)
+        xs.append(torch.cat([Td[None], pd[None], Yd], dim=0)[:, keep].float())
+        ys.append(props[:, keep].float())
+    return torch.cat(xs, dim=1).contiguous(), torch.cat(ys, dim=1).contiguous()
+
+
+def make_pool(ctx, n, seed, device):
+    T, p, Y = W.training_states(n, seed=seed)
+    return label_pool(ctx, T, p, Y, device)
+
+
+def relative_rms(pred, ref):
+    """Per-output relative RMS error (h relative to max(|h|, std of h))."""
+    import torch
+    sh = torch.std(ref[2])
+    out = {}
+    for j, nm in enumerate(OUT_NAMES):
+        s = torch.abs(ref[j])
+        if nm == "h":
+            s = torch.clamp(s, min=float(sh))
+        e = (pred[j] - ref[j]) / s
+        out[nm] = {"rel_rms": float(torch.sqrt(torch.mean(e * e))),
+                   "p99": float(torch.quantile(torch.abs(e[:1 << 24]).float(), 0.99)),
+                   "max": float(torch.max(torch.abs(e)))}
+    return out
+
+
+def evaluate(sg, x, y):
+    """Errors of the surrogate (with its PR fallback) on held-out states."""
+    import torch
+    T, p, Y = x[0].contiguous(), x[1].contiguous(), x[2:]
+    out, fb = sg.infer(T, p, Y)
+    torch.cuda.synchronize()
+    rep = {"all": relative_rms(out, y), "n": int(y.shape[1]), "fallback_fraction": float(fb.float().mean())}
+    keep = fb == 0
+    if int(keep.sum()) > 0:
+        rep["surrogate_only"] = relative_rms(out[:, keep], y[:, keep])
+    return rep
+
+
+def train(sg, x, y, steps, batch=65536, lr0=1e-3, lr_min=1e-5, seed=20231207, log_every=1000):
+    """Adam steps with a cosine-decayed learning rate; returns (losses, seconds)."""
+    import torch
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        lr = lr_min + 0.5 * (lr0 - lr_min) * (1.0 + math.cos(math.pi * s / max(1, steps)))
+        sg.train_step(x, y, batch=batch, lr=lr, sample_seed=(seed << 20) + s + 1, loss_out=loss)
+        if log_every and (s % log_every == 0 or s == steps - 1):
+            losses.append((s, float(loss.item())))
+    torch.cuda.synchronize()
+    return losses, time.perf_counter() - t0
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--pool", type=int, default=1 << 24)
+    ap.add_argument("--heldout", type=int, default=1 << 20)
+    ap.add_argument("--epochs", type=float, default=20.0)
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--width", type=int, default=512)
+    ap.add_argument("--layers", type=int, default=4)
+    ap.add_argument("--seed", type=int, default=20231207)
+    ap.add_argument("--save", default=None)
+    a = ap.parse_args()
+    dev = torch.device("cuda:0")
+    ctx = binding.PropertyContext(W.species_table())
+    t0 = time.perf_counter()
+    x, y = make_pool(ctx, a.pool, a.seed, dev)
+    xh, yh = make_pool(ctx, a.heldout, a.seed + 1, dev)
+    t_data = time.perf_counter() - t0
+    sg = binding.Surrogate(ctx, width=a.width, hidden_layers=a.layers, max_batch=a.batch)
+    sg.fit_normalization(x, y)
+    steps = int(round(a.epochs * x.shape[1] / a.batch))
+    losses, secs = train(sg, x, y, steps, a.batch, a.lr, seed=a.seed)
+    sg.sync_status()
+    flops = 3 * 2 * (11 * a.width + (a.layers - 1) * a.width ** 2 + a.width * 6) * a.batch * steps
+    rep = {"pool": int(x.shape[1]), "steps": steps, "batch": a.batch, "train_seconds": secs,
+           "samples_per_s": steps * a.batch / secs, "train_tflops": flops / secs / 1e12,
+           "data_seconds": t_data, "losses": losses, "heldout": evaluate(sg, xh, yh)}
+    if a.save:
+        sg.save(a.save)
+    print(json.dumps(rep))
+
+
+if __name__ == "__main__":
+    main()
