@@ -1,14 +1,16 @@
 // Tensor-core GEMM for the surrogate MLP: D[M x N] = A[M x K] * B[N x K]^T
 // with BF16 operands (both K-major, loaded by TMA with 128-byte swizzling),
-// an FP32 accumulator in tensor memory (tcgen05.mma, cta_group::1, M = 128)
+// FP32 accumulators in tensor memory (tcgen05.mma, cta_group::1, M = 128)
 // and fused epilogues for every GEMM of the MLP's forward and backward pass.
 //
-// CTA = 6 warps: warp 0 issues TMA loads into an S-stage shared-memory ring,
-// one thread of warp 1 issues the MMAs (K = 16 each, 4 per 64-wide k-block)
-// and commits each stage back to the producer, warps 2-5 drain the
-// accumulator (each warp owns the TMEM lane quarter warp % 4, i.e. 32 rows)
-// and run the epilogue.  One output tile (and one K split) per CTA; two CTAs
-// fit on an SM so that one CTA's epilogue overlaps the other's main loop.
+// Persistent kernel, one CTA per SM, 10 warps: warp 0 issues TMA loads into
+// an S-stage shared-memory ring, one thread of warp 1 issues the MMAs (K = 16
+// each, 4 per 64-wide k-block), warps 2-9 drain the accumulator and run the
+// epilogue (warp w owns TMEM lane quarter w % 4, i.e. 32 rows, and one half of
+// the tile's columns).  The accumulator is double-buffered in TMEM (2 x BN
+// columns), so the epilogue of one tile overlaps the main loop of the next.
+// Tiles are visited with the N index fastest, so the CTAs working on the
+// N-tiles of one M-tile run together and share the A tile through L2.
 #pragma once
 
 #include <cuda.h>
@@ -34,7 +36,8 @@ enum Epi : int {
 
 struct GemmArgs {
     int M, N, K;              // logical sizes; A is [M][K], B is [N][K]
-    int kb_per_split;         // 64-wide k-blocks per K split (gridDim.z splits)
+    int kb_per_split;         // 64-wide k-blocks per K split
+    int m_tiles, n_tiles, splits;   // tile grid (splits along K)
     const float *bias;        // [N]
     __nv_bfloat16 *out;       // [M][ldo] batch-major
     int64_t ldo;
@@ -44,25 +47,28 @@ struct GemmArgs {
     int64_t ldg;
     float *partial;           // kEpiDw: [split][Mpad][N]
     int Mpad;
-    float *colsum;            // [gridDim.x][N] per-CTA column sums of dz (bias gradients)
+    float *colsum;            // [m_tiles][N] per-M-tile column sums of dz (bias gradients)
     float *out6;              // kEpiOutPhys: [6][ld6]
     int64_t ld6;
     const float *out_mean, *out_std;   // [6] de-standardisation
     const float *target;      // kEpiOutLoss: standardised targets [6][ldt]
     int64_t ldt;
     float loss_scale;         // d loss / d y = loss_scale * (y - target)
-    float *loss_part;         // [gridDim.x] per-CTA sum of squared errors
+    float *loss_part;         // [m_tiles] per-M-tile sum of squared errors
     int *err;                 // set to 1 when a bounded wait runs out
 };
+
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 template <int BN>
 struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int S = (BN >= 256) ? 2 : ((98304 / STAGE) < 6 ? (98304 / STAGE) : 6);
-    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
-    static constexpr int BAR_BYTES = 8 * (2 * S + 1) + 16;
+    static constexpr int S = (196608 / STAGE) < 8 ? (196608 / STAGE) : 8;
+    static constexpr uint32_t TMEM_COLS = (2 * BN) < 32 ? 32 : 2 * BN;   // two accumulator buffers
+    static constexpr int BAR_BYTES = 8 * (2 * S + 4) + 16;
     static constexpr int RED_BYTES = 4 * BN * 4 + 64;
     static constexpr int SMEM = 1024 + S * STAGE + BAR_BYTES + RED_BYTES;
 };
@@ -142,34 +148,38 @@ __device__ __forceinline__ float warp_colsum16(float (&v)[16], int lane)
 
 __device__ __forceinline__ void named_barrier_epi()
 {
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
 }
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                      const __grid_constant__ CUtensorMap tmB, const GemmArgs a)
+__global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB, const GemmArgs a)
 {
     using C = Cfg<BN>;
+    constexpr int HALF = (BN >= 32) ? BN / 2 : BN;   // columns per epilogue warp
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::S * C::STAGE);
     uint64_t *empty = full + C::S;
-    uint64_t *accf = empty + C::S;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
+    uint64_t *acc_full = empty + C::S;     // [2]
+    uint64_t *acc_empty = acc_full + 2;    // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     float *red = reinterpret_cast<float *>(smem + C::S * C::STAGE + C::BAR_BYTES);   // [4][BN] + 16
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int kb_total = (a.K + BK - 1) / BK;
-    const int kb0 = blockIdx.z * a.kb_per_split;
-    const int nkb = min(a.kb_per_split, kb_total - kb0);
+    const int tiles_mn = a.m_tiles * a.n_tiles;
+    const int total = tiles_mn * a.splits;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::S; ++s) {
             umma::mbar_init(&full[s], 1);
             umma::mbar_init(&empty[s], 1);
         }
-        umma::mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            umma::mbar_init(&acc_full[b], 1);
+            umma::mbar_init(&acc_empty[b], kEpiWarps);
+        }
         umma::fence_mbar_init();
         umma::tma_prefetch_desc(&tmA);
         umma::tma_prefetch_desc(&tmB);
@@ -185,132 +195,181 @@ __global__ void __launch_bounds__(192, 1) gemm_kernel(const __grid_constant__ CU
     bool fail = false;
 
     if (warp == 0) {
+        // ------------------------------------------------------- TMA producer
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % C::S;
-                const uint32_t ph = (uint32_t)(kb / C::S) & 1u;
-                if (kb >= C::S && !umma::mbar_wait(&empty[s], ph ^ 1u)) { fail = true; break; }
-                uint8_t *st = smem + s * C::STAGE;
-                umma::mbar_arrive_expect_tx(&full[s], C::STAGE);
-                umma::tma_load_2d(st, &tmA, &full[s], (kb0 + kb) * BK, m0);
-                umma::tma_load_2d(st + C::A_BYTES, &tmB, &full[s], (kb0 + kb) * BK, n0);
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < total && !fail; t += gridDim.x) {
+                const int split = t / tiles_mn, r = t % tiles_mn;
+                const int m0 = (r / a.n_tiles) * BM, n0 = (r % a.n_tiles) * BN;
+                const int kb0 = split * a.kb_per_split;
+                const int nkb = min(a.kb_per_split, kb_total - kb0);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % C::S;
+                    const uint32_t ph = (it / C::S) & 1u;
+                    if (it >= (uint32_t)C::S && !umma::mbar_wait(&empty[s], ph ^ 1u)) { fail = true; break; }
+                    uint8_t *st = smem + s * C::STAGE;
+                    umma::mbar_arrive_expect_tx(&full[s], C::STAGE);
+                    umma::tma_load_2d(st, &tmA, &full[s], (kb0 + kb) * BK, m0);
+                    umma::tma_load_2d(st + C::A_BYTES, &tmB, &full[s], (kb0 + kb) * BK, n0);
+                }
             }
+            // no copy may still be landing in shared memory when the CTA exits
+            for (uint32_t k = (it > (uint32_t)C::S ? it - C::S : 0u); k < it; ++k)
+                if (!umma::mbar_wait(&full[k % C::S], (k / C::S) & 1u, 200000000LL)) fail = true;
         }
     } else if (warp == 1) {
+        // -------------------------------------------------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN);
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % C::S;
-                const uint32_t ph = (uint32_t)(kb / C::S) & 1u;
-                if (!umma::mbar_wait(&full[s], ph)) { fail = true; break; }
+            uint32_t it = 0, j = 0;
+            for (int t = blockIdx.x; t < total && !fail; t += gridDim.x, ++j) {
+                const int split = t / tiles_mn;
+                const int kb0 = split * a.kb_per_split;
+                const int nkb = min(a.kb_per_split, kb_total - kb0);
+                const uint32_t buf = j & 1u;
+                if (j >= 2 && !umma::mbar_wait(&acc_empty[buf], ((j >> 1) & 1u) ^ 1u)) { fail = true; break; }
                 umma::tc_fence_after();
-                const uint32_t sa = umma::smem_u32(smem + s * C::STAGE);
-                const uint32_t sb = sa + C::A_BYTES;
+                const uint32_t d_tmem = tmem + buf * BN;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % C::S;
+                    const uint32_t ph = (it / C::S) & 1u;
+                    if (!umma::mbar_wait(&full[s], ph)) { fail = true; break; }
+                    umma::tc_fence_after();
+                    const uint32_t sa = umma::smem_u32(smem + s * C::STAGE);
+                    const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k) {
-                    umma::mma_bf16(tmem, umma::sdesc_kmajor_sw128(sa + k * 32), umma::sdesc_kmajor_sw128(sb + k * 32),
-                                   idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < BK / 16; ++k) {
+                        umma::mma_bf16(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
+                                       umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    }
+                    umma::mma_commit(&empty[s]);
                 }
-                umma::mma_commit(&empty[s]);
+                umma::mma_commit(&acc_full[buf]);
             }
-            umma::mma_commit(accf);
         }
     } else {
-        // ------------------------------------------------------ epilogue
-        const int q = warp & 3;                     // TMEM lane quarter of this warp
+        // ---------------------------------------------------------- epilogue
+        const int ew = warp - 2;                   // 0..7
+        const int q = warp & 3;                    // TMEM lane quarter this warp may access
+        const int hcol = (BN >= 32) ? (ew >> 2) * HALF : 0;   // column half of this warp
+        const bool active = (BN >= 32) || (ew < 4);
         const int row = q * 32 + lane;
-        const int m = m0 + row;
-        const bool mval = m < a.M;
-        if (!umma::mbar_wait(accf, 0)) fail = true;
-        umma::tc_fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
-        float lsum = 0.f;
+        uint32_t j = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++j) {
+            const int split = t / tiles_mn, r = t % tiles_mn;
+            const int mt = r / a.n_tiles;
+            const int m0 = mt * BM, n0 = (r % a.n_tiles) * BN;
+            const int m = m0 + row;
+            const bool mval = m < a.M;
+            const uint32_t buf = j & 1u;
+            // after a timed-out wait this warp skips its work but keeps taking
+            // part in the named barriers, so the other epilogue warps finish
+            if (!fail && !umma::mbar_wait(&acc_full[buf], (j >> 1) & 1u)) fail = true;
+            umma::tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * BN + hcol;
+            float lsum = 0.f;
+            if (active && !fail) {
 #pragma unroll 1
-        for (int c = 0; c < BN / 16; ++c) {
-            uint32_t r[16];
-            umma::tmem_ld16(taddr + c * 16, r);
-            umma::tmem_ld_wait();
-            float v[16];
+                for (int c = 0; c < HALF / 16; ++c) {
+                    uint32_t rr[16];
+                    umma::tmem_ld16(taddr + c * 16, rr);
+                    const int nb = n0 + hcol + c * 16;
+                    float bias[16];
+                    if (EPI == kEpiHidden || EPI == kEpiOutPhys || EPI == kEpiOutLoss) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-            const int nb = n0 + c * 16;
-            if (EPI == kEpiHidden) {
-                float g[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float z = v[j] + __ldg(a.bias + nb + j);
-                    v[j] = gelu_f(z);
-                    g[j] = gelu_grad_f(z);
-                }
-                if (mval) {
-                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-                    if (a.gd) store_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, g);
-                    if (a.outT) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) a.outT[(int64_t)(nb + j) * a.ldoT + m] = __float2bfloat16_rn(v[j]);
+                        for (int jj = 0; jj < 16; ++jj) bias[jj] = __ldg(a.bias + nb + jj);
                     }
-                }
-            } else if (EPI == kEpiOutPhys) {
-                if (mval && c == 0) {
+                    float g[16];
+                    if (EPI == kEpiDx && mval) load_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, g);
+                    umma::tmem_ld_wait();
+                    float v[16];
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) {
-                        const float s = v[j] + __ldg(a.bias + j);
-                        const float qv = s * __ldg(a.out_std + j) + __ldg(a.out_mean + j);
-                        a.out6[(int64_t)j * a.ld6 + m] = (j == 1 || j == 2) ? qv : __expf(qv);
+                    for (int jj = 0; jj < 16; ++jj) v[jj] = __uint_as_float(rr[jj]);
+                    if (EPI == kEpiHidden) {
+                        float gg[16];
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) {
+                            const float z = v[jj] + bias[jj];
+                            v[jj] = gelu_f(z);
+                            if (a.gd) gg[jj] = gelu_grad_f(z);
+                        }
+                        if (mval) {
+                            store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+                            if (a.gd) store_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, gg);
+                            if (a.outT) {
+#pragma unroll
+                                for (int jj = 0; jj < 16; ++jj)
+                                    a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                            }
+                        }
+                    } else if (EPI == kEpiOutPhys) {
+                        if (mval && nb == 0) {
+#pragma unroll
+                            for (int jj = 0; jj < 6; ++jj) {
+                                const float sv = v[jj] + bias[jj];
+                                const float qv = sv * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
+                                a.out6[(int64_t)jj * a.ld6 + m] = (jj == 1 || jj == 2) ? qv : __expf(qv);
+                            }
+                        }
+                    } else if (EPI == kEpiOutLoss) {
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) {
+                            float d = 0.f;
+                            if (mval && nb == 0 && jj < 6) {
+                                const float tv = __ldg(a.target + (int64_t)jj * a.ldt + m);
+                                d = isfinite(tv) ? v[jj] + bias[jj] - tv : 0.f;   // non-finite targets are masked
+                            }
+                            lsum += d * d;
+                            v[jj] = a.loss_scale * d;
+                        }
+                        if (mval) {
+                            store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj)
+                                a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                        }
+                    } else if (EPI == kEpiDx) {
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) v[jj] = mval ? v[jj] * g[jj] : 0.f;
+                        if (mval) {
+                            store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj)
+                                a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                        }
+                    } else {  // kEpiDw
+                        if (m < a.Mpad) {
+                            float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)split * a.Mpad + m) * a.N + nb);
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj)
+                                dst[jj] = make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]);
+                        }
                     }
-                }
-            } else if (EPI == kEpiOutLoss) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float d = 0.f;
-                    if (mval && c == 0 && j < 6) {
-                        const float t = __ldg(a.target + (int64_t)j * a.ldt + m);
-                        d = isfinite(t) ? v[j] + __ldg(a.bias + j) - t : 0.f;   // non-finite targets are masked
+                    if (EPI == kEpiOutLoss || EPI == kEpiDx) {
+                        const float sv = warp_colsum16(v, lane);
+                        if ((lane & 1) == 0) red[q * BN + hcol + c * 16 + (lane >> 1)] = sv;
                     }
-                    lsum += d * d;
-                    v[j] = a.loss_scale * d;
-                }
-                if (mval) {
-                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) a.outT[(int64_t)(nb + j) * a.ldoT + m] = __float2bfloat16_rn(v[j]);
-                }
-            } else if (EPI == kEpiDx) {
-                float g[16];
-                if (mval) load_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, g);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = mval ? v[j] * g[j] : 0.f;
-                if (mval) {
-                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) a.outT[(int64_t)(nb + j) * a.ldoT + m] = __float2bfloat16_rn(v[j]);
-                }
-            } else {  // kEpiDw
-                if (m < a.Mpad) {
-                    float4 *dst = reinterpret_cast<float4 *>(
-                        a.partial + ((int64_t)blockIdx.z * a.Mpad + m) * a.N + nb);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
             }
+            // the accumulator buffer may be reused once every warp has read it
+            umma::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&acc_empty[buf]);
             if (EPI == kEpiOutLoss || EPI == kEpiDx) {
-                const float s = warp_colsum16(v, lane);
-                if ((lane & 1) == 0) red[q * BN + c * 16 + (lane >> 1)] = s;
-            }
-        }
-        if (EPI == kEpiOutLoss || EPI == kEpiDx) {
-            if (EPI == kEpiOutLoss) {
+                if (EPI == kEpiOutLoss) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-                if (lane == 0) red[4 * BN + q] = lsum;
+                    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+                    if (lane == 0 && active) red[4 * BN + q] = lsum;
+                }
+                named_barrier_epi();
+                const int tt = threadIdx.x - 64;
+                for (int col = tt; col < BN; col += 32 * kEpiWarps)
+                    a.colsum[(int64_t)mt * a.N + n0 + col] =
+                        red[col] + red[BN + col] + red[2 * BN + col] + red[3 * BN + col];
+                if (EPI == kEpiOutLoss && tt == 0)
+                    a.loss_part[mt] = red[4 * BN] + red[4 * BN + 1] + red[4 * BN + 2] + red[4 * BN + 3];
+                named_barrier_epi();   // red is reused by the next tile
             }
-            named_barrier_epi();
-            const int t = threadIdx.x - 64;
-            for (int col = t; col < BN; col += 128)
-                a.colsum[(int64_t)blockIdx.x * a.N + n0 + col] =
-                    red[col] + red[BN + col] + red[2 * BN + col] + red[3 * BN + col];
-            if (EPI == kEpiOutLoss && t == 0)
-                a.loss_part[blockIdx.x] = red[4 * BN] + red[4 * BN + 1] + red[4 * BN + 2] + red[4 * BN + 3];
         }
     }
     __syncwarp();   // reconverge each warp (role lanes vs idle lanes) before the CTA barrier

@@ -393,9 +393,20 @@ bool make_map(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, ui
     return r == CUDA_SUCCESS;
 }
 
+int num_sms_current()
+{
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    return sms[dev] > 0 ? sms[dev] : 148;
+}
+
+// Persistent launch: one CTA per SM (or fewer when there are fewer tiles).
 template <int BN, int EPI>
-cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &a, int gx, int gy, int gz,
-                        cudaStream_t st)
+cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a, int m_tiles, int n_tiles,
+                        int splits, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
@@ -404,8 +415,29 @@ cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, const Gemm
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    gemm_kernel<BN, EPI><<<dim3(gx, gy, gz), 192, Cfg<BN>::SMEM, st>>>(ta, tb, a);
+    a.m_tiles = m_tiles;
+    a.n_tiles = n_tiles;
+    a.splits = splits;
+    const int total = m_tiles * n_tiles * splits;
+    const int sms = num_sms_current();
+    gemm_kernel<BN, EPI><<<total < sms ? total : sms, kThreads, Cfg<BN>::SMEM, st>>>(ta, tb, a);
     return cudaGetLastError();
+}
+
+// Widest N tile (256, 128, 64 or 16) that divides N.
+inline int pick_bn(int N) { return (N % 256 == 0) ? 256 : (N % 128 == 0) ? 128 : (N % 64 == 0) ? 64 : 16; }
+
+// Dispatch on the N tile width.
+template <int EPI>
+cudaError_t launch_gemm_n(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &a, int m_tiles, int N,
+                          int splits, cudaStream_t st)
+{
+    switch (pick_bn(N)) {
+    case 256: return launch_gemm<256, EPI>(ta, tb, a, m_tiles, N / 256, splits, st);
+    case 128: return launch_gemm<128, EPI>(ta, tb, a, m_tiles, N / 128, splits, st);
+    case 64: return launch_gemm<64, EPI>(ta, tb, a, m_tiles, N / 64, splits, st);
+    default: return launch_gemm<16, EPI>(ta, tb, a, m_tiles, N / 16, splits, st);
+    }
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -428,18 +460,19 @@ static pr_status build_maps(sg_model *m)
     const int64_t B = m->max_batch, C = m->chunk;
     bool ok = true;
     // weights (forward B operands)
-    ok = ok && make_map(&m->tm_w[0], d.wb[0], KIN, W, KIN, 128);
-    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_w[l], d.wb[l], W, W, W, 128);
+    const uint32_t bw = (uint32_t)pick_bn(W);   // box rows of B operands with N = W
+    ok = ok && make_map(&m->tm_w[0], d.wb[0], KIN, W, KIN, bw);
+    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_w[l], d.wb[l], W, W, W, bw);
     ok = ok && make_map(&m->tm_w[L], d.wb[L], W, NOP, W, 16);
     // transposed weights (input-gradient B operands)
-    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_wt[l], d.wt[l], W, W, W, 128);
-    ok = ok && make_map(&m->tm_wt[L], d.wt[L], KIN, W, KIN, 128);
+    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_wt[l], d.wt[l], W, W, W, bw);
+    ok = ok && make_map(&m->tm_wt[L], d.wt[L], KIN, W, KIN, bw);
     // training activations
     ok = ok && make_map(&m->tm_x0, d.x0, KIN, B, KIN, 128);
     ok = ok && make_map(&m->tm_x0t, d.x0t, B, KIN, B, 64);
     for (int l = 0; l < L; ++l) {
         ok = ok && make_map(&m->tm_h[l], d.h[l], W, B, W, 128);
-        ok = ok && make_map(&m->tm_ht[l], d.ht[l], B, W, B, 128);
+        ok = ok && make_map(&m->tm_ht[l], d.ht[l], B, W, B, bw);
         ok = ok && make_map(&m->tm_dz[l], d.dz[l], W, B, W, 128);
         ok = ok && make_map(&m->tm_dzt[l], d.dzt[l], B, W, B, 128);
     }
@@ -542,7 +575,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     for (int l = 0; l <= L; ++l) {
         const int mp = (l == L) ? MOP : W;
         const int np = d.lay[l].in_pad;
-        const int bn = (np >= 128) ? 128 : 64;
+        const int bn = pick_bn(np);
         const int tiles = (mp / 128) * (np / bn);
         int splits = ctx->num_sms / tiles;
         splits = splits < 1 ? 1 : (splits > kb ? kb : splits);
@@ -674,7 +707,7 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         a.bias = d.master + d.lay[l].b_off;
         a.out = d.h[l]; a.ldo = W; a.outT = d.ht[l]; a.ldoT = d.max_batch; a.gd = d.g[l]; a.ldg = W;
         const CUtensorMap &ta = (l == 0) ? m->tm_x0 : m->tm_h[l - 1];
-        e = launch_gemm<128, kEpiHidden>(ta, m->tm_w[l], a, mt, W / 128, 1, st);
+        e = launch_gemm_n<kEpiHidden>(ta, m->tm_w[l], a, mt, W, 1, st);
         if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) { prgb::set_error("forward: %s", cudaGetErrorString(e)); return PR_ECUDA; }
@@ -697,7 +730,7 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         a.out = d.dz[l - 1]; a.ldo = W; a.outT = d.dzt[l - 1]; a.ldoT = d.max_batch;
         a.colsum = d.colsum[l - 1];
         const CUtensorMap &ta = (l == L) ? m->tm_dzo : m->tm_dz[l];
-        e = launch_gemm<128, kEpiDx>(ta, m->tm_wt[l], a, mt, W / 128, 1, st);
+        e = launch_gemm_n<kEpiDx>(ta, m->tm_wt[l], a, mt, W, 1, st);
         if (e != cudaSuccess) { prgb::set_error("dx: %s", cudaGetErrorString(e)); return PR_ECUDA; }
     }
     // weight gradients: dW_l = dz_l^T h_{l-1}, K = batch, split along K
@@ -709,8 +742,7 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         const int splits = ceil_div(ceil_div(B, 64), d.dw_kps[l]);
         const CUtensorMap &ta = (l == L) ? m->tm_dzot : m->tm_dzt[l];
         const CUtensorMap &tb = (l == 0) ? m->tm_x0t : m->tm_ht[l - 1];
-        if (np >= 128) e = launch_gemm<128, kEpiDw>(ta, tb, a, mp / 128, np / 128, splits, st);
-        else e = launch_gemm<64, kEpiDw>(ta, tb, a, mp / 128, np / 64, splits, st);
+        e = launch_gemm_n<kEpiDw>(ta, tb, a, mp / 128, np, splits, st);
         if (e != cudaSuccess) { prgb::set_error("dw: %s", cudaGetErrorString(e)); return PR_ECUDA; }
         m->last_splits[l] = splits;
     }
@@ -789,7 +821,7 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.bias = d.master + d.lay[l].b_off;
             a.out = d.hi[l & 1]; a.ldo = W;
             const CUtensorMap &ta = (l == 0) ? m->tm_xi : m->tm_hi[(l - 1) & 1];
-            PR_CUDA_TRY((launch_gemm<128, kEpiHidden>(ta, m->tm_w[l], a, mt, W / 128, 1, st)));
+            PR_CUDA_TRY((launch_gemm_n<kEpiHidden>(ta, m->tm_w[l], a, mt, W, 1, st)));
         }
         {
             GemmArgs a = base_args(m);
@@ -890,7 +922,7 @@ pr_status mlp_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
     PR_CHECK_ARG(lda >= K && ldb >= K && ldd >= N && lda % 8 == 0 && ldb % 8 == 0 && ldd % 4 == 0,
                  "mlp_gemm_bf16: leading dimensions (lda, ldb multiples of 8; ldd of 4)");
     PR_CHECK_ARG(prgb::aligned(A, 16) && prgb::aligned(B, 16) && prgb::aligned(D, 16), "mlp_gemm_bf16: 16-byte alignment");
-    const int bn = (N == 16) ? 16 : (N == 64 ? 64 : 128);
+    const int bn = pick_bn((int)N);
     CUtensorMap ta, tb;
     if (!make_map(&ta, A, K, M, lda, 128) || !make_map(&tb, B, K, N, ldb, bn)) {
         prgb::set_error("mlp_gemm_bf16: tensor map encoding failed");
@@ -904,9 +936,8 @@ pr_status mlp_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
     cudaStream_t st = (cudaStream_t)stream;
     const int gx = ceil_div(M, 128), gy = (int)(N / bn);
     cudaError_t e;
-    if (bn == 16) e = launch_gemm<16, kEpiDw>(ta, tb, a, gx, gy, 1, st);
-    else if (bn == 64) e = launch_gemm<64, kEpiDw>(ta, tb, a, gx, gy, 1, st);
-    else e = launch_gemm<128, kEpiDw>(ta, tb, a, gx, gy, 1, st);
+    e = launch_gemm_n<kEpiDw>(ta, tb, a, gx, (int)N, 1, st);
+    (void)gy;
     PR_CUDA_TRY(e);
     return PR_OK;
 }
