@@ -70,17 +70,59 @@ struct Cfg {
     static constexpr uint32_t TMEM_COLS = (2 * BN) < 32 ? 32 : 2 * BN;   // two accumulator buffers
     static constexpr int BAR_BYTES = 8 * (2 * S + 4) + 16;
     static constexpr int RED_BYTES = 4 * BN * 4 + 64;
-    static constexpr int SMEM = 1024 + S * STAGE + BAR_BYTES + RED_BYTES;
+    static constexpr int BIAS_BYTES = 1024 * 4;   // bias of up to 1024 output columns
+    static constexpr int SMEM = 1024 + S * STAGE + BAR_BYTES + RED_BYTES + BIAS_BYTES;
 };
+
+// GeLU(z) = z Phi(z) and GeLU'(z) = Phi(z) + z phi(z), with the normal tail
+// probability from Abramowitz & Stegun 7.1.26:
+//   erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),
+//   t = 1 / (1 + p x),  x >= 0,  |error| <= 1.5e-7,
+// taken at x = |z| / sqrt(2):  Q = (1 - erf(x)) / 2 = P(t) exp(-z^2/2) / 2,
+// Phi(z) = 1 - Q for z >= 0, Q otherwise.  The reciprocal and the exponential
+// are single MUFU operations (rcp.approx, ex2.approx); the error of Phi stays
+// below 3e-7, far under the BF16 rounding of the activations (4e-3).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Phi(z) and exp(-z^2/2)
+__device__ __forceinline__ void normal_cdf(float z, float &Phi, float &e)
+{
+    constexpr float p_s2 = 0.3275911f * 0.70710678118654752f;       // p / sqrt(2)
+    constexpr float h1 = 0.5f * 0.254829592f, h2 = 0.5f * -0.284496736f, h3 = 0.5f * 1.421413741f,
+                    h4 = 0.5f * -1.453152027f, h5 = 0.5f * 1.061405429f;
+    constexpr float mhl2e = -0.5f * 1.4426950408889634f;             // -log2(e)/2
+    const float t = rcp_approx(fmaf(p_s2, fabsf(z), 1.0f));
+    const float P = t * fmaf(fmaf(fmaf(fmaf(h5, t, h4), t, h3), t, h2), t, h1);
+    e = ex2_approx(z * z * mhl2e);
+    const float Q = P * e;
+    Phi = (z >= 0.f) ? 1.0f - Q : Q;
+}
 
 __device__ __forceinline__ float gelu_f(float z)
 {
-    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+    float Phi, e;
+    normal_cdf(z, Phi, e);
+    return z * Phi;
 }
 
-__device__ __forceinline__ float gelu_grad_f(float z)
+__device__ __forceinline__ void gelu_and_grad(float z, float &g, float &dg)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+    float Phi, e;
+    normal_cdf(z, Phi, e);
+    g = z * Phi;
+    dg = fmaf(z * 0.39894228040143268f, e, Phi);   // Phi + z phi(z)
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
@@ -165,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     uint64_t *acc_empty = acc_full + 2;    // [2]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     float *red = reinterpret_cast<float *>(smem + C::S * C::STAGE + C::BAR_BYTES);   // [4][BN] + 16
+    float *sbias = red + 4 * BN + 16;                                                // [N] (N <= 1024)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb_total = (a.K + BK - 1) / BK;
@@ -254,6 +297,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         const int hcol = (BN >= 32) ? (ew >> 2) * HALF : 0;   // column half of this warp
         const bool active = (BN >= 32) || (ew < 4);
         const int row = q * 32 + lane;
+        if (EPI == kEpiHidden || EPI == kEpiOutPhys || EPI == kEpiOutLoss) {
+            for (int col = threadIdx.x - 64; col < a.N; col += 32 * kEpiWarps) sbias[col] = __ldg(a.bias + col);
+            named_barrier_epi();
+        }
         uint32_t j = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++j) {
             const int split = t / tiles_mn, r = t % tiles_mn;
@@ -276,8 +323,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
                     const int nb = n0 + hcol + c * 16;
                     float bias[16];
                     if (EPI == kEpiHidden || EPI == kEpiOutPhys || EPI == kEpiOutLoss) {
+                        const float4 *sb = reinterpret_cast<const float4 *>(sbias + nb);   // broadcast reads
 #pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) bias[jj] = __ldg(a.bias + nb + jj);
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const float4 b4 = sb[jj];
+                            bias[4 * jj] = b4.x; bias[4 * jj + 1] = b4.y; bias[4 * jj + 2] = b4.z; bias[4 * jj + 3] = b4.w;
+                        }
                     }
                     float g[16];
                     if (EPI == kEpiDx && mval) load_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, g);
@@ -287,11 +338,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
                     for (int jj = 0; jj < 16; ++jj) v[jj] = __uint_as_float(rr[jj]);
                     if (EPI == kEpiHidden) {
                         float gg[16];
+                        if (a.gd) {
 #pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) {
-                            const float z = v[jj] + bias[jj];
-                            v[jj] = gelu_f(z);
-                            if (a.gd) gg[jj] = gelu_grad_f(z);
+                            for (int jj = 0; jj < 16; ++jj) gelu_and_grad(v[jj] + bias[jj], v[jj], gg[jj]);
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) v[jj] = gelu_f(v[jj] + bias[jj]);
                         }
                         if (mval) {
                             store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
