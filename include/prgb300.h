@@ -200,6 +200,74 @@ pr_status surrogate_sync_status(sg_model *m);
 pr_status surrogate_save(const sg_model *m, const char *path);
 pr_status surrogate_load(sg_model *m, const char *path);
 
+/* ======================================================================
+ * Continuous-batching property server (many simulations sharing one GPU).
+ * Requests carry FP32 fields in HOST memory (pinned memory keeps the copies
+ * asynchronous; pageable memory works but its copies block the worker).  A
+ * worker thread admits requests in arrival order while their device buffers
+ * fit in the HBM budget, cuts them into `chunk`-cell pieces, fills batches of
+ * up to `max_slots` pieces round-robin across every admitted request, and runs
+ * each batch by replaying a CUDA graph captured for its (power-of-two) slot
+ * count: gather the pieces, evaluate them (forward properties through the
+ * surrogate with its FP64 PR fallback -- or FP32 PR when no model is given --
+ * and T from h by the PR Newton path), scatter the results.  Results do not
+ * depend on batch composition.  The model (if any) must not be used by other
+ * calls while the server runs.
+ * ====================================================================== */
+
+typedef struct sv_server sv_server;
+
+#define SV_PROPS     0   /* out [6][n]: rho, Z, h, cp, mu, lambda */
+#define SV_T_FROM_H  1   /* out [n]: T; status [n] per-cell PR_CELL_* codes */
+
+typedef struct {
+    int32_t kind;        /* SV_PROPS or SV_T_FROM_H */
+    int32_t pad;
+    int64_t n;           /* cells, >= 1 */
+    const float *T;      /* SV_PROPS: T [n]; SV_T_FROM_H: initial guess [n] (HOST) */
+    const float *p;      /* [n] (HOST) */
+    const float *Y;      /* [9][n] species-major (HOST) */
+    const float *h;      /* SV_T_FROM_H: h* [n] (HOST); NULL for SV_PROPS */
+    float *out;          /* HOST output (see kind); written when the request is done */
+    int32_t *status;     /* SV_T_FROM_H per-cell status [n] (HOST) or NULL */
+} sv_request;
+
+typedef struct {
+    int32_t chunk;             /* cells per batch slot: multiple of 128 */
+    int32_t max_slots;         /* slots per batch, 1..256 */
+    int32_t newton_precision;  /* PR_MIXED or PR_FP32 */
+    int32_t pad;
+    size_t hbm_budget_bytes;   /* device memory for admitted requests' buffers */
+} sv_config;
+
+typedef struct {
+    uint64_t submitted, completed, batches, slots_used, slots_launched;
+    int64_t cells;             /* cells of completed requests */
+    size_t bytes_in_use, peak_bytes_in_use;
+    size_t queued, active;
+} sv_stats;
+
+/* Create a server (allocates the HBM budget, staging and descriptor tables,
+ * captures its graphs, starts the worker).  model may be NULL. */
+pr_status serve_create(pr_ctx *ctx, sg_model *model, const sv_config *cfg, sv_server **out);
+
+/* Queue a request; *ticket identifies it.  The host arrays must stay valid
+ * (and `out` untouched) until the request is done.  A request that cannot fit
+ * in the budget even alone completes with result PR_ENOMEM. */
+pr_status serve_submit(sv_server *s, const sv_request *req, uint64_t *ticket);
+
+/* Non-blocking status: *done = 1 when finished; then *result (PR_OK or an
+ * error) and *latency_ms (submit to completion, host clock) are set. */
+pr_status serve_poll(sv_server *s, uint64_t ticket, int *done, pr_status *result, double *latency_ms);
+
+/* Block until the request is done or timeout_ms passes (PR_ETIMEOUT). */
+pr_status serve_wait(sv_server *s, uint64_t ticket, double timeout_ms, pr_status *result, double *latency_ms);
+
+pr_status serve_stats(sv_server *s, sv_stats *out);
+
+/* Stop the worker, wait for the device, release everything. */
+void serve_destroy(sv_server *s);
+
 /* Plain tensor-core GEMM with the kernel the MLP uses: D[M][N] (FP32,
  * row pitch ldd) = A[M][K] * B[N][K]^T with A, B BF16 K-major (row pitches lda,
  * ldb elements), FP32 accumulation.  K a positive multiple of 64; N = 16, 64 or
