@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 flops per cell of the FP64 kernels, from ncu instruction counts
 # (2 x DFMA + DADD + DMUL per launch / cells) on the 128^3 flame-vortex field
-FP64_FLOPS_PER_CELL = {"props_fp64": 1814.0}
+FP64_FLOPS_PER_CELL = {"props_fp64": 1814.0, "newton_fp64": 2767.0}
 # surrogate: 2 x (11*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=11, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sg-pool", type=int, default=1 << 23, help="training states for the surrogate")
     ap.add_argument("--sg-steps", type=int, default=2000, help="Adam steps of batch 65536")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-clients", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=16, help="requests per client")
     return ap.parse_args()
 
 
@@ -242,6 +245,60 @@ def train_surrogate(ctx, dev, args):
     return sg, report
 
 
+def run_serving(ctx, sg, T, p, Y, hs64, args):
+    """The serving workload: clients with flame-vortex fields of grid size
+    log-uniform in [32, 256]^3 (sampled from the 256^3 field), 70 % forward
+    properties / 30 % T-from-h, Poisson arrivals at twice the measured
+    single-stream request rate, 80 GB admission budget."""
+    import torch
+    from paper_2312_04830_gb300 import serving, workloads as W
+    big = {"T": torch.as_tensor(T, dtype=torch.float32), "p": torch.as_tensor(p, dtype=torch.float32),
+           "Y": torch.as_tensor(Y, dtype=torch.float32), "h": hs64.float().cpu()}
+    g, kinds, clients = W.serving_trace(args.serve_clients, args.serve_requests)
+    grid_of = {}
+    for gi, c in zip(g, clients):
+        grid_of.setdefault(int(c), int(gi))            # each client keeps its first grid size
+    t0 = time.perf_counter()
+    fields = {c: serving.client_field(big, gc) for c, gc in grid_of.items()}
+    outs = {c: {"props": torch.empty((6, gc ** 3), dtype=torch.float32).pin_memory(),
+                "T": torch.empty(gc ** 3, dtype=torch.float32).pin_memory(),
+                "status": torch.empty(gc ** 3, dtype=torch.int32).pin_memory()} for c, gc in grid_of.items()}
+    t_fields = time.perf_counter() - t0
+    cells = np.array([grid_of[int(c)] ** 3 for c in clients], dtype=np.int64)
+    srv = serving.Server(ctx, sg, chunk=1 << 18, max_slots=16, budget_bytes=80 << 30)
+    # single-stream rate: requests of the trace served back to back, one at a time
+    ns = min(32, len(g))
+    t1 = time.perf_counter()
+    for i in range(ns):
+        c = int(clients[i])
+        f, o = fields[c], outs[c]
+        if kinds[i] == 0:
+            tk = srv.submit_props(f["T"], f["p"], f["Y"], o["props"])
+        else:
+            tk = srv.submit_T_from_h(f["h"], f["p"], f["Y"], f["T"], o["T"], o["status"])
+        st, res, _ = srv.wait(tk, 600000.0)
+        assert st == 0 and res == 0
+    single = (time.perf_counter() - t1) / ns
+    rate = 2.0 / single
+    arrivals = W.poisson_arrivals(len(g), rate)
+    s0 = srv.stats()
+    lat, makespan = serving.run_trace(srv, fields, g, kinds, clients.astype(np.int64), arrivals, outs)
+    s1 = srv.stats()
+    srv.close()
+    done_cells = int(cells.sum())
+    return {"clients": args.serve_clients, "requests": int(len(g)), "cells": done_cells,
+            "frac_props": float(np.mean(kinds == 0)), "single_stream_s_per_request": single,
+            "arrival_rate_per_s": rate, "makespan_s": makespan, "throughput_cells_per_s": done_cells / makespan,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "latency_ms_props_p99": float(np.percentile(lat[kinds == 0], 99)),
+            "latency_ms_T_from_h_p99": float(np.percentile(lat[kinds == 1], 99)),
+            "batches": int(s1["batches"] - s0["batches"]),
+            "slot_fill": (s1["slots_used"] - s0["slots_used"]) / max(1, s1["slots_launched"] - s0["slots_launched"]),
+            "peak_hbm_in_use_GB": s1["peak_bytes_in_use"] / 1e9, "budget_GB": 80 * 2 ** 30 / 1e9,
+            "chunk": 1 << 18, "max_slots": 16, "host_field_setup_s": t_fields}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -386,6 +443,8 @@ def run_ours(args):
     }
     if sg_report is not None:
         line["surrogate_training"] = sg_report
+    if not args.no_serving and ws == 1:
+        line["serving"] = run_serving(ctx, sg, T, p, Y, hs64, args)
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
