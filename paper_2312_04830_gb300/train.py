@@ -27,7 +27,14 @@ OUT_NAMES = ("rho", "Z", "h", "cp", "mu", "lambda")
 
 def label_pool(ctx, T, p, Y, device, chunk=1 << 23):
     """(x [11][n], y [6][n]) float32 device tensors of the physical states,
-    labelled by the FP64 PR path, host arrays passed in pieces of `chunk`."""
+    labelled by the FP64 PR path, host arrays passed in pieces of `chunk`.
+
+    Physical-outcome filter (the paper's data constraints, Sec. 4.2): positive
+    finite properties, and a dense-fluid viscosity and conductivity of at least
+    half their dilute-gas values at the same T and composition (taken from the
+    same path at p = 1 Pa).  Chung's correlations, extrapolated to cold
+    radical-rich mixtures, can fall far below the dilute values or turn
+    negative; about 0.2 % of the sampled states are dropped."""
     import torch
     xs, ys = [], []
     for a in range(0, T.size, chunk):
@@ -35,7 +42,9 @@ def label_pool(ctx, T, p, Y, device, chunk=1 << 23):
         d = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=device)
         Td, pd, Yd = d(T[a:b]), d(p[a:b]), d(Y[:, a:b])
         props, st = ctx.props(Td, pd, Yd, precision="fp64")
+        dil, _ = ctx.props(Td, torch.ones_like(pd), Yd, precision="fp64", outputs=("mu", "lambda"))
         keep = (st == 0) & torch.all(torch.isfinite(props), dim=0) & torch.all(props[[0, 3, 4, 5]] > 0, dim=0)
+        keep &= (props[4] >= 0.5 * dil[4]) & (props[5] >= 0.5 * dil[5])
         xs.append(torch.cat([Td[None], pd[None], Yd], dim=0)[:, keep].float())
         ys.append(props[:, keep].float())
     return torch.cat(xs, dim=1).contiguous(), torch.cat(ys, dim=1).contiguous()
