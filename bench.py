@@ -66,8 +66,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--sg-pool", type=int, default=1 << 23, help="training states for the surrogate")
-    ap.add_argument("--sg-steps", type=int, default=2000, help="Adam steps of batch 65536")
+    ap.add_argument("--sg-pool", type=int, default=1 << 26, help="training states for the surrogate")
+    ap.add_argument("--sg-epochs", type=float, default=20.0, help="epochs over the pool (batch 65536)")
+    ap.add_argument("--sg-steps", type=int, default=0, help="Adam steps (overrides --sg-epochs when > 0)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-clients", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=16, help="requests per client")
@@ -233,12 +234,14 @@ def train_surrogate(ctx, dev, args):
     sg.close()
     sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=1 << 20)
     sg.fit_normalization(x, y)
-    losses, secs = TR.train(sg, x, y, args.sg_steps, 65536, 1e-3, log_every=max(1, args.sg_steps // 10))
+    steps = args.sg_steps if args.sg_steps > 0 else int(round(args.sg_epochs * x.shape[1] / 65536))
+    losses, secs = TR.train(sg, x, y, steps, 65536, 1e-3, log_every=max(1, steps // 10))
     sg.sync_status()
-    flops = 3 * mlp_flops_per_cell() * 65536 * args.sg_steps
-    report = {"pool": int(x.shape[1]), "steps": args.sg_steps, "batch": 65536, "seconds": secs,
-              "samples_per_s": 65536 * args.sg_steps / secs, "tflops": flops / secs / 1e12,
-              "epochs": 65536 * args.sg_steps / x.shape[1], "data_seconds": t_data,
+    flops = 3 * mlp_flops_per_cell() * 65536 * steps
+    report = {"pool": int(x.shape[1]), "steps": steps, "batch": 65536, "seconds": secs,
+              "samples_per_s": 65536 * steps / secs, "tflops": flops / secs / 1e12,
+              "tensor_frac": flops / secs / 1e12 / 1729.3,
+              "epochs": 65536 * steps / x.shape[1], "data_seconds": t_data,
               "loss_first_last": [losses[0][1], losses[-1][1]],
               "heldout_error_vs_pr_fp64": TR.evaluate(sg, xh, yh)}
     del x, y, xh, yh
