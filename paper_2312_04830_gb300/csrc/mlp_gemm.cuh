@@ -37,7 +37,7 @@ enum Epi : int {
 struct GemmArgs {
     int M, N, K;              // logical sizes; A is [M][K], B is [N][K]
     int kb_per_split;         // 64-wide k-blocks per K split
-    int m_tiles, n_tiles, splits;   // tile grid (splits along K)
+    int m_tiles, n_tiles, splits;   // tile grid (splits along K); gemm_wres_kernel: cluster = n_tiles
     const float *bias;        // [N]
     __nv_bfloat16 *out;       // [M][ldo] batch-major
     int64_t ldo;
@@ -193,6 +193,112 @@ __device__ __forceinline__ void named_barrier_epi()
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
 }
 
+// Epilogue of one accumulator tile for one epilogue warp: drain this warp's
+// 32 rows x HALF columns from TMEM (loads software-pipelined), apply the
+// epilogue, store.  Returns this lane's sum of squared errors (kEpiOutLoss).
+template <int BN, int EPI>
+__device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr, int m, bool mval, int n0, int hcol,
+                                               int q, int lane, int split, float *red, const float *sbias,
+                                               bool active, bool fail)
+{
+    constexpr int HALF = (BN >= 32) ? BN / 2 : BN;
+    float lsum = 0.f;
+    if (active && !fail) {
+        uint32_t rnext[16];
+        umma::tmem_ld16(taddr, rnext);
+#pragma unroll 1
+        for (int c = 0; c < HALF / 16; ++c) {
+            umma::tmem_ld_wait(rnext);
+            uint32_t rr[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) rr[jj] = rnext[jj];
+            // next chunk's load is in flight while this one is processed
+            if (c + 1 < HALF / 16) umma::tmem_ld16(taddr + (c + 1) * 16, rnext);
+            const int nb = n0 + hcol + c * 16;
+            float bias[16];
+            if (EPI == kEpiHidden || EPI == kEpiOutPhys || EPI == kEpiOutLoss) {
+                const float4 *sb = reinterpret_cast<const float4 *>(sbias + nb);   // broadcast reads
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float4 b4 = sb[jj];
+                    bias[4 * jj] = b4.x; bias[4 * jj + 1] = b4.y; bias[4 * jj + 2] = b4.z; bias[4 * jj + 3] = b4.w;
+                }
+            }
+            float g[16];
+            if (EPI == kEpiDx && mval) load_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, g);
+            float v[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] = __uint_as_float(rr[jj]);
+            if (EPI == kEpiHidden) {
+                float gg[16];
+                if (a.gd) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) gelu_and_grad(v[jj] + bias[jj], v[jj], gg[jj]);
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) v[jj] = gelu_f(v[jj] + bias[jj]);
+                }
+                if (mval) {
+                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+                    if (a.gd) store_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, gg);
+                    if (a.outT) {
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj)
+                            a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                    }
+                }
+            } else if (EPI == kEpiOutPhys) {
+                if (mval && nb == 0) {
+#pragma unroll
+                    for (int jj = 0; jj < 6; ++jj) {
+                        const float sv = v[jj] + bias[jj];
+                        const float qv = sv * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
+                        a.out6[(int64_t)jj * a.ld6 + m] = (jj == 1 || jj == 2) ? qv : __expf(qv);
+                    }
+                }
+            } else if (EPI == kEpiOutLoss) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    float d = 0.f;
+                    if (mval && nb == 0 && jj < 6) {
+                        const float tv = __ldg(a.target + (int64_t)jj * a.ldt + m);
+                        d = isfinite(tv) ? v[jj] + bias[jj] - tv : 0.f;   // non-finite targets are masked
+                    }
+                    lsum += d * d;
+                    v[jj] = a.loss_scale * d;
+                }
+                if (mval) {
+                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj)
+                        a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                }
+            } else if (EPI == kEpiDx) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) v[jj] = mval ? v[jj] * g[jj] : 0.f;
+                if (mval) {
+                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj)
+                        a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                }
+            } else {  // kEpiDw
+                if (m < a.Mpad) {
+                    float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)split * a.Mpad + m) * a.N + nb);
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj)
+                        dst[jj] = make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]);
+                }
+            }
+            if (EPI == kEpiOutLoss || EPI == kEpiDx) {
+                const float sv = warp_colsum16(v, lane);
+                if ((lane & 1) == 0) red[q * BN + hcol + c * 16 + (lane >> 1)] = sv;
+            }
+        }
+    }
+    return lsum;
+}
+
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB, const GemmArgs a)
@@ -314,100 +420,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             if (!fail && !umma::mbar_wait(&acc_full[buf], (j >> 1) & 1u)) fail = true;
             umma::tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * BN + hcol;
-            float lsum = 0.f;
-            if (active && !fail) {
-                uint32_t rnext[16];
-                umma::tmem_ld16(taddr, rnext);
-#pragma unroll 1
-                for (int c = 0; c < HALF / 16; ++c) {
-                    umma::tmem_ld_wait(rnext);
-                    uint32_t rr[16];
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) rr[jj] = rnext[jj];
-                    // next chunk's load is in flight while this one is processed
-                    if (c + 1 < HALF / 16) umma::tmem_ld16(taddr + (c + 1) * 16, rnext);
-                    const int nb = n0 + hcol + c * 16;
-                    float bias[16];
-                    if (EPI == kEpiHidden || EPI == kEpiOutPhys || EPI == kEpiOutLoss) {
-                        const float4 *sb = reinterpret_cast<const float4 *>(sbias + nb);   // broadcast reads
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const float4 b4 = sb[jj];
-                            bias[4 * jj] = b4.x; bias[4 * jj + 1] = b4.y; bias[4 * jj + 2] = b4.z; bias[4 * jj + 3] = b4.w;
-                        }
-                    }
-                    float g[16];
-                    if (EPI == kEpiDx && mval) load_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, g);
-                    float v[16];
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) v[jj] = __uint_as_float(rr[jj]);
-                    if (EPI == kEpiHidden) {
-                        float gg[16];
-                        if (a.gd) {
-#pragma unroll
-                            for (int jj = 0; jj < 16; ++jj) gelu_and_grad(v[jj] + bias[jj], v[jj], gg[jj]);
-                        } else {
-#pragma unroll
-                            for (int jj = 0; jj < 16; ++jj) v[jj] = gelu_f(v[jj] + bias[jj]);
-                        }
-                        if (mval) {
-                            store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-                            if (a.gd) store_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, gg);
-                            if (a.outT) {
-#pragma unroll
-                                for (int jj = 0; jj < 16; ++jj)
-                                    a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
-                            }
-                        }
-                    } else if (EPI == kEpiOutPhys) {
-                        if (mval && nb == 0) {
-#pragma unroll
-                            for (int jj = 0; jj < 6; ++jj) {
-                                const float sv = v[jj] + bias[jj];
-                                const float qv = sv * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
-                                a.out6[(int64_t)jj * a.ld6 + m] = (jj == 1 || jj == 2) ? qv : __expf(qv);
-                            }
-                        }
-                    } else if (EPI == kEpiOutLoss) {
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) {
-                            float d = 0.f;
-                            if (mval && nb == 0 && jj < 6) {
-                                const float tv = __ldg(a.target + (int64_t)jj * a.ldt + m);
-                                d = isfinite(tv) ? v[jj] + bias[jj] - tv : 0.f;   // non-finite targets are masked
-                            }
-                            lsum += d * d;
-                            v[jj] = a.loss_scale * d;
-                        }
-                        if (mval) {
-                            store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-#pragma unroll
-                            for (int jj = 0; jj < 16; ++jj)
-                                a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
-                        }
-                    } else if (EPI == kEpiDx) {
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) v[jj] = mval ? v[jj] * g[jj] : 0.f;
-                        if (mval) {
-                            store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-#pragma unroll
-                            for (int jj = 0; jj < 16; ++jj)
-                                a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
-                        }
-                    } else {  // kEpiDw
-                        if (m < a.Mpad) {
-                            float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)split * a.Mpad + m) * a.N + nb);
-#pragma unroll
-                            for (int jj = 0; jj < 4; ++jj)
-                                dst[jj] = make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]);
-                        }
-                    }
-                    if (EPI == kEpiOutLoss || EPI == kEpiDx) {
-                        const float sv = warp_colsum16(v, lane);
-                        if ((lane & 1) == 0) red[q * BN + hcol + c * 16 + (lane >> 1)] = sv;
-                    }
-                }
-            }
+            float lsum = epilogue_tile<BN, EPI>(a, taddr, m, mval, n0, hcol, q, lane, split, red, sbias,
+                                                      active, fail);
             // the accumulator buffer may be reused once every warp has read it
             umma::tc_fence_before();
             __syncwarp();
@@ -433,6 +447,182 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     if (fail) atomicExch(a.err, 1);
     umma::tc_fence_before();
     __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        umma::tc_fence_after();
+        umma::tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Weight-resident GEMM for the layers whose B operand is a weight matrix
+// (forward: B = W [N][K]; input gradient: B = W^T [N][K]), N = 128 * NT with
+// NT in {1, 2, 4, 8} and K <= 512.
+//
+// A cluster of NT CTAs computes the NT column tiles of one 128-row tile: CTA
+// rank r keeps its 128 x K weight slice in shared memory for the whole kernel
+// (loaded once), and each 128 x 64 activation stage is fetched in NT row
+// slices -- each CTA loads one slice with a TMA multicast that lands in every
+// CTA of the cluster.  A stage is refilled only after the MMAs of every CTA
+// have consumed it: each CTA's MMA thread commits with a multicast arrival on
+// the stage's "empty" barrier of every CTA (barrier count NT).  Compared with
+// fetching both operands per tile, L2 reads fall from (A + B) per tile to A/NT.
+// The accumulator is double-buffered in TMEM and the epilogue is the one of
+// gemm_kernel (8 warps, same epilogue variants).
+struct WresCfg {
+    static constexpr int BN = 128;
+    static constexpr int A_BYTES = BM * BK * 2;       // 16 KB per stage
+    static constexpr int KB_MAX = 8;                  // K <= 512
+    static constexpr int W_BYTES = KB_MAX * BN * BK * 2;   // 128 KB
+    static constexpr int S = 5;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;
+    static constexpr int BAR_BYTES = 8 * (2 * S + 6) + 16;
+    static constexpr int RED_BYTES = 4 * BN * 4 + 64;
+    static constexpr int BIAS_BYTES = 1024 * 4;
+    static constexpr int SMEM = 1024 + W_BYTES + S * A_BYTES + BAR_BYTES + RED_BYTES + BIAS_BYTES;
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(kThreads, 1) gemm_wres_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB,
+                                                                const GemmArgs a)
+{
+    using C = WresCfg;
+    constexpr int BN = C::BN;
+    constexpr int HALF = BN / 2;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *wres = smem;
+    uint8_t *aring = smem + C::W_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(aring + C::S * C::A_BYTES);
+    uint64_t *empty = full + C::S;
+    uint64_t *wfull = empty + C::S;
+    uint64_t *acc_full = wfull + 1;      // [2]
+    uint64_t *acc_empty = acc_full + 2;  // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    float *red = reinterpret_cast<float *>(aring + C::S * C::A_BYTES + C::BAR_BYTES);
+    float *sbias = red + 4 * BN + 16;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NT = a.n_tiles;                          // cluster size
+    const uint32_t rank = umma::cluster_ctarank();
+    const int cid = (int)umma::cluster_id_x(), ncl = (int)umma::nclusters_x();
+    const uint16_t mask = (uint16_t)((1u << NT) - 1u);
+    const int kbs = a.K / BK;                          // k-blocks per tile (K multiple of 64)
+    const int slice_rows = BM / NT;
+    const uint32_t slice_bytes = (uint32_t)(C::A_BYTES / NT);
+    const int n0 = (int)rank * BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::S; ++s) {
+            umma::mbar_init(&full[s], 1);
+            umma::mbar_init(&empty[s], (uint32_t)NT);
+        }
+        umma::mbar_init(wfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            umma::mbar_init(&acc_full[b], 1);
+            umma::mbar_init(&acc_empty[b], kEpiWarps);
+        }
+        umma::fence_mbar_init();
+        umma::tma_prefetch_desc(&tmA);
+        umma::tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        umma::tmem_alloc(tmem_slot, C::TMEM_COLS);
+        umma::tmem_relinquish();
+    }
+    umma::tc_fence_before();
+    __syncthreads();
+    umma::cluster_sync();          // every CTA's barriers exist before any multicast reaches them
+    umma::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool fail = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // resident weight slice: rows n0..n0+127, all K
+            umma::mbar_arrive_expect_tx(wfull, (uint32_t)(kbs * BN * BK * 2));
+            for (int kb = 0; kb < kbs; ++kb)
+                umma::tma_load_2d(wres + kb * BN * BK * 2, &tmB, wfull, kb * BK, n0);
+            uint32_t it = 0;
+            for (int mt = cid; mt < a.m_tiles && !fail; mt += ncl) {
+                const int m0 = mt * BM;
+                for (int kb = 0; kb < kbs; ++kb, ++it) {
+                    const int s = it % C::S;
+                    const uint32_t ph = (it / C::S) & 1u;
+                    if (it >= (uint32_t)C::S && !umma::mbar_wait(&empty[s], ph ^ 1u)) { fail = true; break; }
+                    umma::mbar_arrive_expect_tx(&full[s], C::A_BYTES);
+                    umma::tma_load_2d_multicast(aring + s * C::A_BYTES + rank * slice_bytes, &tmA, &full[s], kb * BK,
+                                                m0 + (int)rank * slice_rows, mask);
+                }
+            }
+            for (uint32_t k = (it > (uint32_t)C::S ? it - C::S : 0u); k < it; ++k)
+                if (!umma::mbar_wait(&full[k % C::S], (k / C::S) & 1u, 200000000LL)) fail = true;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN);
+            if (!umma::mbar_wait(wfull, 0)) fail = true;
+            uint32_t it = 0, j = 0;
+            for (int mt = cid; mt < a.m_tiles && !fail; mt += ncl, ++j) {
+                const uint32_t buf = j & 1u;
+                if (j >= 2 && !umma::mbar_wait(&acc_empty[buf], ((j >> 1) & 1u) ^ 1u)) { fail = true; break; }
+                umma::tc_fence_after();
+                const uint32_t d_tmem = tmem + buf * BN;
+                for (int kb = 0; kb < kbs; ++kb, ++it) {
+                    const int s = it % C::S;
+                    const uint32_t ph = (it / C::S) & 1u;
+                    if (!umma::mbar_wait(&full[s], ph)) { fail = true; break; }
+                    umma::tc_fence_after();
+                    const uint32_t sa = umma::smem_u32(aring + s * C::A_BYTES);
+                    const uint32_t sb = umma::smem_u32(wres + kb * BN * BK * 2);
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        umma::mma_bf16(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
+                                       umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    umma::mma_commit_multicast(&empty[s], mask);   // stage free in every CTA of the cluster
+                }
+                umma::mma_commit(&acc_full[buf]);
+            }
+        }
+    } else {
+        const int ew = warp - 2;
+        const int q = warp & 3;
+        const int hcol = (ew >> 2) * HALF;
+        const int row = q * 32 + lane;
+        if (EPI == kEpiHidden) {
+            for (int col = threadIdx.x - 64; col < a.N; col += 32 * kEpiWarps) sbias[col] = __ldg(a.bias + col);
+            named_barrier_epi();
+        }
+        uint32_t j = 0;
+        for (int mt = cid; mt < a.m_tiles; mt += ncl, ++j) {
+            const int m0 = mt * BM;
+            const int m = m0 + row;
+            const bool mval = m < a.M;
+            const uint32_t buf = j & 1u;
+            if (!fail && !umma::mbar_wait(&acc_full[buf], (j >> 1) & 1u)) fail = true;
+            umma::tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * BN + hcol;
+            epilogue_tile<BN, EPI>(a, taddr, m, mval, n0, hcol, q, lane, 0, red, sbias, true, fail);
+            umma::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&acc_empty[buf]);
+            if (EPI == kEpiDx) {
+                named_barrier_epi();
+                const int tt = threadIdx.x - 64;
+                for (int col = tt; col < BN; col += 32 * kEpiWarps)
+                    a.colsum[(int64_t)mt * a.N + n0 + col] =
+                        red[col] + red[BN + col] + red[2 * BN + col] + red[3 * BN + col];
+                named_barrier_epi();
+            }
+        }
+    }
+    __syncwarp();
+    if (fail) atomicExch(a.err, 1);
+    umma::tc_fence_before();
+    __syncthreads();
+    umma::cluster_sync();          // no CTA leaves while peers may still multicast into it
     if (warp == 1) {
         __syncwarp();
         umma::tc_fence_after();
