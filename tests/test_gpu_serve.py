@@ -76,6 +76,8 @@ def test_same_alone_and_in_mix(setup, cuda):
     for (t, out), rq, newton in tickets:
         st, res, lat = srv.wait(t)
         assert st == 0 and res == 0
+    # direct calls only once the server is idle: the model's buffers are shared
+    for (t, out), rq, newton in tickets:
         assert np.array_equal(out, direct(ctx, sg, rq, 1 if newton else 0, cuda), equal_nan=True)
     mixed_R = [out for (t, out), rq, nw in tickets if rq is R][0]
     assert np.array_equal(mixed_R, alone, equal_nan=True)
