@@ -37,7 +37,7 @@ enum Epi : int {
 struct GemmArgs {
     int M, N, K;              // logical sizes; A is [M][K], B is [N][K]
     int kb_per_split;         // 64-wide k-blocks per K split
-    int m_tiles, n_tiles, splits;   // tile grid (splits along K); gemm_wres_kernel: cluster = n_tiles
+    int m_tiles, n_tiles, splits;   // tile grid (splits along K)
     const float *bias;        // [N]
     __nv_bfloat16 *out;       // [M][ldo] batch-major
     int64_t ldo;
@@ -56,6 +56,11 @@ struct GemmArgs {
     float loss_scale;         // d loss / d y = loss_scale * (y - target)
     float *loss_part;         // [m_tiles] per-M-tile sum of squared errors
     int *err;                 // set to 1 when a bounded wait runs out
+    // kEpiHidden / kEpiDx with tma_out != 0: `out` (and `gd` when written) go
+    // out through shared memory and TMA stores of 32 x 64 boxes (128-byte
+    // swizzle); tm_out / tm_gd map those matrices with that box
+    int tma_out;
+    CUtensorMap tm_out, tm_gd;
 };
 
 constexpr int kEpiWarps = 8;
@@ -66,63 +71,50 @@ struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int S = (196608 / STAGE) < 8 ? (196608 / STAGE) : 8;
+    static constexpr int STG_BYTES = kEpiWarps * 8192;   // output staging: two 4 KB boxes per epilogue warp
+    static constexpr int S_FIT = (232448 - 1024 - STG_BYTES - 12288) / STAGE;
+    static constexpr int S = S_FIT < 8 ? S_FIT : 8;
     static constexpr uint32_t TMEM_COLS = (2 * BN) < 32 ? 32 : 2 * BN;   // two accumulator buffers
     static constexpr int BAR_BYTES = 8 * (2 * S + 4) + 16;
     static constexpr int RED_BYTES = 4 * BN * 4 + 64;
     static constexpr int BIAS_BYTES = 1024 * 4;   // bias of up to 1024 output columns
-    static constexpr int SMEM = 1024 + S * STAGE + BAR_BYTES + RED_BYTES + BIAS_BYTES;
+    static constexpr int SMEM = 1024 + S * STAGE + STG_BYTES + BAR_BYTES + RED_BYTES + BIAS_BYTES;
 };
 
-// GeLU(z) = z Phi(z) and GeLU'(z) = Phi(z) + z phi(z), with the normal tail
-// probability from Abramowitz & Stegun 7.1.25:
-//   erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3) exp(-x^2),  t = 1 / (1 + p x),
-//   x >= 0,  |error| <= 2.5e-5,
-// taken at x = |z| / sqrt(2):  Q = (1 - erf(x)) / 2 = P(t) exp(-z^2/2).
-// Then Phi = 1/2 + sgn(z) (1/2 - Q) and GeLU = z/2 + |z| (1/2 - Q), one FMA
-// after 1/2 - Q.  The error of Phi (<= 1.3e-5) is far under the BF16 rounding
-// of the activations (3.9e-3); training and inference use the same function.
-// The reciprocal and the exponential are single MUFU operations.
-__device__ __forceinline__ float rcp_approx(float x)
+// GeLU in its tanh form (Hendrycks & Gimpel 2016),
+//   GeLU(z) ~ z/2 (1 + tanh(k (z + c z^3))),  k = sqrt(2/pi), c = 0.044715,
+// with the hardware tanh.approx.f32 (one MUFU operation), and its exact
+// derivative
+//   GeLU'(z) = (1 + t)/2 + z/2 (1 - t^2) k (1 + 3 c z^2),  t = tanh(k (z + c z^3)).
+// The tanh form differs from z Phi(z) by at most 5e-4 and tanh.approx has a
+// relative error below 2^-10.9; both are under the BF16 rounding of the
+// activations (3.9e-3).  Training and inference use this same function.
+__device__ __forceinline__ float tanh_approx(float x)
 {
     float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// u = 1/2 - Q(z) and e = exp(-z^2/2)
-__device__ __forceinline__ void half_minus_tail(float z, float &u, float &e)
-{
-    constexpr float p_s2 = 0.47047f * 0.70710678118654752f;          // p / sqrt(2)
-    constexpr float h1 = 0.5f * 0.3480242f, h2 = 0.5f * -0.0958798f, h3 = 0.5f * 0.7478556f;
-    constexpr float mhl2e = -0.5f * 1.4426950408889634f;             // -log2(e)/2
-    const float t = rcp_approx(fmaf(p_s2, fabsf(z), 1.0f));
-    const float P = t * fmaf(fmaf(h3, t, h2), t, h1);
-    e = ex2_approx((z * mhl2e) * z);
-    u = fmaf(-P, e, 0.5f);
-}
+constexpr float kGeluK = 0.7978845608028654f;            // sqrt(2/pi)
+constexpr float kGeluKC = 0.7978845608028654f * 0.044715f;
 
 __device__ __forceinline__ float gelu_f(float z)
 {
-    float u, e;
-    half_minus_tail(z, u, e);
-    return fmaf(fabsf(z), u, 0.5f * z);
+    const float z2 = z * z;
+    const float t = tanh_approx(z * fmaf(kGeluKC, z2, kGeluK));
+    const float hz = 0.5f * z;
+    return fmaf(hz, t, hz);
 }
 
 __device__ __forceinline__ void gelu_and_grad(float z, float &g, float &dg)
 {
-    float u, e;
-    half_minus_tail(z, u, e);
-    g = fmaf(fabsf(z), u, 0.5f * z);
-    const float Phi = 0.5f + copysignf(u, z);
-    dg = fmaf(z * 0.39894228040143268f, e, Phi);   // Phi + z phi(z)
+    const float z2 = z * z;
+    const float t = tanh_approx(z * fmaf(kGeluKC, z2, kGeluK));
+    const float hz = 0.5f * z;
+    g = fmaf(hz, t, hz);
+    const float dk = fmaf(3.0f * kGeluKC, z2, kGeluK);      // d/dz of k (z + c z^3)
+    dg = fmaf(hz * fmaf(-t, t, 1.0f), dk, fmaf(0.5f, t, 0.5f));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
@@ -152,6 +144,21 @@ __device__ __forceinline__ void load_row16_bf16(const __nv_bfloat16 *src, float 
         v[2 * k] = f.x;
         v[2 * k + 1] = f.y;
     }
+}
+
+// 16 BF16 of row `row` (0..31), columns 16*c4 .. 16*c4+15 (c4 = 0..3), into a
+// 32 x 64 staging box laid out as TMA's 128-byte swizzle: the 16-byte piece j
+// of the 128-byte row r sits at piece j ^ (r % 8).
+__device__ __forceinline__ void stage_row16_bf16(uint8_t *box, int row, int c4, const float (&v)[16])
+{
+    const uint4 lo = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                pack_bf16(v[6], v[7]));
+    const uint4 hi = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
+                                pack_bf16(v[14], v[15]));
+    uint8_t *r = box + row * 128;
+    const int j0 = 2 * c4, x = row & 7;
+    *reinterpret_cast<uint4 *>(r + ((j0 ^ x) << 4)) = lo;
+    *reinterpret_cast<uint4 *>(r + (((j0 + 1) ^ x) << 4)) = hi;
 }
 
 // Sum 16 per-lane values over the 32 lanes of a warp; afterwards even lane L
@@ -199,9 +206,15 @@ __device__ __forceinline__ void named_barrier_epi()
 template <int BN, int EPI>
 __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr, int m, bool mval, int n0, int hcol,
                                                int q, int lane, int split, float *red, const float *sbias,
-                                               bool active, bool fail)
+                                               bool active, bool fail, uint8_t *stg, int m0)
 {
     constexpr int HALF = (BN >= 32) ? BN / 2 : BN;
+    // TMA-store path: this warp's 32 rows x 64 columns of `out` (and of `gd`
+    // when written) are staged as 128-byte-swizzled boxes and stored by lane 0,
+    // one bulk group per 64 columns; the next group first waits until the
+    // previous boxes have been read out of shared memory
+    const bool tma = (EPI == kEpiHidden || EPI == kEpiDx) && a.tma_out && (HALF % 64 == 0);
+    uint8_t *sh = stg, *sg = stg + 4096;
     float lsum = 0.f;
     if (active && !fail) {
         uint32_t rnext[16];
@@ -215,6 +228,10 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
             // next chunk's load is in flight while this one is processed
             if (c + 1 < HALF / 16) umma::tmem_ld16(taddr + (c + 1) * 16, rnext);
             const int nb = n0 + hcol + c * 16;
+            if (tma && (c & 3) == 0) {
+                if (lane == 0) umma::bulk_wait_read0();
+                __syncwarp();
+            }
             float bias[16];
             if (EPI == kEpiHidden || EPI == kEpiOutPhys || EPI == kEpiOutLoss) {
                 const float4 *sb = reinterpret_cast<const float4 *>(sbias + nb);   // broadcast reads
@@ -238,9 +255,15 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) v[jj] = gelu_f(v[jj] + bias[jj]);
                 }
+                if (tma) {
+                    stage_row16_bf16(sh, lane, c & 3, v);
+                    if (a.gd) stage_row16_bf16(sg, lane, c & 3, gg);
+                }
                 if (mval) {
-                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-                    if (a.gd) store_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, gg);
+                    if (!tma) {
+                        store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+                        if (a.gd) store_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, gg);
+                    }
                     if (a.outT) {
 #pragma unroll
                         for (int jj = 0; jj < 16; ++jj)
@@ -276,8 +299,9 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
             } else if (EPI == kEpiDx) {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) v[jj] = mval ? v[jj] * g[jj] : 0.f;
+                if (tma) stage_row16_bf16(sh, lane, c & 3, v);
                 if (mval) {
-                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+                    if (!tma) store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj)
                         a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
@@ -288,6 +312,15 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj)
                         dst[jj] = make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]);
+                }
+            }
+            if (tma && (c & 3) == 3) {
+                umma::fence_async_smem();   // staging writes visible to the TMA engine
+                __syncwarp();
+                if (lane == 0) {
+                    umma::tma_store_2d(&a.tm_out, sh, nb - 48, m0 + q * 32);
+                    if (EPI == kEpiHidden && a.gd) umma::tma_store_2d(&a.tm_gd, sg, nb - 48, m0 + q * 32);
+                    umma::bulk_commit();
                 }
             }
             if (EPI == kEpiOutLoss || EPI == kEpiDx) {
@@ -301,18 +334,20 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                           const __grid_constant__ CUtensorMap tmB, const GemmArgs a)
+                                                           const __grid_constant__ CUtensorMap tmB,
+                                                           const __grid_constant__ GemmArgs a)
 {
     using C = Cfg<BN>;
     constexpr int HALF = (BN >= 32) ? BN / 2 : BN;   // columns per epilogue warp
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::S * C::STAGE);
+    uint8_t *stg_base = smem + C::S * C::STAGE;   // 1024-aligned: stages are whole KB
+    uint64_t *full = reinterpret_cast<uint64_t *>(stg_base + C::STG_BYTES);
     uint64_t *empty = full + C::S;
     uint64_t *acc_full = empty + C::S;     // [2]
     uint64_t *acc_empty = acc_full + 2;    // [2]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
-    float *red = reinterpret_cast<float *>(smem + C::S * C::STAGE + C::BAR_BYTES);   // [4][BN] + 16
+    float *red = reinterpret_cast<float *>(stg_base + C::STG_BYTES + C::BAR_BYTES);   // [4][BN] + 16
     float *sbias = red + 4 * BN + 16;                                                // [N] (N <= 1024)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -421,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             umma::tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * BN + hcol;
             float lsum = epilogue_tile<BN, EPI>(a, taddr, m, mval, n0, hcol, q, lane, split, red, sbias,
-                                                      active, fail);
+                                                      active, fail, stg_base + ew * 8192, m0);
             // the accumulator buffer may be reused once every warp has read it
             umma::tc_fence_before();
             __syncwarp();
@@ -443,6 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             }
         }
     }
+    if (warp >= 2 && lane == 0) umma::bulk_wait0();   // staged stores complete before shared memory goes
     __syncwarp();   // reconverge each warp (role lanes vs idle lanes) before the CTA barrier
     if (fail) atomicExch(a.err, 1);
     umma::tc_fence_before();
@@ -454,180 +490,5 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     }
 }
 
-
-// ---------------------------------------------------------------------------
-// Weight-resident GEMM for the layers whose B operand is a weight matrix
-// (forward: B = W [N][K]; input gradient: B = W^T [N][K]), N = 128 * NT with
-// NT in {1, 2, 4, 8} and K <= 512.
-//
-// A cluster of NT CTAs computes the NT column tiles of one 128-row tile: CTA
-// rank r keeps its 128 x K weight slice in shared memory for the whole kernel
-// (loaded once), and each 128 x 64 activation stage is fetched in NT row
-// slices -- each CTA loads one slice with a TMA multicast that lands in every
-// CTA of the cluster.  A stage is refilled only after the MMAs of every CTA
-// have consumed it: each CTA's MMA thread commits with a multicast arrival on
-// the stage's "empty" barrier of every CTA (barrier count NT).  Compared with
-// fetching both operands per tile, L2 reads fall from (A + B) per tile to A/NT.
-// The accumulator is double-buffered in TMEM and the epilogue is the one of
-// gemm_kernel (8 warps, same epilogue variants).
-struct WresCfg {
-    static constexpr int BN = 128;
-    static constexpr int A_BYTES = BM * BK * 2;       // 16 KB per stage
-    static constexpr int KB_MAX = 8;                  // K <= 512
-    static constexpr int W_BYTES = KB_MAX * BN * BK * 2;   // 128 KB
-    static constexpr int S = 5;
-    static constexpr uint32_t TMEM_COLS = 2 * BN;
-    static constexpr int BAR_BYTES = 8 * (2 * S + 6) + 16;
-    static constexpr int RED_BYTES = 4 * BN * 4 + 64;
-    static constexpr int BIAS_BYTES = 1024 * 4;
-    static constexpr int SMEM = 1024 + W_BYTES + S * A_BYTES + BAR_BYTES + RED_BYTES + BIAS_BYTES;
-};
-
-template <int EPI>
-__global__ void __launch_bounds__(kThreads, 1) gemm_wres_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                                const __grid_constant__ CUtensorMap tmB,
-                                                                const GemmArgs a)
-{
-    using C = WresCfg;
-    constexpr int BN = C::BN;
-    constexpr int HALF = BN / 2;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *wres = smem;
-    uint8_t *aring = smem + C::W_BYTES;
-    uint64_t *full = reinterpret_cast<uint64_t *>(aring + C::S * C::A_BYTES);
-    uint64_t *empty = full + C::S;
-    uint64_t *wfull = empty + C::S;
-    uint64_t *acc_full = wfull + 1;      // [2]
-    uint64_t *acc_empty = acc_full + 2;  // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
-    float *red = reinterpret_cast<float *>(aring + C::S * C::A_BYTES + C::BAR_BYTES);
-    float *sbias = red + 4 * BN + 16;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int NT = a.n_tiles;                          // cluster size
-    const uint32_t rank = umma::cluster_ctarank();
-    const int cid = (int)umma::cluster_id_x(), ncl = (int)umma::nclusters_x();
-    const uint16_t mask = (uint16_t)((1u << NT) - 1u);
-    const int kbs = a.K / BK;                          // k-blocks per tile (K multiple of 64)
-    const int slice_rows = BM / NT;
-    const uint32_t slice_bytes = (uint32_t)(C::A_BYTES / NT);
-    const int n0 = (int)rank * BN;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C::S; ++s) {
-            umma::mbar_init(&full[s], 1);
-            umma::mbar_init(&empty[s], (uint32_t)NT);
-        }
-        umma::mbar_init(wfull, 1);
-        for (int b = 0; b < 2; ++b) {
-            umma::mbar_init(&acc_full[b], 1);
-            umma::mbar_init(&acc_empty[b], kEpiWarps);
-        }
-        umma::fence_mbar_init();
-        umma::tma_prefetch_desc(&tmA);
-        umma::tma_prefetch_desc(&tmB);
-    }
-    if (warp == 1) {
-        umma::tmem_alloc(tmem_slot, C::TMEM_COLS);
-        umma::tmem_relinquish();
-    }
-    umma::tc_fence_before();
-    __syncthreads();
-    umma::cluster_sync();          // every CTA's barriers exist before any multicast reaches them
-    umma::tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    bool fail = false;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            // resident weight slice: rows n0..n0+127, all K
-            umma::mbar_arrive_expect_tx(wfull, (uint32_t)(kbs * BN * BK * 2));
-            for (int kb = 0; kb < kbs; ++kb)
-                umma::tma_load_2d(wres + kb * BN * BK * 2, &tmB, wfull, kb * BK, n0);
-            uint32_t it = 0;
-            for (int mt = cid; mt < a.m_tiles && !fail; mt += ncl) {
-                const int m0 = mt * BM;
-                for (int kb = 0; kb < kbs; ++kb, ++it) {
-                    const int s = it % C::S;
-                    const uint32_t ph = (it / C::S) & 1u;
-                    if (it >= (uint32_t)C::S && !umma::mbar_wait(&empty[s], ph ^ 1u)) { fail = true; break; }
-                    umma::mbar_arrive_expect_tx(&full[s], C::A_BYTES);
-                    umma::tma_load_2d_multicast(aring + s * C::A_BYTES + rank * slice_bytes, &tmA, &full[s], kb * BK,
-                                                m0 + (int)rank * slice_rows, mask);
-                }
-            }
-            for (uint32_t k = (it > (uint32_t)C::S ? it - C::S : 0u); k < it; ++k)
-                if (!umma::mbar_wait(&full[k % C::S], (k / C::S) & 1u, 200000000LL)) fail = true;
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN);
-            if (!umma::mbar_wait(wfull, 0)) fail = true;
-            uint32_t it = 0, j = 0;
-            for (int mt = cid; mt < a.m_tiles && !fail; mt += ncl, ++j) {
-                const uint32_t buf = j & 1u;
-                if (j >= 2 && !umma::mbar_wait(&acc_empty[buf], ((j >> 1) & 1u) ^ 1u)) { fail = true; break; }
-                umma::tc_fence_after();
-                const uint32_t d_tmem = tmem + buf * BN;
-                for (int kb = 0; kb < kbs; ++kb, ++it) {
-                    const int s = it % C::S;
-                    const uint32_t ph = (it / C::S) & 1u;
-                    if (!umma::mbar_wait(&full[s], ph)) { fail = true; break; }
-                    umma::tc_fence_after();
-                    const uint32_t sa = umma::smem_u32(aring + s * C::A_BYTES);
-                    const uint32_t sb = umma::smem_u32(wres + kb * BN * BK * 2);
-#pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        umma::mma_bf16(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
-                                       umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
-                    umma::mma_commit_multicast(&empty[s], mask);   // stage free in every CTA of the cluster
-                }
-                umma::mma_commit(&acc_full[buf]);
-            }
-        }
-    } else {
-        const int ew = warp - 2;
-        const int q = warp & 3;
-        const int hcol = (ew >> 2) * HALF;
-        const int row = q * 32 + lane;
-        if (EPI == kEpiHidden) {
-            for (int col = threadIdx.x - 64; col < a.N; col += 32 * kEpiWarps) sbias[col] = __ldg(a.bias + col);
-            named_barrier_epi();
-        }
-        uint32_t j = 0;
-        for (int mt = cid; mt < a.m_tiles; mt += ncl, ++j) {
-            const int m0 = mt * BM;
-            const int m = m0 + row;
-            const bool mval = m < a.M;
-            const uint32_t buf = j & 1u;
-            if (!fail && !umma::mbar_wait(&acc_full[buf], (j >> 1) & 1u)) fail = true;
-            umma::tc_fence_after();
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * BN + hcol;
-            epilogue_tile<BN, EPI>(a, taddr, m, mval, n0, hcol, q, lane, 0, red, sbias, true, fail);
-            umma::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) umma::mbar_arrive(&acc_empty[buf]);
-            if (EPI == kEpiDx) {
-                named_barrier_epi();
-                const int tt = threadIdx.x - 64;
-                for (int col = tt; col < BN; col += 32 * kEpiWarps)
-                    a.colsum[(int64_t)mt * a.N + n0 + col] =
-                        red[col] + red[BN + col] + red[2 * BN + col] + red[3 * BN + col];
-                named_barrier_epi();
-            }
-        }
-    }
-    __syncwarp();
-    if (fail) atomicExch(a.err, 1);
-    umma::tc_fence_before();
-    __syncthreads();
-    umma::cluster_sync();          // no CTA leaves while peers may still multicast into it
-    if (warp == 1) {
-        __syncwarp();
-        umma::tc_fence_after();
-        umma::tmem_dealloc(tmem, C::TMEM_COLS);
-    }
-}
 
 }  // namespace mlp

@@ -424,48 +424,6 @@ cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a
     return cudaGetLastError();
 }
 
-// Weight-resident launch: clusters of N/128 CTAs (the column tiles of one
-// 128-row tile), as many clusters as can be co-resident, each walking its
-// row tiles.  A is the activation map with boxes of 128/cluster rows, B the
-// weight map with boxes of 128 rows.
-template <int EPI>
-cudaError_t launch_wres(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a, int m_tiles, int N, cudaStream_t st)
-{
-    const int nt = N / 128;
-    static int max_clusters[9] = {0};
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_wres_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             WresCfg::SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = nt;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = WresCfg::SMEM;
-    cfg.stream = st;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if (!max_clusters[nt]) {
-        cfg.gridDim = dim3(nt * num_sms_current(), 1, 1);
-        int mc = 0;
-        cudaError_t e = cudaOccupancyMaxActiveClusters(&mc, gemm_wres_kernel<EPI>, &cfg);
-        if (e != cudaSuccess) return e;
-        max_clusters[nt] = mc > 0 ? mc : 1;
-    }
-    const int ncl = m_tiles < max_clusters[nt] ? m_tiles : max_clusters[nt];
-    cfg.gridDim = dim3(ncl * nt, 1, 1);
-    a.m_tiles = m_tiles;
-    a.n_tiles = nt;
-    a.splits = 1;
-    return cudaLaunchKernelEx(&cfg, gemm_wres_kernel<EPI>, ta, tb, a);
-}
-
 // Widest N tile (256, 128, 64 or 16) that divides N.
 inline int pick_bn(int N) { return (N % 256 == 0) ? 256 : (N % 128 == 0) ? 128 : (N % 64 == 0) ? 64 : 16; }
 
@@ -524,24 +482,14 @@ static pr_status build_maps(sg_model *m)
     ok = ok && make_map(&m->tm_xi, d.xi, KIN, C, KIN, 128);
     ok = ok && make_map(&m->tm_hi[0], d.hi[0], W, C, W, 128);
     ok = ok && make_map(&m->tm_hi[1], d.hi[1], W, C, W, 128);
-    // weight-resident maps (hidden widths up to 512: K <= 512 fits the resident slice)
-    m->wres = (W <= 512);
-    if (m->wres) {
-        const uint32_t sr = (uint32_t)(128 / (W / 128));   // activation rows per CTA of a cluster
-        ok = ok && make_map(&m->tm_x0_mc, d.x0, KIN, B, KIN, sr);
-        for (int l = 0; l < L; ++l) {
-            ok = ok && make_map(&m->tm_h_mc[l], d.h[l], W, B, W, sr);
-            ok = ok && make_map(&m->tm_dz_mc[l], d.dz[l], W, B, W, sr);
-        }
-        ok = ok && make_map(&m->tm_dzo_mc, d.dzo, KIN, B, KIN, sr);
-        ok = ok && make_map(&m->tm_xi_mc, d.xi, KIN, C, KIN, sr);
-        ok = ok && make_map(&m->tm_hi_mc[0], d.hi[0], W, C, W, sr);
-        ok = ok && make_map(&m->tm_hi_mc[1], d.hi[1], W, C, W, sr);
-        ok = ok && make_map(&m->tm_w128[0], d.wb[0], KIN, W, KIN, 128);
-        for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_w128[l], d.wb[l], W, W, W, 128);
-        for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_wt128[l], d.wt[l], W, W, W, 128);
-        ok = ok && make_map(&m->tm_wt128[L], d.wt[L], KIN, W, KIN, 128);
+    // epilogue stores
+    for (int l = 0; l < L; ++l) {
+        ok = ok && make_map(&m->ts_h[l], d.h[l], W, B, W, 32);
+        ok = ok && make_map(&m->ts_g[l], d.g[l], W, B, W, 32);
+        ok = ok && make_map(&m->ts_dz[l], d.dz[l], W, B, W, 32);
     }
+    ok = ok && make_map(&m->ts_hi[0], d.hi[0], W, C, W, 32);
+    ok = ok && make_map(&m->ts_hi[1], d.hi[1], W, C, W, 32);
     if (!ok) {
         prgb::set_error("surrogate: cuTensorMapEncodeTiled unavailable or failed");
         return PR_ECUDA;
@@ -766,13 +714,9 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         a.M = (int)B; a.N = W; a.K = (l == 0) ? KIN : W; a.kb_per_split = a.K / 64;
         a.bias = d.master + d.lay[l].b_off;
         a.out = d.h[l]; a.ldo = W; a.outT = d.ht[l]; a.ldoT = d.max_batch; a.gd = d.g[l]; a.ldg = W;
-        if (m->wres) {
-            const CUtensorMap &ta = (l == 0) ? m->tm_x0_mc : m->tm_h_mc[l - 1];
-            e = launch_wres<kEpiHidden>(ta, m->tm_w128[l], a, mt, W, st);
-        } else {
-            const CUtensorMap &ta = (l == 0) ? m->tm_x0 : m->tm_h[l - 1];
-            e = launch_gemm_n<kEpiHidden>(ta, m->tm_w[l], a, mt, W, 1, st);
-        }
+        a.tma_out = 1; a.tm_out = m->ts_h[l]; a.tm_gd = m->ts_g[l];
+        const CUtensorMap &ta = (l == 0) ? m->tm_x0 : m->tm_h[l - 1];
+        e = launch_gemm_n<kEpiHidden>(ta, m->tm_w[l], a, mt, W, 1, st);
         if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) { prgb::set_error("forward: %s", cudaGetErrorString(e)); return PR_ECUDA; }
@@ -793,14 +737,10 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         a.M = (int)B; a.N = W; a.K = (l == L) ? KIN : W; a.kb_per_split = a.K / 64;
         a.gd = d.g[l - 1]; a.ldg = W;
         a.out = d.dz[l - 1]; a.ldo = W; a.outT = d.dzt[l - 1]; a.ldoT = d.max_batch;
+        a.tma_out = 1; a.tm_out = m->ts_dz[l - 1];
         a.colsum = d.colsum[l - 1];
-        if (m->wres) {
-            const CUtensorMap &ta = (l == L) ? m->tm_dzo_mc : m->tm_dz_mc[l];
-            e = launch_wres<kEpiDx>(ta, m->tm_wt128[l], a, mt, W, st);
-        } else {
-            const CUtensorMap &ta = (l == L) ? m->tm_dzo : m->tm_dz[l];
-            e = launch_gemm_n<kEpiDx>(ta, m->tm_wt[l], a, mt, W, 1, st);
-        }
+        const CUtensorMap &ta = (l == L) ? m->tm_dzo : m->tm_dz[l];
+        e = launch_gemm_n<kEpiDx>(ta, m->tm_wt[l], a, mt, W, 1, st);
         if (e != cudaSuccess) { prgb::set_error("dx: %s", cudaGetErrorString(e)); return PR_ECUDA; }
     }
     // weight gradients: dW_l = dz_l^T h_{l-1}, K = batch, split along K
@@ -890,13 +830,9 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.M = (int)mc; a.N = W; a.K = (l == 0) ? KIN : W; a.kb_per_split = a.K / 64;
             a.bias = d.master + d.lay[l].b_off;
             a.out = d.hi[l & 1]; a.ldo = W;
-            if (m->wres) {
-                const CUtensorMap &ta = (l == 0) ? m->tm_xi_mc : m->tm_hi_mc[(l - 1) & 1];
-                PR_CUDA_TRY((launch_wres<kEpiHidden>(ta, m->tm_w128[l], a, mt, W, st)));
-            } else {
-                const CUtensorMap &ta = (l == 0) ? m->tm_xi : m->tm_hi[(l - 1) & 1];
-                PR_CUDA_TRY((launch_gemm_n<kEpiHidden>(ta, m->tm_w[l], a, mt, W, 1, st)));
-            }
+            a.tma_out = 1; a.tm_out = m->ts_hi[l & 1];
+            const CUtensorMap &ta = (l == 0) ? m->tm_xi : m->tm_hi[(l - 1) & 1];
+            PR_CUDA_TRY((launch_gemm_n<kEpiHidden>(ta, m->tm_w[l], a, mt, W, 1, st)));
         }
         {
             GemmArgs a = base_args(m);

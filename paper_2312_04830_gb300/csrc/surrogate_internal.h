@@ -96,9 +96,7 @@ struct sg_model {
     CUtensorMap tm_w[SG_MAX_HIDDEN + 1], tm_wt[SG_MAX_HIDDEN + 1];
     CUtensorMap tm_x0, tm_x0t, tm_h[SG_MAX_HIDDEN], tm_ht[SG_MAX_HIDDEN], tm_dz[SG_MAX_HIDDEN],
         tm_dzt[SG_MAX_HIDDEN], tm_dzo, tm_dzot, tm_xi, tm_hi[2];
-    // weight-resident GEMM: activations in boxes of 128/cluster rows, weights in boxes of 128 rows
-    bool wres;
-    CUtensorMap tm_x0_mc, tm_h_mc[SG_MAX_HIDDEN], tm_dz_mc[SG_MAX_HIDDEN], tm_dzo_mc, tm_xi_mc, tm_hi_mc[2];
-    CUtensorMap tm_w128[SG_MAX_HIDDEN + 1], tm_wt128[SG_MAX_HIDDEN + 1];
+    // epilogue TMA-store maps (32-row boxes): h, GeLU'(z), dz, inference h
+    CUtensorMap ts_h[SG_MAX_HIDDEN], ts_g[SG_MAX_HIDDEN], ts_dz[SG_MAX_HIDDEN], ts_hi[2];
     std::vector<void *> allocs;
 };

@@ -61,14 +61,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Wait for phase `parity` of `bar` to complete; false after ~`max_cycles`.
+// try_wait suspends the thread in hardware until the phase completes or a
+// short system time limit passes, so the hot path just polls again; only a
+// wait that has already lasted ~1M cycles backs off with nanosleep.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long max_cycles = 4000000000LL)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > max_cycles) return false;
-        __nanosleep(32);
+        const long long dt = clock64() - t0;
+        if (dt > max_cycles) return false;
+        if (dt > 1000000LL) __nanosleep(256);
     }
 }
 
@@ -89,48 +93,23 @@ __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *t
         : "memory");
 }
 
-// Multicast variant: the box lands at the same shared-memory offset in every
-// CTA of the cluster named in `cta_mask`, and completes `bytes` on the
-// mbarrier at the same offset in each of them.
-__device__ __forceinline__ void tma_load_2d_multicast(void *smem_dst, const CUtensorMap *tm, uint64_t *bar, int c0,
-                                                      int c1, uint16_t cta_mask)
+// 2-D tiled store of a shared-memory box (laid out as the tensor map's box,
+// swizzle included) to global memory at element coordinates (c0, c1); rows or
+// columns outside the tensor are not written.  Tracked by bulk groups.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *tm, const void *smem_src, int c0, int c1)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;"
-        ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1),
-        "h"(cta_mask)
-        : "memory");
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+                 ::"l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(smem_src)), "r"(c0), "r"(c1)
+                 : "memory");
 }
 
-// ------------------------------------------------------------- clusters
-__device__ __forceinline__ uint32_t cluster_ctarank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t cluster_id_x()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
+// All committed bulk stores of this thread have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t nclusters_x()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
-
-// Every thread of every CTA of the cluster arrives, then waits for all.
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n"
-                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
+// All committed bulk stores of this thread have completed.
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // --------------------------------------------------------------- tcgen05
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols)
@@ -173,16 +152,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
-}
-
-// Arrive once on the mbarrier at this offset in every CTA of `cta_mask` when
-// this thread's previously issued MMAs have completed.
-__device__ __forceinline__ void mma_commit_multicast(uint64_t *bar, uint16_t cta_mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-        ::"r"(smem_u32(bar)), "h"(cta_mask)
-        : "memory");
 }
 
 // 32 TMEM lanes x 16 consecutive 32-bit columns: thread t of the warp gets
