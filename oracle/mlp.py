@@ -6,7 +6,10 @@ activations trained with PyTorch; the configuration here has 11 inputs
 (log rho, Z, h, log cp, log mu, log lambda), inputs and outputs standardised.
 
 Definitions (plain, unfused):
-  * GeLU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2   (exact form)
+  * GeLU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2   (exact form, "erf")
+    or Hendrycks & Gimpel's tanh form ("tanh"), Phi(z) replaced by
+    (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) / 2; the paper names GeLU
+    without saying which, the tensor-core path computes the tanh form
   * layer l:  z_l = W_l h_{l-1} + b_l,  h_l = GeLU(z_l)  (linear last layer)
   * loss on standardised targets s:  L = mean_{b, j} (yhat_bj - s_bj)^2
     (the targets are logarithms or scaled values, so squared errors are
@@ -32,12 +35,23 @@ def _erf(x):
     return np.vectorize(math.erf, otypes=[np.float64])(x)
 
 
-def gelu(z):
+TANH_C = math.sqrt(2.0 / math.pi)
+TANH_A = 0.044715
+
+
+def gelu(z, form="erf"):
+    if form == "tanh":
+        return 0.5 * z * (1.0 + np.tanh(TANH_C * (z + TANH_A * z ** 3)))
     return 0.5 * z * (1.0 + _erf(z / SQRT2))
 
 
-def gelu_grad(z):
-    """d/dz [z Phi(z)] = Phi(z) + z phi(z)."""
+def gelu_grad(z, form="erf"):
+    """d/dz GeLU(z): Phi(z) + z phi(z) for the exact form; for the tanh
+    form, with u = c (z + a z^3) and t = tanh u,
+    (1 + t) / 2 + z (1 - t^2) c (1 + 3 a z^2) / 2."""
+    if form == "tanh":
+        t = np.tanh(TANH_C * (z + TANH_A * z ** 3))
+        return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * TANH_C * (1.0 + 3.0 * TANH_A * z * z)
     return 0.5 * (1.0 + _erf(z / SQRT2)) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
 
 
@@ -51,13 +65,13 @@ def init_params(sizes, seed=0):
     return params
 
 
-def forward(params, X):
+def forward(params, X, form="erf"):
     """X [B, n_in] -> (yhat [B, n_out], cache of (z_l, h_l))."""
     h = np.asarray(X, dtype=np.float64)
     cache = [(None, h)]
     for li, (W, b) in enumerate(params):
         z = h @ W.T + b
-        h = gelu(z) if li + 1 < len(params) else z
+        h = gelu(z, form) if li + 1 < len(params) else z
         cache.append((z, h))
     return h, cache
 
@@ -66,7 +80,7 @@ def loss(yhat, s):
     return float(np.mean((yhat - s) ** 2))
 
 
-def backward(params, cache, yhat, s):
+def backward(params, cache, yhat, s, form="erf"):
     """Gradients of `loss` w.r.t. every (W_l, b_l)."""
     B, J = yhat.shape
     dz = 2.0 * (yhat - s) / (B * J)
@@ -77,7 +91,7 @@ def backward(params, cache, yhat, s):
         grads[li] = (dz.T @ h_prev, dz.sum(axis=0))
         if li > 0:
             dh = dz @ W
-            dz = dh * gelu_grad(cache[li][0])
+            dz = dh * gelu_grad(cache[li][0], form)
     return grads
 
 

@@ -77,9 +77,9 @@ def test_gradients_match_oracle(ctx, orc, species, cuda, width, layers, batch):
     sizes = [11] + [width] * layers + [6]
     params = unflatten(sg.get_params(), sizes)
     s_in, s_out = standardise(x, y, norm)
-    yhat, cache = omlp.forward(params, s_in)
+    yhat, cache = omlp.forward(params, s_in, "tanh")
     l_orc = omlp.loss(yhat, s_out)
-    grads = omlp.backward(params, cache, yhat, s_out)
+    grads = omlp.backward(params, cache, yhat, s_out, "tanh")
     assert float(loss.item()) == pytest.approx(l_orc, rel=2e-2)
     g_orc = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
     off = 0
@@ -130,7 +130,7 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
     norm = sg.get_normalization().astype(np.float64)
     params = unflatten(sg.get_params(), [11, 512, 512, 512, 512, 6])
     s_in, _ = standardise(x[:, :n], y[:, :n], norm)
-    yhat, _ = omlp.forward(params, s_in)
+    yhat, _ = omlp.forward(params, s_in, "tanh")
     s_gpu = (omlp.output_targets(out) - norm[22:28]) / norm[28:34]
     err = np.abs(s_gpu - yhat)
     print("standardised output error: median", np.median(err), "max", err.max())

@@ -19,14 +19,30 @@ def test_gelu_identities():
     assert mlp.gelu(np.array([1.0]))[0] == pytest.approx(0.8413447460685429, rel=1e-12)
 
 
-def test_gelu_grad_matches_finite_difference():
+def test_gelu_tanh_form_against_exact():
+    """The tanh form keeps GeLU(0) = 0 and the odd-part identity (tanh is
+    odd) and stays within 5e-4 of the exact form everywhere (its largest
+    deviation, 4.7e-4, is near |z| = 2.7); a wrong cubic coefficient or
+    scale would break that bound."""
+    z = np.linspace(-8, 8, 16001)
+    t = mlp.gelu(z, "tanh")
+    assert mlp.gelu(np.array([0.0]), "tanh")[0] == 0.0
+    np.testing.assert_allclose(mlp.gelu(-z, "tanh"), t - z, atol=1e-14)
+    dev = np.abs(t - mlp.gelu(z))
+    assert dev.max() < 5e-4 and dev.max() > 4e-4
+    assert mlp.gelu(np.array([12.0]), "tanh")[0] == pytest.approx(12.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("form", ["erf", "tanh"])
+def test_gelu_grad_matches_finite_difference(form):
     z = np.linspace(-5, 5, 101)
     h = 1e-6
-    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
-    np.testing.assert_allclose(mlp.gelu_grad(z), fd, rtol=1e-8, atol=1e-10)
+    fd = (mlp.gelu(z + h, form) - mlp.gelu(z - h, form)) / (2 * h)
+    np.testing.assert_allclose(mlp.gelu_grad(z, form), fd, rtol=1e-8, atol=1e-10)
 
 
-def test_backward_matches_finite_difference():
+@pytest.mark.parametrize("form", ["erf", "tanh"])
+def test_backward_matches_finite_difference(form):
     """Every gradient of a tiny 5-layer net against central differences of
     the loss (FP64, step 1e-6)."""
     sizes = [11, 7, 6, 5, 4, 6]
@@ -34,8 +50,8 @@ def test_backward_matches_finite_difference():
     rng = np.random.default_rng(4)
     X = rng.normal(size=(9, 11))
     s = rng.normal(size=(9, 6))
-    yhat, cache = mlp.forward(params, X)
-    grads = mlp.backward(params, cache, yhat, s)
+    yhat, cache = mlp.forward(params, X, form)
+    grads = mlp.backward(params, cache, yhat, s, form)
     h = 1e-6
     for li, (W, b) in enumerate(params):
         for k, P in enumerate((W, b)):
@@ -43,9 +59,9 @@ def test_backward_matches_finite_difference():
             for idx in range(0, flat.size, max(1, flat.size // 7)):
                 old = flat[idx]
                 flat[idx] = old + h
-                lp = mlp.loss(mlp.forward(params, X)[0], s)
+                lp = mlp.loss(mlp.forward(params, X, form)[0], s)
                 flat[idx] = old - h
-                lm = mlp.loss(mlp.forward(params, X)[0], s)
+                lm = mlp.loss(mlp.forward(params, X, form)[0], s)
                 flat[idx] = old
                 fd = (lp - lm) / (2 * h)
                 g = grads[li][k].reshape(-1)[idx]
