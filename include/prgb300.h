@@ -62,6 +62,7 @@ typedef enum { PR_FP64 = 0, PR_FP32 = 1, PR_MIXED = 2 } pr_precision;
                                         critical-point values 0.457235529 / 0.077796074 */
 #define PR_FLAG_TRANSPORT_XAVG    2  /* mu, lambda = mole-fraction average of pure-species Chung
                                         values instead of Chung's mixture rules */
+#define PR_FLAG_NEWTON_FP64_ONLY  4  /* PR_FP64 inversion without the FP32 warm start */
 
 #define PR_MAX_SPECIES 32
 
@@ -106,7 +107,13 @@ pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n,
  * inside the bracket [60, 5000] K, starting from T_guess (clipped to the
  * bracket).  A Newton step that leaves the current bracket, or follows a step
  * that did not halve |f|, is replaced by bisection.  Converged when
- * |dT| <= rtol T or |f| <= rtol max(|h*|, cp T).
+ * |dT| <= rtol T or |f| <= rtol max(|h*|, cp T).  PR_FP64 first runs plain
+ * Newton on the FP32 thermodynamics (at most 8 steps, until a step is below
+ * 1e-5 T) and starts the FP64 iteration from that root, or from T_guess when
+ * the FP32 steps fail or do not settle; the FP64 iteration alone decides
+ * convergence, so the result meets the same FP64 tolerance
+ * (PR_FLAG_NEWTON_FP64_ONLY turns the warm start off).  iters counts the
+ * FP64 iterations.
  *   hstar, p, T_guess [n]; Y [N][ldY]; T_out [n] output;
  *   cell_status [n] (required), iters [n] (NULL allowed);
  *   max_iter in 1..1000; rtol in [1e-15, 1e-2].

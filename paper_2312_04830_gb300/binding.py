@@ -20,6 +20,7 @@ PR_FP64, PR_FP32, PR_MIXED = 0, 1, 2
 PRECISIONS = {"fp64": PR_FP64, "fp32": PR_FP32, "mixed": PR_MIXED}
 PR_FLAG_PRINTED_CONSTANTS = 1
 PR_FLAG_TRANSPORT_XAVG = 2
+PR_FLAG_NEWTON_FP64_ONLY = 4
 OUTPUTS = ("rho", "Z", "h", "cp", "mu", "lambda")
 
 CELL_STATUS = {0: "ok", 1: "newton_maxit", 2: "h_out_of_range", 3: "no_root", 4: "bad_input", 5: "ambiguous"}
@@ -92,7 +93,8 @@ def _prec(p) -> int:
 class PropertyContext:
     """A species table resident on the current CUDA device (pr_create)."""
 
-    def __init__(self, species, printed_constants: bool = False, transport_xavg: bool = False):
+    def __init__(self, species, printed_constants: bool = False, transport_xavg: bool = False,
+                 newton_fp64_only: bool = False):
         self._keep = {}
         arr = lambda name, a: self._keep.setdefault(name, np.ascontiguousarray(a, dtype=np.float64))
         n = int(species.n)
@@ -100,7 +102,8 @@ class PropertyContext:
         t = _SpeciesTable()
         t.n_species = n
         t.flags = (PR_FLAG_PRINTED_CONSTANTS if printed_constants else 0) | \
-                  (PR_FLAG_TRANSPORT_XAVG if transport_xavg else 0)
+                  (PR_FLAG_TRANSPORT_XAVG if transport_xavg else 0) | \
+                  (PR_FLAG_NEWTON_FP64_ONLY if newton_fp64_only else 0)
         for f in ("W", "Tc", "pc", "omega", "Vc", "dipole", "kappa", "T_mid"):
             setattr(t, f, arr(f, getattr(species, f)).ctypes.data)
         t.nasa_lo = arr("nasa_lo", species.nasa_lo).ctypes.data

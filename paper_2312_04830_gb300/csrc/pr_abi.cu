@@ -147,7 +147,7 @@ pr_status pr_create(const pr_species_table *tbl, pr_ctx **out)
     PR_CHECK_ARG(tbl->W && tbl->Tc && tbl->pc && tbl->omega && tbl->Vc && tbl->dipole && tbl->kappa &&
                      tbl->nasa_lo && tbl->nasa_hi && tbl->T_mid,
                  "pr_create: null species array");
-    PR_CHECK_ARG((tbl->flags & ~(PR_FLAG_PRINTED_CONSTANTS | PR_FLAG_TRANSPORT_XAVG)) == 0,
+    PR_CHECK_ARG((tbl->flags & ~(PR_FLAG_PRINTED_CONSTANTS | PR_FLAG_TRANSPORT_XAVG | PR_FLAG_NEWTON_FP64_ONLY)) == 0,
                  "pr_create: unknown flags 0x%x", tbl->flags);
     HostTable *h = new (std::nothrow) HostTable();
     if (!h) { prgb::set_error("pr_create: host allocation failed"); return PR_ENOMEM; }
@@ -306,13 +306,15 @@ pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n, const void *hst
         NewtonArgs<double> a{n, ldY, (const double *)hstar, (const double *)p, (const double *)Y,
                              (const double *)T_guess, (double *)T_out, cell_status, iters,
                              (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64,
-                             ctx->n_species, ctx->flags, max_iter, rtol};
+                             ctx->n_species, ctx->flags, max_iter, rtol,
+                             (const SpeciesRec<float> *)ctx->d_sp32, ctx->d_pair32, ctx->d_kij32};
         if (ctx->ns_pad == 9) launch_newton<double, double, 9>(a, kij, occ, ctx->num_sms, st);
         else launch_newton<double, double, 32>(a, kij, occ, ctx->num_sms, st);
     } else {
         NewtonArgs<float> a{n, ldY, (const float *)hstar, (const float *)p, (const float *)Y, (const float *)T_guess,
                             (float *)T_out, cell_status, iters, (const SpeciesRec<float> *)ctx->d_sp32,
-                            ctx->d_pair32, ctx->d_kij32, ctx->n_species, ctx->flags, max_iter, rtol};
+                            ctx->d_pair32, ctx->d_kij32, ctx->n_species, ctx->flags, max_iter, rtol,
+                            nullptr, nullptr, nullptr};
         if (prec == PR_FP32) {
             if (ctx->ns_pad == 9) launch_newton<float, float, 9>(a, kij, occ, ctx->num_sms, st);
             else launch_newton<float, float, 32>(a, kij, occ, ctx->num_sms, st);

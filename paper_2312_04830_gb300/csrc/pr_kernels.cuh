@@ -93,6 +93,9 @@ struct NewtonArgs {
     const Real *pair, *kij;
     int N, flags, max_iter;
     double rtol;
+    // FP32 tables for the warm start of the FP64 inversion (FP64 kernel only)
+    const SpeciesRec<float> *sp32;
+    const float *pair32, *kij32;
 };
 
 // h(T) and cp(T) of a cell at fixed p and composition; status 0 or an error.
@@ -108,11 +111,43 @@ __device__ __noinline__ int eval_h(const Comp<Real, NS> &c, double T, Real p, co
     return kOk;
 }
 
+// Warm start of the FP64 inversion: plain Newton on the FP32 thermodynamics
+// from T0 until a step is below 1e-5 T (at most 8 steps).  Returns the FP32
+// root, or T0 when a step fails, leaves [kTLo, kTHi] or does not settle (the
+// FP64 iteration then starts from T0 as it would without a warm start).
+template <int NS, bool KIJ>
+__device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, double T0, double hs, double p,
+                                               const SpeciesRec<float> *sp, const float *kij)
+{
+    Comp<float, NS> c;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) c.x[k] = (float)c64.x[k];
+    c.Wbar = (float)c64.Wbar;
+    c.bm = (float)c64.bm;
+    double T = T0;
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        double h, cp;
+        if (eval_h<float, float, NS, KIJ>(c, T, (float)p, sp, kij, h, cp) || !(cp > 0)) return T0;
+        const double Tn = T - (h - hs) / cp;
+        if (!(Tn > kTLo && Tn < kTHi)) return T0;
+        const bool done = fabs(Tn - T) <= 1e-5 * Tn;
+        T = Tn;
+        if (done) return T;
+    }
+    return T0;
+}
+
 template <typename Real, typename RZ, int NS, bool KIJ>
 __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a)
 {
     __shared__ Smem<Real, NS, KIJ> s;
     stage<Real, NS, KIJ>(s, a.sp, a.pair, a.kij);
+    // FP64 inversion: FP32 tables for the warm start
+    constexpr bool kFp64 = sizeof(Real) == 8;
+    __shared__ Smem<float, NS, KIJ> s32[1];
+    const bool warm = kFp64 && !(a.flags & PR_FLAG_NEWTON_FP64_ONLY);
+    if (warm) stage<float, NS, KIJ>(s32[0], a.sp32, a.pair32, a.kij32);
     // FP32 thermodynamics resolve h to ~1e-7 of its scale: floor the tolerance
     const double rtol = (sizeof(Real) == 4) ? fmax(a.rtol, 2e-6) : a.rtol;
     const double jump_tol = (sizeof(Real) == 4) ? 2e-5 : 1e-6;
@@ -130,6 +165,9 @@ __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a
             double lo = kTLo, hi = kTHi;
             bool lo_done = false, hi_done = false;   // endpoint h evaluated (range checked)
             double T = fmin(fmax(Tg, lo), hi);
+            if constexpr (kFp64) {
+                if (warm) T = warm_start_fp32<NS, KIJ>(c, T, hs, (double)p, s32[0].sp, s32[0].kij);
+            }
             double fprev = INFINITY;
             st = kMaxIt;
             Tres = T;
