@@ -39,7 +39,11 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 flops per cell of the FP64 kernels, from ncu instruction counts
 # (2 x DFMA + DADD + DMUL per launch / cells) on the 128^3 flame-vortex field
-FP64_FLOPS_PER_CELL = {"props_fp64": 1814.0, "newton_fp64": 2767.0}
+# (profiles/fp64_kernels_counts_flame_vortex_128.md)
+FP64_FLOPS_PER_CELL = {"props_fp64": 1815.0, "newton_fp64": 1469.0}
+# DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
+# / cells) of the same capture; a full launch moves this x its cells
+TRAFFIC_BYTES_PER_CELL = {"props_fp64": 125.9, "newton_fp64": 108.3}
 # surrogate: 2 x (11*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=11, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
@@ -422,7 +426,8 @@ def run_ours(args):
     d = roof_paths[dom]
     if "fp64_tflops" in d:
         roofline = {"bound": "alu", "kernel": dom, "achieved": d["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": d["fp64_frac"], "traffic": None,
+                    "unit": "TFLOP/s", "frac": d["fp64_frac"],
+                    "traffic": TRAFFIC_BYTES_PER_CELL[dom] * n if dom in TRAFFIC_BYTES_PER_CELL else None,
                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (unit counts and clock)"}
     elif "tensor_tflops" in d:
         roofline = {"bound": "tensor", "kernel": dom, "achieved": d["tensor_tflops"], "peak": bf16_peak,
