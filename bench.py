@@ -397,6 +397,25 @@ def run_ours(args):
     value = evals / (elapsed_ms * 1e-3)
     fb_frac = float(fb.float().mean()) if sg is not None else None
 
+    # error of the reduced-precision paths on the field against the FP64 PR
+    # path's outputs of the last timed step (rel RMS, p99, max per property)
+    field_err = None
+    if rank == 0:
+        from paper_2312_04830_gb300 import train as TR
+        ref = out64.float()
+        ok = torch.all(torch.isfinite(ref), dim=0)
+        field_err = {"props_fp32": TR.relative_rms(out32[:, ok], ref[:, ok])}
+        if sg is not None:
+            field_err["surrogate_bf16"] = TR.relative_rms(outsg[:, ok], ref[:, ok])
+            # the same on the cells that pass the training data's constraints
+            # (dense mu, lambda at least half the dilute values)
+            dil, _ = ctx.props(T64, torch.ones_like(p64), Y64, "fp64", outputs=("mu", "lambda"))
+            phys = ok & (out64[4] >= 0.5 * dil[4]) & (out64[5] >= 0.5 * dil[5])
+            del dil
+            field_err["surrogate_bf16_physical"] = TR.relative_rms(outsg[:, phys], ref[:, phys])
+            field_err["physical_cells"] = int(phys.sum())
+        field_err["cells"] = int(ok.sum())
+
     # ----------------------------------------------------------- e2e
     e2e = None
     if not args.no_e2e:
@@ -445,6 +464,7 @@ def run_ours(args):
                    "cells": n, "paths": paths, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (FP64 inputs 1.5 GB per path call)"},
         "paths": roof_paths,
+        "field_error_vs_pr_fp64": field_err,
         "roofline": roofline,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,

@@ -128,9 +128,11 @@ pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n,
 /* ======================================================================
  * Surrogate MLP (Sec. 4: the DNN that replaces the property evaluation).
  * Inputs per cell: [log T, p, Y_1..Y_9] (9 species, the context's order);
- * outputs: [rho, Z, h, cp, mu, lambda] learned as [log rho, Z, h, log cp,
- * log mu, log lambda], inputs and outputs standardised with statistics of the
- * training pool.  Hidden layers use GeLU (Sec. 4.1) in its tanh form,
+ * outputs: [rho, Z, h, cp, mu, lambda] learned as [log rho, Z, h - h_ig,
+ * log cp, log mu, log lambda], inputs and outputs standardised with statistics
+ * of the training pool; h_ig(T, Y) = sum_k Y_k h_k(T) / W_k is the NASA-7
+ * ideal-gas enthalpy (Sec. 2), evaluated exactly and added to the network's
+ * departure.  Checkpoints carry format 2 (this target).  Hidden layers use GeLU (Sec. 4.1) in its tanh form,
  * 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).  Forward and
  * backward GEMMs run on the tensor cores (BF16 operands, FP32 accumulation);
  * master weights and Adam moments are FP32.

@@ -72,6 +72,8 @@ def lib():
             vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
             L.orc_props.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32]
             L.orc_props.restype = None
+            L.orc_h_ideal.argtypes = [vp, i64, vp, vp, vp]
+            L.orc_h_ideal.restype = None
             L.orc_diagnose.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
             L.orc_diagnose.restype = None
             L.orc_T_from_h.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32]
@@ -134,6 +136,15 @@ def props(sp, T, p, Y, threads: int = 0, **kw):
     st = np.empty(n, dtype=np.int32)
     lib().orc_props(tb.ref, n, _ptr(T), _ptr(p), _ptr(Y), _ptr(out), _ptr(st), int(threads))
     return out, st
+
+
+def h_ideal(sp, T, Y, **kw):
+    """Mass-specific ideal-gas enthalpy sum_k Y_k h_k(T) / W_k [J/kg] (NASA-7)."""
+    tb = sp if isinstance(sp, Table) else Table(sp, **kw)
+    T, _, Y = _soa(T, 0.0, Y, tb.n)
+    h = np.empty(T.size)
+    lib().orc_h_ideal(tb.ref, T.size, _ptr(T), _ptr(Y), _ptr(h))
+    return h
 
 
 def diagnose(sp, T, p, Y, **kw):

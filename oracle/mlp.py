@@ -122,12 +122,16 @@ def input_features(T, p, Y):
     return np.column_stack([np.log(T), p, np.asarray(Y).T])
 
 
-def output_targets(props):
-    """props [6, B] = rho, Z, h, cp, mu, lambda -> [log rho, Z, h, log cp, log mu, log lambda], [B, 6]."""
+def output_targets(props, h_ig):
+    """props [6, B] = rho, Z, h, cp, mu, lambda and the ideal-gas enthalpy
+    h_ig [B] of the same states -> [log rho, Z, h - h_ig, log cp, log mu,
+    log lambda], [B, 6].  The network learns the enthalpy departure; the
+    ideal-gas part (NASA-7, exact) is added back to its output."""
     rho, Z, h, cp, mu, lam = props
-    return np.column_stack([np.log(rho), Z, h, np.log(cp), np.log(mu), np.log(lam)])
+    return np.column_stack([np.log(rho), Z, h - h_ig, np.log(cp), np.log(mu), np.log(lam)])
 
 
-def targets_to_props(q):
+def targets_to_props(q, h_ig):
     """Inverse of output_targets: [B, 6] -> [6, B]."""
-    return np.vstack([np.exp(q[:, 0]), q[:, 1], q[:, 2], np.exp(q[:, 3]), np.exp(q[:, 4]), np.exp(q[:, 5])])
+    return np.vstack([np.exp(q[:, 0]), q[:, 1], q[:, 2] + h_ig, np.exp(q[:, 3]), np.exp(q[:, 4]),
+                      np.exp(q[:, 5])])

@@ -493,6 +493,22 @@ void orc_props(const orc_species *sp, int64_t n, const double *T, const double *
     (void)nthreads;
 }
 
+/* Mass-specific ideal-gas enthalpy h_ig = sum_k Y_k h_k(T) / W_k [J/kg] of n
+ * cells (NASA-7, the ideal-gas part of the enthalpy, Sec. 2), SoA as
+ * orc_props. */
+void orc_h_ideal(const orc_species *sp, int64_t n, const double *T, const double *Y, double *h)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < sp->N; ++k) {
+            double cpR, hRT;
+            nasa7(sp->nasa_lo + 7 * k, sp->nasa_hi + 7 * k, sp->T_mid[k], T[i], &cpR, &hRT, NULL);
+            s += Y[(int64_t)k * n + i] * hRT * ORC_R * T[i] / (sp->W[k] * 1e-3);
+        }
+        h[i] = s;
+    }
+}
+
 /* Diagnostics for n cells (serial). */
 void orc_diagnose(const orc_species *sp, int64_t n, const double *T, const double *p, const double *Y,
                   double *out, int32_t *status, orc_diag *diag)

@@ -57,6 +57,7 @@ struct GemmArgs {
     float *out6;              // kEpiOutPhys: [6][ld6]
     int64_t ld6;
     const float *out_mean, *out_std;   // [6] de-standardisation
+    const float *add_h;       // kEpiOutPhys: per-row term added to output 2 (h) after de-standardisation
     const float *target;      // kEpiOutLoss: standardised targets [6][ldt]
     int64_t ldt;
     float loss_scale;         // d loss / d y = loss_scale * (y - target)
@@ -281,7 +282,8 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
 #pragma unroll
                     for (int jj = 0; jj < 6; ++jj) {
                         const float sv = v[jj] + bias[jj];
-                        const float qv = sv * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
+                        float qv = sv * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
+                        if (jj == 2 && a.add_h) qv += __ldg(a.add_h + m);
                         a.out6[(int64_t)jj * a.ld6 + m] = (jj == 1 || jj == 2) ? qv : __expf(qv);
                     }
                 }

@@ -3,8 +3,11 @@
 // states outside the training hull.
 //
 // Network: 11 inputs [log T, p, Y_1..Y_9] -> H hidden layers of width W with
-// GeLU -> 6 outputs [log rho, Z, h, log cp, log mu, log lambda]; inputs and
-// outputs standardised with statistics of the training pool.  Layer l computes
+// GeLU -> 6 outputs [log rho, Z, h - h_ig, log cp, log mu, log lambda]; inputs
+// and outputs standardised with statistics of the training pool.  The network
+// learns the enthalpy departure from the ideal-gas enthalpy h_ig(T, Y) =
+// sum_k Y_k h_k(T) / W_k (NASA-7, Sec. 2), which is evaluated exactly (FP32)
+// and added back to its output.  Layer l computes
 // z = W_l h + b_l with BF16 operands and FP32 accumulation (mlp_gemm.cuh);
 // master weights and Adam moments are FP32.
 //
@@ -57,14 +60,38 @@ __device__ __forceinline__ void features(const float *x, int64_t ldx, int64_t i,
     for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
 }
 
-// Targets from raw properties: [log rho, Z, h, log cp, log mu, log lambda].
-__device__ __forceinline__ void targets(const float *y, int64_t ldy, int64_t i, float (&q)[NOUT])
+// Mass-specific ideal-gas enthalpy sum_k Y_k h_k(T) / W_k [J/kg] from the
+// NASA-7 records (molar h = R (a1 T + a2 T^2/2 + ... + a5 T^5/5 + a6)).
+__device__ __forceinline__ float h_ideal(float T, const float (&Y)[9], const void *sp32)
+{
+    const SpeciesRec<float> *sp = static_cast<const SpeciesRec<float> *>(sp32);
+    float h = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float *e = (T < __ldg(&sp[k].T_mid)) ? sp[k].h_lo : sp[k].h_hi;
+        float hk = __ldg(e + 4);
+#pragma unroll
+        for (int j = 3; j >= 0; --j) hk = fmaf(hk, T, __ldg(e + j));
+        hk = fmaf(hk, T, __ldg(e + 5));
+        h = fmaf(Y[k] * __ldg(&sp[k].inv_W), hk, h);
+    }
+    return h;
+}
+
+// Targets from raw properties and inputs x = [T, p, Y_1..Y_9]:
+// [log rho, Z, h - h_ig(T, Y), log cp, log mu, log lambda].
+__device__ __forceinline__ void targets(const float *x, int64_t ldx, const float *y, int64_t ldy, int64_t i,
+                                        const void *sp32, float (&q)[NOUT])
 {
 #pragma unroll
     for (int j = 0; j < NOUT; ++j) {
         const float v = __ldg(y + (int64_t)j * ldy + i);
         q[j] = (j == 1 || j == 2) ? v : logf(v);
     }
+    float Yk[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Yk[k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
+    q[2] -= h_ideal(__ldg(x + i), Yk, sp32);
 }
 
 // ------------------------------------------------------------ init params
@@ -105,7 +132,8 @@ __global__ void refresh_bf16_kernel(SgDev d)
 // ----------------------------------------------------------- normalization
 // Per-block partial sums (FP64) of the 17 features / targets: sum, sum of
 // squares, min, max.
-__global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, const float *y, int64_t ldy, double *part)
+__global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, const float *y, int64_t ldy,
+                                    const void *sp32, double *part)
 {
     double s[NSTAT], s2[NSTAT], mn[NSTAT], mx[NSTAT];
     double cnt = 0;
@@ -114,7 +142,7 @@ __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, cons
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float f[NIN], q[NOUT];
         features(x, ldx, i, f);
-        targets(y, ldy, i, q);
+        targets(x, ldx, y, ldy, i, sp32, q);
         bool fin = true;
 #pragma unroll
         for (int k = 0; k < NSTAT; ++k) fin = fin && isfinite((k < NIN) ? f[k] : q[k - NIN]);
@@ -201,7 +229,7 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
         if (sample_seed != 0 || n_pool != B) src = (int64_t)(splitmix64(sample_seed ^ ((uint64_t)r * 0xD1B54A32D192ED03ull)) % (uint64_t)n_pool);
         float f[NIN], q[NOUT];
         features(x, ldx, src, f);
-        targets(y, ldy, src, q);
+        targets(x, ldx, y, ldy, src, d.sp32, q);
         float v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = (k < NIN) ? (f[k] - nm[k]) / nm[NIN + k] : 0.f;
@@ -239,6 +267,10 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
             }
         }
         store_row16_bf16(d.xi + r * KIN, v);
+        float Yk[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Yk[k] = f[2 + k];
+        d.hig[r] = h_ideal(__ldg(T + i), Yk, d.sp32);
         if (flags) flags[i] = out ? 1 : 0;
         if (out) list[atomicAdd(count, 1u)] = (int32_t)r;
     }
@@ -573,6 +605,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     d.width = m->width;
     d.hidden = m->hidden;
     d.max_batch = m->max_batch;
+    d.sp32 = ctx->d_sp32;
     const int W = m->width, L = m->hidden;
     const int64_t B = m->max_batch, C = m->chunk;
     cudaError_t e = cudaSuccess;
@@ -641,6 +674,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     alloc((void **)&m->d_err, 4);
     alloc((void **)&m->d_normpart, (size_t)m->norm_blocks * (NSTAT + 1) * 4 * 8);
     alloc((void **)&d.xi, C * KIN * 2);
+    alloc((void **)&d.hig, C * 4);
     alloc((void **)&d.hi[0], C * W * 2);
     alloc((void **)&d.hi[1], C * W * 2);
     alloc((void **)&m->d_list, C * 4);
@@ -735,7 +769,7 @@ pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, in
 {
     PR_CHECK_ARG(m && x && y && n > 0 && ldx >= n && ldy >= n, "surrogate_fit_normalization: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->d_normpart);
+    norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->dev.sp32, m->d_normpart);
     norm_final_kernel<<<1, 32, 0, st>>>(m->norm_blocks, m->d_normpart, m->dev.norm);
     PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
@@ -880,6 +914,7 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.bias = d.master + d.lay[L].b_off;
             a.out6 = out + r0; a.ld6 = ldo;
             a.out_mean = d.norm + 2 * NIN; a.out_std = d.norm + 2 * NIN + NOUT;
+            a.add_h = d.hig;
             PR_CUDA_TRY((launch_gemm<16, kEpiOutPhys>(m->tm_hi[(L - 1) & 1], m->tm_w[L], a, mt, 1, 1, st)));
         }
         // FP64 Peng-Robinson for the cells outside the training hull
@@ -925,7 +960,8 @@ pr_status surrogate_save(const sg_model *m, const char *path)
     FILE *f = fopen(path, "wb");
     if (!f) { prgb::set_error("surrogate_save: cannot open %s", path); return PR_EINVAL; }
     const char magic[4] = {'P', 'R', 'S', 'G'};
-    const int32_t hdr[4] = {1, m->width, m->hidden, 0};
+    // format 2: the enthalpy output is the departure from the ideal-gas enthalpy
+    const int32_t hdr[4] = {2, m->width, m->hidden, 0};
     const int64_t step = m->step;
     bool ok = fwrite(magic, 1, 4, f) == 4 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&step, 8, 1, f) == 1 &&
               fwrite(&n, 8, 1, f) == 1 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
@@ -944,7 +980,7 @@ pr_status surrogate_load(sg_model *m, const char *path)
     int64_t step = 0, n = 0;
     bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "PRSG", 4) == 0 && fread(hdr, 4, 4, f) == 4 &&
               fread(&step, 8, 1, f) == 1 && fread(&n, 8, 1, f) == 1;
-    ok = ok && hdr[0] == 1 && hdr[1] == m->width && hdr[2] == m->hidden && n == m->dev.n_master;
+    ok = ok && hdr[0] == 2 && hdr[1] == m->width && hdr[2] == m->hidden && n == m->dev.n_master;
     std::vector<float> buf;
     if (ok) {
         buf.resize(3 * n + SG_NORM_FLOATS);

@@ -43,6 +43,8 @@ struct SgDev {
     float *loss_part;                       // [B/128]
     // inference chunk buffers
     __nv_bfloat16 *xi, *hi[2];
+    float *hig;                             // ideal-gas enthalpy of the chunk's cells [chunk]
+    const void *sp32;                       // the context's FP32 species records (NASA-7 data)
 };
 
 struct ParamRef {

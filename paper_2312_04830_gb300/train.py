@@ -65,9 +65,10 @@ def relative_rms(pred, ref):
         if nm == "h":
             s = torch.clamp(s, min=float(sh))
         e = (pred[j] - ref[j]) / s
+        a = torch.abs(e[:1 << 24]).float()
         out[nm] = {"rel_rms": float(torch.sqrt(torch.mean(e * e))),
-                   "p99": float(torch.quantile(torch.abs(e[:1 << 24]).float(), 0.99)),
-                   "max": float(torch.max(torch.abs(e)))}
+                   "p50": float(torch.quantile(a, 0.5)), "p99": float(torch.quantile(a, 0.99)),
+                   "max": float(torch.max(torch.abs(e))), "frac_over_1pct": float(torch.mean((a > 0.01).float()))}
     return out
 
 

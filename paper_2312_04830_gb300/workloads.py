@@ -17,7 +17,7 @@ Table 1 and Sec. 3.3; the paper's CFD data are not available):
   flame-sheet profile, p = 10 MPa.
 * ``newton_targets``     -- the perturbed temperatures whose enthalpies feed the
   T(h, p, Y) inversion.
-* ``training_states``    -- half uniform cells, half flame-sheet states plus noise.
+* ``training_states``    -- half uniform cells, half flame-sheet states (half of them with noise).
 * ``serving_trace``      -- Poisson arrivals of uneven-size client requests.
 """
 from __future__ import annotations
@@ -231,22 +231,27 @@ def newton_targets(T: np.ndarray, seed: int = 20231205, rel: float = 0.05,
     return np.clip(T * (1.0 + rng.uniform(-rel, rel, T.size)), lo, hi)
 
 
-def manifold_states(n: int, seed: int, p_jitter: bool = True):
+def manifold_states(n: int, seed: int, p_jitter: bool = True, exact_frac: float = 0.5):
     """Flame-sheet states with noise: Z ~ U[0,1]; T (1 + N(0, 0.03));
-    Y <- normalise(Y + 0.02 Dirichlet(0.5)); p = 10 MPa x U[0.95, 1.05]."""
+    Y <- normalise(Y + 0.02 Dirichlet(0.5)) for a fraction 1 - exact_frac of
+    the states, the flame-sheet composition itself for the others (fields of
+    flame sheets have exact zeros in Y, a corner of the simplex that noisy
+    compositions do not reach); p = 10 MPa x U[0.95, 1.05]."""
     rng = np.random.default_rng(seed)
     Zmix = rng.uniform(0.0, 1.0, n)
     T, Y = flame_sheet_state(Zmix)
     T = T * (1.0 + rng.normal(0.0, 0.03, n))
     T = np.clip(T, 100.0, 3500.0)
-    Y = Y + 0.02 * dirichlet_half(rng, len(SPECIES), n)
+    noisy = rng.uniform(0.0, 1.0, n) >= exact_frac
+    Y = Y + 0.02 * dirichlet_half(rng, len(SPECIES), n) * noisy
     Y /= Y.sum(axis=0, keepdims=True)
     p = P_REF * (rng.uniform(0.95, 1.05, n) if p_jitter else np.ones(n))
     return T, p, np.ascontiguousarray(Y)
 
 
 def training_states(n: int, seed: int = 20231207):
-    """Half uniform cells (as ``uniform_cells``), half noisy flame-sheet states."""
+    """Half uniform cells (as ``uniform_cells``), half flame-sheet states (as
+    ``manifold_states``: half of them with noisy compositions)."""
     n_u = n // 2
     Tu, pu, Yu = uniform_cells(n_u, seed)
     Tm, pm, Ym = manifold_states(n - n_u, seed + 1000003)

@@ -54,10 +54,16 @@ def unflatten(flat, sizes):
     return params
 
 
-def standardise(x, y, norm):
+def h_ig_of(species, x):
+    """Oracle ideal-gas enthalpy of the (float32) pool states x = [T, p, Y]."""
+    import oracle
+    return oracle.h_ideal(species, x[0].astype(np.float64), x[2:].astype(np.float64))
+
+
+def standardise(x, y, norm, species):
     f = np.vstack([np.log(x[0].astype(np.float64)), x[1], x[2:]]).T
     s_in = (f - norm[0:11]) / norm[11:22]
-    q = omlp.output_targets(y.astype(np.float64))
+    q = omlp.output_targets(y.astype(np.float64), h_ig_of(species, x))
     s_out = (q - norm[22:28]) / norm[28:34]
     return s_in, s_out
 
@@ -76,7 +82,7 @@ def test_gradients_match_oracle(ctx, orc, species, cuda, width, layers, batch):
     norm = sg.get_normalization().astype(np.float64)
     sizes = [11] + [width] * layers + [6]
     params = unflatten(sg.get_params(), sizes)
-    s_in, s_out = standardise(x, y, norm)
+    s_in, s_out = standardise(x, y, norm, species)
     yhat, cache = omlp.forward(params, s_in, "tanh")
     l_orc = omlp.loss(yhat, s_out)
     grads = omlp.backward(params, cache, yhat, s_out, "tanh")
@@ -129,9 +135,9 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
     assert fb.sum() == 0
     norm = sg.get_normalization().astype(np.float64)
     params = unflatten(sg.get_params(), [11, 512, 512, 512, 512, 6])
-    s_in, _ = standardise(x[:, :n], y[:, :n], norm)
+    s_in, _ = standardise(x[:, :n], y[:, :n], norm, species)
     yhat, _ = omlp.forward(params, s_in, "tanh")
-    s_gpu = (omlp.output_targets(out) - norm[22:28]) / norm[28:34]
+    s_gpu = (omlp.output_targets(out, h_ig_of(species, x[:, :n])) - norm[22:28]) / norm[28:34]
     err = np.abs(s_gpu - yhat)
     print("standardised output error: median", np.median(err), "max", err.max())
     assert np.median(err) < 0.01

@@ -96,4 +96,7 @@ def test_output_transform_roundtrip():
     rng = np.random.default_rng(0)
     props = np.vstack([rng.uniform(1, 1000, 5), rng.uniform(0.1, 1.2, 5), rng.uniform(-1e7, 1e7, 5),
                        rng.uniform(1e3, 1e5, 5), rng.uniform(1e-6, 1e-3, 5), rng.uniform(1e-2, 1, 5)])
-    np.testing.assert_allclose(mlp.targets_to_props(mlp.output_targets(props)), props, rtol=1e-14)
+    h_ig = rng.uniform(-1e7, 1e7, 5)
+    q = mlp.output_targets(props, h_ig)
+    np.testing.assert_allclose(q[:, 2], props[2] - h_ig, rtol=1e-15)
+    np.testing.assert_allclose(mlp.targets_to_props(q, h_ig), props, rtol=1e-14, atol=1e-8)

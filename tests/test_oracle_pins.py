@@ -171,6 +171,22 @@ def test_low_pressure_limit(orc, species):
         assert out[5, i] == pytest.approx(di["lambda_dilute"], rel=1e-6)
 
 
+def test_h_ideal_is_the_low_pressure_enthalpy(orc, species):
+    """The batch ideal-gas enthalpy (the surrogate's exact part) equals the
+    full enthalpy in the p -> 0 limit and the per-cell diagnostic h_ig, on
+    uniform and flame-sheet states, both NASA ranges."""
+    T, _, Y = W.uniform_cells(400, seed=6)
+    T = 700.0 + (T - 100.0) * (2800.0 / 3400.0)
+    Tm, _, Ym = W.manifold_states(400, seed=7)
+    T, Y = np.concatenate([T, np.maximum(Tm, 700.0)]), np.concatenate([Y, Ym], axis=1)
+    hig = orc.h_ideal(species, T, Y)
+    out, st, d = orc.diagnose(species, T, np.full(T.size, 1e-3), Y)
+    assert np.all(st == 0)
+    scale = np.maximum(np.abs(out[2]), out[3] * T)
+    assert np.all(np.abs(hig - out[2]) <= 1e-9 * scale)
+    assert np.array_equal(hig, np.array([di["h_ig"] for di in d]))
+
+
 # JANAF / CODATA standard enthalpies of formation at 298.15 K [kJ/mol] and
 # ideal-gas cp [J/(mol K)]; checks the NASA-7 evaluation (and the data).
 HF298 = {"CH4": -74.6, "O2": 0.0, "CO2": -393.51, "H2O": -241.83, "CO": -110.53, "H2": 0.0,
