@@ -44,8 +44,8 @@ FP64_FLOPS_PER_CELL = {"props_fp64": 1815.0, "newton_fp64": 1469.0}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
 # / cells) of the same capture; a full launch moves this x its cells
 TRAFFIC_BYTES_PER_CELL = {"props_fp64": 125.9, "newton_fp64": 108.3}
-# surrogate: 2 x (11*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
-def mlp_flops_per_cell(width=512, layers=4, n_in=11, n_out=6):
+# surrogate: 2 x (13*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
+def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
 
 # Algorithmic bytes per cell of each path (N = 9 species): inputs + outputs
@@ -408,9 +408,9 @@ def run_ours(args):
         if sg is not None:
             field_err["surrogate_bf16"] = TR.relative_rms(outsg[:, ok], ref[:, ok])
             # the same on the cells that pass the training data's constraints
-            # (dense mu, lambda at least half the dilute values)
+            # (dense mu, lambda at least TR.DILUTE_FLOOR of the dilute values)
             dil, _ = ctx.props(T64, torch.ones_like(p64), Y64, "fp64", outputs=("mu", "lambda"))
-            phys = ok & (out64[4] >= 0.5 * dil[4]) & (out64[5] >= 0.5 * dil[5])
+            phys = ok & (out64[4] >= TR.DILUTE_FLOOR * dil[4]) & (out64[5] >= TR.DILUTE_FLOOR * dil[5])
             del dil
             field_err["surrogate_bf16_physical"] = TR.relative_rms(outsg[:, phys], ref[:, phys])
             field_err["physical_cells"] = int(phys.sum())

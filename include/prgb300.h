@@ -127,12 +127,14 @@ pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n,
 
 /* ======================================================================
  * Surrogate MLP (Sec. 4: the DNN that replaces the property evaluation).
- * Inputs per cell: [log T, p, Y_1..Y_9] (9 species, the context's order);
+ * Inputs per cell: [log T, p, Y_1..Y_9, T_pc / T, log W] (9 species, the
+ * context's order; T_pc = sum_k X_k Tc_k by Kay's rule, W the mean molar mass
+ * [kg/mol], both from the raw T, Y);
  * outputs: [rho, Z, h, cp, mu, lambda] learned as [log rho, Z, h - h_ig,
  * log cp, log mu, log lambda], inputs and outputs standardised with statistics
  * of the training pool; h_ig(T, Y) = sum_k Y_k h_k(T) / W_k is the NASA-7
  * ideal-gas enthalpy (Sec. 2), evaluated exactly and added to the network's
- * departure.  Checkpoints carry format 2 (this target).  Hidden layers use GeLU (Sec. 4.1) in its tanh form,
+ * departure.  Checkpoints carry format 3 (these inputs and targets).  Hidden layers use GeLU (Sec. 4.1) in its tanh form,
  * 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).  Forward and
  * backward GEMMs run on the tensor cores (BF16 operands, FP32 accumulation);
  * master weights and Adam moments are FP32.
@@ -147,7 +149,7 @@ typedef struct {
     int32_t infer_chunk;    /* rows per inference chunk; multiple of 128 */
 } sg_config;
 
-#define SG_NORM_FLOATS 56  /* in_mean[11] in_std[11] out_mean[6] out_std[6] hull_lo[11] hull_hi[11] + 2 pad */
+#define SG_NORM_FLOATS 64  /* in_mean[13] in_std[13] out_mean[6] out_std[6] hull_lo[13] hull_hi[13] */
 
 /* Create a model bound to `ctx` (which must hold exactly 9 species; it is
  * used for the Peng-Robinson fallback).  Weights ~ U(-1/sqrt(fan_in),

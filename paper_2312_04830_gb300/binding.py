@@ -183,8 +183,8 @@ class _SgConfig(ctypes.Structure):
                 ("infer_chunk", ctypes.c_int32)]
 
 
-SG_NORM_FLOATS = 56
-N_IN, N_OUT = 11, 6
+SG_NORM_FLOATS = 64
+N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
 def _sg_lib():
@@ -274,7 +274,7 @@ class Surrogate:
     @staticmethod
     def _pool(x, y):
         import torch
-        for nm, t, rows in (("x", x, N_IN), ("y", y, N_OUT)):
+        for nm, t, rows in (("x", x, N_RAW), ("y", y, N_OUT)):
             if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
                 raise PrError(f"{nm} must be a float32 CUDA tensor")
             if t.dim() != 2 or t.shape[0] != rows or t.stride(1) != 1:

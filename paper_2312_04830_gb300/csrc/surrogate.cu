@@ -2,7 +2,8 @@
 // on the tensor cores, with the FP64 Peng-Robinson path as the fallback for
 // states outside the training hull.
 //
-// Network: 11 inputs [log T, p, Y_1..Y_9] -> H hidden layers of width W with
+// Network: 13 inputs [log T, p, Y_1..Y_9, T_pc / T, log W] -> H hidden layers
+// of width W with
 // GeLU -> 6 outputs [log rho, Z, h - h_ig, log cp, log mu, log lambda]; inputs
 // and outputs standardised with statistics of the training pool.  The network
 // learns the enthalpy departure from the ideal-gas enthalpy h_ig(T, Y) =
@@ -34,7 +35,7 @@ using prk::SpeciesRec;
 
 namespace {
 
-constexpr int NIN = 11, NOUT = 6;
+constexpr int NIN = 13, NOUT = 6;
 constexpr int KIN = 64;      // padded input width (one 64-wide k-block)
 constexpr int NOP = 16;      // padded output width
 constexpr int MOP = 128;     // padded output rows of the last layer's weight gradient
@@ -51,13 +52,34 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 
 __device__ __forceinline__ float uniform01(uint64_t h) { return (float)((h >> 40) * (1.0 / 16777216.0)); }
 
-// Features of one cell from raw inputs: [log T, p, Y_1..Y_9].
-__device__ __forceinline__ void features(const float *x, int64_t ldx, int64_t i, float (&f)[NIN])
+// Derived features from T and Y: the inverse pseudo-reduced temperature
+// T_pc / T (T_pc = sum_k X_k Tc_k, Kay's rule over mole fractions X) and the
+// log of the mean molar mass [kg/mol].
+__device__ __forceinline__ void derived_features(float T, const float *Y, const void *sp32, float &tpc_over_T,
+                                                 float &logW)
 {
-    f[0] = logf(__ldg(x + i));
+    const SpeciesRec<float> *sp = static_cast<const SpeciesRec<float> *>(sp32);
+    float s = 0.f, st = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float nk = Y[k] * __ldg(&sp[k].inv_W);   // moles per kg
+        s += nk;
+        st = fmaf(nk, __ldg(&sp[k].Tc), st);
+    }
+    tpc_over_T = st / (s * T);
+    logW = -logf(s);
+}
+
+// Features of one cell from raw inputs x = [T, p, Y_1..Y_9]:
+// [log T, p, Y_1..Y_9, T_pc / T, log W].
+__device__ __forceinline__ void features(const float *x, int64_t ldx, int64_t i, const void *sp32, float (&f)[NIN])
+{
+    const float T = __ldg(x + i);
+    f[0] = logf(T);
     f[1] = __ldg(x + ldx + i);
 #pragma unroll
     for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
+    derived_features(T, f + 2, sp32, f[11], f[12]);
 }
 
 // Mass-specific ideal-gas enthalpy sum_k Y_k h_k(T) / W_k [J/kg] from the
@@ -141,7 +163,7 @@ __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, cons
     for (int k = 0; k < NSTAT; ++k) { s[k] = 0; s2[k] = 0; mn[k] = 1e300; mx[k] = -1e300; }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float f[NIN], q[NOUT];
-        features(x, ldx, i, f);
+        features(x, ldx, i, sp32, f);
         targets(x, ldx, y, ldy, i, sp32, q);
         bool fin = true;
 #pragma unroll
@@ -228,7 +250,7 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
         int64_t src = r;
         if (sample_seed != 0 || n_pool != B) src = (int64_t)(splitmix64(sample_seed ^ ((uint64_t)r * 0xD1B54A32D192ED03ull)) % (uint64_t)n_pool);
         float f[NIN], q[NOUT];
-        features(x, ldx, src, f);
+        features(x, ldx, src, d.sp32, f);
         targets(x, ldx, y, ldy, src, d.sp32, q);
         float v[16];
 #pragma unroll
@@ -251,10 +273,12 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < mc; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = r0 + r;
         float f[NIN];
-        f[0] = logf(__ldg(T + i));
+        const float Ti = __ldg(T + i);
+        f[0] = logf(Ti);
         f[1] = __ldg(p + i);
 #pragma unroll
         for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(Y + (int64_t)k * ldY + i);
+        derived_features(Ti, f + 2, d.sp32, f[11], f[12]);
         bool out = false;
         float v[16];
 #pragma unroll
@@ -270,7 +294,7 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
         float Yk[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Yk[k] = f[2 + k];
-        d.hig[r] = h_ideal(__ldg(T + i), Yk, d.sp32);
+        d.hig[r] = h_ideal(Ti, Yk, d.sp32);
         if (flags) flags[i] = out ? 1 : 0;
         if (out) list[atomicAdd(count, 1u)] = (int32_t)r;
     }
@@ -960,8 +984,9 @@ pr_status surrogate_save(const sg_model *m, const char *path)
     FILE *f = fopen(path, "wb");
     if (!f) { prgb::set_error("surrogate_save: cannot open %s", path); return PR_EINVAL; }
     const char magic[4] = {'P', 'R', 'S', 'G'};
-    // format 2: the enthalpy output is the departure from the ideal-gas enthalpy
-    const int32_t hdr[4] = {2, m->width, m->hidden, 0};
+    // format 3: 13 inputs (with T_pc / T and log W); the enthalpy output is the
+    // departure from the ideal-gas enthalpy
+    const int32_t hdr[4] = {3, m->width, m->hidden, 0};
     const int64_t step = m->step;
     bool ok = fwrite(magic, 1, 4, f) == 4 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&step, 8, 1, f) == 1 &&
               fwrite(&n, 8, 1, f) == 1 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
@@ -980,7 +1005,7 @@ pr_status surrogate_load(sg_model *m, const char *path)
     int64_t step = 0, n = 0;
     bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "PRSG", 4) == 0 && fread(hdr, 4, 4, f) == 4 &&
               fread(&step, 8, 1, f) == 1 && fread(&n, 8, 1, f) == 1;
-    ok = ok && hdr[0] == 2 && hdr[1] == m->width && hdr[2] == m->hidden && n == m->dev.n_master;
+    ok = ok && hdr[0] == 3 && hdr[1] == m->width && hdr[2] == m->hidden && n == m->dev.n_master;
     std::vector<float> buf;
     if (ok) {
         buf.resize(3 * n + SG_NORM_FLOATS);

@@ -23,6 +23,9 @@ import numpy as np
 from . import binding, workloads as W
 
 OUT_NAMES = ("rho", "Z", "h", "cp", "mu", "lambda")
+# physical-outcome filter: dense mu and lambda at least this fraction of their
+# dilute-gas values at the same T and composition
+DILUTE_FLOOR = 0.9
 
 
 def label_pool(ctx, T, p, Y, device, chunk=1 << 23):
@@ -31,10 +34,12 @@ def label_pool(ctx, T, p, Y, device, chunk=1 << 23):
 
     Physical-outcome filter (the paper's data constraints, Sec. 4.2): positive
     finite properties, and a dense-fluid viscosity and conductivity of at least
-    half their dilute-gas values at the same T and composition (taken from the
-    same path at p = 1 Pa).  Chung's correlations, extrapolated to cold
-    radical-rich mixtures, can fall far below the dilute values or turn
-    negative; about 0.2 % of the sampled states are dropped."""
+    DILUTE_FLOOR times their dilute-gas values at the same T and composition
+    (taken from the same path at p = 1 Pa).  Chung's dense correction,
+    extrapolated to radical- and water-rich mixtures, can fall far below the
+    dilute values or turn negative, where the excess viscosity of a gas is
+    positive or, at high reduced temperature, only slightly negative; about
+    1.7 % of the sampled states are dropped."""
     import torch
     xs, ys = [], []
     for a in range(0, T.size, chunk):
@@ -44,7 +49,7 @@ def label_pool(ctx, T, p, Y, device, chunk=1 << 23):
         props, st = ctx.props(Td, pd, Yd, precision="fp64")
         dil, _ = ctx.props(Td, torch.ones_like(pd), Yd, precision="fp64", outputs=("mu", "lambda"))
         keep = (st == 0) & torch.all(torch.isfinite(props), dim=0) & torch.all(props[[0, 3, 4, 5]] > 0, dim=0)
-        keep &= (props[4] >= 0.5 * dil[4]) & (props[5] >= 0.5 * dil[5])
+        keep &= (props[4] >= DILUTE_FLOOR * dil[4]) & (props[5] >= DILUTE_FLOOR * dil[5])
         xs.append(torch.cat([Td[None], pd[None], Yd], dim=0)[:, keep].float())
         ys.append(props[:, keep].float())
     return torch.cat(xs, dim=1).contiguous(), torch.cat(ys, dim=1).contiguous()

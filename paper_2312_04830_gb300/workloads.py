@@ -232,13 +232,18 @@ def newton_targets(T: np.ndarray, seed: int = 20231205, rel: float = 0.05,
 
 
 def manifold_states(n: int, seed: int, p_jitter: bool = True, exact_frac: float = 0.5):
-    """Flame-sheet states with noise: Z ~ U[0,1]; T (1 + N(0, 0.03));
+    """Flame-sheet states with noise: Z ~ U[0,1] for half of the states and
+    Z = (1 + tanh s) / 2 with s ~ U[-5, 5] for the other half (the mixture
+    fractions of a thin flame, piled up at the pure-oxidiser and pure-fuel
+    ends as in the flame-vortex field); T (1 + N(0, 0.03));
     Y <- normalise(Y + 0.02 Dirichlet(0.5)) for a fraction 1 - exact_frac of
     the states, the flame-sheet composition itself for the others (fields of
     flame sheets have exact zeros in Y, a corner of the simplex that noisy
     compositions do not reach); p = 10 MPa x U[0.95, 1.05]."""
     rng = np.random.default_rng(seed)
     Zmix = rng.uniform(0.0, 1.0, n)
+    thin = rng.uniform(0.0, 1.0, n) < 0.5
+    Zmix[thin] = 0.5 * (1.0 + np.tanh(rng.uniform(-5.0, 5.0, int(thin.sum()))))
     T, Y = flame_sheet_state(Zmix)
     T = T * (1.0 + rng.normal(0.0, 0.03, n))
     T = np.clip(T, 100.0, 3500.0)

@@ -60,11 +60,22 @@ def h_ig_of(species, x):
     return oracle.h_ideal(species, x[0].astype(np.float64), x[2:].astype(np.float64))
 
 
+def features(x, species):
+    """Network inputs [log T, p, Y_1..Y_9, T_pc / T, log W] of raw states
+    x = [T, p, Y] (float64): Kay's-rule pseudo-critical temperature over
+    mole fractions and the mean molar mass [kg/mol]."""
+    T, p, Y = x[0].astype(np.float64), x[1].astype(np.float64), x[2:].astype(np.float64)
+    nmol = Y / (species.W[:, None] * 1e-3)
+    s = nmol.sum(axis=0)
+    tpc = (nmol * species.Tc[:, None]).sum(axis=0) / s
+    return np.vstack([np.log(T), p, Y, tpc / T, -np.log(s)])
+
+
 def standardise(x, y, norm, species):
-    f = np.vstack([np.log(x[0].astype(np.float64)), x[1], x[2:]]).T
-    s_in = (f - norm[0:11]) / norm[11:22]
+    f = features(x, species).T
+    s_in = (f - norm[0:13]) / norm[13:26]
     q = omlp.output_targets(y.astype(np.float64), h_ig_of(species, x))
-    s_out = (q - norm[22:28]) / norm[28:34]
+    s_out = (q - norm[26:32]) / norm[32:38]
     return s_in, s_out
 
 
@@ -80,7 +91,7 @@ def test_gradients_match_oracle(ctx, orc, species, cuda, width, layers, batch):
     sg.sync_status()
     g_gpu = grad.cpu().numpy().astype(np.float64)
     norm = sg.get_normalization().astype(np.float64)
-    sizes = [11] + [width] * layers + [6]
+    sizes = [13] + [width] * layers + [6]
     params = unflatten(sg.get_params(), sizes)
     s_in, s_out = standardise(x, y, norm, species)
     yhat, cache = omlp.forward(params, s_in, "tanh")
@@ -134,10 +145,10 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
     out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy()
     assert fb.sum() == 0
     norm = sg.get_normalization().astype(np.float64)
-    params = unflatten(sg.get_params(), [11, 512, 512, 512, 512, 6])
+    params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 6])
     s_in, _ = standardise(x[:, :n], y[:, :n], norm, species)
     yhat, _ = omlp.forward(params, s_in, "tanh")
-    s_gpu = (omlp.output_targets(out, h_ig_of(species, x[:, :n])) - norm[22:28]) / norm[28:34]
+    s_gpu = (omlp.output_targets(out, h_ig_of(species, x[:, :n])) - norm[26:32]) / norm[32:38]
     err = np.abs(s_gpu - yhat)
     print("standardised output error: median", np.median(err), "max", err.max())
     assert np.median(err) < 0.01
@@ -165,8 +176,8 @@ def test_fallback_outside_hull_is_pr_fp64(ctx, orc, species, cuda):
     sg.sync_status()
     out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy()
     norm = sg.get_normalization()
-    f = np.vstack([np.log(x32[0]), x32[1], x32[2:]]).astype(np.float32)
-    lo, hi = norm[34:45, None], norm[45:56, None]
+    f = features(x32, species).astype(np.float32)
+    lo, hi = norm[38:51, None], norm[51:64, None]
     outside = np.any((f < lo) | (f > hi), axis=0)
     assert np.all(outside[(Tall > 4000) | (Tall < 80)])
     near = np.any(np.abs(f - lo) < 1e-5 * np.abs(lo) + 1e-7, axis=0) | np.any(np.abs(f - hi) < 1e-5 * np.abs(hi) + 1e-7, axis=0)
