@@ -184,6 +184,7 @@ class _SgConfig(ctypes.Structure):
 
 
 SG_NORM_FLOATS = 64
+SG_OPT_FUSED_INFER = 1
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
@@ -211,6 +212,8 @@ def _sg_lib():
         L.surrogate_loss_grad.restype = i32
         L.surrogate_infer.argtypes = [vp, i64, vp, vp, vp, i64, vp, i64, vp, vp]
         L.surrogate_infer.restype = i32
+        L.surrogate_set_option.argtypes = [vp, i32, i32]
+        L.surrogate_set_option.restype = i32
         L.surrogate_sync_status.argtypes = [vp]
         L.surrogate_sync_status.restype = i32
         L.surrogate_save.argtypes = [vp, ctypes.c_char_p]
@@ -236,6 +239,11 @@ class Surrogate:
               "surrogate_create")
         self.handle = h
         self.width, self.hidden_layers, self.max_batch = width, hidden_layers, max_batch
+
+    def set_fused_infer(self, on: bool):
+        """All layers of an inference chunk in one persistent launch (True,
+        the default where the width allows it) or one launch per layer."""
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_FUSED_INFER, int(bool(on))), "surrogate_set_option")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -114,6 +114,20 @@ __device__ __forceinline__ float gelu_f(float z)
     return fmaf(hz, t, hz);
 }
 
+// gelu_f of z = a + b on two lanes at once with the packed FP32 instructions
+// of sm_100 (FADD2 / FMUL2 / FFMA2): the same operations in the same order as
+// gelu_f(a + b), so the same bits, in about half the FP32 instructions.
+__device__ __forceinline__ float2 gelu2(float2 a, float2 b)
+{
+    const float2 z = __fadd2_rn(a, b);
+    const float2 z2 = __fmul2_rn(z, z);
+    const float2 p = __ffma2_rn(make_float2(kGeluKC, kGeluKC), z2, make_float2(kGeluK, kGeluK));
+    const float2 u = __fmul2_rn(z, p);
+    const float2 t = make_float2(tanh_approx(u.x), tanh_approx(u.y));
+    const float2 hz = __fmul2_rn(make_float2(0.5f, 0.5f), z);
+    return __ffma2_rn(hz, t, hz);
+}
+
 __device__ __forceinline__ void gelu_and_grad(float z, float &g, float &dg)
 {
     const float z2 = z * z;

@@ -25,6 +25,7 @@
 #include <new>
 #include <vector>
 
+#include "mlp_fused.cuh"
 #include "mlp_gemm.cuh"
 #include "pr_device.cuh"
 #include "pr_internal.h"
@@ -449,6 +450,21 @@ bool make_map(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, ui
     return r == CUDA_SUCCESS;
 }
 
+// The stack of L rings [L][rows][inner] (BF16), boxes of 64 x box_rows x 1.
+bool make_map_3d(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, uint64_t depth, uint32_t box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {inner, rows, depth};
+    cuuint64_t strides[2] = {inner * 2, inner * rows * 2};
+    cuuint32_t box[3] = {64, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 int num_sms_current()
 {
     static int sms[64] = {0};
@@ -535,6 +551,40 @@ cudaError_t launch_gemm_n(const CUtensorMap &ta, const CUtensorMap &tb, const Ge
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// One cooperative launch of the fused inference kernel (all CTAs resident:
+// they wait on one another's arrival counters).
+cudaError_t launch_fused(const FusedArgs &fa, cudaStream_t st)
+{
+    static int dev_ready[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const int smem_max = FusedCfg::kMaxSmem;
+    if (!dev_ready[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_fused_kernel, kFusedThreads, smem_max);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        dev_ready[dev] = 1;
+    }
+    const int sms = num_sms_current();
+    const long long g = fa.total < sms ? fa.total : sms;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3((unsigned)g, 1, 1);
+    cfg.blockDim = dim3(kFusedThreads, 1, 1);
+    cfg.dynamicSmemBytes = FusedCfg::smem_bytes(fa.L, fa.W);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, mlp_fused_kernel, fa);
+}
+
 GemmArgs base_args(sg_model *m)
 {
     GemmArgs a;
@@ -586,6 +636,15 @@ static pr_status build_maps(sg_model *m)
     }
     ok = ok && make_map(&m->ts_hi[0], d.hi[0], W, C, W, 32);
     ok = ok && make_map(&m->ts_hi[1], d.hi[1], W, C, W, 32);
+    // fused inference
+    if (m->fused_ok) {
+        ok = ok && make_map(&m->tmf_w[0], d.wb[0], KIN, W, KIN, kFusedBN);
+        for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tmf_w[l], d.wb[l], W, W, W, kFusedBN);
+        m->tmf_w[L] = m->tm_w[L];
+        const int64_t rr = (int64_t)m->fused_ring * 128;
+        ok = ok && make_map_3d(&m->tmf_ring_ld, m->ring, W, rr, L, 128);
+        ok = ok && make_map_3d(&m->tmf_ring_st, m->ring, W, rr, L, 32);
+    }
     if (!ok) {
         prgb::set_error("surrogate: cuTensorMapEncodeTiled unavailable or failed");
         return PR_ECUDA;
@@ -699,6 +758,22 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     alloc((void **)&m->d_normpart, (size_t)m->norm_blocks * (NSTAT + 1) * 4 * 8);
     alloc((void **)&d.xi, C * KIN * 2);
     alloc((void **)&d.hig, C * 4);
+    // fused inference (mlp_fused.cuh): consecutive layers D slots apart, about
+    // three rounds of the grid (an item's inputs are released about two rounds
+    // after its producer item's turn); a ring row block is rewritten about
+    // three rounds after its readers' turn
+    m->fused_ok = (W % kFusedBN == 0) && W <= 1024 && L <= SG_MAX_HIDDEN &&
+                  FusedCfg::smem_bytes(L, W) <= FusedCfg::kMaxSmem;
+    if (m->fused_ok) {
+        const int G = ctx->num_sms, n_t = W / kFusedBN, ips = L * n_t + 1;
+        const int lagmin = (G + 2 * ips + ips - 1) / ips;   // slots with D ips > G + ips
+        const int three_rounds = (3 * G + ips - 1) / ips;
+        m->fused_D = three_rounds > lagmin + 4 ? three_rounds : lagmin + 4;
+        m->fused_ring = 2 * m->fused_D + 4;
+        alloc((void **)&m->ring, (size_t)L * m->fused_ring * 128 * W * 2);
+        alloc((void **)&m->d_done, (size_t)ceil_div(C, 128) * (L + 1) * 4);
+    }
+    m->fused_on = m->fused_ok;
     alloc((void **)&d.hi[0], C * W * 2);
     alloc((void **)&d.hi[1], C * W * 2);
     alloc((void **)&m->d_list, C * 4);
@@ -923,7 +998,24 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
         prep_infer_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, used_fallback, m->d_list,
                                                                  m->d_count);
         PR_CUDA_TRY(cudaGetLastError());
-        for (int l = 0; l < L; ++l) {
+        if (m->fused_on) {
+            // every layer in one cooperative launch (mlp_fused.cuh)
+            FusedArgs fa;
+            memset(&fa, 0, sizeof(fa));
+            fa.tm_x = m->tm_xi;
+            fa.tm_ring_ld = m->tmf_ring_ld;
+            fa.tm_ring_st = m->tmf_ring_st;
+            for (int l = 0; l <= L; ++l) { fa.tm_w[l] = m->tmf_w[l]; fa.bias[l] = d.master + d.lay[l].b_off; }
+            fa.M = (int)mc; fa.R = mt; fa.L = L; fa.W = W; fa.D = m->fused_D; fa.ring = m->fused_ring;
+            fa.n_t = W / kFusedBN; fa.ips = L * fa.n_t + 1;
+            fa.total = (long long)(fa.R + (long long)L * fa.D) * fa.ips;
+            fa.out6 = out + r0; fa.ld6 = ldo;
+            fa.out_mean = d.norm + 2 * NIN; fa.out_std = d.norm + 2 * NIN + NOUT;
+            fa.add_h = d.hig; fa.done = m->d_done; fa.err = m->d_err;
+            PR_CUDA_TRY(cudaMemsetAsync(m->d_done, 0, (size_t)mt * (L + 1) * 4, st));
+            PR_CUDA_TRY(launch_fused(fa, st));
+        }
+        for (int l = 0; l < L && !m->fused_on; ++l) {
             GemmArgs a = base_args(m);
             a.M = (int)mc; a.N = W; a.K = (l == 0) ? KIN : W; a.kb_per_split = a.K / 64;
             a.bias = d.master + d.lay[l].b_off;
@@ -932,7 +1024,7 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             const CUtensorMap &ta = (l == 0) ? m->tm_xi : m->tm_hi[(l - 1) & 1];
             PR_CUDA_TRY((launch_gemm_n<kEpiHidden>(ta, m->tm_w[l], a, mt, W, 1, st)));
         }
-        {
+        if (!m->fused_on) {
             GemmArgs a = base_args(m);
             a.M = (int)mc; a.N = NOP; a.K = W; a.kb_per_split = W / 64;
             a.bias = d.master + d.lay[L].b_off;
@@ -954,6 +1046,22 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
         PR_CUDA_TRY(cudaGetLastError());
     }
     return PR_OK;
+}
+
+pr_status surrogate_set_option(sg_model *m, int option, int value)
+{
+    PR_CHECK_ARG(m != nullptr, "surrogate_set_option: null model");
+    switch (option) {
+    case SG_OPT_FUSED_INFER:
+        PR_CHECK_ARG(value == 0 || (value == 1 && m->fused_ok),
+                     "surrogate_set_option: fused inference needs a width that is a multiple of 256, <= 1024, "
+                     "and its biases within shared memory");
+        m->fused_on = value;
+        return PR_OK;
+    default:
+        PR_CHECK_ARG(false, "surrogate_set_option: unknown option %d", option);
+    }
+    return PR_EINVAL;
 }
 
 pr_status surrogate_sync_status(sg_model *m)

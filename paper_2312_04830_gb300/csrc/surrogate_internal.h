@@ -100,5 +100,11 @@ struct sg_model {
         tm_dzt[SG_MAX_HIDDEN], tm_dzo, tm_dzot, tm_xi, tm_hi[2];
     // epilogue TMA-store maps (32-row boxes): h, GeLU'(z), dz, inference h
     CUtensorMap ts_h[SG_MAX_HIDDEN], ts_g[SG_MAX_HIDDEN], ts_dz[SG_MAX_HIDDEN], ts_hi[2];
+    // fused inference (mlp_fused.cuh): activation ring, its maps, the weight
+    // maps with 256-row boxes, per-(row block, layer) arrival counters
+    int fused_ok, fused_on, fused_D, fused_ring;
+    __nv_bfloat16 *ring;                    // [L][fused_ring * 128][W]
+    uint32_t *d_done;
+    CUtensorMap tmf_w[SG_MAX_HIDDEN + 1], tmf_ring_ld, tmf_ring_st;
     std::vector<void *> allocs;
 };

@@ -156,6 +156,33 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
     sg.close()
 
 
+@pytest.mark.parametrize("width,layers,chunk,n", [(512, 4, 32768, 70000), (256, 2, 16384, 40961),
+                                                   (512, 1, 1024, 300)])
+def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers, chunk, n):
+    """All layers of a chunk in one persistent launch (activation ring in L2,
+    cross-CTA arrival counters) give the same bits as one launch per layer:
+    chunks longer than the ring (ring slots reused), a ragged last chunk, and
+    a chunk shorter than the grid."""
+    import torch
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=width, hidden_layers=layers, max_batch=1024, infer_chunk=chunk, seed=21)
+    x, y = make_pool(orc, species, 4000, seed=22)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    T, p, Y = W.uniform_cells(n, seed=23)
+    T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=cuda)
+    Td, pd, Yd = d(T), d(p), d(Y)
+    outs = []
+    for fused in (True, False):
+        sg.set_fused_infer(fused)
+        o, fb = sg.infer(Td, pd, Yd)
+        sg.sync_status()
+        outs.append(o.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)
+    assert np.isfinite(outs[0]).mean() > 0.9
+    sg.close()
+
+
 def test_fallback_outside_hull_is_pr_fp64(ctx, orc, species, cuda):
     """Cells outside the training hull take the FP64 Peng-Robinson path: their
     outputs equal the oracle's (rounded to FP32) and they are flagged."""
