@@ -206,7 +206,7 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
 /* Model options.  SG_OPT_FUSED_INFER (default 1 when available): run all
  * layers of an inference chunk in one persistent cooperative launch whose
  * activations stay in L2-sized rings (widths that are multiples of 256, up
- * to 1024, hidden_layers x width <= 2304); 0 runs one GEMM launch per layer.  Both give identical outputs.
+ * to 1024, hidden_layers x width <= 4560); 0 runs one GEMM launch per layer.  Both give identical outputs.
  * PR_EINVAL for an unknown option or a value the model cannot take. */
 #define SG_OPT_FUSED_INFER 1
 pr_status surrogate_set_option(sg_model *m, int option, int value);
