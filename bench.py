@@ -48,6 +48,10 @@ TRAFFIC_BYTES_PER_CELL = {"props_fp64": 125.9, "newton_fp64": 108.3}
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
 
+# rows per surrogate inference chunk: all layers of a chunk run in one
+# persistent launch, activations in L2-resident rings
+SG_CHUNK = 1 << 22
+
 # Algorithmic bytes per cell of each path (N = 9 species): inputs + outputs
 # that the path must move, FP64: T, p, Y[9] in, 6 outputs + int32 status out.
 N_SPECIES = 9
@@ -232,11 +236,11 @@ def train_surrogate(ctx, dev, args):
     x, y = TR.make_pool(ctx, args.sg_pool, 20231207, dev)
     xh, yh = TR.make_pool(ctx, 1 << 20, 20231208, dev)
     t_data = time.perf_counter() - t0
-    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=1 << 20)
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=SG_CHUNK)
     sg.fit_normalization(x, y)
     TR.train(sg, x, y, 20, 65536, 1e-3, log_every=0)          # warm-up steps
     sg.close()
-    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=1 << 20)
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=SG_CHUNK)
     sg.fit_normalization(x, y)
     steps = args.sg_steps if args.sg_steps > 0 else int(round(args.sg_epochs * x.shape[1] / 65536))
     losses, secs = TR.train(sg, x, y, steps, 65536, 1e-3, log_every=max(1, steps // 10))
@@ -353,8 +357,8 @@ def run_ours(args):
     if sg is not None:
         paths.append("surrogate_bf16")
         calls["surrogate_bf16"] = lambda: sg.infer(T32, p32, Y32, out=outsg, used_fallback=fb)
-        n_chunks = (n + (1 << 20) - 1) >> 20
-        launches["surrogate_bf16"] = n_chunks * (1 + 5 + 1)     # prep, 5 GEMMs, fallback per chunk
+        n_chunks = (n + SG_CHUNK - 1) // SG_CHUNK
+        launches["surrogate_bf16"] = n_chunks * (1 + 1 + 1)     # prep, fused MLP, fallback per chunk
     launches_per_step = sum(launches.values())
 
     def step(ev=None):

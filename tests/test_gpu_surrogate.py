@@ -254,3 +254,59 @@ def test_training_reduces_loss_and_checkpoint_roundtrip(ctx, orc, species, cuda,
     assert np.array_equal(sg.get_params(), sg2.get_params())
     sg.close()
     sg2.close()
+
+
+def test_trained_surrogate_gain_on_flame_field(ctx, cuda):
+    """What the trained network gains over the property evaluation without it,
+    on the 128^3 flame-vortex field: a 4 x 512 surrogate trained on the GPU for
+    2 000 steps on a 1 Mi-state PR-labelled pool reproduces the FP64 PR path
+    within a few per cent (below 1 % for rho, Z, h, cp, lambda; viscosity is
+    the hardest output) on the cells that satisfy the training data's
+    physical constraints, and evaluates them at least as fast as the FP64 PR
+    path.  On this GPU the FP32 PR path is faster still: the network's gain
+    is over FP64 evaluation only (1.6 MFLOP of tensor work per cell against
+    ~1800 FP64 flops on the 1/64-rate FP64 pipe)."""
+    import torch
+    from paper_2312_04830_gb300 import binding, train as TR
+    torch.manual_seed(0)
+    x, y = TR.make_pool(ctx, 1 << 20, 20231207, cuda)
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=1 << 21, seed=3)
+    sg.fit_normalization(x, y)
+    TR.train(sg, x, y, 2000, 65536, 1e-3, log_every=0)
+    sg.sync_status()
+    del x, y
+    T, p, Y = W.flame_vortex_field(128)[:3]
+    d64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=cuda)
+    T64, p64, Y64 = d64(T), d64(p), d64(Y)
+    T32, p32, Y32 = T64.float(), p64.float(), Y64.float().contiguous()
+    out64, st = ctx.props(T64, p64, Y64, "fp64")
+    dil, _ = ctx.props(T64, torch.ones_like(p64), Y64, "fp64", outputs=("mu", "lambda"))
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, r
+
+    t64, _ = timed(lambda: ctx.props(T64, p64, Y64, "fp64", out=out64))
+    t32, _ = timed(lambda: ctx.props(T32, p32, Y32, "fp32"))
+    tsg, (osg, fb) = timed(lambda: sg.infer(T32, p32, Y32))
+    sg.sync_status()
+    ref = out64.float()
+    phys = (st == 0) & (ref[4] >= TR.DILUTE_FLOOR * dil[4]) & (ref[5] >= TR.DILUTE_FLOOR * dil[5])
+    assert float(phys.float().mean()) > 0.99
+    err = TR.relative_rms(osg[:, phys], ref[:, phys])
+    rms = {k: v["rel_rms"] for k, v in err.items()}
+    print("ms: fp64 %.3f fp32 %.3f surrogate %.3f; rel RMS %s; fallback %.4f" %
+          (t64, t32, tsg, rms, float(fb.float().mean())))
+    for k in ("rho", "Z", "h", "cp", "lambda"):
+        assert rms[k] < 0.01, (k, rms[k])
+    assert rms["mu"] < 0.03
+    assert tsg < 1.05 * t64          # the gain over FP64 evaluation (measured ~1.1x at 256^3)
+    assert t32 < tsg                 # and none over FP32 evaluation on this GPU
+    sg.close()
