@@ -90,6 +90,20 @@ def dist_env():
     return ws, rank, local
 
 
+def job_throughput(local_ms, units_per_rank, ws, device):
+    """Whole-job throughput of a weak-scaling run: every rank processed
+    units_per_rank units in local_ms; the job took the slowest rank's time.
+    Returns (units of all ranks / s, max-over-ranks ms).  Collective over the
+    default process group when ws > 1 (NCCL on the GPUs, gloo in the tests)."""
+    ms = float(local_ms)
+    if ws > 1:
+        import torch
+        tt = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    return units_per_rank * ws / (ms * 1e-3), ms
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -391,14 +405,8 @@ def run_ours(args):
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if ws > 1:
-        tt = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    value, elapsed_ms = job_throughput(t_start.elapsed_time(t_end), n * len(paths) * args.steps, ws, dev)
     per_path_ms = {nm: statistics.mean(e[nm][0].elapsed_time(e[nm][1]) for e in evs) for nm in paths}
-    evals = n * len(paths) * args.steps * ws
-    value = evals / (elapsed_ms * 1e-3)
     fb_frac = float(fb.float().mean()) if sg is not None else None
 
     # error of the reduced-precision paths on the field against the FP64 PR
@@ -538,12 +546,8 @@ def run_e2e(ctx, sg, T, p, Y, hs64, hs32, dev, stream, steps, ws):
         one()
     b.record(stream)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    return {"value": n * n_paths * steps * ws / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    value, ms = job_throughput(a.elapsed_time(b), n * n_paths * steps, ws, dev)
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps}
 
 
