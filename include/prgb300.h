@@ -113,7 +113,11 @@ pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n,
  * the FP32 steps fail or do not settle; the FP64 iteration alone decides
  * convergence, so the result meets the same FP64 tolerance
  * (PR_FLAG_NEWTON_FP64_ONLY turns the warm start off).  iters counts the
- * FP64 iterations.
+ * FP64 iterations.  PR_MIXED iterates on the FP32 thermodynamics (FP64 cubic
+ * root) and re-solves in FP64, from that root, the cells where it failed and
+ * those in the pseudo-boiling band (cp above 3 x the ideal-gas cp), where
+ * the FP32 iteration is least reliable; there its T is the FP64 solution
+ * rounded to FP32.  iters then counts both iterations.
  *   hstar, p, T_guess [n]; Y [N][ldY]; T_out [n] output;
  *   cell_status [n] (required), iters [n] (NULL allowed);
  *   max_iter in 1..1000; rtol in [1e-15, 1e-2].

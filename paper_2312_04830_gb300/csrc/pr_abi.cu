@@ -307,14 +307,16 @@ pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n, const void *hst
                              (const double *)T_guess, (double *)T_out, cell_status, iters,
                              (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64,
                              ctx->n_species, ctx->flags, max_iter, rtol,
-                             (const SpeciesRec<float> *)ctx->d_sp32, ctx->d_pair32, ctx->d_kij32};
+                             (const SpeciesRec<float> *)ctx->d_sp32, ctx->d_pair32, ctx->d_kij32,
+                             nullptr, nullptr, nullptr};
         if (ctx->ns_pad == 9) launch_newton<double, double, 9>(a, kij, occ, ctx->num_sms, st);
         else launch_newton<double, double, 32>(a, kij, occ, ctx->num_sms, st);
     } else {
         NewtonArgs<float> a{n, ldY, (const float *)hstar, (const float *)p, (const float *)Y, (const float *)T_guess,
                             (float *)T_out, cell_status, iters, (const SpeciesRec<float> *)ctx->d_sp32,
                             ctx->d_pair32, ctx->d_kij32, ctx->n_species, ctx->flags, max_iter, rtol,
-                            nullptr, nullptr, nullptr};
+                            nullptr, nullptr, nullptr,
+                            (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64};
         if (prec == PR_FP32) {
             if (ctx->ns_pad == 9) launch_newton<float, float, 9>(a, kij, occ, ctx->num_sms, st);
             else launch_newton<float, float, 32>(a, kij, occ, ctx->num_sms, st);

@@ -11,6 +11,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "pr_device.cuh"
 
 namespace prk {
@@ -96,6 +98,9 @@ struct NewtonArgs {
     // FP32 tables for the warm start of the FP64 inversion (FP64 kernel only)
     const SpeciesRec<float> *sp32;
     const float *pair32, *kij32;
+    // FP64 tables for the FP64 re-solve of the mixed inversion (mixed kernel only)
+    const SpeciesRec<double> *sp64;
+    const double *pair64, *kij64;
 };
 
 // h(T) and cp(T) of a cell at fixed p and composition; status 0 or an error.
@@ -138,6 +143,107 @@ __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, doub
     return T0;
 }
 
+// Safeguarded Newton on f(T) = h(T) - h* from T inside [kTLo, kTHi]: a step
+// that leaves the bracket, or follows one that did not halve |f|, becomes a
+// bisection; before leaning on a bracket end whose h is unknown, h* is checked
+// to lie inside the range.  Converged when |f| <= rtol max(|h*|, cp T), or
+// when |dT| <= rtol T and h at the new T is within jump_tol (else h* sits in a
+// jump of h(T)).  Returns the status; Tres, iters and the last cp out.
+template <typename Real, typename RZ, int NS, bool KIJ>
+__device__ __forceinline__ int newton_solve(const Comp<Real, NS> &c, double hs, Real p, double T,
+                                            const SpeciesRec<Real> *sp, const Real *kij, int max_iter, double rtol,
+                                            double jump_tol, double &Tres, int &iters, double &cp_last)
+{
+    double lo = kTLo, hi = kTHi;
+    bool lo_done = false, hi_done = false;   // endpoint h evaluated (range checked)
+    double fprev = INFINITY;
+    int st = kMaxIt, it;
+    Tres = T;
+    cp_last = 0.0;
+#pragma unroll 1
+    for (it = 1; it <= max_iter; ++it) {
+        double h, cp;
+        int e = eval_h<Real, RZ, NS, KIJ>(c, T, p, sp, kij, h, cp);
+        if (e) { st = e; Tres = T; break; }
+        cp_last = cp;
+        const double f = h - hs;
+        if (fabs(f) <= rtol * fmax(fabs(hs), fabs(cp) * T)) { st = kOk; Tres = T; break; }
+        if (f < 0) lo = T; else hi = T;
+        double Tn = T - f / cp;
+        const bool newton_ok = (cp > 0) && (Tn > lo) && (Tn < hi) && (fabs(f) <= 0.5 * fabs(fprev));
+        if (!newton_ok) Tn = 0.5 * (lo + hi);
+        if (!newton_ok && ((lo == kTLo && !lo_done) || (hi == kTHi && !hi_done))) {
+            const bool use_lo = (lo == kTLo && !lo_done);
+            const double Te = use_lo ? kTLo : kTHi;
+            double he, cpe;
+            int e2 = eval_h<Real, RZ, NS, KIJ>(c, Te, p, sp, kij, he, cpe);
+            if (e2) { st = e2; Tres = T; break; }
+            if (use_lo) lo_done = true; else hi_done = true;
+            if ((use_lo && hs < he) || (!use_lo && hs > he)) { st = kHRange; Tres = Te; break; }
+        }
+        fprev = f;
+        if (fabs(Tn - T) <= rtol * T) {
+            Tres = Tn;
+            double h2, cp2;
+            if (eval_h<Real, RZ, NS, KIJ>(c, Tn, p, sp, kij, h2, cp2)) { st = kNoRoot; break; }
+            cp_last = cp2;
+            st = (fabs(h2 - hs) <= jump_tol * fmax(fabs(hs), fabs(cp2) * Tn)) ? kOk : kHRange;
+            break;
+        }
+        T = Tn;
+        Tres = T;
+    }
+    iters = it > max_iter ? max_iter : it;
+    return st;
+}
+
+// Mass-specific ideal-gas cp of a cell [J/(kg K)] (NASA-7).
+template <typename Real, int NS>
+__device__ __forceinline__ double cp_ideal_mass(const Comp<Real, NS> &c, Real T, const SpeciesRec<Real> *sp)
+{
+    Real s = 0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const Real *a = (T < sp[k].T_mid) ? sp[k].cp_lo : sp[k].cp_hi;
+        const Real cpk = M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(a[4], T, a[3]), T, a[2]), T, a[1]), T, a[0]);
+        s = M<Real>::fma(c.x[k], cpk, s);
+    }
+    return (double)s / (double)c.Wbar;
+}
+
+// Composition in FP64 from FP32 mass fractions (the FP64 re-solve of the
+// mixed inversion works on exactly the caller's FP32 inputs).
+template <int NS>
+__device__ __forceinline__ bool comp_fp64_of_fp32(Comp<double, NS> &c, const float *__restrict__ Y, int64_t ldY,
+                                                  int64_t i, int N, const SpeciesRec<double> *sp)
+{
+    double ysum = 0, s = 0;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const double y = (k < N) ? (double)__ldg(Y + (int64_t)k * ldY + i) : 0.0;
+        ok = ok && (y >= 0.0) && isfinite(y);
+        ysum += y;
+        c.x[k] = y * sp[k].inv_W;
+        s += c.x[k];
+    }
+    ok = ok && (fabs(ysum - 1.0) <= 1e-6) && (s > 0.0);
+    const double inv_s = 1.0 / s;
+    double bm = 0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        c.x[k] *= inv_s;
+        bm = fma(c.x[k], sp[k].b, bm);
+    }
+    c.Wbar = inv_s;
+    c.bm = bm;
+    return ok;
+}
+
+// cp above this multiple of the ideal-gas cp marks the pseudo-boiling band
+// (and the near-critical region), where the mixed inversion re-solves in FP64.
+constexpr double kPseudoCriticalCp = 3.0;
+
 template <typename Real, typename RZ, int NS, bool KIJ>
 __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a)
 {
@@ -148,6 +254,10 @@ __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a
     __shared__ Smem<float, NS, KIJ> s32[1];
     const bool warm = kFp64 && !(a.flags & PR_FLAG_NEWTON_FP64_ONLY);
     if (warm) stage<float, NS, KIJ>(s32[0], a.sp32, a.pair32, a.kij32);
+    // mixed inversion (FP32 with the FP64 cubic): FP64 tables for the re-solve
+    constexpr bool kMixed = sizeof(Real) == 4 && sizeof(RZ) == 8;
+    __shared__ typename std::conditional<kMixed, Smem<double, NS, KIJ>, char>::type s64[1];
+    if constexpr (kMixed) stage<double, NS, KIJ>(s64[0], a.sp64, a.pair64, a.kij64);
     // FP32 thermodynamics resolve h to ~1e-7 of its scale: floor the tolerance
     const double rtol = (sizeof(Real) == 4) ? fmax(a.rtol, 2e-6) : a.rtol;
     const double jump_tol = (sizeof(Real) == 4) ? 2e-5 : 1e-6;
@@ -162,49 +272,30 @@ __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a
         int st = kBadInput, it = 0;
         double Tres = nan("");
         if (ok) {
-            double lo = kTLo, hi = kTHi;
-            bool lo_done = false, hi_done = false;   // endpoint h evaluated (range checked)
-            double T = fmin(fmax(Tg, lo), hi);
+            double T = fmin(fmax(Tg, kTLo), kTHi);
             if constexpr (kFp64) {
                 if (warm) T = warm_start_fp32<NS, KIJ>(c, T, hs, (double)p, s32[0].sp, s32[0].kij);
             }
-            double fprev = INFINITY;
-            st = kMaxIt;
-            Tres = T;
-#pragma unroll 1
-            for (it = 1; it <= a.max_iter; ++it) {
-                double h, cp;
-                int e = eval_h<Real, RZ, NS, KIJ>(c, T, p, s.sp, s.kij, h, cp);
-                if (e) { st = e; Tres = T; break; }
-                const double f = h - hs;
-                if (fabs(f) <= rtol * fmax(fabs(hs), fabs(cp) * T)) { st = kOk; Tres = T; break; }
-                if (f < 0) lo = T; else hi = T;
-                double Tn = T - f / cp;
-                const bool newton_ok = (cp > 0) && (Tn > lo) && (Tn < hi) && (fabs(f) <= 0.5 * fabs(fprev));
-                if (!newton_ok) Tn = 0.5 * (lo + hi);
-                // the next iterate leans on a bracket end whose h is unknown:
-                // check that h* lies inside the range first
-                if (!newton_ok && ((lo == kTLo && !lo_done) || (hi == kTHi && !hi_done))) {
-                    const bool use_lo = (lo == kTLo && !lo_done);
-                    const double Te = use_lo ? kTLo : kTHi;
-                    double he, cpe;
-                    int e2 = eval_h<Real, RZ, NS, KIJ>(c, Te, p, s.sp, s.kij, he, cpe);
-                    if (e2) { st = e2; Tres = T; break; }
-                    if (use_lo) lo_done = true; else hi_done = true;
-                    if ((use_lo && hs < he) || (!use_lo && hs > he)) { st = kHRange; Tres = Te; break; }
+            double cp_last;
+            st = newton_solve<Real, RZ, NS, KIJ>(c, hs, p, T, s.sp, s.kij, a.max_iter, rtol, jump_tol, Tres, it,
+                                                 cp_last);
+            if constexpr (kMixed) {
+                // FP64 where FP32 is least reliable: failed cells, and cells in
+                // the pseudo-boiling band, from the FP32 root (or the guess)
+                const bool band = st == kOk && cp_last > kPseudoCriticalCp * cp_ideal_mass<Real, NS>(c, (Real)Tres, s.sp);
+                if (st != kOk || band) {
+                    Comp<double, NS> c64;
+                    if (comp_fp64_of_fp32<NS>(c64, a.Y, a.ldY, i, a.N, s64[0].sp)) {
+                        const double T0 = (st == kOk) ? Tres : fmin(fmax(Tg, kTLo), kTHi);
+                        double T64, cp64;
+                        int it64;
+                        st = newton_solve<double, double, NS, KIJ>(c64, hs, (double)p, T0, s64[0].sp, s64[0].kij,
+                                                                   a.max_iter, a.rtol, 1e-6, T64, it64, cp64);
+                        Tres = T64;
+                        it += it64;
+                    }
                 }
-                fprev = f;
-                if (fabs(Tn - T) <= rtol * T) {
-                    Tres = Tn;
-                    double h2, cp2;
-                    if (eval_h<Real, RZ, NS, KIJ>(c, Tn, p, s.sp, s.kij, h2, cp2)) { st = kNoRoot; break; }
-                    st = (fabs(h2 - hs) <= jump_tol * fmax(fabs(hs), fabs(cp2) * Tn)) ? kOk : kHRange;
-                    break;
-                }
-                T = Tn;
-                Tres = T;
             }
-            if (it > a.max_iter) it = a.max_iter;
         }
         a.Tout[i] = (Real)Tres;
         a.status[i] = st;

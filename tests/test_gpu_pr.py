@@ -231,3 +231,52 @@ def test_reduced_precision_error_budget(ctx, orc, species, cuda, precision):
     for name, s in summ.items():
         assert s["median"] < 1e-5, (name, s)
         assert s["p99"] < 1e-3, (name, s)
+
+
+def test_mixed_inversion_fp64_in_pseudo_boiling_band(ctx, orc, species, cuda):
+    """The mixed inversion re-solves in FP64 the cells whose cp exceeds three
+    times the ideal-gas cp (the pseudo-boiling band near the pseudo-critical
+    line): there its T equals the FP64 inversion's to FP32 rounding, on
+    O2 and CH4 across their pseudo-boiling temperatures at 10 MPa and on
+    near-pure LOX and CH4 mixtures.  Outside the band it stays the FP32
+    iteration, within the FP32 error budget."""
+    import torch
+    rng = np.random.default_rng(31)
+    n = 4096
+    k_o2, k_ch4 = W.SPECIES.index("O2"), W.SPECIES.index("CH4")
+    Y = np.zeros((9, n))
+    T = np.empty(n)
+    half = n // 2
+    Y[k_o2, :half] = 1.0
+    T[:half] = rng.uniform(140.0, 200.0, half)               # O2: Tc 154.6 K
+    Y[k_ch4, half:] = 1.0
+    T[half:] = rng.uniform(190.0, 280.0, n - half)           # CH4: Tc 190.6 K
+    mix = rng.uniform(0, 1, n) < 0.3                         # a trace of products on some cells
+    Y[:, mix] = 0.97 * Y[:, mix] + 0.03 * W.dirichlet_half(rng, 9, int(mix.sum()))
+    p = np.full(n, 10e6)
+    Tt = np.clip(T * (1 + rng.uniform(-0.03, 0.03, n)), 100.0, 3500.0)
+    d64 = lambda a: to_dev(a, torch.float64, cuda)
+    hs, st0 = ctx.props(d64(Tt), d64(p), d64(Y), outputs=("h", "cp"))
+    assert int((st0 != 0).sum()) == 0
+    # the FP64 reference sees the same FP32-rounded inputs as the mixed path
+    f32 = lambda a: to_dev(a, torch.float32, cuda)
+    h32, p32, Y32, T32 = hs[2].float().contiguous(), f32(p), f32(Y), f32(T)
+    T64, s64, _ = ctx.T_from_h(h32.double(), p32.double(), Y32.double(), T32.double(), "fp64")
+    Tm, sm, _ = ctx.T_from_h(h32, p32, Y32, T32, "mixed", rtol=1e-10)
+    Tf, sf, _ = ctx.T_from_h(h32, p32, Y32, T32, "fp32", rtol=1e-10)
+    T64, s64, Tm, sm, Tf = (a.cpu().numpy() for a in (T64, s64, Tm, sm, Tf))
+    # the band, from the FP64 path's cp and the oracle's ideal-gas enthalpy
+    cp = hs[3].cpu().numpy()
+    dT = 1e-3 * Tt
+    cp_ig = (orc.h_ideal(species, Tt + dT, Y) - orc.h_ideal(species, Tt - dT, Y)) / (2 * dT)
+    ratio = cp / cp_ig
+    ok = (s64 == 0) & (sm == 0)
+    assert ok.mean() > 0.99
+    band = ok & (ratio > 3.3)
+    out = ok & (ratio < 2.7)
+    assert band.sum() > 300 and out.sum() > 300
+    e_m = np.abs(Tm.astype(np.float64) - T64) / T64
+    e_f = np.abs(Tf.astype(np.float64) - T64) / T64
+    print("band cells", int(band.sum()), "mixed max", e_m[band].max(), "fp32 max", e_f[band].max())
+    assert e_m[band].max() < 1.2e-7                           # FP64 result rounded to FP32
+    assert np.median(e_m[out]) < 1e-5 and e_m[out].max() < 1e-3
