@@ -72,6 +72,8 @@ def lib():
             vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
             L.orc_props.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32]
             L.orc_props.restype = None
+            L.orc_props_ext.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32]
+            L.orc_props_ext.restype = None
             L.orc_h_ideal.argtypes = [vp, i64, vp, vp, vp]
             L.orc_h_ideal.restype = None
             L.orc_diagnose.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
@@ -135,6 +137,17 @@ def props(sp, T, p, Y, threads: int = 0, **kw):
     out = np.empty((6, n))
     st = np.empty(n, dtype=np.int32)
     lib().orc_props(tb.ref, n, _ptr(T), _ptr(p), _ptr(Y), _ptr(out), _ptr(st), int(threads))
+    return out, st
+
+
+def props_ext(sp, T, p, Y, threads: int = 0, **kw):
+    """(out[8, n] = rho, Z, h, cp, mu, lambda, psi, alpha; status[n])."""
+    tb = sp if isinstance(sp, Table) else Table(sp, **kw)
+    T, p, Y = _soa(T, p, Y, tb.n)
+    n = T.size
+    out = np.empty((8, n))
+    st = np.empty(n, dtype=np.int32)
+    lib().orc_props_ext(tb.ref, n, _ptr(T), _ptr(p), _ptr(Y), _ptr(out), _ptr(st), int(threads))
     return out, st
 
 

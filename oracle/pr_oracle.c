@@ -493,6 +493,46 @@ void orc_props(const orc_species *sp, int64_t n, const double *T, const double *
     (void)nthreads;
 }
 
+/* Batch with the two further outputs of the paper's networks (Sec. 4.1):
+ * out[8*n] as rho, Z, h, cp, mu, lambda, psi, alpha blocks of n, where
+ *   psi   = (d rho / d p) at constant h [s^2/m^2], written out as the chain
+ *           (d rho/d p)_T + (d rho/d T)_p (d T/d p)_h with
+ *           (d T/d p)_h = -(d h/d p)_T / cp and (d h/d p)_T = V - T (d V/d T)_p,
+ *           every partial from the PR equation's (dp/dT)_V and (dp/dV)_T;
+ *   alpha = lambda / cp [kg/(m s)], the thermal diffusivity of the enthalpy
+ *           equation in the form an OpenFOAM-derived solver carries it. */
+void orc_props_ext(const orc_species *sp, int64_t n, const double *T, const double *p, const double *Y,
+                   double *out, int32_t *status, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        double o[6];
+        orc_diag d;
+        int st = orc_cell(sp, T[i], p[i], Y + i, (ptrdiff_t)n, o, &d);
+        for (int q = 0; q < 6; ++q) out[q * n + i] = o[q];
+        double psi = NAN, alpha = NAN;
+        if (st == ORC_OK || st == ORC_AMBIGUOUS) {
+            const double W = d.Wbar;                          /* kg/mol */
+            const double V = d.Z * ORC_R * T[i] / p[i];       /* m^3/mol */
+            const double cp_molar = o[3] * W;                 /* J/(mol K) */
+            const double drho_dp_T = -W / (V * V * d.dpdV);
+            const double dV_dT_p = -d.dpdT / d.dpdV;
+            const double drho_dT_p = -W / (V * V) * dV_dT_p;
+            const double dh_dp_T = V - T[i] * dV_dT_p;        /* J/(mol Pa) */
+            const double dT_dp_h = -dh_dp_T / cp_molar;
+            psi = drho_dp_T + drho_dT_p * dT_dp_h;
+            alpha = o[5] / o[3];
+        }
+        out[6 * n + i] = psi;
+        out[7 * n + i] = alpha;
+        if (status) status[i] = st;
+    }
+    (void)nthreads;
+}
+
 /* Mass-specific ideal-gas enthalpy h_ig = sum_k Y_k h_k(T) / W_k [J/kg] of n
  * cells (NASA-7, the ideal-gas part of the enthalpy, Sec. 2), SoA as
  * orc_props. */

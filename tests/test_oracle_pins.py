@@ -474,3 +474,43 @@ def test_chung_dilute_conductivity_between_eucken_forms(orc, species, name):
         meu = (1.32 * di["cv_ig_molar"] + 1.77 * R) * di["mu_dilute"] / M
         lo, hi = min(eu, meu), max(eu, meu)
         assert 0.92 * lo <= di["lambda_dilute"] <= 1.08 * hi
+
+
+# ------------------------------------------------- psi = (d rho / d p)_h
+def test_psi_against_constant_enthalpy_differences(orc, species):
+    """psi (Sec. 4.1: d rho / d p at constant enthalpy) against central
+    differences of rho(p) along constant h, each side through the oracle's own
+    T(h, p) inversion: uniform cells, flame-sheet states and pure O2 across
+    its pseudo-boiling temperatures at 10 MPa."""
+    T, p, Y = W.uniform_cells(300, seed=11)
+    Tm, pm, Ym = W.manifold_states(300, seed=12)
+    n = 200
+    Yo = np.zeros((9, n))
+    Yo[W.SPECIES.index("O2")] = 1.0
+    T = np.concatenate([T, Tm, np.linspace(140.0, 200.0, n)])
+    p = np.concatenate([p, pm, np.full(n, 1e7)])
+    Y = np.concatenate([Y, Ym, Yo], axis=1)
+    o, st = orc.props_ext(species, T, p, Y)
+    dp = 1e-5 * p
+    Tp, s1, _ = orc.T_from_h(species, o[2], p + dp, Y, T)
+    Tn, s2, _ = orc.T_from_h(species, o[2], p - dp, Y, T)
+    rp, _ = orc.props(species, Tp, p + dp, Y)
+    rn, _ = orc.props(species, Tn, p - dp, Y)
+    ok = (st == 0) & (s1 == 0) & (s2 == 0)
+    assert ok.sum() > 750
+    fd = (rp[0] - rn[0]) / (2 * dp)
+    np.testing.assert_allclose(o[6][ok], fd[ok], rtol=1e-7)
+
+
+def test_psi_ideal_gas_limit(orc, species):
+    """At 1 Pa the gas is ideal: constant h means constant T, so
+    psi = rho / p = W / (R T)."""
+    T, _, Y = W.uniform_cells(200, seed=13)
+    T = 700.0 + (T - 100.0) * (2800.0 / 3400.0)
+    p = np.ones(T.size)
+    o, st = orc.props_ext(species, T, p, Y)
+    assert np.all(st == 0)
+    np.testing.assert_allclose(o[6], o[0] / p, rtol=1e-7)
+    # the other outputs are those of props; alpha is lambda / cp by definition
+    o6, _ = orc.props(species, T, p, Y)
+    assert np.array_equal(o[:6], o6)
