@@ -103,6 +103,20 @@ pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n,
                    void *rho, void *Z, void *h, void *cp, void *mu, void *lambda,
                    int32_t *cell_status, void *stream);
 
+/* pr_props plus the two further outputs the paper's networks provide to its
+ * solver (Sec. 4.1), from the same evaluation:
+ *   psi   [n]  d rho / d p at constant enthalpy [s^2/m^2] (the solver's
+ *              compressibility), from the PR equation's partial derivatives;
+ *   alpha [n]  thermal diffusivity of the enthalpy equation, lambda / cp
+ *              [kg/(m s)] (the form an OpenFOAM-derived solver carries; divide
+ *              by rho for m^2/s).
+ * Any output may be NULL; asking for alpha runs the transport step.  Same
+ * precisions, layouts, status codes and errors as pr_props. */
+pr_status pr_props_ext(pr_ctx *ctx, pr_precision prec, int64_t n,
+                       const void *T, const void *p, const void *Y, int64_t ldY,
+                       void *rho, void *Z, void *h, void *cp, void *mu, void *lambda,
+                       void *psi, void *alpha, int32_t *cell_status, void *stream);
+
 /* Inversion T(h*, p, Y) by safeguarded Newton on f(T) = h(T) - h*, f' = cp,
  * inside the bracket [60, 5000] K, starting from T_guess (clipped to the
  * bracket).  A Newton step that leaves the current bracket, or follows a step

@@ -22,6 +22,7 @@ PR_FLAG_PRINTED_CONSTANTS = 1
 PR_FLAG_TRANSPORT_XAVG = 2
 PR_FLAG_NEWTON_FP64_ONLY = 4
 OUTPUTS = ("rho", "Z", "h", "cp", "mu", "lambda")
+OUTPUTS_EXT = OUTPUTS + ("psi", "alpha")
 
 CELL_STATUS = {0: "ok", 1: "newton_maxit", 2: "h_out_of_range", 3: "no_root", 4: "bad_input", 5: "ambiguous"}
 
@@ -54,6 +55,8 @@ def lib():
             L.pr_destroy.argtypes = [vp]
             L.pr_destroy.restype = None
             L.pr_props.argtypes = [vp, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.pr_props_ext.argtypes = [vp, i32, i64, vp, vp, vp, i64] + [vp] * 8 + [vp, vp]
+            L.pr_props_ext.restype = i32
             L.pr_props.restype = i32
             L.pr_T_from_h.argtypes = [vp, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, i32, d, vp]
             L.pr_T_from_h.restype = i32
@@ -155,6 +158,20 @@ class PropertyContext:
         ptrs = [(_ptr(out[q]) if OUTPUTS[q] in outputs else None) for q in range(6)]
         check(lib().pr_props(self.handle, prec, n, _ptr(T), _ptr(p), _ptr(Y), ldY, *ptrs, _ptr(status),
                              _stream(stream)), "pr_props")
+        return out, status
+
+    def props_ext(self, T, p, Y, precision="fp64", out=None, status=None, outputs=OUTPUTS_EXT, stream=None):
+        """pr_props_ext; returns (out[8, n] rows rho, Z, h, cp, mu, lambda, psi, alpha; status[n])."""
+        import torch
+        prec = _prec(precision)
+        n, ldY = self._cells(prec, T, p, Y)
+        if out is None:
+            out = torch.empty((8, n), dtype=_dtype_of(prec), device=T.device)
+        if status is None:
+            status = torch.empty(n, dtype=torch.int32, device=T.device)
+        ptrs = [(_ptr(out[q]) if OUTPUTS_EXT[q] in outputs else None) for q in range(8)]
+        check(lib().pr_props_ext(self.handle, prec, n, _ptr(T), _ptr(p), _ptr(Y), ldY, *ptrs, _ptr(status),
+                                 _stream(stream)), "pr_props_ext")
         return out, status
 
     def T_from_h(self, hstar, p, Y, T_guess, precision="fp64", max_iter=60, rtol=1e-13, T_out=None,

@@ -243,9 +243,9 @@ static pr_status check_arrays(int64_t n, size_t esz, std::initializer_list<const
     return PR_OK;
 }
 
-pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n, const void *T, const void *p, const void *Y,
-                   int64_t ldY, void *rho, void *Z, void *h, void *cp, void *mu, void *lambda,
-                   int32_t *cell_status, void *stream)
+static pr_status props_impl(pr_ctx *ctx, pr_precision prec, int64_t n, const void *T, const void *p, const void *Y,
+                            int64_t ldY, void *rho, void *Z, void *h, void *cp, void *mu, void *lambda, void *psi,
+                            void *alpha, int32_t *cell_status, void *stream)
 {
     PR_CHECK_ARG(ctx != nullptr, "pr_props: null context");
     PR_CHECK_ARG(prec == PR_FP64 || prec == PR_FP32 || prec == PR_MIXED, "pr_props: bad precision %d", (int)prec);
@@ -253,7 +253,7 @@ pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n, const void *T, con
     if (n == 0) return PR_OK;
     PR_CHECK_ARG(ldY >= n, "pr_props: ldY (%lld) < n (%lld)", (long long)ldY, (long long)n);
     const size_t esz = (prec == PR_FP64) ? 8 : 4;
-    pr_status s = check_arrays(n, esz, {T, p, Y}, {rho, Z, h, cp, mu, lambda}, "pr_props");
+    pr_status s = check_arrays(n, esz, {T, p, Y}, {rho, Z, h, cp, mu, lambda, psi, alpha}, "pr_props");
     if (s) return s;
     PR_CHECK_ARG(prgb::aligned(cell_status, 4), "pr_props: cell_status misaligned");
     cudaStream_t st = (cudaStream_t)stream;
@@ -263,14 +263,14 @@ pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n, const void *T, con
         PropsArgs<double> a{n, ldY, (const double *)T, (const double *)p, (const double *)Y, (double *)rho,
                             (double *)Z, (double *)h, (double *)cp, (double *)mu, (double *)lambda, cell_status,
                             (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64,
-                            ctx->n_species, ctx->flags};
+                            ctx->n_species, ctx->flags, (double *)psi, (double *)alpha};
         if (ctx->ns_pad == 9) launch_props<double, double, 9>(a, kij, occ, ctx->num_sms, st);
         else launch_props<double, double, 32>(a, kij, occ, ctx->num_sms, st);
     } else {
         PropsArgs<float> a{n, ldY, (const float *)T, (const float *)p, (const float *)Y, (float *)rho,
                            (float *)Z, (float *)h, (float *)cp, (float *)mu, (float *)lambda, cell_status,
                            (const SpeciesRec<float> *)ctx->d_sp32, ctx->d_pair32, ctx->d_kij32,
-                           ctx->n_species, ctx->flags};
+                           ctx->n_species, ctx->flags, (float *)psi, (float *)alpha};
         if (prec == PR_FP32) {
             if (ctx->ns_pad == 9) launch_props<float, float, 9>(a, kij, occ, ctx->num_sms, st);
             else launch_props<float, float, 32>(a, kij, occ, ctx->num_sms, st);
@@ -281,6 +281,20 @@ pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n, const void *T, con
     }
     PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
+}
+
+pr_status pr_props(pr_ctx *ctx, pr_precision prec, int64_t n, const void *T, const void *p, const void *Y,
+                   int64_t ldY, void *rho, void *Z, void *h, void *cp, void *mu, void *lambda,
+                   int32_t *cell_status, void *stream)
+{
+    return props_impl(ctx, prec, n, T, p, Y, ldY, rho, Z, h, cp, mu, lambda, nullptr, nullptr, cell_status, stream);
+}
+
+pr_status pr_props_ext(pr_ctx *ctx, pr_precision prec, int64_t n, const void *T, const void *p, const void *Y,
+                       int64_t ldY, void *rho, void *Z, void *h, void *cp, void *mu, void *lambda, void *psi,
+                       void *alpha, int32_t *cell_status, void *stream)
+{
+    return props_impl(ctx, prec, n, T, p, Y, ldY, rho, Z, h, cp, mu, lambda, psi, alpha, cell_status, stream);
 }
 
 pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n, const void *hstar, const void *p, const void *Y,

@@ -283,6 +283,7 @@ struct Thermo {
     Real Z, rho_mol;      // compressibility, molar density [mol/m^3]
     Real h, cp;           // J/kg, J/(kg K)
     Real cv_ig_molar;     // ideal-gas molar cv [J/(mol K)]
+    Real dpdT, dpdV;      // (dp/dT)_V [Pa/K], (dp/dV)_T [Pa mol/m^3], V molar
     int status;
 };
 
@@ -340,6 +341,8 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
     o.h = (h_ig + h_dep) * iW;
     o.cp = (cp_ig + cp_dep) * iW;
     o.cv_ig_molar = cp_ig - Real(kR);
+    o.dpdT = dpdT;
+    o.dpdV = dpdV;
 }
 
 // ------------------------------------------------------------ transport

@@ -51,14 +51,31 @@ struct PropsArgs {
     const SpeciesRec<Real> *sp;
     const Real *pair, *kij;
     int N, flags;
+    Real *psi, *alpha;   // (d rho/d p)_h [s^2/m^2], lambda/cp [kg/(m s)]; NULL to skip
 };
+
+// psi = (d rho / d p) at constant h (Sec. 4.1) from the EOS partials of the
+// cell: (d rho/d p)_T + (d rho/d T)_p (d T/d p)_h, (d T/d p)_h =
+// -(d h/d p)_T / cp, (d h/d p)_T = V - T (d V/d T)_p, (d V/d T)_p = -(dp/dT)_V
+// / (dp/dV)_T; molar V, cp, mean molar mass W.
+template <typename Real>
+__device__ __forceinline__ Real psi_h(const Thermo<Real> &th, Real T, Real W)
+{
+    const Real V = Real(1) / th.rho_mol;
+    const Real iV2 = th.rho_mol * th.rho_mol;
+    const Real dV_dT = -th.dpdT / th.dpdV;
+    const Real drho_dp_T = -W * iV2 / th.dpdV;
+    const Real drho_dT_p = -W * iV2 * dV_dT;
+    const Real dh_dp_T = V - T * dV_dT;
+    return drho_dp_T - drho_dT_p * dh_dp_T / (th.cp * W);
+}
 
 template <typename Real, typename RZ, int NS, bool KIJ>
 __global__ void __launch_bounds__(kBlock) props_kernel(const PropsArgs<Real> a)
 {
     __shared__ Smem<Real, NS, KIJ> s;
     stage<Real, NS, KIJ>(s, a.sp, a.pair, a.kij);
-    const bool want_tr = (a.mu != nullptr) || (a.lam != nullptr);
+    const bool want_tr = (a.mu != nullptr) || (a.lam != nullptr) || (a.alpha != nullptr);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         const Real T = __ldg(a.T + i), p = __ldg(a.p + i);
@@ -80,6 +97,8 @@ __global__ void __launch_bounds__(kBlock) props_kernel(const PropsArgs<Real> a)
         if (a.cp) a.cp[i] = good ? th.cp : nanv;
         if (a.mu) a.mu[i] = good ? mu : nanv;
         if (a.lam) a.lam[i] = good ? lam : nanv;
+        if (a.psi) a.psi[i] = good ? psi_h<Real>(th, T, c.Wbar) : nanv;
+        if (a.alpha) a.alpha[i] = good ? lam / th.cp : nanv;
         if (a.status) a.status[i] = th.status;
     }
 }

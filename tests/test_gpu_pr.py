@@ -280,3 +280,76 @@ def test_mixed_inversion_fp64_in_pseudo_boiling_band(ctx, orc, species, cuda):
     print("band cells", int(band.sum()), "mixed max", e_m[band].max(), "fp32 max", e_f[band].max())
     assert e_m[band].max() < 1.2e-7                           # FP64 result rounded to FP32
     assert np.median(e_m[out]) < 1e-5 and e_m[out].max() < 1e-3
+
+
+# ------------------------------------------- psi and thermal diffusivity
+def _psi_condition(orc, species, T, p, Y, idx, h=1e-7):
+    """Componentwise condition number of the oracle's psi in (T, p, Y_k)."""
+    base, _ = orc.props_ext(species, T[idx], p[idx], Y[:, idx])
+    kap = np.zeros(idx.size)
+    for which in ["T", "p"] + list(range(Y.shape[0])):
+        qs = []
+        for sgn in (1.0, -1.0):
+            Tt, pt, Yt = T[idx].copy(), p[idx].copy(), Y[:, idx].copy()
+            if which == "T":
+                Tt *= 1 + sgn * h
+            elif which == "p":
+                pt *= 1 + sgn * h
+            else:
+                Yt[which] *= 1 + sgn * h
+            q, _ = orc.props_ext(species, Tt, pt, Yt)
+            qs.append(q[6])
+        kap += np.nan_to_num(np.abs(qs[0] - qs[1]) / (2 * h * np.abs(base[6])), nan=0.0, posinf=0.0)
+    return kap
+
+
+def test_props_ext_psi_alpha_fp64(ctx, orc, species, cuda):
+    """pr_props_ext in FP64 against the oracle on uniform cells and the 32^3
+    flame-vortex field: psi within 1e-10 (or within its input sensitivity,
+    1e-10 + 1e3 eps k_psi, where the oracle shows it ill-conditioned), alpha
+    within the GPU's own lambda and cp errors plus 1e-12, the first six
+    outputs identical to pr_props'; near-critical roots (cond > 1e4) are
+    left out as for cp."""
+    import torch
+    from .parity import EPS
+    T1, p1, Y1 = W.uniform_cells(8192, seed=41)
+    T2, p2, Y2 = W.flame_vortex_field(32)[:3]
+    T, p, Y = np.concatenate([T1, T2]), np.concatenate([p1, p2]), np.concatenate([Y1, Y2], axis=1)
+    d = lambda a: to_dev(a, torch.float64, cuda)
+    g8, gs = ctx.props_ext(d(T), d(p), d(Y))
+    g6, _ = ctx.props(d(T), d(p), d(Y))
+    g8, gs, g6 = g8.cpu().numpy(), gs.cpu().numpy(), g6.cpu().numpy()
+    assert np.array_equal(g8[:6], g6, equal_nan=True)
+    o, ost, cond = oracle_props(orc, species, T, p, Y)
+    o8, ost8 = orc.props_ext(species, T, p, Y)
+    assert np.array_equal(o8[:6], o, equal_nan=True) and np.array_equal(ost8, ost)
+    well = (ost == 0) & (gs == 0) & (cond <= 1e4)
+    assert well.sum() > 40000
+    rel = lambda q: np.abs(g8[q] - o8[q]) / np.abs(o8[q])
+    e_psi, e_alpha = rel(6), rel(7)
+    assert np.all(e_alpha[well] <= 1e-12 + rel(5)[well] + rel(3)[well])
+    idx = np.nonzero(well & (e_psi > 1e-10))[0]
+    print("psi cells above 1e-10:", idx.size, "of", int(well.sum()), "max", e_psi[well].max())
+    assert idx.size < 0.01 * well.sum()
+    if idx.size:
+        kap = _psi_condition(orc, species, T, p, Y, idx)
+        assert np.all(e_psi[idx] <= 1e-10 + 1e3 * EPS * kap)
+    # status and NaNs as pr_props
+    bad = (ost != 0) & (ost != 5)
+    assert np.all(np.isnan(g8[6:, bad]))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_props_ext_reduced_precision(ctx, orc, species, cuda, precision):
+    import torch
+    T, p, Y = W.flame_vortex_field(32)[:3]
+    T32, p32, Y32 = (a.astype(np.float32).astype(np.float64) for a in (T, p, Y))
+    d = lambda a: to_dev(a, torch.float32, cuda)
+    g, gs = ctx.props_ext(d(T32), d(p32), d(Y32), precision=precision)
+    g, gs = g.cpu().numpy().astype(np.float64), gs.cpu().numpy()
+    o, ost = orc.props_ext(species, T32, p32, Y32)
+    ok = (ost == 0) & (gs == 0)
+    for q, name in ((6, "psi"), (7, "alpha")):
+        e = np.abs(g[q, ok] - o[q, ok]) / np.abs(o[q, ok])
+        print(precision, name, np.median(e), np.percentile(e, 99))
+        assert np.median(e) < 1e-5 and np.percentile(e, 99) < 1e-3
