@@ -227,6 +227,22 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * to 1024, hidden_layers x width <= 4560); 0 runs one GEMM launch per layer.  Both give identical outputs.
  * PR_EINVAL for an unknown option or a value the model cannot take. */
 #define SG_OPT_FUSED_INFER 1
+/* SG_OPT_MODE: SG_MODE_FORWARD (default) or SG_MODE_INVERSE, the paper's own
+ * arrangement (Sec. 4.1: the networks take enthalpy, pressure and composition
+ * and return the temperature and the properties the solver needs).  Set it
+ * before fitting the normalisation and training; checkpoints record it.  In
+ * the inverse mode:
+ *   pools:  x = [h*, p, Y_1..Y_9] (h* in J/kg), y = [T, rho, psi, mu, alpha,
+ *           cp] (pr_props_ext's units; alpha = lambda / cp);
+ *   inputs: [h* - h_f(Y), p, Y_1..Y_9, log T_pc, log W] with h_f(Y) = sum_k
+ *           Y_k h_k(298.15 K) / W_k (formation enthalpies removed);
+ *   surrogate_infer: the T argument holds h*, and out [6][ldo] receives
+ *           [T, rho, psi, mu, alpha, cp]; cells outside the training hull get
+ *           the FP64 inversion started from the network's T, then
+ *           pr_props_ext's values at that T (NaN where the inversion fails). */
+#define SG_OPT_MODE 2
+#define SG_MODE_FORWARD 0
+#define SG_MODE_INVERSE 1
 pr_status surrogate_set_option(sg_model *m, int option, int value);
 
 /* Synchronise the device and report PR_ETIMEOUT if a tensor-core kernel gave

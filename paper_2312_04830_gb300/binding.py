@@ -202,6 +202,7 @@ class _SgConfig(ctypes.Structure):
 
 SG_NORM_FLOATS = 64
 SG_OPT_FUSED_INFER = 1
+SG_OPT_MODE, SG_MODE_FORWARD, SG_MODE_INVERSE = 2, 0, 1
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
@@ -256,6 +257,13 @@ class Surrogate:
               "surrogate_create")
         self.handle = h
         self.width, self.hidden_layers, self.max_batch = width, hidden_layers, max_batch
+
+    def set_mode(self, mode: str):
+        """'forward' (T, p, Y -> rho, Z, h, cp, mu, lambda) or 'inverse' (h*, p, Y
+        -> T, rho, psi, mu, alpha, cp); set before fitting and training."""
+        v = {"forward": SG_MODE_FORWARD, "inverse": SG_MODE_INVERSE}[mode]
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_MODE, v), "surrogate_set_option")
+        self.mode = mode
 
     def set_fused_infer(self, on: bool):
         """All layers of an inference chunk in one persistent launch (True,

@@ -66,7 +66,8 @@ struct FusedArgs {
     float *out6;                          // [6][ld6] physical outputs of the chunk's rows
     long long ld6;
     const float *out_mean, *out_std;      // [6] de-standardisation
-    const float *add_h;                   // per-row term added to output 2 (h)
+    const float *add_h;                   // per-row term added to output 2 (h), or NULL
+    int log_mask;                         // bit j set = output j was learned as its logarithm
     uint32_t *done;                       // [R][L + 1] arrival counters, zero at launch
     int *err;                             // set to 1 when a bounded wait runs out
 };
@@ -370,8 +371,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
 #pragma unroll
                         for (int jj = 0; jj < 6; ++jj) {
                             float qv = (__uint_as_float(rr[jj]) + sb[jj]) * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
-                            if (jj == 2) qv += __ldg(a.add_h + m);
-                            a.out6[(long long)jj * a.ld6 + m] = (jj == 1 || jj == 2) ? qv : __expf(qv);
+                            if (jj == 2 && a.add_h) qv += __ldg(a.add_h + m);
+                            a.out6[(long long)jj * a.ld6 + m] = ((a.log_mask >> jj) & 1) ? __expf(qv) : qv;
                         }
                     }
                 }

@@ -58,6 +58,7 @@ struct GemmArgs {
     int64_t ld6;
     const float *out_mean, *out_std;   // [6] de-standardisation
     const float *add_h;       // kEpiOutPhys: per-row term added to output 2 (h) after de-standardisation
+    int log_mask;             // kEpiOutPhys: bit j set = output j was learned as its logarithm
     const float *target;      // kEpiOutLoss: standardised targets [6][ldt]
     int64_t ldt;
     float loss_scale;         // d loss / d y = loss_scale * (y - target)
@@ -298,7 +299,7 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                         const float sv = v[jj] + bias[jj];
                         float qv = sv * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
                         if (jj == 2 && a.add_h) qv += __ldg(a.add_h + m);
-                        a.out6[(int64_t)jj * a.ld6 + m] = (jj == 1 || jj == 2) ? qv : __expf(qv);
+                        a.out6[(int64_t)jj * a.ld6 + m] = ((a.log_mask >> jj) & 1) ? __expf(qv) : qv;
                     }
                 }
             } else if (EPI == kEpiOutLoss) {

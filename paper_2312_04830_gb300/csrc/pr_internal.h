@@ -54,3 +54,6 @@ struct pr_ctx {
     int occ_props[3][2]; // resident blocks per SM: [precision][kij]
     int occ_newton[3][2];
 };
+
+// SG_MODE_FORWARD or SG_MODE_INVERSE of a surrogate (surrogate.cu).
+int sg_mode_of(const sg_model *m);

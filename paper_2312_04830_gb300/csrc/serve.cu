@@ -426,6 +426,7 @@ pr_status serve_create(pr_ctx *ctx, sg_model *model, const sv_config *cfg, sv_se
     PR_CHECK_ARG(cfg->newton_precision == PR_MIXED || cfg->newton_precision == PR_FP32,
                  "serve_create: newton_precision must be PR_MIXED or PR_FP32 (FP32 I/O)");
     PR_CHECK_ARG(cfg->hbm_budget_bytes >= (size_t)1 << 20, "serve_create: budget below 1 MiB");
+    PR_CHECK_ARG(!model || sg_mode_of(model) == SG_MODE_FORWARD, "serve_create: the server takes a forward model");
     sv_server *s = new (std::nothrow) sv_server();
     if (!s) { prgb::set_error("serve_create: host allocation failed"); return PR_ENOMEM; }
     s->ctx = ctx;

@@ -29,6 +29,7 @@
 #include "mlp_gemm.cuh"
 #include "pr_device.cuh"
 #include "pr_internal.h"
+#include "pr_kernels.cuh"
 #include "surrogate_internal.h"
 
 using namespace mlp;
@@ -71,16 +72,39 @@ __device__ __forceinline__ void derived_features(float T, const float *Y, const 
     logW = -logf(s);
 }
 
-// Features of one cell from raw inputs x = [T, p, Y_1..Y_9]:
-// [log T, p, Y_1..Y_9, T_pc / T, log W].
-__device__ __forceinline__ void features(const float *x, int64_t ldx, int64_t i, const void *sp32, float (&f)[NIN])
+__device__ __forceinline__ float h_ideal(float T, const float (&Y)[9], const void *sp32);
+
+// Features of one cell from its first raw input v0, p and Y (in f[1..10]):
+//   forward model (v0 = T):  [log T, p, Y_1..Y_9, T_pc / T, log W];
+//   inverse model (v0 = h*): [h* - h_f(Y), p, Y_1..Y_9, log T_pc, log W], where
+//   h_f(Y) = sum_k Y_k h_k(298.15 K) / W_k removes the formation enthalpies, so
+//   that the first input is the sensible-plus-departure enthalpy.
+__device__ __forceinline__ void cell_features(int mode, float v0, const void *sp32, float (&f)[NIN])
 {
-    const float T = __ldg(x + i);
-    f[0] = logf(T);
+    float tpc_over_T, logW;
+    if (mode == SG_MODE_INVERSE) {
+        float Yk[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Yk[k] = f[2 + k];
+        derived_features(1.0f, f + 2, sp32, tpc_over_T, logW);   // T = 1: T_pc itself
+        f[0] = v0 - h_ideal(298.15f, Yk, sp32);
+        f[11] = logf(tpc_over_T);
+    } else {
+        derived_features(v0, f + 2, sp32, tpc_over_T, logW);
+        f[0] = logf(v0);
+        f[11] = tpc_over_T;
+    }
+    f[12] = logW;
+}
+
+// Features of pool row i, x = [v0, p, Y_1..Y_9] (v0 = T, or h* for the inverse model).
+__device__ __forceinline__ void features(const float *x, int64_t ldx, int64_t i, const void *sp32, int mode,
+                                         float (&f)[NIN])
+{
     f[1] = __ldg(x + ldx + i);
 #pragma unroll
     for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
-    derived_features(T, f + 2, sp32, f[11], f[12]);
+    cell_features(mode, __ldg(x + i), sp32, f);
 }
 
 // Mass-specific ideal-gas enthalpy sum_k Y_k h_k(T) / W_k [J/kg] from the
@@ -101,16 +125,24 @@ __device__ __forceinline__ float h_ideal(float T, const float (&Y)[9], const voi
     return h;
 }
 
+// Outputs learned as logarithms (bit j: output j).
+constexpr int kLogMaskForward = 0x39;   // rho, cp, mu, lambda
+constexpr int kLogMaskInverse = 0x3F;   // all six
+
 // Targets from raw properties and inputs x = [T, p, Y_1..Y_9]:
-// [log rho, Z, h - h_ig(T, Y), log cp, log mu, log lambda].
+//   forward model, y = [rho, Z, h, cp, mu, lambda]:
+//     [log rho, Z, h - h_ig(T, Y), log cp, log mu, log lambda];
+//   inverse model, y = [T, rho, psi, mu, alpha, cp]: the six logarithms.
 __device__ __forceinline__ void targets(const float *x, int64_t ldx, const float *y, int64_t ldy, int64_t i,
-                                        const void *sp32, float (&q)[NOUT])
+                                        const void *sp32, int mode, float (&q)[NOUT])
 {
+    const int lm = (mode == SG_MODE_INVERSE) ? kLogMaskInverse : kLogMaskForward;
 #pragma unroll
     for (int j = 0; j < NOUT; ++j) {
         const float v = __ldg(y + (int64_t)j * ldy + i);
-        q[j] = (j == 1 || j == 2) ? v : logf(v);
+        q[j] = ((lm >> j) & 1) ? logf(v) : v;
     }
+    if (mode == SG_MODE_INVERSE) return;
     float Yk[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Yk[k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
@@ -156,7 +188,7 @@ __global__ void refresh_bf16_kernel(SgDev d)
 // Per-block partial sums (FP64) of the 17 features / targets: sum, sum of
 // squares, min, max.
 __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, const float *y, int64_t ldy,
-                                    const void *sp32, double *part)
+                                    const void *sp32, int mode, double *part)
 {
     double s[NSTAT], s2[NSTAT], mn[NSTAT], mx[NSTAT];
     double cnt = 0;
@@ -164,8 +196,8 @@ __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, cons
     for (int k = 0; k < NSTAT; ++k) { s[k] = 0; s2[k] = 0; mn[k] = 1e300; mx[k] = -1e300; }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float f[NIN], q[NOUT];
-        features(x, ldx, i, sp32, f);
-        targets(x, ldx, y, ldy, i, sp32, q);
+        features(x, ldx, i, sp32, mode, f);
+        targets(x, ldx, y, ldy, i, sp32, mode, q);
         bool fin = true;
 #pragma unroll
         for (int k = 0; k < NSTAT; ++k) fin = fin && isfinite((k < NIN) ? f[k] : q[k - NIN]);
@@ -251,8 +283,8 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
         int64_t src = r;
         if (sample_seed != 0 || n_pool != B) src = (int64_t)(splitmix64(sample_seed ^ ((uint64_t)r * 0xD1B54A32D192ED03ull)) % (uint64_t)n_pool);
         float f[NIN], q[NOUT];
-        features(x, ldx, src, d.sp32, f);
-        targets(x, ldx, y, ldy, src, d.sp32, q);
+        features(x, ldx, src, d.sp32, d.mode, f);
+        targets(x, ldx, y, ldy, src, d.sp32, d.mode, q);
         float v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = (k < NIN) ? (f[k] - nm[k]) / nm[NIN + k] : 0.f;
@@ -274,12 +306,11 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < mc; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = r0 + r;
         float f[NIN];
-        const float Ti = __ldg(T + i);
-        f[0] = logf(Ti);
+        const float Ti = __ldg(T + i);   // h* for the inverse model
         f[1] = __ldg(p + i);
 #pragma unroll
         for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(Y + (int64_t)k * ldY + i);
-        derived_features(Ti, f + 2, d.sp32, f[11], f[12]);
+        cell_features(d.mode, Ti, d.sp32, f);
         bool out = false;
         float v[16];
 #pragma unroll
@@ -295,7 +326,7 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
         float Yk[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Yk[k] = f[2 + k];
-        d.hig[r] = h_ideal(Ti, Yk, d.sp32);
+        if (d.mode != SG_MODE_INVERSE) d.hig[r] = h_ideal(Ti, Yk, d.sp32);
         if (flags) flags[i] = out ? 1 : 0;
         if (out) list[atomicAdd(count, 1u)] = (int32_t)r;
     }
@@ -352,6 +383,63 @@ __global__ void __launch_bounds__(128) fallback_kernel(const int32_t *list, cons
                 prk::transport<double, NS>(c, Tv, th, s_sp, s_pair, flags, mu, lam);
                 o[0] = (float)(pv * c.Wbar / (th.Z * prk::kR * Tv));
                 o[1] = (float)th.Z; o[2] = (float)th.h; o[3] = (float)th.cp; o[4] = (float)mu; o[5] = (float)lam;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) out[(int64_t)q * ldo + i] = o[q];
+    }
+}
+
+// FP64 Peng-Robinson fallback of the inverse model for the listed cells: the
+// safeguarded FP64 inversion T(h*, p, Y), started from the network's own T
+// (clamped to the bracket), then rho, psi, mu, alpha, cp at that T; NaN where
+// the inversion fails.
+template <int NS, bool KIJ>
+__global__ void __launch_bounds__(128) fallback_inverse_kernel(const int32_t *list, const unsigned int *count,
+                                                               int64_t r0, const float *H, const float *p,
+                                                               const float *Y, int64_t ldY, float *out, int64_t ldo,
+                                                               const SpeciesRec<double> *sp, const double *pair,
+                                                               const double *kij, int N, int flags)
+{
+    __shared__ SpeciesRec<double> s_sp[NS];
+    __shared__ double s_pair[NS * NS];
+    __shared__ double s_kij[NS * NS];
+    {
+        const double *src = reinterpret_cast<const double *>(sp);
+        double *dst = reinterpret_cast<double *>(s_sp);
+        for (int j = threadIdx.x; j < (int)(NS * sizeof(SpeciesRec<double>) / 8); j += blockDim.x) dst[j] = src[j];
+        for (int j = threadIdx.x; j < NS * NS; j += blockDim.x) { s_pair[j] = pair[j]; s_kij[j] = kij[j]; }
+    }
+    __syncthreads();
+    const unsigned int n = *count;
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int64_t i = r0 + list[t];
+        const double hv = (double)__ldg(H + i), pv = (double)__ldg(p + i);
+        prk::Comp<double, NS> c;
+        bool ok = prk::comp_fp64_of_fp32<NS>(c, Y, ldY, i, N, s_sp) && (pv > 0) && isfinite(hv) && isfinite(pv);
+        float o[6];
+        for (int q = 0; q < 6; ++q) o[q] = __int_as_float(0x7fc00000);
+        if (ok) {
+            double T0 = (double)out[i];   // the network's T
+            if (!(T0 == T0)) T0 = 300.0;
+            T0 = fmin(fmax(T0, prk::kTLo), prk::kTHi);
+            double T, cpl;
+            int it;
+            const int st = prk::newton_solve<double, double, NS, KIJ>(c, hv, pv, T0, s_sp, s_kij, 60, 1e-12, 1e-6, T,
+                                                                     it, cpl);
+            if (st == prk::kOk) {
+                prk::Thermo<double> th;
+                prk::thermo<double, double, NS, KIJ>(c, T, pv, s_sp, s_kij, th);
+                if (th.status != prk::kNoRoot) {
+                    double mu, lam;
+                    prk::transport<double, NS>(c, T, th, s_sp, s_pair, flags, mu, lam);
+                    o[0] = (float)T;
+                    o[1] = (float)(pv * c.Wbar / (th.Z * prk::kR * T));
+                    o[2] = (float)prk::psi_h<double>(th, T, c.Wbar);
+                    o[3] = (float)mu;
+                    o[4] = (float)(lam / th.cp);
+                    o[5] = (float)th.cp;
+                }
             }
         }
 #pragma unroll
@@ -868,7 +956,8 @@ pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, in
 {
     PR_CHECK_ARG(m && x && y && n > 0 && ldx >= n && ldy >= n, "surrogate_fit_normalization: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->dev.sp32, m->d_normpart);
+    norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->dev.sp32, m->dev.mode,
+                                                         m->d_normpart);
     norm_final_kernel<<<1, 32, 0, st>>>(m->norm_blocks, m->d_normpart, m->dev.norm);
     PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
@@ -1011,7 +1100,9 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             fa.total = (long long)(fa.R + (long long)L * fa.D) * fa.ips;
             fa.out6 = out + r0; fa.ld6 = ldo;
             fa.out_mean = d.norm + 2 * NIN; fa.out_std = d.norm + 2 * NIN + NOUT;
-            fa.add_h = d.hig; fa.done = m->d_done; fa.err = m->d_err;
+            fa.add_h = (d.mode == SG_MODE_INVERSE) ? nullptr : d.hig;
+            fa.log_mask = (d.mode == SG_MODE_INVERSE) ? kLogMaskInverse : kLogMaskForward;
+            fa.done = m->d_done; fa.err = m->d_err;
             PR_CUDA_TRY(cudaMemsetAsync(m->d_done, 0, (size_t)mt * (L + 1) * 4, st));
             PR_CUDA_TRY(launch_fused(fa, st));
         }
@@ -1030,12 +1121,23 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.bias = d.master + d.lay[L].b_off;
             a.out6 = out + r0; a.ld6 = ldo;
             a.out_mean = d.norm + 2 * NIN; a.out_std = d.norm + 2 * NIN + NOUT;
-            a.add_h = d.hig;
+            a.add_h = (d.mode == SG_MODE_INVERSE) ? nullptr : d.hig;
+            a.log_mask = (d.mode == SG_MODE_INVERSE) ? kLogMaskInverse : kLogMaskForward;
             PR_CUDA_TRY((launch_gemm<16, kEpiOutPhys>(m->tm_hi[(L - 1) & 1], m->tm_w[L], a, mt, 1, 1, st)));
         }
         // FP64 Peng-Robinson for the cells outside the training hull
         const int fb = ctx->num_sms * 4;
-        if (ctx->has_kij)
+        const SpeciesRec<double> *sp64 = (const SpeciesRec<double> *)ctx->d_sp64;
+        if (d.mode == SG_MODE_INVERSE) {
+            if (ctx->has_kij)
+                fallback_inverse_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
+                                                                     ldo, sp64, ctx->d_pair64, ctx->d_kij64,
+                                                                     ctx->n_species, ctx->flags);
+            else
+                fallback_inverse_kernel<9, false><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
+                                                                      ldo, sp64, ctx->d_pair64, ctx->d_kij64,
+                                                                      ctx->n_species, ctx->flags);
+        } else if (ctx->has_kij)
             fallback_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out, ldo,
                                                          (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64,
                                                          ctx->d_kij64, ctx->n_species, ctx->flags);
@@ -1048,6 +1150,12 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
     return PR_OK;
 }
 
+}  // extern "C"
+
+int sg_mode_of(const sg_model *m) { return m->dev.mode; }
+
+extern "C" {
+
 pr_status surrogate_set_option(sg_model *m, int option, int value)
 {
     PR_CHECK_ARG(m != nullptr, "surrogate_set_option: null model");
@@ -1057,6 +1165,11 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
                      "surrogate_set_option: fused inference needs a width that is a multiple of 256, <= 1024, "
                      "and its biases within shared memory");
         m->fused_on = value;
+        return PR_OK;
+    case SG_OPT_MODE:
+        PR_CHECK_ARG(value == SG_MODE_FORWARD || value == SG_MODE_INVERSE, "surrogate_set_option: bad mode %d",
+                     value);
+        m->dev.mode = value;
         return PR_OK;
     default:
         PR_CHECK_ARG(false, "surrogate_set_option: unknown option %d", option);
@@ -1094,7 +1207,7 @@ pr_status surrogate_save(const sg_model *m, const char *path)
     const char magic[4] = {'P', 'R', 'S', 'G'};
     // format 3: 13 inputs (with T_pc / T and log W); the enthalpy output is the
     // departure from the ideal-gas enthalpy
-    const int32_t hdr[4] = {3, m->width, m->hidden, 0};
+    const int32_t hdr[4] = {3, m->width, m->hidden, m->dev.mode};
     const int64_t step = m->step;
     bool ok = fwrite(magic, 1, 4, f) == 4 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&step, 8, 1, f) == 1 &&
               fwrite(&n, 8, 1, f) == 1 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
@@ -1113,7 +1226,8 @@ pr_status surrogate_load(sg_model *m, const char *path)
     int64_t step = 0, n = 0;
     bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "PRSG", 4) == 0 && fread(hdr, 4, 4, f) == 4 &&
               fread(&step, 8, 1, f) == 1 && fread(&n, 8, 1, f) == 1;
-    ok = ok && hdr[0] == 3 && hdr[1] == m->width && hdr[2] == m->hidden && n == m->dev.n_master;
+    ok = ok && hdr[0] == 3 && hdr[1] == m->width && hdr[2] == m->hidden && hdr[3] == m->dev.mode &&
+         n == m->dev.n_master;
     std::vector<float> buf;
     if (ok) {
         buf.resize(3 * n + SG_NORM_FLOATS);

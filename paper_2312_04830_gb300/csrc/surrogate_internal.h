@@ -44,6 +44,7 @@ struct SgDev {
     // inference chunk buffers
     __nv_bfloat16 *xi, *hi[2];
     float *hig;                             // ideal-gas enthalpy of the chunk's cells [chunk]
+    int mode;                               // SG_MODE_FORWARD or SG_MODE_INVERSE
     const void *sp32;                       // the context's FP32 species records (NASA-7 data)
 };
 

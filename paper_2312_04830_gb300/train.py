@@ -55,20 +55,47 @@ def label_pool(ctx, T, p, Y, device, chunk=1 << 23):
     return torch.cat(xs, dim=1).contiguous(), torch.cat(ys, dim=1).contiguous()
 
 
+INVERSE_OUT_NAMES = ("T", "rho", "psi", "mu", "alpha", "cp")
+
+
+def label_pool_inverse(ctx, T, p, Y, device, chunk=1 << 23):
+    """Pool of the inverse model (Sec. 4.1's arrangement): x = [h, p, Y] and
+    y = [T, rho, psi, mu, alpha, cp], float32, from pr_props_ext in FP64 on the
+    states (T, p, Y), with the same physical-outcome filter as label_pool and
+    psi > 0 (a stable fluid's density rises with pressure at constant h)."""
+    import torch
+    xs, ys = [], []
+    for a in range(0, T.size, chunk):
+        b = min(T.size, a + chunk)
+        d = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=device)
+        Td, pd, Yd = d(T[a:b]), d(p[a:b]), d(Y[:, a:b])
+        o, st = ctx.props_ext(Td, pd, Yd, precision="fp64")
+        dil, _ = ctx.props(Td, torch.ones_like(pd), Yd, precision="fp64", outputs=("mu", "lambda"))
+        keep = (st == 0) & torch.all(torch.isfinite(o), dim=0) & torch.all(o[[0, 3, 4, 5, 6, 7]] > 0, dim=0)
+        keep &= (o[4] >= DILUTE_FLOOR * dil[4]) & (o[5] >= DILUTE_FLOOR * dil[5])
+        xs.append(torch.cat([o[2][None], pd[None], Yd], dim=0)[:, keep].float())
+        ys.append(torch.stack([Td, o[0], o[6], o[4], o[7], o[3]])[:, keep].float())
+    return torch.cat(xs, dim=1).contiguous(), torch.cat(ys, dim=1).contiguous()
+
+
+def make_pool_inverse(ctx, n, seed, device):
+    T, p, Y = W.training_states(n, seed=seed)
+    return label_pool_inverse(ctx, T, p, Y, device)
+
+
 def make_pool(ctx, n, seed, device):
     T, p, Y = W.training_states(n, seed=seed)
     return label_pool(ctx, T, p, Y, device)
 
 
-def relative_rms(pred, ref):
+def relative_rms(pred, ref, names=OUT_NAMES):
     """Per-output relative RMS error (h relative to max(|h|, std of h))."""
     import torch
-    sh = torch.std(ref[2])
     out = {}
-    for j, nm in enumerate(OUT_NAMES):
+    for j, nm in enumerate(names):
         s = torch.abs(ref[j])
         if nm == "h":
-            s = torch.clamp(s, min=float(sh))
+            s = torch.clamp(s, min=float(torch.std(ref[j])))
         e = (pred[j] - ref[j]) / s
         a = torch.abs(e[:1 << 24]).float()
         out[nm] = {"rel_rms": float(torch.sqrt(torch.mean(e * e))),
