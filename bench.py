@@ -61,6 +61,7 @@ BYTES_PER_CELL = {
     "props_fp32": (2 + N_SPECIES) * 4 + 6 * 4 + 4,
     "newton_fp32": (3 + N_SPECIES) * 4 + 4 + 4 + 4,
     "surrogate_bf16": (2 + N_SPECIES) * 4 + 6 * 4 + 1,
+    "surrogate_inverse_bf16": (2 + N_SPECIES) * 4 + 6 * 4 + 1,
 }
 
 
@@ -242,13 +243,16 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- our arm
 def train_surrogate(ctx, dev, args):
-    """Train the surrogate on PR-labelled states (untimed set-up of the
-    inference path; its own throughput and held-out error are reported)."""
+    """Train the surrogates on PR-labelled states (untimed set-up of the
+    inference paths; their own throughput and held-out error are reported):
+    the forward model and, on the same states, the inverse model."""
     import torch
-    from paper_2312_04830_gb300 import binding, train as TR
+    from paper_2312_04830_gb300 import binding, train as TR, workloads as W
     t0 = time.perf_counter()
-    x, y = TR.make_pool(ctx, args.sg_pool, 20231207, dev)
-    xh, yh = TR.make_pool(ctx, 1 << 20, 20231208, dev)
+    Tp, pp, Yp = W.training_states(args.sg_pool, seed=20231207)
+    Th, ph, Yh = W.training_states(1 << 20, seed=20231208)
+    x, y = TR.label_pool(ctx, Tp, pp, Yp, dev)
+    xh, yh = TR.label_pool(ctx, Th, ph, Yh, dev)
     t_data = time.perf_counter() - t0
     sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=SG_CHUNK)
     sg.fit_normalization(x, y)
@@ -267,7 +271,20 @@ def train_surrogate(ctx, dev, args):
               "loss_first_last": [losses[0][1], losses[-1][1]],
               "heldout_error_vs_pr_fp64": TR.evaluate(sg, xh, yh)}
     del x, y, xh, yh
-    return sg, report
+    # the inverse model (h, p, Y -> T, rho, psi, mu, alpha, cp), same recipe
+    x, y = TR.label_pool_inverse(ctx, Tp, pp, Yp, dev)
+    del Tp, pp, Yp
+    sgi = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=SG_CHUNK)
+    sgi.set_mode("inverse")
+    sgi.fit_normalization(x, y)
+    steps_i = args.sg_steps if args.sg_steps > 0 else int(round(args.sg_epochs * x.shape[1] / 65536))
+    losses_i, secs_i = TR.train(sgi, x, y, steps_i, 65536, 1e-3, log_every=max(1, steps_i // 10))
+    sgi.sync_status()
+    report["inverse"] = {"pool": int(x.shape[1]), "steps": steps_i, "seconds": secs_i,
+                         "samples_per_s": 65536 * steps_i / secs_i,
+                         "loss_first_last": [losses_i[0][1], losses_i[-1][1]]}
+    del x, y
+    return sg, sgi, report
 
 
 def run_serving(ctx, sg, T, p, Y, hs64, args):
@@ -337,7 +354,7 @@ def run_ours(args):
 
     species = W.species_table()
     ctx = binding.PropertyContext(species)
-    sg, sg_report = (None, None) if args.no_surrogate else train_surrogate(ctx, dev, args)
+    sg, sgi, sg_report = (None, None, None) if args.no_surrogate else train_surrogate(ctx, dev, args)
     T, p, Y, Ttrue = make_field(args.grid)
     n = T.size
 
@@ -354,6 +371,13 @@ def run_ours(args):
     out64 = torch.empty((6, n), dtype=torch.float64, device=dev)
     out32 = torch.empty((6, n), dtype=torch.float32, device=dev)
     outsg = torch.empty((6, n), dtype=torch.float32, device=dev)
+    outsi = torch.empty((6, n), dtype=torch.float32, device=dev)
+    fbi = torch.empty(n, dtype=torch.uint8, device=dev)
+    # the inverse model's input: the field's own enthalpy (the flow's h, as the
+    # paper's solver hands it over), from the FP64 path
+    hT, _ = ctx.props(T64, p64, Y64, precision="fp64", outputs=("h",))
+    hi32 = hT[2].float().contiguous()
+    del hT
     fb = torch.empty(n, dtype=torch.uint8, device=dev)
     st = torch.empty(n, dtype=torch.int32, device=dev)
     Tn64, Tn32 = torch.empty_like(T64), torch.empty_like(T32)
@@ -373,6 +397,10 @@ def run_ours(args):
         calls["surrogate_bf16"] = lambda: sg.infer(T32, p32, Y32, out=outsg, used_fallback=fb)
         n_chunks = (n + SG_CHUNK - 1) // SG_CHUNK
         launches["surrogate_bf16"] = n_chunks * (1 + 1 + 1)     # prep, fused MLP, fallback per chunk
+        # the inverse model: h*, p, Y -> T, rho, psi, mu, alpha, cp (the paper's arrangement)
+        paths.append("surrogate_inverse_bf16")
+        calls["surrogate_inverse_bf16"] = lambda: sgi.infer(hi32, p32, Y32, out=outsi, used_fallback=fbi)
+        launches["surrogate_inverse_bf16"] = n_chunks * (1 + 1 + 1)
     launches_per_step = sum(launches.values())
 
     def step(ev=None):
@@ -426,12 +454,24 @@ def run_ours(args):
             del dil
             field_err["surrogate_bf16_physical"] = TR.relative_rms(outsg[:, phys], ref[:, phys])
             field_err["physical_cells"] = int(phys.sum())
+            # inverse model against the field's T and pr_props_ext there (FP64), physical cells
+            Tt64 = T64
+            o8, st8 = ctx.props_ext(Tt64, p64, Y64, "fp64")
+            dil, _ = ctx.props(Tt64, torch.ones_like(p64), Y64, "fp64", outputs=("mu", "lambda"))
+            physi = (st8 == 0) & torch.all(torch.isfinite(o8), dim=0) & (o8[4] >= TR.DILUTE_FLOOR * dil[4]) & \
+                (o8[5] >= TR.DILUTE_FLOOR * dil[5])
+            refi = torch.stack([Tt64, o8[0], o8[6], o8[4], o8[7], o8[3]]).float()
+            field_err["surrogate_inverse_bf16_physical"] = TR.relative_rms(outsi[:, physi], refi[:, physi],
+                                                                           TR.INVERSE_OUT_NAMES)
+            field_err["inverse_physical_cells"] = int(physi.sum())
+            del o8, dil, refi, Tt64
         field_err["cells"] = int(ok.sum())
 
     # ----------------------------------------------------------- e2e
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(ctx, sg, T, p, Y, hs64, hs32, dev, stream, max(2, min(args.steps, 4)), ws)
+        e2e = run_e2e(ctx, sg, sgi, hi32 if sgi is not None else None, T, p, Y, hs64, hs32, dev, stream,
+                      max(2, min(args.steps, 4)), ws)
 
     if rank != 0:
         if ws > 1:
@@ -449,9 +489,14 @@ def run_ours(args):
         if nm in FP64_FLOPS_PER_CELL:
             tf = FP64_FLOPS_PER_CELL[nm] * n / sec / 1e12
             r.update({"fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS})
-        if nm == "surrogate_bf16":
-            tf = mlp_flops_per_cell() * n * (1.0 - fb_frac) / sec / 1e12
-            r.update({"tensor_tflops": tf, "tensor_frac": tf / bf16_peak, "fallback_fraction": fb_frac})
+        if nm in ("surrogate_bf16", "surrogate_inverse_bf16"):
+            ff = fb_frac if nm == "surrogate_bf16" else float(fbi.float().mean())
+            tf = mlp_flops_per_cell() * n * (1.0 - ff) / sec / 1e12
+            r.update({"tensor_tflops": tf, "tensor_frac": tf / bf16_peak, "fallback_fraction": ff})
+        if nm == "surrogate_inverse_bf16":
+            # the path it replaces: the FP64 inversion, then the FP64 properties
+            r["speedup_vs_fp64_inversion_plus_props"] = (per_path_ms["newton_fp64"] +
+                                                        per_path_ms["props_fp64"]) / per_path_ms[nm]
         roof_paths[nm] = r
     dom = max(per_path_ms, key=per_path_ms.get)
     d = roof_paths[dom]
@@ -496,7 +541,7 @@ def run_ours(args):
     return 0
 
 
-def run_e2e(ctx, sg, T, p, Y, hs64, hs32, dev, stream, steps, ws):
+def run_e2e(ctx, sg, sgi, hi32, T, p, Y, hs64, hs32, dev, stream, steps, ws):
     """Same metric through the C ABI with HOST buffers: per step, pinned-host
     inputs are copied to the device, every path runs, and every output is
     copied back to pinned host memory."""
@@ -507,6 +552,8 @@ def run_e2e(ctx, sg, T, p, Y, hs64, hs32, dev, stream, steps, ws):
               hs64.cpu().pin_memory(), pin(T, torch.float64)]
     h_in32 = [pin(T, torch.float32), pin(p, torch.float32), pin(Y, torch.float32),
               hs32.cpu().pin_memory(), pin(T, torch.float32)]
+    if sgi is not None:
+        h_in32.append(hi32.cpu().pin_memory())   # the inverse model's h (the field's own)
     d_in64 = [torch.empty_like(x, device=dev) for x in h_in64]
     d_in32 = [torch.empty_like(x, device=dev) for x in h_in32]
     o64 = torch.empty((6, n), dtype=torch.float64, device=dev)
@@ -517,12 +564,16 @@ def run_e2e(ctx, sg, T, p, Y, hs64, hs32, dev, stream, steps, ws):
     sts = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
     it = torch.empty(n, dtype=torch.int32, device=dev)
     d_out = [o64, t64, o32, t32] + sts
+    osi = torch.empty((6, n), dtype=torch.float32, device=dev)
+    fbi = torch.empty(n, dtype=torch.uint8, device=dev)
     if sg is not None:
         d_out += [osg, fbd]
+    if sgi is not None:
+        d_out += [osi, fbi]
     h_out = [torch.empty_like(x, device="cpu").pin_memory() for x in d_out]
     h2d = sum(x.numel() * x.element_size() for x in h_in64 + h_in32)
     d2h = sum(x.numel() * x.element_size() for x in h_out)
-    n_paths = 4 + (1 if sg is not None else 0)
+    n_paths = 4 + (1 if sg is not None else 0) + (1 if sgi is not None else 0)
 
     def one():
         for h, d in zip(h_in64 + h_in32, d_in64 + d_in32):
@@ -533,6 +584,8 @@ def run_e2e(ctx, sg, T, p, Y, hs64, hs32, dev, stream, steps, ws):
         ctx.T_from_h(d_in32[3], d_in32[1], d_in32[2], d_in32[4], "fp32", T_out=t32, status=sts[3], iters=it)
         if sg is not None:
             sg.infer(d_in32[0], d_in32[1], d_in32[2], out=osg, used_fallback=fbd)
+        if sgi is not None:
+            sgi.infer(d_in32[5], d_in32[1], d_in32[2], out=osi, used_fallback=fbi)
         for d, h in zip(d_out, h_out):
             h.copy_(d, non_blocking=True)
 
