@@ -321,11 +321,13 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
     const Real iW = Real(1) / c.Wbar;
 
     // departures (in RZ where the root enters, then Real)
-    const RZ dp = RZ(1.0 + kSqrt2), dm = RZ(1.0 - kSqrt2);
-    const RZ L = M<RZ>::log1p(RZ(2.0 * kSqrt2) * B / (Zz + dm * B));   // ln[(Z + dp B)/(Z + dm B)]
-    (void)dp;
+    const RZ dm = RZ(1.0 - kSqrt2);
+    // ln[(Z + (1 + sqrt 2) B)/(Z + (1 - sqrt 2) B)] = log1p(2 sqrt 2 B / (Z + (1 - sqrt 2) B)):
+    // the argument from the root's precision; the logarithm at the outputs'
+    // (the mixed path keeps FP64 for the root alone)
+    const RZ larg = RZ(2.0 * kSqrt2) * B / (Zz + dm * B);
     const Real Z = (Real)Zz;
-    const Real Lr = (Real)L;
+    const Real Lr = M<Real>::log1p((Real)larg);
     const Real inv2s2b = Real(1) / (Real(2.0 * kSqrt2) * bm);
     const Real h_dep = M<Real>::fma(RT, (Real)(Zz - RZ(1)), M<Real>::fma(T, dam, -am) * inv2s2b * Lr);
     const Real cv_dep = T * d2am * inv2s2b * Lr;
