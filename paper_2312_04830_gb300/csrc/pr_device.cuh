@@ -401,12 +401,18 @@ template <> __device__ __forceinline__ double chung_cond<double>(int i, int j) {
 template <> __device__ __forceinline__ float chung_cond<float>(int i, int j) { return kChungCond[i][j]; }
 
 // Chung dense-fluid mu [Pa s] and lambda [W/(m K)] for corresponding-states
-// parameters (Tc [K], Vc [cm^3/mol], omega, M [g/mol], mu_r^4, kappa).
+// parameters (Tc [K], Vc [cm^3/mol] and its cube root cVc, omega, M [g/mol],
+// mu_r^4, kappa).  The square roots of T*, M T and Tc / M all follow from
+// sqrt(T / Tc) and sqrt(M Tc).
 template <typename Real>
-__device__ __forceinline__ void chung_dense(Real Tc, Real Vc, Real omega, Real Mg, Real mur4, Real kap,
+__device__ __forceinline__ void chung_dense(Real Tc, Real Vc, Real cVc, Real omega, Real Mg, Real mur4, Real kap,
                                             Real T, Real rho_mol, Real cv_molar, Real &mu, Real &lam)
 {
-    const Real Ts = Real(1.2593) * T / Tc;
+    const Real Tr = T / Tc;
+    const Real sTr = M<Real>::sqrt(Tr);
+    const Real sMTc = M<Real>::sqrt(Mg * Tc);
+    const Real iMg = Real(1) / Mg;
+    const Real Ts = Real(1.2593) * Tr;
     const Real Fc = Real(1) - Real(0.2756) * omega + Real(0.059035) * mur4 + kap;
     const Real lnTs = M<Real>::log(Ts);
     const Real Ov = Real(1.16145) * M<Real>::exp(Real(-0.14874) * lnTs) + Real(0.52487) * M<Real>::exp(Real(-0.77320) * Ts)
@@ -418,32 +424,31 @@ __device__ __forceinline__ void chung_dense(Real Tc, Real Vc, Real omega, Real M
 #pragma unroll
     for (int i = 0; i < 10; ++i)
         E[i] = chung_visc<Real>(i, 0) + chung_visc<Real>(i, 1) * omega + chung_visc<Real>(i, 2) * mur4 + chung_visc<Real>(i, 3) * kap;
-    const Real fy4 = (y > Real(0)) ? -M<Real>::expm1(-E[3] * y) / y : E[3];
+    const Real iy = Real(1) / y;
+    const Real fy4 = (y > Real(0)) ? -M<Real>::expm1(-E[3] * y) * iy : E[3];
     const Real G2 = (E[0] * fy4 + E[1] * G1 * M<Real>::exp(E[4] * y) + E[2] * G1) / (E[0] * E[3] + E[1] + E[2]);
     const Real iTs = Real(1) / Ts;
     const Real etass = E[6] * y * y * G2 * M<Real>::exp(E[7] + iTs * (E[8] + E[9] * iTs));
-    const Real sqTs = M<Real>::sqrt(Ts);
+    const Real sqTs = Real(1.1221853679316978) * sTr;   // sqrt(1.2593) sqrt(Tr)
     const Real iOv = Real(1) / Ov;
     const Real etas = sqTs * iOv * Fc * (Real(1) / G2 + E[5] * y) + etass;
-    const Real cVc = M<Real>::cbrt(Vc);
     const Real iVc23 = Real(1) / (cVc * cVc);
-    mu = etas * Real(36.344e-7) * M<Real>::sqrt(Mg * Tc) * iVc23;
-    const Real eta0 = Real(40.785e-7) * Fc * M<Real>::sqrt(Mg * T) * iVc23 * iOv;
+    mu = etas * Real(36.344e-7) * sMTc * iVc23;
+    const Real eta0 = Real(40.785e-7) * Fc * (sMTc * sTr) * iVc23 * iOv;   // sqrt(M T)
     Real Bc[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i)
         Bc[i] = chung_cond<Real>(i, 0) + chung_cond<Real>(i, 1) * omega + chung_cond<Real>(i, 2) * mur4 + chung_cond<Real>(i, 3) * kap;
-    const Real fyb4 = (y > Real(0)) ? -M<Real>::expm1(-Bc[3] * y) / y : Bc[3];
+    const Real fyb4 = (y > Real(0)) ? -M<Real>::expm1(-Bc[3] * y) * iy : Bc[3];
     const Real H2 = (Bc[0] * fyb4 + Bc[1] * G1 * M<Real>::exp(Bc[4] * y) + Bc[2] * G1) / (Bc[0] * Bc[3] + Bc[1] + Bc[2]);
-    const Real Tr = T / Tc;
     const Real al = cv_molar * Real(1.0 / kR) - Real(1.5);
     const Real be = Real(0.7862) - Real(0.7109) * omega + Real(1.3168) * omega * omega;
     const Real Zp = Real(2.0) + Real(10.5) * Tr * Tr;
     const Real Psi = Real(1) + al * ((Real(0.215) + Real(0.28288) * al - Real(1.061) * be + Real(0.26665) * Zp) /
                                      (Real(0.6366) + be * Zp + Real(1.061) * al * be));
-    const Real Mkg = Mg * Real(1e-3);
-    const Real q = Real(3.586e-3) * M<Real>::sqrt(Tc / Mkg) * iVc23;
-    lam = Real(31.2) * eta0 * Psi / Mkg * (Real(1) / H2 + Bc[5] * y) + q * Bc[6] * y * y * M<Real>::sqrt(Tr) * H2;
+    const Real iMkg = Real(1e3) * iMg;
+    const Real q = Real(3.586e-3) * (Real(31.622776601683793) * sMTc * iMg) * iVc23;   // sqrt(Tc / M[kg/mol])
+    lam = Real(31.2) * eta0 * Psi * iMkg * (Real(1) / H2 + Bc[5] * y) + q * Bc[6] * y * y * sTr * H2;
 }
 
 // Chung's mixture rules.  With the combining rules sigma_ij = sqrt(sigma_i
@@ -462,8 +467,8 @@ __device__ __forceinline__ void transport(const Comp<Real, NS> &c, Real T, const
         for (int k = 0; k < NS; ++k) {
             if (c.x[k] == Real(0)) continue;
             Real mk, lk;
-            chung_dense<Real>(sp[k].Tc, sp[k].Vc, sp[k].omega, sp[k].M, sp[k].mur4, sp[k].kap, T, th.rho_mol,
-                              th.cv_ig_molar, mk, lk);
+            chung_dense<Real>(sp[k].Tc, sp[k].Vc, M<Real>::cbrt(sp[k].Vc), sp[k].omega, sp[k].M, sp[k].mur4,
+                              sp[k].kap, T, th.rho_mol, th.cv_ig_molar, mk, lk);
             m = M<Real>::fma(c.x[k], mk, m);
             l = M<Real>::fma(c.x[k], lk, l);
         }
@@ -497,7 +502,7 @@ __device__ __forceinline__ void transport(const Comp<Real, NS> &c, Real T, const
     const Real Tcm = Real(1.2593) * em;
     const Real murd = Real(131.3 * 131.3) / (Vcm * Tcm);   // mu_r^2 / mu^2
     const Real mur4 = mu4 * murd * murd;
-    chung_dense<Real>(Tcm, Vcm, wm, Mm, mur4, km, T, th.rho_mol, th.cv_ig_molar, mu, lam);
+    chung_dense<Real>(Tcm, Vcm, sm * Real(1.0 / 0.809), wm, Mm, mur4, km, T, th.rho_mol, th.cv_ig_molar, mu, lam);
 }
 
 }  // namespace prk
