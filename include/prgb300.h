@@ -241,6 +241,15 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  *           the FP64 inversion started from the network's T, then
  *           pr_props_ext's values at that T (NaN where the inversion fails). */
 #define SG_OPT_MODE 2
+/* SG_OPT_WAIT_LIMIT_KCYCLES: limit, in thousands of SM clock cycles, of every
+ * bounded wait of the fused inference kernel (0: the default, 4e9 cycles,
+ * about 2 s).  When a wait runs out the kernel stops waiting, finishes without
+ * its results and flags the model: surrogate_sync_status returns PR_ETIMEOUT
+ * and clears the flag, and the next call runs normally.
+ * SG_OPT_TEST_STALL: test hook for that path; 1 makes layer 1 of the first
+ * row block of every chunk wait for an arrival that never comes. */
+#define SG_OPT_WAIT_LIMIT_KCYCLES 3
+#define SG_OPT_TEST_STALL 4
 #define SG_MODE_FORWARD 0
 #define SG_MODE_INVERSE 1
 pr_status surrogate_set_option(sg_model *m, int option, int value);

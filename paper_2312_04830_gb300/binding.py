@@ -203,6 +203,7 @@ class _SgConfig(ctypes.Structure):
 SG_NORM_FLOATS = 64
 SG_OPT_FUSED_INFER = 1
 SG_OPT_MODE, SG_MODE_FORWARD, SG_MODE_INVERSE = 2, 0, 1
+SG_OPT_WAIT_LIMIT_KCYCLES, SG_OPT_TEST_STALL = 3, 4
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
@@ -269,6 +270,17 @@ class Surrogate:
         """All layers of an inference chunk in one persistent launch (True,
         the default where the width allows it) or one launch per layer."""
         check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_FUSED_INFER, int(bool(on))), "surrogate_set_option")
+
+    def set_wait_limit(self, kcycles: int):
+        """Limit, in thousands of SM clock cycles, of every bounded wait in the
+        fused inference kernel; 0 restores the default (4e9 cycles)."""
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_WAIT_LIMIT_KCYCLES, int(kcycles)),
+              "surrogate_set_option")
+
+    def set_test_stall(self, on: bool):
+        """Test hook: make one dependency of the fused kernel unreachable, so
+        that its bounded wait runs out and sync_status raises."""
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_TEST_STALL, int(bool(on))), "surrogate_set_option")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -70,6 +70,8 @@ struct FusedArgs {
     int log_mask;                         // bit j set = output j was learned as its logarithm
     uint32_t *done;                       // [R][L + 1] arrival counters, zero at launch
     int *err;                             // set to 1 when a bounded wait runs out
+    long long wait_cycles;                // limit of every bounded wait
+    int stall_test;                       // test hook: layer 1 of row block 0 waits for one arrival too many
 };
 
 struct FusedCfg {
@@ -226,10 +228,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                 if (!t.valid) continue;
                 bool ok = true;
                 if (t.l > 0)   // the input: layer l - 1 of this block
-                    ok = wait_count(done + (long long)t.r * stride_l + (t.l - 1), fused_target(a, t.l - 1), a.err);
+                    ok = wait_count(done + (long long)t.r * stride_l + (t.l - 1),
+                                    fused_target(a, t.l - 1) + ((a.stall_test && t.r == 0 && t.l == 1) ? 1u : 0u),
+                                    a.err, a.wait_cycles);
                 if (ok && t.l < L && t.r >= a.ring)   // the ring row block's previous readers
                     ok = wait_count(done + (long long)(t.r - a.ring) * stride_l + (t.l + 1), fused_target(a, t.l + 1),
-                                    a.err);
+                                    a.err, a.wait_cycles);
                 if (!ok) { fail = true; break; }
                 umma::fence_proxy_async_global();   // the producers' stores, seen by this CTA's TMA loads
                 const bool out_l = t.l == L;
@@ -239,7 +243,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % C::S;
                     const uint32_t ph = (it / C::S) & 1u;
-                    if (it >= (uint32_t)C::S && !umma::mbar_wait(&empty[s], ph ^ 1u)) { fail = true; break; }
+                    if (it >= (uint32_t)C::S && !umma::mbar_wait(&empty[s], ph ^ 1u, a.wait_cycles)) {
+                        fail = true;
+                        break;
+                    }
                     uint8_t *st = smem + s * C::STAGE;
                     umma::mbar_arrive_expect_tx(&full[s], bytes);
                     if (t.l == 0)
@@ -265,13 +272,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                 const int nkb = (t.l == 0) ? 1 : W / BK;
                 const uint32_t idesc = out_l ? umma::idesc_bf16_f32(BM, kFusedOutBN) : umma::idesc_bf16_f32(BM, kFusedBN);
                 const uint32_t buf = jacc & 1u;
-                if (jacc >= 2 && !umma::mbar_wait(&acc_empty[buf], ((jacc >> 1) & 1u) ^ 1u)) { fail = true; break; }
+                if (jacc >= 2 && !umma::mbar_wait(&acc_empty[buf], ((jacc >> 1) & 1u) ^ 1u, a.wait_cycles)) {
+                    fail = true;
+                    break;
+                }
                 umma::tc_fence_after();
                 const uint32_t d_tmem = tmem + buf * kFusedBN;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % C::S;
                     const uint32_t ph = (it / C::S) & 1u;
-                    if (!umma::mbar_wait(&full[s], ph)) { fail = true; break; }
+                    if (!umma::mbar_wait(&full[s], ph, a.wait_cycles)) { fail = true; break; }
                     umma::tc_fence_after();
                     const uint32_t sa = umma::smem_u32(smem + s * C::STAGE);
                     const uint32_t sb = sa + C::A_BYTES;
@@ -302,7 +312,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
             ++jacc;
             // after a timed-out wait this warp skips its work but keeps walking
             // the items (the other warps never wait on it)
-            if (!fail && !umma::mbar_wait(&acc_full[buf], ((jacc - 1) >> 1) & 1u)) fail = true;
+            if (!fail && !umma::mbar_wait(&acc_full[buf], ((jacc - 1) >> 1) & 1u, a.wait_cycles)) fail = true;
             fail = __any_sync(0xffffffffu, fail);   // warp-uniform: tcgen05.ld needs the whole warp
             umma::tc_fence_after();
             if (pending) {   // the deferred item's stores have had this item's main loop to land

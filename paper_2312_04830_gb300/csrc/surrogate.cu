@@ -1103,6 +1103,8 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             fa.add_h = (d.mode == SG_MODE_INVERSE) ? nullptr : d.hig;
             fa.log_mask = (d.mode == SG_MODE_INVERSE) ? kLogMaskInverse : kLogMaskForward;
             fa.done = m->d_done; fa.err = m->d_err;
+            fa.wait_cycles = m->wait_cycles > 0 ? m->wait_cycles : 4000000000LL;
+            fa.stall_test = m->stall_test;
             PR_CUDA_TRY(cudaMemsetAsync(m->d_done, 0, (size_t)mt * (L + 1) * 4, st));
             PR_CUDA_TRY(launch_fused(fa, st));
         }
@@ -1165,6 +1167,13 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
                      "surrogate_set_option: fused inference needs a width that is a multiple of 256, <= 1024, "
                      "and its biases within shared memory");
         m->fused_on = value;
+        return PR_OK;
+    case SG_OPT_WAIT_LIMIT_KCYCLES:
+        PR_CHECK_ARG(value >= 0, "surrogate_set_option: wait limit must be >= 0");
+        m->wait_cycles = 1000LL * value;
+        return PR_OK;
+    case SG_OPT_TEST_STALL:
+        m->stall_test = value != 0;
         return PR_OK;
     case SG_OPT_MODE:
         PR_CHECK_ARG(value == SG_MODE_FORWARD || value == SG_MODE_INVERSE, "surrogate_set_option: bad mode %d",

@@ -104,6 +104,8 @@ struct sg_model {
     // fused inference (mlp_fused.cuh): activation ring, its maps, the weight
     // maps with 256-row boxes, per-(row block, layer) arrival counters
     int fused_ok, fused_on, fused_D, fused_ring;
+    long long wait_cycles;                  // bounded-wait limit of the fused kernel
+    int stall_test;                         // SG_OPT_TEST_STALL
     __nv_bfloat16 *ring;                    // [L][fused_ring * 128][W]
     uint32_t *d_done;
     CUtensorMap tmf_w[SG_MAX_HIDDEN + 1], tmf_ring_ld, tmf_ring_st;

@@ -183,6 +183,40 @@ def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers
     sg.close()
 
 
+def test_fused_inference_wait_timeout_is_reported(ctx, orc, species, cuda):
+    """Failure detection of the persistent kernel: with one arrival counter
+    made unreachable and a short wait limit (20M cycles, ~10 ms), the waits
+    run out, the kernel finishes, the host gets PR_ETIMEOUT, and the context
+    stays usable: the next launches give the per-layer result bit for bit."""
+    import torch
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=32768, seed=31)
+    x, y = make_pool(orc, species, 4000, seed=32)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    T, p, Y = W.uniform_cells(50000, seed=33)
+    T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=cuda)
+    Td, pd, Yd = d(T), d(p), d(Y)
+    sg.set_wait_limit(20000)
+    sg.set_test_stall(True)
+    sg.infer(Td, pd, Yd)
+    with pytest.raises(binding.PrError, match="status -4"):
+        sg.sync_status()
+    sg.sync_status()   # the flag is cleared once reported
+    sg.set_test_stall(False)
+    sg.set_wait_limit(0)
+    outs = []
+    for fused in (True, False):
+        sg.set_fused_infer(fused)
+        o, _ = sg.infer(Td, pd, Yd)
+        sg.sync_status()
+        outs.append(o.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)
+    with pytest.raises(binding.PrError):
+        sg.set_wait_limit(-1)
+    sg.close()
+
+
 def test_fallback_outside_hull_is_pr_fp64(ctx, orc, species, cuda):
     """Cells outside the training hull take the FP64 Peng-Robinson path: their
     outputs equal the oracle's (rounded to FP32) and they are flagged."""
