@@ -4,7 +4,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
 legs of ``bench.py`` may import this package.  The product library (the CUDA
 path) never calls it and shares no code with it.
 
-* ``pr_oracle.c`` -- Peng-Robinson / vdW mixing / NASA-7 / Chung / Newton, per
+* ``pr_oracle.c`` -- Peng-Robinson / vdW mixing / NASA-7 / Chung / Newton, and the
+  per-species standard-state enthalpies and mixture-averaged diffusion, per
   cell, in FP64 (see the header of that file for the passages it follows).
 * ``mlp.py``      -- the surrogate MLP forward, backward and Adam step in
   float64 NumPy.
@@ -86,6 +87,10 @@ def lib():
             L.orc_pr_constants.restype = None
             L.orc_pr_gres.argtypes = [d, d, d]
             L.orc_pr_gres.restype = d
+            L.orc_species_props.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, i32]
+            L.orc_species_props.restype = None
+            L.orc_neufeld_omega_d.argtypes = [d]
+            L.orc_neufeld_omega_d.restype = d
             L.orc_max_threads.argtypes = []
             L.orc_max_threads.restype = i32
             _lib = L
@@ -188,6 +193,39 @@ def T_from_h(sp, hstar, p, Y, Tguess, max_iter: int = 60, rtol: float = 1e-13, t
     lib().orc_T_from_h(tb.ref, n, _ptr(hstar), _ptr(p), _ptr(Y), _ptr(Tg), _ptr(Tout), _ptr(st), _ptr(it),
                        int(max_iter), float(rtol), int(threads))
     return Tout, st, it
+
+
+class Corr(ctypes.Structure):
+    _fields_ = [("n_Tr", ctypes.c_int32), ("n_pr", ctypes.c_int32), ("Tr", ctypes.c_void_p),
+                ("pr", ctypes.c_void_p), ("f", ctypes.c_void_p)]
+
+
+def species_props(sp, T, p, Y, corr=None, threads: int = 0, **kw):
+    """(hk_RT[N, n], Dk[N, n], status[n]): the per-species standard-state
+    enthalpies h_k/(R T) and mixture-averaged diffusion coefficients [m^2/s].
+    ``corr`` = (Tr axis, pr axis, f[len(Tr), len(pr)]) is the high-pressure
+    correction table (None: no correction)."""
+    tb = sp if isinstance(sp, Table) else Table(sp, **kw)
+    T, p, Y = _soa(T, p, Y, tb.n)
+    n = T.size
+    hk = np.empty((tb.n, n))
+    Dk = np.empty((tb.n, n))
+    st = np.empty(n, dtype=np.int32)
+    cref = None
+    if corr is not None:
+        Tr, pr, f = (np.ascontiguousarray(a, dtype=np.float64) for a in corr)
+        assert f.shape == (Tr.size, pr.size)
+        keep = (Tr, pr, f)
+        cs = Corr(Tr.size, pr.size, _ptr(Tr), _ptr(pr), _ptr(f))
+        cref = ctypes.byref(cs)
+    lib().orc_species_props(tb.ref, cref, n, _ptr(T), _ptr(p), _ptr(Y), _ptr(hk), _ptr(Dk), _ptr(st), int(threads))
+    if corr is not None:
+        del keep
+    return hk, Dk, st
+
+
+def neufeld_omega_d(Ts):
+    return lib().orc_neufeld_omega_d(float(Ts))
 
 
 def cubic_real_roots(c2, c1, c0):

@@ -549,6 +549,129 @@ void orc_h_ideal(const orc_species *sp, int64_t n, const double *T, const double
     }
 }
 
+/* ---------------------------------------------------------------------- */
+/* Per-species outputs of the paper's networks (Sec. 4.1, the list of seven
+ * networks; Sec. 2 for the diffusion model).
+ *
+ * hk_RT[k]: the nondimensional standard-state enthalpy h_k^0(T) / (R T) of the
+ *   NASA-7 fit of species k.
+ * Dk[k]: the mixture-averaged diffusion coefficient of species k [m^2/s],
+ *   D_km = (1 - Y_k) / sum_{j != k} X_j / D_kj, from the binary coefficients
+ *   of the Chapman-Enskog theory (Poling, Prausnitz & O'Connell, Eq. 11-3.2):
+ *     D_kj [cm^2/s] = 0.00266 T^(3/2) / (p[bar] M_kj^(1/2) sigma_kj^2 Omega_D),
+ *     M_kj = 2 / (1/M_k + 1/M_j) [g/mol], sigma_kj = (sigma_k + sigma_j)/2 [A],
+ *     eps_kj = sqrt(eps_k eps_j), Omega_D(T* = T / eps_kj) by Neufeld et
+ *     al. (1972), with the Lennard-Jones parameters of Chung's corresponding
+ *     states, sigma = 0.809 Vc^(1/3), eps/k = Tc / 1.2593.
+ *   A species with no partner in the cell (sum empty) gets its
+ *   self-diffusion coefficient D_kk.
+ *   The high-pressure correction the paper takes from Takahashi multiplies
+ *   every D_kj p by f(T_r, p_r); here f is a caller table (bilinear in T_r
+ *   and p_r, clamped to its edges; none means f = 1) evaluated at the
+ *   mixture's pseudo-reduced state by Kay's rule, T_r = T / sum X_i Tc_i,
+ *   p_r = p / sum X_i pc_i.
+ */
+typedef struct {
+    int32_t n_Tr, n_pr;
+    const double *Tr, *pr;      /* ascending axes */
+    const double *f;            /* n_Tr x n_pr, row-major (T_r rows) */
+} orc_corr;
+
+/* Neufeld et al. (1972) reduced collision integral for diffusion. */
+static double neufeld_omega_d(double Ts)
+{
+    return 1.06036 / pow(Ts, 0.15610) + 0.19300 / exp(0.47635 * Ts) + 1.03587 / exp(1.52996 * Ts)
+           + 1.76474 / exp(3.89411 * Ts);
+}
+
+double orc_neufeld_omega_d(double Ts) { return neufeld_omega_d(Ts); }
+
+/* Binary diffusion coefficient [m^2/s] of species i and j at T, p. */
+static double binary_d(const orc_species *sp, int i, int j, double T, double p)
+{
+    const double sig_i = 0.809 * cbrt(sp->Vc[i]), sig_j = 0.809 * cbrt(sp->Vc[j]);
+    const double eps_i = sp->Tc[i] / 1.2593, eps_j = sp->Tc[j] / 1.2593;
+    const double sig = 0.5 * (sig_i + sig_j);
+    const double eps = sqrt(eps_i * eps_j);
+    const double Mij = 2.0 / (1.0 / sp->W[i] + 1.0 / sp->W[j]);
+    const double om = neufeld_omega_d(T / eps);
+    const double d_cgs = 0.00266 * pow(T, 1.5) / ((p / 1e5) * sqrt(Mij) * sig * sig * om);
+    return d_cgs * 1e-4;
+}
+
+/* Bilinear interpolation of the correction table at (x, y), clamped. */
+static double corr_eval(const orc_corr *c, double x, double y)
+{
+    if (!c) return 1.0;
+    if (x < c->Tr[0]) x = c->Tr[0];
+    if (x > c->Tr[c->n_Tr - 1]) x = c->Tr[c->n_Tr - 1];
+    if (y < c->pr[0]) y = c->pr[0];
+    if (y > c->pr[c->n_pr - 1]) y = c->pr[c->n_pr - 1];
+    int i = 0, j = 0;
+    while (i < c->n_Tr - 2 && x > c->Tr[i + 1]) ++i;
+    while (j < c->n_pr - 2 && y > c->pr[j + 1]) ++j;
+    const double tx = (x - c->Tr[i]) / (c->Tr[i + 1] - c->Tr[i]);
+    const double ty = (y - c->pr[j]) / (c->pr[j + 1] - c->pr[j]);
+    const double f00 = c->f[i * c->n_pr + j], f01 = c->f[i * c->n_pr + j + 1];
+    const double f10 = c->f[(i + 1) * c->n_pr + j], f11 = c->f[(i + 1) * c->n_pr + j + 1];
+    return (1.0 - tx) * ((1.0 - ty) * f00 + ty * f01) + tx * ((1.0 - ty) * f10 + ty * f11);
+}
+
+void orc_species_props(const orc_species *sp, const orc_corr *corr, int64_t n, const double *T, const double *p,
+                       const double *Y, double *hk_RT, double *Dk, int32_t *status, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        const int N = sp->N;
+        double X[64];
+        double ysum = 0.0, msum = 0.0;
+        int ok = isfinite(T[i]) && isfinite(p[i]) && T[i] > 0.0 && p[i] > 0.0;
+        for (int k = 0; k < N; ++k) {
+            const double y = Y[(int64_t)k * n + i];
+            if (!(y >= 0.0) || !isfinite(y)) ok = 0;
+            ysum += y;
+            X[k] = y / sp->W[k];
+            msum += X[k];
+        }
+        if (!(fabs(ysum - 1.0) <= 1e-6) || !(msum > 0.0)) ok = 0;
+        if (!ok) {
+            for (int k = 0; k < N; ++k) {
+                if (hk_RT) hk_RT[(int64_t)k * n + i] = NAN;
+                if (Dk) Dk[(int64_t)k * n + i] = NAN;
+            }
+            if (status) status[i] = ORC_BAD_INPUT;
+            continue;
+        }
+        for (int k = 0; k < N; ++k) X[k] /= msum;
+        for (int k = 0; k < N; ++k) {
+            double cpR, hRT;
+            nasa7(sp->nasa_lo + 7 * k, sp->nasa_hi + 7 * k, sp->T_mid[k], T[i], &cpR, &hRT, NULL);
+            if (hk_RT) hk_RT[(int64_t)k * n + i] = hRT;
+        }
+        if (Dk) {
+            double Tpc = 0.0, ppc = 0.0;
+            for (int k = 0; k < N; ++k) {
+                Tpc += X[k] * sp->Tc[k];
+                ppc += X[k] * sp->pc[k];
+            }
+            const double f = corr_eval(corr, T[i] / Tpc, p[i] / ppc);
+            for (int k = 0; k < N; ++k) {
+                double s = 0.0;
+                for (int j = 0; j < N; ++j)
+                    if (j != k) s += X[j] / binary_d(sp, k, j, T[i], p[i]);
+                const double y = Y[(int64_t)k * n + i];
+                const double d0 = (s > 0.0) ? (1.0 - y) / s : binary_d(sp, k, k, T[i], p[i]);
+                Dk[(int64_t)k * n + i] = f * d0;
+            }
+        }
+        if (status) status[i] = ORC_OK;
+    }
+    (void)nthreads;
+}
+
 /* Diagnostics for n cells (serial). */
 void orc_diagnose(const orc_species *sp, int64_t n, const double *T, const double *p, const double *Y,
                   double *out, int32_t *status, orc_diag *diag)
