@@ -117,6 +117,43 @@ pr_status pr_props_ext(pr_ctx *ctx, pr_precision prec, int64_t n,
                        void *rho, void *Z, void *h, void *cp, void *mu, void *lambda,
                        void *psi, void *alpha, int32_t *cell_status, void *stream);
 
+/* Per-species outputs of the paper's networks (Sec. 4.1: the nondimensional
+ * standard-state enthalpies and the mixture-averaged diffusion coefficients
+ * of each species; Sec. 2: binary diffusion with a high-pressure correction).
+ *   hk_RT [N][ldo]  h_k^0(T) / (R T) of the NASA-7 fit of each species;
+ *   Dk    [N][ldo]  mixture-averaged diffusion coefficient [m^2/s],
+ *                   D_km = (1 - Y_k) / sum_{j != k} X_j / D_kj, with the
+ *                   Chapman-Enskog binary D_kj (Neufeld's collision integral;
+ *                   Lennard-Jones sigma = 0.809 Vc^(1/3), eps/k = Tc / 1.2593,
+ *                   arithmetic-mean sigma_kj, geometric-mean eps_kj, pair
+ *                   molar mass 2 / (1/W_k + 1/W_j)); a species with no other
+ *                   species in the cell gets its self-diffusion D_kk; every
+ *                   D_kj is multiplied by the factor set with
+ *                   pr_set_diffusion_correction (1 when none is set).
+ *   T, p [n]; Y [N][ldY]; either output may be NULL; ldo >= n.
+ *   cell_status [n] int32 (NULL allowed): PR_CELL_OK or PR_CELL_BAD_INPUT
+ *   (NaN outputs).  No cubic is solved: PR_MIXED computes as PR_FP32.
+ * Pointers aligned to their element size; n = 0 is a no-op. */
+pr_status pr_species_props(pr_ctx *ctx, pr_precision prec, int64_t n,
+                           const void *T, const void *p, const void *Y, int64_t ldY,
+                           void *hk_RT, void *Dk, int64_t ldo, int32_t *cell_status, void *stream);
+
+/* High-pressure correction of the binary diffusion coefficients (Sec. 2 names
+ * Takahashi's): f(T_r, p_r) = (D p) / (D p)_low-pressure as a table on the
+ * caller's grid, interpolated bilinearly and held at its edge values outside,
+ * evaluated at the mixture's pseudo-reduced state (Kay's rule,
+ * T_r = T / sum X_k Tc_k, p_r = p / sum X_k pc_k).  Takahashi's chart is data
+ * the caller supplies; the library ships none.
+ *   Tr [n_Tr], pr [n_pr]: strictly increasing, finite; 2..64 points each.
+ *   f [n_Tr][n_pr] (row-major, T_r rows): finite, >= 0.
+ * All arrays are HOST memory, copied.  corr = NULL removes the correction.
+ * Synchronises the device; do not call while work of this context runs. */
+typedef struct {
+    int32_t n_Tr, n_pr;
+    const double *Tr, *pr, *f;
+} pr_diffusion_correction;
+pr_status pr_set_diffusion_correction(pr_ctx *ctx, const pr_diffusion_correction *corr);
+
 /* Inversion T(h*, p, Y) by safeguarded Newton on f(T) = h(T) - h*, f' = cp,
  * inside the bracket [60, 5000] K, starting from T_guess (clipped to the
  * bracket).  A Newton step that leaves the current bracket, or follows a step

@@ -34,6 +34,11 @@ class PrError(RuntimeError):
     pass
 
 
+class _DiffCorr(ctypes.Structure):
+    _fields_ = [("n_Tr", ctypes.c_int32), ("n_pr", ctypes.c_int32), ("Tr", ctypes.c_void_p),
+                ("pr", ctypes.c_void_p), ("f", ctypes.c_void_p)]
+
+
 class _SpeciesTable(ctypes.Structure):
     _fields_ = [("n_species", ctypes.c_int32), ("flags", ctypes.c_int32)] + [
         (f, ctypes.c_void_p) for f in ("W", "Tc", "pc", "omega", "Vc", "dipole", "kappa",
@@ -58,6 +63,10 @@ def lib():
             L.pr_props_ext.argtypes = [vp, i32, i64, vp, vp, vp, i64] + [vp] * 8 + [vp, vp]
             L.pr_props_ext.restype = i32
             L.pr_props.restype = i32
+            L.pr_species_props.argtypes = [vp, i32, i64, vp, vp, vp, i64, vp, vp, i64, vp, vp]
+            L.pr_species_props.restype = i32
+            L.pr_set_diffusion_correction.argtypes = [vp, vp]
+            L.pr_set_diffusion_correction.restype = i32
             L.pr_T_from_h.argtypes = [vp, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, i32, d, vp]
             L.pr_T_from_h.restype = i32
             L.pr_last_error.argtypes = []
@@ -173,6 +182,32 @@ class PropertyContext:
         check(lib().pr_props_ext(self.handle, prec, n, _ptr(T), _ptr(p), _ptr(Y), ldY, *ptrs, _ptr(status),
                                  _stream(stream)), "pr_props_ext")
         return out, status
+
+    def species_props(self, T, p, Y, precision="fp64", hk=True, Dk=True, status=None, stream=None):
+        """pr_species_props; returns (hk_RT[N, n] or None, Dk[N, n] or None, status[n]):
+        per-species h_k/(R T) and mixture-averaged diffusion coefficients [m^2/s]."""
+        import torch
+        prec = _prec(precision)
+        n, ldY = self._cells(prec, T, p, Y)
+        mk = lambda on: torch.empty((self.n_species, n), dtype=_dtype_of(prec), device=T.device) if on else None
+        hk_t, dk_t = mk(hk), mk(Dk)
+        if status is None:
+            status = torch.empty(n, dtype=torch.int32, device=T.device)
+        check(lib().pr_species_props(self.handle, prec, n, _ptr(T), _ptr(p), _ptr(Y), ldY, _ptr(hk_t), _ptr(dk_t),
+                                     n, _ptr(status), _stream(stream)), "pr_species_props")
+        return hk_t, dk_t, status
+
+    def set_diffusion_correction(self, Tr=None, pr=None, f=None):
+        """High-pressure factor f(T_r, p_r) of the binary diffusion coefficients
+        as a table (Tr rows, pr columns); no arguments remove it."""
+        if Tr is None:
+            check(lib().pr_set_diffusion_correction(self.handle, None), "pr_set_diffusion_correction")
+            return
+        Tr, pr, f = (np.ascontiguousarray(a, dtype=np.float64) for a in (Tr, pr, f))
+        if f.shape != (Tr.size, pr.size):
+            raise PrError("f must be [len(Tr), len(pr)]")
+        c = _DiffCorr(Tr.size, pr.size, Tr.ctypes.data, pr.ctypes.data, f.ctypes.data)
+        check(lib().pr_set_diffusion_correction(self.handle, ctypes.byref(c)), "pr_set_diffusion_correction")
 
     def T_from_h(self, hstar, p, Y, T_guess, precision="fp64", max_iter=60, rtol=1e-13, T_out=None,
                  status=None, iters=None, stream=None):

@@ -211,6 +211,10 @@ pr_status pr_create(const pr_species_table *tbl, pr_ctx **out)
         pr_destroy(c);
         return (e == cudaErrorMemoryAllocation) ? PR_ENOMEM : PR_ECUDA;
     }
+    if (pr_status ss = prgb::species_tables_init(c, tbl)) {
+        pr_destroy(c);
+        return ss;
+    }
     fill_occ<double, double>(NS, c->occ_props[PR_FP64], c->occ_newton[PR_FP64]);
     fill_occ<float, float>(NS, c->occ_props[PR_FP32], c->occ_newton[PR_FP32]);
     fill_occ<float, double>(NS, c->occ_props[PR_MIXED], c->occ_newton[PR_MIXED]);
@@ -228,6 +232,7 @@ void pr_destroy(pr_ctx *c)
     cudaFree(c->d_pair32);
     cudaFree(c->d_kij64);
     cudaFree(c->d_kij32);
+    prgb::species_tables_free(c);
     delete c;
 }
 

@@ -53,7 +53,21 @@ struct pr_ctx {
     float *d_kij32;
     int occ_props[3][2]; // resident blocks per SM: [precision][kij]
     int occ_newton[3][2];
+    // per-species outputs (pr_species.cu): Kay's-rule and diffusion pair
+    // constants, the optional high-pressure correction table
+    double *d_dtab64;
+    float *d_dtab32;
+    double *d_corr64;
+    float *d_corr32;
+    int corr_nT, corr_nP;
+    int occ_species[2];  // [FP64, FP32]
 };
+
+namespace prgb {
+// Build / release the per-species tables of a context (pr_species.cu).
+pr_status species_tables_init(pr_ctx *c, const pr_species_table *tbl);
+void species_tables_free(pr_ctx *c);
+}  // namespace prgb
 
 // SG_MODE_FORWARD or SG_MODE_INVERSE of a surrogate (surrogate.cu).
 int sg_mode_of(const sg_model *m);

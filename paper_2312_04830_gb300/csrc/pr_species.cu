@@ -1,0 +1,326 @@
+// Per-species outputs of the property networks (Sec. 4.1 lists, among the
+// seven networks, the nondimensional standard-state enthalpies and the
+// mixture-averaged diffusion coefficients of every species; Sec. 2 names the
+// binary diffusion model with Takahashi's high-pressure correction):
+//
+//   h_k^0 / (R T)   NASA-7 fit of species k;
+//   D_km            = (1 - Y_k) / sum_{j != k} X_j / D_kj  (mass-fraction form
+//                     of the mixture average), a species alone in its cell
+//                     taking its self-diffusion coefficient D_kk;
+//   D_kj            Chapman-Enskog, D_kj = c_kj T^(3/2) / (p Omega_D(T / eps_kj)),
+//                     c_kj = 0.0266 / (M_kj^(1/2) sigma_kj^2) [m^2 Pa/(s K^1.5)]
+//                     (0.00266 cm^2 bar units), Neufeld's Omega_D,
+//                     sigma = 0.809 Vc^(1/3) [A], eps/k = Tc / 1.2593 (Chung's
+//                     corresponding states), sigma_kj arithmetic, eps_kj
+//                     geometric, M_kj = 2 / (1/W_k + 1/W_j) [g/mol];
+//   f(T_r, p_r)     optional caller table multiplying every D_kj p, bilinear
+//                     and edge-clamped, at the mixture's Kay's-rule state.
+//
+// One thread per cell.  The pair terms are symmetric, so each unordered pair
+// evaluates its collision integral once (four exponentials) and feeds both
+// species' sums.  Pair constants (1/eps, -ln eps, 1/c) are derived on the
+// host when the context is created and staged in shared memory per CTA.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pr_device.cuh"
+#include "pr_internal.h"
+
+namespace {
+
+using prk::M;
+using prk::SpeciesRec;
+
+constexpr int kSpBlock = 128;
+constexpr int kCorrMax = 64;
+constexpr int kCorrFloats = 2 * kCorrMax + kCorrMax * kCorrMax;
+
+// Neufeld et al. (1972) fit of the Lennard-Jones Omega^(1,1)*.
+constexpr double kNA = 1.06036, kNB = 0.15610, kNC = 0.19300, kND = 0.47635;
+constexpr double kNE = 1.03587, kNF = 1.52996, kNG = 1.76474, kNH = 3.89411;
+
+// Flat per-context table: tc[NS], pc[NS], ie[NS*NS], nle[NS*NS], ic[NS*NS].
+inline size_t dtab_len(int NS) { return 2 * (size_t)NS + 3 * (size_t)NS * NS; }
+
+template <typename Real>
+struct SpArgs {
+    int64_t n, ldY, ldo;
+    const Real *T, *p, *Y;
+    Real *hk, *Dk;
+    int32_t *status;
+    const SpeciesRec<Real> *sp;
+    const Real *dtab;
+    const Real *corr;     // Tr[cT], pr[cP], f[cT][cP]; cT = 0: no correction
+    int N, cT, cP;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real omega_d(Real Ts, Real lnTs)
+{
+    return Real(kNA) * M<Real>::exp(Real(-kNB) * lnTs) + Real(kNC) * M<Real>::exp(Real(-kND) * Ts) +
+           Real(kNE) * M<Real>::exp(Real(-kNF) * Ts) + Real(kNG) * M<Real>::exp(Real(-kNH) * Ts);
+}
+
+// Bilinear, clamped to the table's edges.
+template <typename Real>
+__device__ __forceinline__ Real corr_factor(const Real *__restrict__ c, int cT, int cP, Real x, Real y)
+{
+    const Real *Tr = c, *pr = c + cT, *f = c + cT + cP;
+    x = fmin(fmax(x, Tr[0]), Tr[cT - 1]);
+    y = fmin(fmax(y, pr[0]), pr[cP - 1]);
+    int i = 0, j = 0;
+    while (i < cT - 2 && x > Tr[i + 1]) ++i;
+    while (j < cP - 2 && y > pr[j + 1]) ++j;
+    const Real tx = (x - Tr[i]) / (Tr[i + 1] - Tr[i]);
+    const Real ty = (y - pr[j]) / (pr[j + 1] - pr[j]);
+    const Real *r0 = f + i * cP + j, *r1 = r0 + cP;
+    const Real g0 = M<Real>::fma(ty, r0[1] - r0[0], r0[0]);
+    const Real g1 = M<Real>::fma(ty, r1[1] - r1[0], r1[0]);
+    return M<Real>::fma(tx, g1 - g0, g0);
+}
+
+template <typename Real, int NS>
+__global__ void __launch_bounds__(kSpBlock) species_kernel(const SpArgs<Real> a)
+{
+    __shared__ Real s_h[2][NS][6];
+    __shared__ Real s_tmid[NS], s_iW[NS];
+    __shared__ Real s_tab[2 * NS + 3 * NS * NS];
+    for (int e = threadIdx.x; e < NS * 6; e += blockDim.x) {
+        const int k = e / 6, j = e % 6;
+        s_h[0][k][j] = a.sp[k].h_lo[j];
+        s_h[1][k][j] = a.sp[k].h_hi[j];
+    }
+    for (int k = threadIdx.x; k < NS; k += blockDim.x) {
+        s_tmid[k] = a.sp[k].T_mid;
+        s_iW[k] = a.sp[k].inv_W;
+    }
+    for (int e = threadIdx.x; e < 2 * NS + 3 * NS * NS; e += blockDim.x) s_tab[e] = a.dtab[e];
+    __syncthreads();
+    const Real *tc = s_tab, *pc = s_tab + NS, *ie = s_tab + 2 * NS, *nle = ie + NS * NS, *ic = nle + NS * NS;
+
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        const Real T = __ldg(a.T + i), p = __ldg(a.p + i);
+        Real y[NS], x[NS];
+        Real ysum = 0, s = 0;
+        bool ok = (T > Real(0)) && (p > Real(0)) && M<Real>::finite(T) && M<Real>::finite(p);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            y[k] = (k < a.N) ? __ldg(a.Y + (int64_t)k * a.ldY + i) : Real(0);
+            ok = ok && (y[k] >= Real(0)) && M<Real>::finite(y[k]);
+            ysum += y[k];
+            x[k] = y[k] * s_iW[k];
+            s += x[k];
+        }
+        ok = ok && (M<Real>::fabs(ysum - Real(1)) <= Real(1e-6)) && (s > Real(0));
+        if (a.status) a.status[i] = ok ? prk::kOk : prk::kBadInput;
+        if (!ok) {
+            const Real nanv = M<Real>::nan();
+            for (int k = 0; k < a.N; ++k) {
+                if (a.hk) a.hk[(int64_t)k * a.ldo + i] = nanv;
+                if (a.Dk) a.Dk[(int64_t)k * a.ldo + i] = nanv;
+            }
+            continue;
+        }
+        if (a.hk) {
+            const Real iRT = Real(1) / (Real(prk::kR) * T);
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                if (k >= a.N) break;
+                const Real *e = s_h[T < s_tmid[k] ? 0 : 1][k];
+                const Real h = M<Real>::fma(
+                    M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(e[4], T, e[3]), T, e[2]), T, e[1]), T, e[0]),
+                    T, e[5]);
+                a.hk[(int64_t)k * a.ldo + i] = h * iRT;
+            }
+        }
+        if (a.Dk) {
+            const Real inv_s = Real(1) / s;
+            Real Tpc = 0, ppc = 0;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                x[k] *= inv_s;
+                Tpc = M<Real>::fma(x[k], tc[k], Tpc);
+                ppc = M<Real>::fma(x[k], pc[k], ppc);
+            }
+            const Real f = (a.cT > 0) ? corr_factor<Real>(a.corr, a.cT, a.cP, T / Tpc, p / ppc) : Real(1);
+            const Real lnT = M<Real>::log(T);
+            Real acc[NS];
+#pragma unroll
+            for (int k = 0; k < NS; ++k) acc[k] = 0;
+#pragma unroll
+            for (int k = 0; k < NS - 1; ++k) {
+                if (k >= a.N - 1) break;
+#pragma unroll
+                for (int j = k + 1; j < NS; ++j) {
+                    if (j >= a.N) break;
+                    const int q = k * NS + j;
+                    const Real om = omega_d<Real>(T * ie[q], lnT + nle[q]);
+                    const Real w = om * ic[q];
+                    acc[k] = M<Real>::fma(x[j], w, acc[k]);
+                    acc[j] = M<Real>::fma(x[k], w, acc[j]);
+                }
+            }
+            const Real scale = f * T * M<Real>::sqrt(T) / p;   // f T^(3/2) / p
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                if (k >= a.N) break;
+                Real d;
+                if (acc[k] > Real(0)) {
+                    d = (Real(1) - y[k]) * scale / acc[k];
+                } else {   // alone in the cell: self-diffusion
+                    const int q = k * NS + k;
+                    d = scale / (omega_d<Real>(T * ie[q], lnT + nle[q]) * ic[q]);
+                }
+                a.Dk[(int64_t)k * a.ldo + i] = d;
+            }
+        }
+    }
+}
+
+template <typename Real, int NS>
+void launch_species(const SpArgs<Real> &a, int occ, int sms, cudaStream_t st)
+{
+    int64_t need = (a.n + kSpBlock - 1) / kSpBlock;
+    const int64_t cap = (int64_t)occ * sms;
+    const int g = (int)(need < cap ? need : cap);
+    species_kernel<Real, NS><<<g, kSpBlock, 0, st>>>(a);
+}
+
+template <typename Real, int NS>
+int occ_of()
+{
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, species_kernel<Real, NS>, kSpBlock, 0);
+    return o > 0 ? o : 1;
+}
+
+}  // namespace
+
+namespace prgb {
+
+// Pair constants from the validated species table (entries of species >= N
+// are zero and never read).
+pr_status species_tables_init(pr_ctx *c, const pr_species_table *tbl)
+{
+    const int N = tbl->n_species, NS = c->ns_pad;
+    std::vector<double> t(dtab_len(NS), 0.0);
+    double *tc = t.data(), *pc = tc + NS, *ie = pc + NS, *nle = ie + NS * NS, *ic = nle + NS * NS;
+    for (int k = 0; k < N; ++k) {
+        tc[k] = tbl->Tc[k];
+        pc[k] = tbl->pc[k];
+    }
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j) {
+            const double sk = 0.809 * std::cbrt(tbl->Vc[k]), sj = 0.809 * std::cbrt(tbl->Vc[j]);
+            const double sig = 0.5 * (sk + sj);
+            const double eps = std::sqrt((tbl->Tc[k] / 1.2593) * (tbl->Tc[j] / 1.2593));
+            const double Mkj = 2.0 / (1.0 / tbl->W[k] + 1.0 / tbl->W[j]);
+            const double ckj = 0.0266 / (std::sqrt(Mkj) * sig * sig);
+            ie[k * NS + j] = 1.0 / eps;
+            nle[k * NS + j] = -std::log(eps);
+            ic[k * NS + j] = 1.0 / ckj;
+        }
+    std::vector<float> t32(t.size());
+    for (size_t e = 0; e < t.size(); ++e) t32[e] = (float)t[e];
+    PR_CUDA_TRY(cudaMalloc(&c->d_dtab64, t.size() * sizeof(double)));
+    PR_CUDA_TRY(cudaMalloc(&c->d_dtab32, t.size() * sizeof(float)));
+    PR_CUDA_TRY(cudaMalloc(&c->d_corr64, kCorrFloats * sizeof(double)));
+    PR_CUDA_TRY(cudaMalloc(&c->d_corr32, kCorrFloats * sizeof(float)));
+    PR_CUDA_TRY(cudaMemcpy(c->d_dtab64, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+    PR_CUDA_TRY(cudaMemcpy(c->d_dtab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->corr_nT = c->corr_nP = 0;
+    c->occ_species[0] = (NS == 9) ? occ_of<double, 9>() : occ_of<double, 32>();
+    c->occ_species[1] = (NS == 9) ? occ_of<float, 9>() : occ_of<float, 32>();
+    return PR_OK;
+}
+
+void species_tables_free(pr_ctx *c)
+{
+    cudaFree(c->d_dtab64);
+    cudaFree(c->d_dtab32);
+    cudaFree(c->d_corr64);
+    cudaFree(c->d_corr32);
+}
+
+}  // namespace prgb
+
+extern "C" {
+
+pr_status pr_set_diffusion_correction(pr_ctx *ctx, const pr_diffusion_correction *corr)
+{
+    PR_CHECK_ARG(ctx != nullptr, "pr_set_diffusion_correction: null context");
+    if (corr == nullptr) {
+        PR_CUDA_TRY(cudaDeviceSynchronize());
+        ctx->corr_nT = ctx->corr_nP = 0;
+        return PR_OK;
+    }
+    const int nT = corr->n_Tr, nP = corr->n_pr;
+    PR_CHECK_ARG(nT >= 2 && nT <= kCorrMax && nP >= 2 && nP <= kCorrMax,
+                 "pr_set_diffusion_correction: table %d x %d outside 2..%d", nT, nP, kCorrMax);
+    PR_CHECK_ARG(corr->Tr && corr->pr && corr->f, "pr_set_diffusion_correction: null array");
+    for (int i = 0; i < nT; ++i)
+        PR_CHECK_ARG(std::isfinite(corr->Tr[i]) && (i == 0 || corr->Tr[i] > corr->Tr[i - 1]),
+                     "pr_set_diffusion_correction: Tr must be finite and strictly increasing");
+    for (int j = 0; j < nP; ++j)
+        PR_CHECK_ARG(std::isfinite(corr->pr[j]) && (j == 0 || corr->pr[j] > corr->pr[j - 1]),
+                     "pr_set_diffusion_correction: pr must be finite and strictly increasing");
+    for (int e = 0; e < nT * nP; ++e)
+        PR_CHECK_ARG(std::isfinite(corr->f[e]) && corr->f[e] >= 0.0,
+                     "pr_set_diffusion_correction: factors must be finite and >= 0");
+    std::vector<double> t(nT + nP + nT * nP);
+    std::memcpy(t.data(), corr->Tr, nT * sizeof(double));
+    std::memcpy(t.data() + nT, corr->pr, nP * sizeof(double));
+    std::memcpy(t.data() + nT + nP, corr->f, (size_t)nT * nP * sizeof(double));
+    std::vector<float> t32(t.size());
+    for (size_t e = 0; e < t.size(); ++e) t32[e] = (float)t[e];
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    PR_CUDA_TRY(cudaMemcpy(ctx->d_corr64, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+    PR_CUDA_TRY(cudaMemcpy(ctx->d_corr32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    ctx->corr_nT = nT;
+    ctx->corr_nP = nP;
+    return PR_OK;
+}
+
+pr_status pr_species_props(pr_ctx *ctx, pr_precision prec, int64_t n, const void *T, const void *p, const void *Y,
+                           int64_t ldY, void *hk_RT, void *Dk, int64_t ldo, int32_t *cell_status, void *stream)
+{
+    PR_CHECK_ARG(ctx != nullptr, "pr_species_props: null context");
+    PR_CHECK_ARG(prec == PR_FP64 || prec == PR_FP32 || prec == PR_MIXED, "pr_species_props: bad precision %d",
+                 (int)prec);
+    PR_CHECK_ARG(n >= 0, "pr_species_props: n < 0");
+    if (n == 0) return PR_OK;
+    PR_CHECK_ARG(ldY >= n, "pr_species_props: ldY (%lld) < n (%lld)", (long long)ldY, (long long)n);
+    PR_CHECK_ARG((hk_RT == nullptr && Dk == nullptr) || ldo >= n, "pr_species_props: ldo (%lld) < n (%lld)",
+                 (long long)ldo, (long long)n);
+    const size_t esz = (prec == PR_FP64) ? 8 : 4;
+    for (const void *q : {T, p, Y}) {
+        PR_CHECK_ARG(q != nullptr, "pr_species_props: required array is NULL");
+        PR_CHECK_ARG(prgb::aligned(q, esz), "pr_species_props: array not aligned to %zu bytes", esz);
+    }
+    for (const void *q : {hk_RT, Dk})
+        PR_CHECK_ARG(prgb::aligned(q, esz), "pr_species_props: array not aligned to %zu bytes", esz);
+    PR_CHECK_ARG(prgb::aligned(cell_status, 4), "pr_species_props: cell_status misaligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool nine = ctx->ns_pad == 9;
+    if (prec == PR_FP64) {
+        SpArgs<double> a{n, ldY, ldo, (const double *)T, (const double *)p, (const double *)Y, (double *)hk_RT,
+                         (double *)Dk, cell_status, (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_dtab64,
+                         ctx->d_corr64, ctx->n_species, ctx->corr_nT, ctx->corr_nP};
+        if (nine) launch_species<double, 9>(a, ctx->occ_species[0], ctx->num_sms, st);
+        else launch_species<double, 32>(a, ctx->occ_species[0], ctx->num_sms, st);
+    } else {
+        SpArgs<float> a{n, ldY, ldo, (const float *)T, (const float *)p, (const float *)Y, (float *)hk_RT,
+                        (float *)Dk, cell_status, (const SpeciesRec<float> *)ctx->d_sp32, ctx->d_dtab32,
+                        ctx->d_corr32, ctx->n_species, ctx->corr_nT, ctx->corr_nP};
+        if (nine) launch_species<float, 9>(a, ctx->occ_species[1], ctx->num_sms, st);
+        else launch_species<float, 32>(a, ctx->occ_species[1], ctx->num_sms, st);
+    }
+    PR_CUDA_TRY(cudaGetLastError());
+    return PR_OK;
+}
+
+}  // extern "C"
