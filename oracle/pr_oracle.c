@@ -556,7 +556,10 @@ void orc_h_ideal(const orc_species *sp, int64_t n, const double *T, const double
  * hk_RT[k]: the nondimensional standard-state enthalpy h_k^0(T) / (R T) of the
  *   NASA-7 fit of species k.
  * Dk[k]: the mixture-averaged diffusion coefficient of species k [m^2/s],
- *   D_km = (1 - Y_k) / sum_{j != k} X_j / D_kj, from the binary coefficients
+ *   D_km = (1 - Y_k) / sum_{j != k} X_j / D_kj, with 1 - Y_k taken as the
+ *   other species' share of the mass, sum_{j != k} Y_j / sum_j Y_j (the same
+ *   number when the Y sum to 1, and without the cancellation of 1 - Y_k as
+ *   Y_k -> 1), from the binary coefficients
  *   of the Chapman-Enskog theory (Poling, Prausnitz & O'Connell, Eq. 11-3.2):
  *     D_kj [cm^2/s] = 0.00266 T^(3/2) / (p[bar] M_kj^(1/2) sigma_kj^2 Omega_D),
  *     M_kj = 2 / (1/M_k + 1/M_j) [g/mol], sigma_kj = (sigma_k + sigma_j)/2 [A],
@@ -662,8 +665,10 @@ void orc_species_props(const orc_species *sp, const orc_corr *corr, int64_t n, c
                 double s = 0.0;
                 for (int j = 0; j < N; ++j)
                     if (j != k) s += X[j] / binary_d(sp, k, j, T[i], p[i]);
-                const double y = Y[(int64_t)k * n + i];
-                const double d0 = (s > 0.0) ? (1.0 - y) / s : binary_d(sp, k, k, T[i], p[i]);
+                double others = 0.0;
+                for (int j = 0; j < N; ++j)
+                    if (j != k) others += Y[(int64_t)j * n + i];
+                const double d0 = (s > 0.0) ? (others / ysum) / s : binary_d(sp, k, k, T[i], p[i]);
                 Dk[(int64_t)k * n + i] = f * d0;
             }
         }

@@ -143,6 +143,19 @@ def test_binary_mixture_ratio_is_molar_mass_ratio(orc, species, pair):
     assert np.allclose(Dk[a] / Dk[b], species.W[b] / species.W[a], rtol=1e-12)
 
 
+def test_diffusion_invariant_to_mass_fraction_scale(orc, species):
+    """X_k and the mass share of the other species, sum_{j != k} Y_j / sum Y_j,
+    are both invariant to a common factor on Y (inputs whose sum is off 1 by
+    less than the accepted 1e-6), so D_k is too; 1 - Y_k would not be."""
+    T, p, Y = W.uniform_cells(256, seed=12)
+    Y[:, :64] = 0.0
+    Y[2, :64], Y[5, :64] = 1 - 2.0 ** -40, 2.0 ** -40     # a species at the edge of purity
+    _, D0, _ = orc.species_props(species, T, p, Y)
+    _, D1, st = orc.species_props(species, T, p, Y * (1 + 5e-7))
+    assert np.all(st == 0)
+    assert np.allclose(D1, D0, rtol=2e-14, atol=0)
+
+
 def test_trace_limits_are_the_binary_coefficient(orc, species):
     """A in trace amount in B and B in trace amount in A both diffuse with the
     one binary D_AB (the pair terms are symmetric)."""
