@@ -62,6 +62,9 @@ BYTES_PER_CELL = {
     "newton_fp32": (3 + N_SPECIES) * 4 + 4 + 4 + 4,
     "surrogate_bf16": (2 + N_SPECIES) * 4 + 6 * 4 + 1,
     "surrogate_inverse_bf16": (2 + N_SPECIES) * 4 + 6 * 4 + 1,
+    # per-species outputs: T, p, Y in; h_k/(R T) and D_k for every species + status out
+    "species_fp64": (2 + N_SPECIES) * 8 + 2 * N_SPECIES * 8 + 4,
+    "species_fp32": (2 + N_SPECIES) * 4 + 2 * N_SPECIES * 4 + 4,
 }
 
 
@@ -79,6 +82,7 @@ def parse():
     ap.add_argument("--sg-epochs", type=float, default=20.0, help="epochs over the pool (batch 65536)")
     ap.add_argument("--sg-steps", type=int, default=0, help="Adam steps (overrides --sg-epochs when > 0)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-species", action="store_true", help="skip timing the per-species outputs")
     ap.add_argument("--serve-clients", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=16, help="requests per client")
     return ap.parse_args()
@@ -437,6 +441,40 @@ def run_ours(args):
     per_path_ms = {nm: statistics.mean(e[nm][0].elapsed_time(e[nm][1]) for e in evs) for nm in paths}
     fb_frac = float(fb.float().mean()) if sg is not None else None
 
+    # per-species outputs (h_k/(R T), mixture-averaged D_k) on the same field,
+    # timed on their own after the step: they are not among the step's paths
+    next_rows = None
+    if not args.no_species:
+        hk64, dk64 = (torch.empty((9, n), dtype=torch.float64, device=dev) for _ in range(2))
+        hk32, dk32 = (torch.empty((9, n), dtype=torch.float32, device=dev) for _ in range(2))
+        sp_calls = {
+            "species_fp64": lambda: ctx.species_props(T64, p64, Y64, "fp64", hk=hk64, Dk=dk64, status=st),
+            "species_fp32": lambda: ctx.species_props(T32, p32, Y32, "fp32", hk=hk32, Dk=dk32, status=st),
+        }
+        next_rows = {}
+        for nm, fn in sp_calls.items():
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(args.steps, 3)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            r = {"ms": ms, "cell_evals_per_s": n / (ms * 1e-3), "bytes_per_cell": BYTES_PER_CELL[nm],
+                 "algorithmic_GBps": BYTES_PER_CELL[nm] * n / (ms * 1e-3) / 1e9}
+            if nm in FP64_FLOPS_PER_CELL:
+                tf = FP64_FLOPS_PER_CELL[nm] * n / (ms * 1e-3) / 1e12
+                r.update({"fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS})
+            next_rows[nm] = r
+        rel = lambda a, b: float(((a.double() - b).abs() / b.abs().clamp_min(1.0)).max())
+        next_rows["species_fp32_max_rel_err_vs_fp64"] = {"hk_RT": rel(hk32, hk64),
+                                                         "Dk": float(((dk32.double() - dk64).abs() / dk64).max())}
+        del hk64, dk64, hk32, dk32
+
     # error of the reduced-precision paths on the field against the FP64 PR
     # path's outputs of the last timed step (rel RMS, p99, max per property)
     field_err = None
@@ -523,6 +561,7 @@ def run_ours(args):
         "paths": roof_paths,
         "field_error_vs_pr_fp64": field_err,
         "roofline": roofline,
+        "next_rows": next_rows,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

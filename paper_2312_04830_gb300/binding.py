@@ -185,11 +185,20 @@ class PropertyContext:
 
     def species_props(self, T, p, Y, precision="fp64", hk=True, Dk=True, status=None, stream=None):
         """pr_species_props; returns (hk_RT[N, n] or None, Dk[N, n] or None, status[n]):
-        per-species h_k/(R T) and mixture-averaged diffusion coefficients [m^2/s]."""
+        per-species h_k/(R T) and mixture-averaged diffusion coefficients [m^2/s].
+        hk / Dk: True (allocate), False (skip) or a [N, n] tensor to fill."""
         import torch
         prec = _prec(precision)
         n, ldY = self._cells(prec, T, p, Y)
-        mk = lambda on: torch.empty((self.n_species, n), dtype=_dtype_of(prec), device=T.device) if on else None
+
+        def mk(o):
+            if o is True:
+                return torch.empty((self.n_species, n), dtype=_dtype_of(prec), device=T.device)
+            if o is False or o is None:
+                return None
+            if o.dtype != _dtype_of(prec) or tuple(o.shape) != (self.n_species, n) or not o.is_contiguous():
+                raise PrError(f"species output must be a contiguous [{self.n_species}, {n}] {_dtype_of(prec)} tensor")
+            return o
         hk_t, dk_t = mk(hk), mk(Dk)
         if status is None:
             status = torch.empty(n, dtype=torch.int32, device=T.device)

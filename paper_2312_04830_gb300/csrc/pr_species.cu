@@ -5,7 +5,9 @@
 //
 //   h_k^0 / (R T)   NASA-7 fit of species k;
 //   D_km            = (1 - Y_k) / sum_{j != k} X_j / D_kj  (mass-fraction form
-//                     of the mixture average), a species alone in its cell
+//                     of the mixture average), 1 - Y_k evaluated as
+//                     sum_{j != k} Y_j / sum_j Y_j (no cancellation as Y_k -> 1,
+//                     which FP32 inputs reach), a species alone in its cell
 //                     taking its self-diffusion coefficient D_kk;
 //   D_kj            Chapman-Enskog, D_kj = c_kj T^(3/2) / (p Omega_D(T / eps_kj)),
 //                     c_kj = 0.0266 / (M_kj^(1/2) sigma_kj^2) [m^2 Pa/(s K^1.5)]
@@ -17,9 +19,13 @@
 //                     and edge-clamped, at the mixture's Kay's-rule state.
 //
 // One thread per cell.  The pair terms are symmetric, so each unordered pair
-// evaluates its collision integral once (four exponentials) and feeds both
-// species' sums.  Pair constants (1/eps, -ln eps, 1/c) are derived on the
-// host when the context is created and staged in shared memory per CTA.
+// evaluates its collision integral once and feeds both species' sums.  In
+// Neufeld's Omega_D = A T*^-B + C e^(-D T*) + E e^(-F T*) + G e^(-H T*) the
+// power term factors as A T^-B eps_kj^B (one power per cell, a constant per
+// pair), and an exponential term whose argument exceeds 40 is dropped: it is
+// below 8e-18 while Omega_D >= 0.4, under half an FP64 ulp of the sum.  Pair
+// constants (1/eps, eps^B, 1/c) are derived on the host when the context is
+// created and staged in shared memory per CTA.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -42,7 +48,7 @@ constexpr int kCorrFloats = 2 * kCorrMax + kCorrMax * kCorrMax;
 constexpr double kNA = 1.06036, kNB = 0.15610, kNC = 0.19300, kND = 0.47635;
 constexpr double kNE = 1.03587, kNF = 1.52996, kNG = 1.76474, kNH = 3.89411;
 
-// Flat per-context table: tc[NS], pc[NS], ie[NS*NS], nle[NS*NS], ic[NS*NS].
+// Flat per-context table: tc[NS], pc[NS], ie[NS*NS], epsB[NS*NS], ic[NS*NS].
 inline size_t dtab_len(int NS) { return 2 * (size_t)NS + 3 * (size_t)NS * NS; }
 
 template <typename Real>
@@ -57,11 +63,15 @@ struct SpArgs {
     int N, cT, cP;
 };
 
+// Omega_D at T* = Ts, with pw = T*^-B given.
 template <typename Real>
-__device__ __forceinline__ Real omega_d(Real Ts, Real lnTs)
+__device__ __forceinline__ Real omega_d(Real Ts, Real pw)
 {
-    return Real(kNA) * M<Real>::exp(Real(-kNB) * lnTs) + Real(kNC) * M<Real>::exp(Real(-kND) * Ts) +
-           Real(kNE) * M<Real>::exp(Real(-kNF) * Ts) + Real(kNG) * M<Real>::exp(Real(-kNH) * Ts);
+    Real om = Real(kNA) * pw;
+    if (Ts < Real(40.0 / kND)) om = M<Real>::fma(Real(kNC), M<Real>::exp(Real(-kND) * Ts), om);
+    if (Ts < Real(40.0 / kNF)) om = M<Real>::fma(Real(kNE), M<Real>::exp(Real(-kNF) * Ts), om);
+    if (Ts < Real(40.0 / kNH)) om = M<Real>::fma(Real(kNG), M<Real>::exp(Real(-kNH) * Ts), om);
+    return om;
 }
 
 // Bilinear, clamped to the table's edges.
@@ -99,7 +109,7 @@ __global__ void __launch_bounds__(kSpBlock) species_kernel(const SpArgs<Real> a)
     }
     for (int e = threadIdx.x; e < 2 * NS + 3 * NS * NS; e += blockDim.x) s_tab[e] = a.dtab[e];
     __syncthreads();
-    const Real *tc = s_tab, *pc = s_tab + NS, *ie = s_tab + 2 * NS, *nle = ie + NS * NS, *ic = nle + NS * NS;
+    const Real *tc = s_tab, *pc = s_tab + NS, *ie = s_tab + 2 * NS, *epsB = ie + NS * NS, *ic = epsB + NS * NS;
 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
@@ -147,7 +157,7 @@ __global__ void __launch_bounds__(kSpBlock) species_kernel(const SpArgs<Real> a)
                 ppc = M<Real>::fma(x[k], pc[k], ppc);
             }
             const Real f = (a.cT > 0) ? corr_factor<Real>(a.corr, a.cT, a.cP, T / Tpc, p / ppc) : Real(1);
-            const Real lnT = M<Real>::log(T);
+            const Real TmB = M<Real>::exp(Real(-kNB) * M<Real>::log(T));   // T^-B
             Real acc[NS];
 #pragma unroll
             for (int k = 0; k < NS; ++k) acc[k] = 0;
@@ -158,22 +168,37 @@ __global__ void __launch_bounds__(kSpBlock) species_kernel(const SpArgs<Real> a)
                 for (int j = k + 1; j < NS; ++j) {
                     if (j >= a.N) break;
                     const int q = k * NS + j;
-                    const Real om = omega_d<Real>(T * ie[q], lnT + nle[q]);
+                    const Real om = omega_d<Real>(T * ie[q], TmB * epsB[q]);
                     const Real w = om * ic[q];
                     acc[k] = M<Real>::fma(x[j], w, acc[k]);
                     acc[j] = M<Real>::fma(x[k], w, acc[j]);
                 }
             }
             const Real scale = f * T * M<Real>::sqrt(T) / p;   // f T^(3/2) / p
+            // sum_{j != k} y_j from prefix and suffix sums
+            Real others[NS];
+            Real run = 0;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                others[k] = run;
+                run += y[k];
+            }
+            run = 0;
+#pragma unroll
+            for (int k = NS - 1; k >= 0; --k) {
+                others[k] += run;
+                run += y[k];
+            }
+            const Real iys = Real(1) / ysum;
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
                 if (k >= a.N) break;
                 Real d;
                 if (acc[k] > Real(0)) {
-                    d = (Real(1) - y[k]) * scale / acc[k];
+                    d = others[k] * iys * scale / acc[k];
                 } else {   // alone in the cell: self-diffusion
                     const int q = k * NS + k;
-                    d = scale / (omega_d<Real>(T * ie[q], lnT + nle[q]) * ic[q]);
+                    d = scale / (omega_d<Real>(T * ie[q], TmB * epsB[q]) * ic[q]);
                 }
                 a.Dk[(int64_t)k * a.ldo + i] = d;
             }
@@ -208,7 +233,7 @@ pr_status species_tables_init(pr_ctx *c, const pr_species_table *tbl)
 {
     const int N = tbl->n_species, NS = c->ns_pad;
     std::vector<double> t(dtab_len(NS), 0.0);
-    double *tc = t.data(), *pc = tc + NS, *ie = pc + NS, *nle = ie + NS * NS, *ic = nle + NS * NS;
+    double *tc = t.data(), *pc = tc + NS, *ie = pc + NS, *epsB = ie + NS * NS, *ic = epsB + NS * NS;
     for (int k = 0; k < N; ++k) {
         tc[k] = tbl->Tc[k];
         pc[k] = tbl->pc[k];
@@ -221,7 +246,7 @@ pr_status species_tables_init(pr_ctx *c, const pr_species_table *tbl)
             const double Mkj = 2.0 / (1.0 / tbl->W[k] + 1.0 / tbl->W[j]);
             const double ckj = 0.0266 / (std::sqrt(Mkj) * sig * sig);
             ie[k * NS + j] = 1.0 / eps;
-            nle[k * NS + j] = -std::log(eps);
+            epsB[k * NS + j] = std::pow(eps, kNB);
             ic[k * NS + j] = 1.0 / ckj;
         }
     std::vector<float> t32(t.size());

@@ -173,6 +173,21 @@ def test_species_fp32_error_budget(ctx, orc, species, cuda):
         assert np.median(edk) < 1e-6 and np.percentile(edk, 99) < 1e-5
 
 
+def test_species_fp32_near_pure_cells(ctx, orc, species, cuda):
+    """FP32 on the flame field, whose cells run from pure O2 to pure CH4 through
+    mass fractions within an FP32 ulp of 1: no cancellation in 1 - Y_k."""
+    T, p, Y = W.flame_vortex_field(32)
+    r = lambda a: a.astype(np.float32).astype(np.float64)
+    T, p, Y = r(T), r(p), r(Y)
+    o = orc.species_props(species, T, p, Y)
+    hk, dk, st = run(ctx, T, p, Y, cuda, precision="fp32")
+    m = (st == 0) & (o[2] == 0)
+    assert m.all()
+    edk = np.abs(dk[:, m] - o[1][:, m]) / o[1][:, m]
+    print("flame field FP32 D_k max rel err", edk.max())
+    assert edk.max() < 1e-5
+
+
 def test_species_full_field_sampled(ctx, orc, species, cuda):
     """The 128^3 flame-vortex field in one launch; 20000 sampled cells against
     the oracle."""
