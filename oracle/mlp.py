@@ -13,7 +13,8 @@ Definitions (plain, unfused):
   * layer l:  z_l = W_l h_{l-1} + b_l,  h_l = GeLU(z_l)  (linear last layer)
   * loss on standardised targets s:  L = mean_{b, j} (yhat_bj - s_bj)^2
     (the targets are logarithms or scaled values, so squared errors are
-    relative errors: the relative-MSE loss)
+    relative errors: the relative-MSE loss), or the paper's L1 norm (Sec. 4.3)
+    L = mean_{b, j} |yhat_bj - s_bj|, whose gradient takes sign(0) = 0
   * backward: the chain rule, layer by layer
   * Adam (Kingma & Ba): m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
     p <- p - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
@@ -76,14 +77,16 @@ def forward(params, X, form="erf"):
     return h, cache
 
 
-def loss(yhat, s):
+def loss(yhat, s, kind="mse"):
+    if kind == "l1":
+        return float(np.mean(np.abs(yhat - s)))
     return float(np.mean((yhat - s) ** 2))
 
 
-def backward(params, cache, yhat, s, form="erf"):
-    """Gradients of `loss` w.r.t. every (W_l, b_l)."""
+def backward(params, cache, yhat, s, form="erf", kind="mse"):
+    """Gradients of `loss` (of the same kind) w.r.t. every (W_l, b_l)."""
     B, J = yhat.shape
-    dz = 2.0 * (yhat - s) / (B * J)
+    dz = (np.sign(yhat - s) if kind == "l1" else 2.0 * (yhat - s)) / (B * J)
     grads = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         W, _ = params[li]

@@ -41,31 +41,44 @@ def test_gelu_grad_matches_finite_difference(form):
     np.testing.assert_allclose(mlp.gelu_grad(z, form), fd, rtol=1e-8, atol=1e-10)
 
 
-@pytest.mark.parametrize("form", ["erf", "tanh"])
-def test_backward_matches_finite_difference(form):
+@pytest.mark.parametrize("form,kind", [("erf", "mse"), ("tanh", "mse"), ("tanh", "l1")])
+def test_backward_matches_finite_difference(form, kind):
     """Every gradient of a tiny 5-layer net against central differences of
-    the loss (FP64, step 1e-6)."""
+    the loss (FP64, step 1e-6, 1e-5 for L1); for the L1 loss no residual is
+    within 1e-3 of its kink, so the step never crosses one."""
     sizes = [11, 7, 6, 5, 4, 6]
     params = mlp.init_params(sizes, seed=3)
     rng = np.random.default_rng(4)
     X = rng.normal(size=(9, 11))
     s = rng.normal(size=(9, 6))
     yhat, cache = mlp.forward(params, X, form)
-    grads = mlp.backward(params, cache, yhat, s, form)
-    h = 1e-6
+    assert np.abs(yhat - s).min() > 1e-3
+    grads = mlp.backward(params, cache, yhat, s, form, kind)
+    h = 1e-6 if kind == "mse" else 1e-5   # L1: a larger step keeps round-off (eps L / h) below 1e-10
     for li, (W, b) in enumerate(params):
         for k, P in enumerate((W, b)):
             flat = P.reshape(-1)
             for idx in range(0, flat.size, max(1, flat.size // 7)):
                 old = flat[idx]
                 flat[idx] = old + h
-                lp = mlp.loss(mlp.forward(params, X, form)[0], s)
+                lp = mlp.loss(mlp.forward(params, X, form)[0], s, kind)
                 flat[idx] = old - h
-                lm = mlp.loss(mlp.forward(params, X, form)[0], s)
+                lm = mlp.loss(mlp.forward(params, X, form)[0], s, kind)
                 flat[idx] = old
                 fd = (lp - lm) / (2 * h)
                 g = grads[li][k].reshape(-1)[idx]
                 assert g == pytest.approx(fd, rel=1e-6, abs=1e-10), (li, k, idx)
+
+
+def test_l1_loss_closed_form():
+    """The L1 loss is the mean absolute residual; its output gradient is
+    sign(residual) / (B J), zero where the residual is zero."""
+    yhat = np.array([[1.0, -2.0, 0.5], [0.0, 3.0, -1.0]])
+    s = np.array([[0.0, -2.0, 1.5], [1.0, 1.0, -1.0]])
+    assert mlp.loss(yhat, s, "l1") == pytest.approx((1 + 0 + 1 + 1 + 2 + 0) / 6)
+    params = [(np.eye(3), np.zeros(3))]
+    g = mlp.backward(params, [(None, yhat)], yhat, s, "tanh", "l1")
+    assert np.allclose(g[0][1], np.array([0.0, 1.0, -1.0]) / 6)
 
 
 def test_adam_first_step_is_signed_lr():
