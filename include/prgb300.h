@@ -122,7 +122,8 @@ pr_status pr_props_ext(pr_ctx *ctx, pr_precision prec, int64_t n,
  * of each species; Sec. 2: binary diffusion with a high-pressure correction).
  *   hk_RT [N][ldo]  h_k^0(T) / (R T) of the NASA-7 fit of each species;
  *   Dk    [N][ldo]  mixture-averaged diffusion coefficient [m^2/s],
- *                   D_km = (1 - Y_k) / sum_{j != k} X_j / D_kj, with the
+ *                   D_km = (1 - Y_k) / sum_{j != k} X_j / D_kj (1 - Y_k
+ *                   taken as sum_{j != k} Y_j / sum_j Y_j), with the
  *                   Chapman-Enskog binary D_kj (Neufeld's collision integral;
  *                   Lennard-Jones sigma = 0.809 Vc^(1/3), eps/k = Tc / 1.2593,
  *                   arithmetic-mean sigma_kj, geometric-mean eps_kj, pair
@@ -287,6 +288,14 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * row block of every chunk wait for an arrival that never comes. */
 #define SG_OPT_WAIT_LIMIT_KCYCLES 3
 #define SG_OPT_TEST_STALL 4
+/* SG_OPT_LOSS: the training loss on the standardised targets.
+ * SG_LOSS_REL_MSE (default): mean squared error (relative, the targets being
+ * logarithms or scaled values); SG_LOSS_L1: the paper's L1 norm (Sec. 4.3),
+ * mean |y - target|, output gradient sign(y - target) / (batch * 6) with
+ * sign(0) = 0.  Non-finite targets are masked in both. */
+#define SG_OPT_LOSS 5
+#define SG_LOSS_REL_MSE 0
+#define SG_LOSS_L1 1
 #define SG_MODE_FORWARD 0
 #define SG_MODE_INVERSE 1
 pr_status surrogate_set_option(sg_model *m, int option, int value);

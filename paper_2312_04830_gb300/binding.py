@@ -248,6 +248,7 @@ SG_NORM_FLOATS = 64
 SG_OPT_FUSED_INFER = 1
 SG_OPT_MODE, SG_MODE_FORWARD, SG_MODE_INVERSE = 2, 0, 1
 SG_OPT_WAIT_LIMIT_KCYCLES, SG_OPT_TEST_STALL = 3, 4
+SG_OPT_LOSS, SG_LOSS_REL_MSE, SG_LOSS_L1 = 5, 0, 1
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
@@ -314,6 +315,13 @@ class Surrogate:
         """All layers of an inference chunk in one persistent launch (True,
         the default where the width allows it) or one launch per layer."""
         check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_FUSED_INFER, int(bool(on))), "surrogate_set_option")
+
+    def set_loss(self, kind: str):
+        """Training loss: 'mse' (relative MSE on the standardised targets, the
+        default) or 'l1' (the paper's L1 norm)."""
+        v = {"mse": SG_LOSS_REL_MSE, "l1": SG_LOSS_L1}[kind]
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_LOSS, v), "surrogate_set_option")
+        self.loss_kind = kind
 
     def set_wait_limit(self, kcycles: int):
         """Limit, in thousands of SM clock cycles, of every bounded wait in the

@@ -34,7 +34,7 @@ constexpr int BK = 64;
 enum Epi : int {
     kEpiHidden = 0,    // h = GeLU(acc + b) -> out; (train) h^T -> outT, GeLU'(acc + b) -> gd
     kEpiOutPhys = 1,   // y = acc + b (n < 6) -> de-standardise -> physical properties out6[6][ld6]
-    kEpiOutLoss = 2,   // y = acc + b; d = y - target (0 where the target is not finite); loss += d^2;
+    kEpiOutLoss = 2,   // y = acc + b; d = y - target (0 where the target is not finite); loss += d^2 (or |d|);
                        // dz = scale d -> out, outT, colsum
     kEpiDx = 3,        // dz = acc * gd -> out, outT, colsum
     kEpiDw = 4,        // partial[split][m][n] = acc (FP32)
@@ -61,8 +61,9 @@ struct GemmArgs {
     int log_mask;             // kEpiOutPhys: bit j set = output j was learned as its logarithm
     const float *target;      // kEpiOutLoss: standardised targets [6][ldt]
     int64_t ldt;
-    float loss_scale;         // d loss / d y = loss_scale * (y - target)
-    float *loss_part;         // [m_tiles] per-M-tile sum of squared errors
+    float loss_scale;         // d loss / d y = loss_scale * (y - target), or loss_scale * sign(y - target) (l1)
+    float *loss_part;         // [m_tiles] per-M-tile sum of squared (l1: absolute) errors
+    int l1;                   // kEpiOutLoss: 1 = L1 loss, 0 = squared error
     int *err;                 // set to 1 when a bounded wait runs out
     // kEpiHidden / kEpiDx with tma_out != 0: `out` (and `gd` when written) go
     // out through shared memory and TMA stores of 32 x 64 boxes (128-byte
@@ -310,8 +311,13 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                         const float tv = __ldg(a.target + (int64_t)jj * a.ldt + m);
                         d = isfinite(tv) ? v[jj] + bias[jj] - tv : 0.f;   // non-finite targets are masked
                     }
-                    lsum += d * d;
-                    v[jj] = a.loss_scale * d;
+                    if (a.l1) {
+                        lsum += fabsf(d);
+                        v[jj] = a.loss_scale * (float)((d > 0.f) - (d < 0.f));
+                    } else {
+                        lsum += d * d;
+                        v[jj] = a.loss_scale * d;
+                    }
                 }
                 if (mval) {
                     store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);

@@ -987,7 +987,9 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         GemmArgs a = base_args(m);
         a.M = (int)B; a.N = NOP; a.K = W; a.kb_per_split = W / 64;
         a.bias = d.master + d.lay[L].b_off;
-        a.target = d.tgt; a.ldt = d.max_batch; a.loss_scale = 2.0f / (float)(B * NOUT);
+        a.target = d.tgt; a.ldt = d.max_batch;
+        a.l1 = m->loss_l1;
+        a.loss_scale = (m->loss_l1 ? 1.0f : 2.0f) / (float)(B * NOUT);
         a.out = d.dzo; a.ldo = KIN; a.outT = d.dzot; a.ldoT = d.max_batch;
         a.colsum = d.colsum[L]; a.loss_part = d.loss_part;
         e = launch_gemm<16, kEpiOutLoss>(m->tm_h[L - 1], m->tm_w[L], a, mt, 1, 1, st);
@@ -1174,6 +1176,10 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
         return PR_OK;
     case SG_OPT_TEST_STALL:
         m->stall_test = value != 0;
+        return PR_OK;
+    case SG_OPT_LOSS:
+        PR_CHECK_ARG(value == SG_LOSS_REL_MSE || value == SG_LOSS_L1, "surrogate_set_option: bad loss %d", value);
+        m->loss_l1 = value == SG_LOSS_L1;
         return PR_OK;
     case SG_OPT_MODE:
         PR_CHECK_ARG(value == SG_MODE_FORWARD || value == SG_MODE_INVERSE, "surrogate_set_option: bad mode %d",

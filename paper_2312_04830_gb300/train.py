@@ -83,9 +83,32 @@ def make_pool_inverse(ctx, n, seed, device):
     return label_pool_inverse(ctx, T, p, Y, device)
 
 
-def make_pool(ctx, n, seed, device):
-    T, p, Y = W.training_states(n, seed=seed)
+def make_pool(ctx, n, seed, device, data="mixed", a2=20.0):
+    """Labelled pool of n states: "mixed" (half uniform cells, half noisy
+    flame-sheet states) or "augmented" (the paper's augmentation around the
+    cells of a flame-vortex field, W.augmented_field_states)."""
+    if data == "augmented":
+        T, p, Y = W.augmented_field_states(n, seed=seed, a2=a2)
+    else:
+        T, p, Y = W.training_states(n, seed=seed)
     return label_pool(ctx, T, p, Y, device)
+
+
+def evaluate_field(sg, ctx, grid, device):
+    """Errors of the surrogate on the flame-vortex field against the FP64 PR
+    path, on all cells and on the cells that pass the physical-outcome filter."""
+    import torch
+    T, p, Y = W.flame_vortex_field(grid)
+    d64 = lambda v: torch.as_tensor(v, dtype=torch.float64, device=device)
+    T64, p64, Y64 = d64(T), d64(p), d64(Y)
+    ref, st = ctx.props(T64, p64, Y64, precision="fp64")
+    dil, _ = ctx.props(T64, torch.ones_like(p64), Y64, precision="fp64", outputs=("mu", "lambda"))
+    out, fb = sg.infer(T64.float(), p64.float(), Y64.float())
+    ok = (st == 0) & torch.all(torch.isfinite(ref), dim=0)
+    phys = ok & (ref[4] >= DILUTE_FLOOR * dil[4]) & (ref[5] >= DILUTE_FLOOR * dil[5])
+    return {"cells": int(ok.sum()), "all": relative_rms(out[:, ok], ref[:, ok].float()),
+            "physical_cells": int(phys.sum()), "physical": relative_rms(out[:, phys], ref[:, phys].float()),
+            "fallback_fraction": float(fb.float().mean())}
 
 
 def relative_rms(pred, ref, names=OUT_NAMES):
@@ -145,22 +168,32 @@ def main():
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--seed", type=int, default=20231207)
     ap.add_argument("--save", default=None)
+    ap.add_argument("--loss", choices=("mse", "l1"), default="mse",
+                    help="relative MSE on standardised targets, or the paper's L1 norm")
+    ap.add_argument("--data", choices=("mixed", "augmented"), default="mixed",
+                    help="uniform + flame-sheet states, or the paper's augmentation around a field")
+    ap.add_argument("--a2", type=float, default=20.0, help="divisor a2 of the augmentation")
+    ap.add_argument("--eval-field", type=int, default=128, help="flame-vortex field edge for the field error")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     ctx = binding.PropertyContext(W.species_table())
     t0 = time.perf_counter()
-    x, y = make_pool(ctx, a.pool, a.seed, dev)
+    x, y = make_pool(ctx, a.pool, a.seed, dev, a.data, a.a2)
     xh, yh = make_pool(ctx, a.heldout, a.seed + 1, dev)
     t_data = time.perf_counter() - t0
     sg = binding.Surrogate(ctx, width=a.width, hidden_layers=a.layers, max_batch=a.batch)
+    sg.set_loss(a.loss)
     sg.fit_normalization(x, y)
     steps = int(round(a.epochs * x.shape[1] / a.batch))
     losses, secs = train(sg, x, y, steps, a.batch, a.lr, seed=a.seed)
     sg.sync_status()
-    flops = 3 * 2 * (11 * a.width + (a.layers - 1) * a.width ** 2 + a.width * 6) * a.batch * steps
+    flops = 3 * 2 * (13 * a.width + (a.layers - 1) * a.width ** 2 + a.width * 6) * a.batch * steps
     rep = {"pool": int(x.shape[1]), "steps": steps, "batch": a.batch, "train_seconds": secs,
            "samples_per_s": steps * a.batch / secs, "train_tflops": flops / secs / 1e12,
-           "data_seconds": t_data, "losses": losses, "heldout": evaluate(sg, xh, yh)}
+           "data_seconds": t_data, "losses": losses, "loss": a.loss, "data": a.data,
+           "heldout": evaluate(sg, xh, yh)}
+    if a.eval_field > 0:
+        rep["field"] = evaluate_field(sg, ctx, a.eval_field, dev)
     if a.save:
         sg.save(a.save)
     print(json.dumps(rep))

@@ -264,6 +264,29 @@ def training_states(n: int, seed: int = 20231207):
             np.ascontiguousarray(np.concatenate([Yu, Ym], axis=1)))
 
 
+def augmented_field_states(n: int, seed: int, grid: int = 64, a2: float = 20.0):
+    """The paper's data augmentation (Sec. 4.2, its equation for t): new states
+    t = c + a1 (max(h) - min(h)) / a2 around samples c of a flow field, for
+    every variable h, with a1 ~ U[-1, 1] drawn per state and variable and a2 a
+    fixed divisor.  The samples c are cells of the flame-vortex field (the
+    stand-in for the paper's first TGV time steps); T is clipped to
+    [100, 3500] K, mass fractions to [0, 1] and renormalised (the paper's
+    constraint that mixture fractions stay in [0, 1]); the positivity of the
+    density is left to the labelling filter.  p, uniform in the field, has no
+    range and so stays at the field's value."""
+    rng = np.random.default_rng(seed)
+    Tc, pc, Yc = flame_vortex_field(grid)
+    pick = rng.integers(0, Tc.size, n)
+    T, p, Y = Tc[pick], pc[pick], Yc[:, pick]
+    span = lambda v, axis=None: v.max(axis=axis) - v.min(axis=axis)
+    T = np.clip(T + rng.uniform(-1.0, 1.0, n) * span(Tc) / a2, 100.0, 3500.0)
+    p = p + rng.uniform(-1.0, 1.0, n) * span(pc) / a2
+    Y = Y + rng.uniform(-1.0, 1.0, Y.shape) * (span(Yc, axis=1) / a2)[:, None]
+    Y = np.clip(Y, 0.0, 1.0)
+    Y /= Y.sum(axis=0, keepdims=True)
+    return T, p, np.ascontiguousarray(Y)
+
+
 def serving_trace(n_clients: int = 64, per_client: int = 16, seed: int = 20231206,
                   g_lo: int = 32, g_hi: int = 256, frac_props: float = 0.7):
     """Request trace: per request a grid edge g = round(exp(U[ln g_lo, ln g_hi])),

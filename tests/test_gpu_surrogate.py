@@ -111,6 +111,39 @@ def test_gradients_match_oracle(ctx, orc, species, cuda, width, layers, batch):
     sg.close()
 
 
+def test_l1_loss_gradients_match_oracle(ctx, orc, species, cuda):
+    """The paper's L1 training loss (SG_OPT_LOSS): loss and every gradient
+    against the float64 oracle MLP with the L1 loss."""
+    from paper_2312_04830_gb300 import binding
+    width, layers, batch = 128, 2, 512
+    sg = binding.Surrogate(ctx, width=width, hidden_layers=layers, max_batch=batch, infer_chunk=1024, seed=17)
+    sg.set_loss("l1")
+    x, y = make_pool(orc, species, batch + 64, seed=15)
+    x, y = x[:, :batch], y[:, :batch]
+    xd, yd = to_dev(x, cuda), to_dev(y, cuda)
+    sg.fit_normalization(xd, yd)
+    loss, grad = sg.loss_grad(xd, yd, batch)
+    sg.sync_status()
+    g_gpu = grad.cpu().numpy().astype(np.float64)
+    norm = sg.get_normalization().astype(np.float64)
+    params = unflatten(sg.get_params(), [13] + [width] * layers + [6])
+    s_in, s_out = standardise(x, y, norm, species)
+    yhat, cache = omlp.forward(params, s_in, "tanh")
+    assert float(loss.item()) == pytest.approx(omlp.loss(yhat, s_out, "l1"), rel=2e-2)
+    grads = omlp.backward(params, cache, yhat, s_out, "tanh", "l1")
+    off = 0
+    for li, (gW, gb) in enumerate(grads):
+        for name, go in (("W", gW.ravel()), ("b", gb)):
+            gg = g_gpu[off:off + go.size]
+            off += go.size
+            rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
+            cos = float(gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go)))
+            assert rel < 5e-2 and cos > 0.998, (li, name, rel, cos)
+    with pytest.raises(binding.PrError):
+        binding.check(binding._sg_lib().surrogate_set_option(sg.handle, binding.SG_OPT_LOSS, 7), "set")
+    sg.close()
+
+
 def test_adam_step_matches_oracle(ctx, orc, species, cuda):
     """One Adam step from zero moments equals the oracle's update with the
     GPU's own gradients (isolates the optimiser kernel)."""
