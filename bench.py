@@ -35,12 +35,17 @@ METRIC = "cell-evals/s: PR FP64/FP32 vs BF16 MLP at <=1% rel err; %HBM roofline;
 UNIT = "cell-evals/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# FP64 (non-tensor) peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 (non-tensor) peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz;
+# the roofline uses the DFMA throughput measured on the device (pr_measure_peak)
+# when that succeeds, this nominal figure otherwise
+FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = FP64_PEAK_NOMINAL_TFLOPS
 # FP64 flops per cell of the FP64 kernels, from ncu instruction counts
 # (2 x DFMA + DADD + DMUL per launch / cells) on the 128^3 flame-vortex field
 # (profiles/fp64_kernels_counts_flame_vortex_128.md)
-FP64_FLOPS_PER_CELL = {"props_fp64": 1710.0, "newton_fp64": 1469.0}
+FP64_FLOPS_PER_CELL = {"props_fp64": 1710.0, "newton_fp64": 1469.0,
+                       # per-species outputs (profiles/species_kernel_fp64_flame_vortex_128.md)
+                       "species_fp64": 4117.0}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
 # / cells) of the same capture; a full launch moves this x its cells
 TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 108.0}
@@ -358,6 +363,17 @@ def run_ours(args):
 
     species = W.species_table()
     ctx = binding.PropertyContext(species)
+    # arithmetic-pipe peaks of this device (roofline denominators of the FP64 / FP32 paths)
+    global FP64_PEAK_TFLOPS
+    pipe_peaks = {"fp64_tflops_nominal": FP64_PEAK_NOMINAL_TFLOPS}
+    try:
+        pipe_peaks.update({"fp64_tflops": binding.measure_peak("fp64_fma") / 1e12,
+                           "fp32_tflops": binding.measure_peak("fp32_fma") / 1e12,
+                           "mufu_ex2_per_s": binding.measure_peak("mufu_ex2")})
+        FP64_PEAK_TFLOPS = pipe_peaks["fp64_tflops"]
+        pipe_peaks["fp64_source"] = "measured (pr_measure_peak, DFMA chains)"
+    except binding.PrError as e:
+        pipe_peaks["fp64_source"] = f"nominal (measurement failed: {e})"
     sg, sgi, sg_report = (None, None, None) if args.no_surrogate else train_surrogate(ctx, dev, args)
     T, p, Y, Ttrue = make_field(args.grid)
     n = T.size
@@ -540,9 +556,11 @@ def run_ours(args):
     d = roof_paths[dom]
     if "fp64_tflops" in d:
         roofline = {"bound": "alu", "kernel": dom, "achieved": d["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                    "peak_nominal": FP64_PEAK_NOMINAL_TFLOPS,
                     "unit": "TFLOP/s", "frac": d["fp64_frac"],
                     "traffic": TRAFFIC_BYTES_PER_CELL[dom] * n if dom in TRAFFIC_BYTES_PER_CELL else None,
-                    "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (unit counts and clock)"}
+                    "peak_source": "FP64 pipe, " + pipe_peaks["fp64_source"] +
+                                   "; nominal 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
     elif "tensor_tflops" in d:
         roofline = {"bound": "tensor", "kernel": dom, "achieved": d["tensor_tflops"], "peak": bf16_peak,
                     "unit": "TFLOP/s", "frac": d["tensor_frac"], "traffic": None,
@@ -562,6 +580,7 @@ def run_ours(args):
         "field_error_vs_pr_fp64": field_err,
         "roofline": roofline,
         "next_rows": next_rows,
+        "pipe_peaks": pipe_peaks,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

@@ -155,6 +155,19 @@ typedef struct {
 } pr_diffusion_correction;
 pr_status pr_set_diffusion_correction(pr_ctx *ctx, const pr_diffusion_correction *corr);
 
+/* Measured throughput of an arithmetic pipe on the current device, the
+ * roofline denominator of the kernels it bounds (a diagnostic; synchronous,
+ * about 0.1 s):
+ *   PR_PEAK_FP64_FMA  FP64 flops/s (an FMA counts two), the FP64 paths;
+ *   PR_PEAK_FP32_FMA  FP32 flops/s;
+ *   PR_PEAK_MUFU_EX2  exp2 evaluations/s of the special-function unit.
+ * Every thread runs eight independent FMA (or ex2) chains; the best of three
+ * timed launches is kept.  *ops_per_s is a HOST pointer. */
+#define PR_PEAK_FP64_FMA 0
+#define PR_PEAK_FP32_FMA 1
+#define PR_PEAK_MUFU_EX2 2
+pr_status pr_measure_peak(int kind, double *ops_per_s);
+
 /* Inversion T(h*, p, Y) by safeguarded Newton on f(T) = h(T) - h*, f' = cp,
  * inside the bracket [60, 5000] K, starting from T_guess (clipped to the
  * bracket).  A Newton step that leaves the current bracket, or follows a step

@@ -34,6 +34,17 @@ class PrError(RuntimeError):
     pass
 
 
+PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "mufu_ex2": 2}
+
+
+def measure_peak(kind: str) -> float:
+    """Measured throughput of one arithmetic pipe on the current device:
+    flops/s for 'fp64_fma' and 'fp32_fma', exp2/s for 'mufu_ex2'."""
+    v = ctypes.c_double(0.0)
+    check(lib().pr_measure_peak(PEAK_KINDS[kind], ctypes.byref(v)), "pr_measure_peak")
+    return v.value
+
+
 class _DiffCorr(ctypes.Structure):
     _fields_ = [("n_Tr", ctypes.c_int32), ("n_pr", ctypes.c_int32), ("Tr", ctypes.c_void_p),
                 ("pr", ctypes.c_void_p), ("f", ctypes.c_void_p)]
@@ -67,6 +78,8 @@ def lib():
             L.pr_species_props.restype = i32
             L.pr_set_diffusion_correction.argtypes = [vp, vp]
             L.pr_set_diffusion_correction.restype = i32
+            L.pr_measure_peak.argtypes = [i32, vp]
+            L.pr_measure_peak.restype = i32
             L.pr_T_from_h.argtypes = [vp, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, i32, d, vp]
             L.pr_T_from_h.restype = i32
             L.pr_last_error.argtypes = []

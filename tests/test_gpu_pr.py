@@ -353,3 +353,19 @@ def test_props_ext_reduced_precision(ctx, orc, species, cuda, precision):
         e = np.abs(g[q, ok] - o[q, ok]) / np.abs(o[q, ok])
         print(precision, name, np.median(e), np.percentile(e, 99))
         assert np.median(e) < 1e-5 and np.percentile(e, 99) < 1e-3
+
+
+def test_measured_pipe_peaks(prlib, cuda):
+    """The pipe microbenchmarks: DFMA throughput near the unit-count figure
+    (152 SMs x 2 DFMA/clk x 2 flops at 1.5-2.1 GHz), FP32 FMA far above it
+    (GB300's FP64 rate is 1/64 of FP32), and a positive exp2 rate."""
+    from paper_2312_04830_gb300 import binding
+    fp64 = binding.measure_peak("fp64_fma")
+    fp32 = binding.measure_peak("fp32_fma")
+    ex2 = binding.measure_peak("mufu_ex2")
+    print("measured peaks: FP64 %.3f TFLOP/s, FP32 %.1f TFLOP/s, ex2 %.3g /s" % (fp64 / 1e12, fp32 / 1e12, ex2))
+    assert 152 * 4 * 1.5e9 * 0.8 < fp64 < 152 * 4 * 2.1e9 * 1.05
+    assert fp32 > 30 * fp64
+    assert ex2 > 1e12
+    with pytest.raises(binding.PrError):
+        binding.check(prlib.pr_measure_peak(9, None), "pr_measure_peak")
