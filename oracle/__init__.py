@@ -91,6 +91,8 @@ def lib():
             L.orc_species_props.restype = None
             L.orc_neufeld_omega_d.argtypes = [d]
             L.orc_neufeld_omega_d.restype = d
+            L.orc_bilger_z.argtypes = [i32, vp, vp, vp, vp, i64, vp, vp]
+            L.orc_bilger_z.restype = None
             L.orc_max_threads.argtypes = []
             L.orc_max_threads.restype = i32
             _lib = L
@@ -222,6 +224,19 @@ def species_props(sp, T, p, Y, corr=None, threads: int = 0, **kw):
     if corr is not None:
         del keep
     return hk, Dk, st
+
+
+def bilger_z(sp, atoms, Y_fuel, Y_ox, Y):
+    """Bilger's mixture fraction of n cells (Y [N, n]); atoms [N, 3] = C, H, O."""
+    W = np.ascontiguousarray(sp.W, dtype=np.float64)
+    N = W.size
+    a = np.ascontiguousarray(atoms, dtype=np.int32).reshape(N, 3)
+    yf = np.ascontiguousarray(Y_fuel, dtype=np.float64)
+    yo = np.ascontiguousarray(Y_ox, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(N, -1)
+    Z = np.empty(Y.shape[1])
+    lib().orc_bilger_z(N, _ptr(a), _ptr(W), _ptr(yf), _ptr(yo), Y.shape[1], _ptr(Y), _ptr(Z))
+    return Z
 
 
 def neufeld_omega_d(Ts):

@@ -677,6 +677,35 @@ void orc_species_props(const orc_species *sp, const orc_corr *corr, int64_t n, c
     (void)nthreads;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Bilger's mixture fraction (the networks' composition input, Sec. 4.1):
+ * element mass fractions Z_e = sum_k a_ek W_e Y_k / W_k of carbon, hydrogen and
+ * oxygen (a_ek atoms of element e in species k, atomic masses W_e), Bilger's
+ * coupling function beta = 2 Z_C / W_C + Z_H / (2 W_H) - Z_O / W_O, and
+ * Z = (beta - beta_ox) / (beta_fuel - beta_ox) between the oxidiser and fuel
+ * streams.  atoms: N x 3 (C, H, O); W: species molar masses [g/mol]. */
+static double bilger_beta(int N, const int32_t *atoms, const double *W, const double *Y, ptrdiff_t ys)
+{
+    const double WC = 12.011, WH = 1.008, WO = 15.999;
+    double ZC = 0.0, ZH = 0.0, ZO = 0.0;
+    for (int k = 0; k < N; ++k) {
+        const double y = Y[(ptrdiff_t)k * ys];
+        ZC += atoms[3 * k + 0] * WC * y / W[k];
+        ZH += atoms[3 * k + 1] * WH * y / W[k];
+        ZO += atoms[3 * k + 2] * WO * y / W[k];
+    }
+    return 2.0 * ZC / WC + ZH / (2.0 * WH) - ZO / WO;
+}
+
+void orc_bilger_z(int N, const int32_t *atoms, const double *W, const double *Y_fuel, const double *Y_ox,
+                  int64_t n, const double *Y, double *Z)
+{
+    const double bf = bilger_beta(N, atoms, W, Y_fuel, 1);
+    const double bo = bilger_beta(N, atoms, W, Y_ox, 1);
+    for (int64_t i = 0; i < n; ++i)
+        Z[i] = (bilger_beta(N, atoms, W, Y + i, (ptrdiff_t)n) - bo) / (bf - bo);
+}
+
 /* Diagnostics for n cells (serial). */
 void orc_diagnose(const orc_species *sp, int64_t n, const double *T, const double *p, const double *Y,
                   double *out, int32_t *status, orc_diag *diag)

@@ -42,6 +42,12 @@ import numpy as np
 
 SPECIES = ("CH4", "O2", "CO2", "H2O", "CO", "H2", "OH", "H", "O")
 
+# atoms of carbon, hydrogen and oxygen per molecule (Bilger's mixture fraction)
+ATOMS_CHO = ((1, 4, 0), (0, 0, 2), (1, 0, 2), (0, 2, 1), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 1, 0), (0, 0, 1))
+# the two streams of the flame-vortex field: pure CH4 fuel, pure O2 oxidiser
+Y_FUEL = (1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+Y_OX = (0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+
 # molar mass [g/mol]
 W_G_PER_MOL = (16.043, 31.998, 44.009, 18.015, 28.010, 2.016, 17.007, 1.008, 15.999)
 # critical temperature [K]
