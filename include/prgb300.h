@@ -155,6 +155,21 @@ typedef struct {
 } pr_diffusion_correction;
 pr_status pr_set_diffusion_correction(pr_ctx *ctx, const pr_diffusion_correction *corr);
 
+/* Bilger's mixture fraction, the composition input of the paper's networks
+ * (Sec. 4.1): Z = (beta - beta_ox) / (beta_fuel - beta_ox) with Bilger's
+ * coupling function beta = 2 Z_C / W_C + Z_H / (2 W_H) - Z_O / W_O of the
+ * element mass fractions Z_e, i.e. beta = sum_k Y_k (2 a_Ck + a_Hk / 2 - a_Ok)
+ * / W_k.  pr_set_bilger takes HOST arrays: atoms [N][3] = carbon, hydrogen and
+ * oxygen atoms per molecule of each species, Y_fuel [N] and Y_ox [N] the
+ * stream compositions (PR_EINVAL when their coupling functions are equal);
+ * it synchronises the device.  pr_bilger_z: Y [N][ldY], Z [n] outputs (FP64
+ * or FP32 by prec; no validation, NaN propagates); PR_EINVAL before
+ * pr_set_bilger.  Z leaves [0, 1] for compositions that are not mixtures of
+ * the two streams (pure H2: Z > 1). */
+pr_status pr_set_bilger(pr_ctx *ctx, const int32_t *atoms, const double *Y_fuel, const double *Y_ox);
+pr_status pr_bilger_z(pr_ctx *ctx, pr_precision prec, int64_t n, const void *Y, int64_t ldY, void *Z,
+                      void *stream);
+
 /* Measured throughput of an arithmetic pipe on the current device, the
  * roofline denominator of the kernels it bounds (a diagnostic; synchronous,
  * about 0.1 s):
@@ -203,7 +218,9 @@ pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n,
  * log cp, log mu, log lambda], inputs and outputs standardised with statistics
  * of the training pool; h_ig(T, Y) = sum_k Y_k h_k(T) / W_k is the NASA-7
  * ideal-gas enthalpy (Sec. 2), evaluated exactly and added to the network's
- * departure.  Checkpoints carry format 3 (these inputs and targets).  Hidden layers use GeLU (Sec. 4.1) in its tanh form,
+ * departure.  Checkpoints carry format 4 (these inputs and targets and the
+ * Box-Cox parameters; format 3 files, without them, still load).  Hidden
+ * layers use GeLU (Sec. 4.1) in its tanh form,
  * 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).  Forward and
  * backward GEMMs run on the tensor cores (BF16 operands, FP32 accumulation);
  * master weights and Adam moments are FP32.
@@ -311,7 +328,22 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
 #define SG_LOSS_L1 1
 #define SG_MODE_FORWARD 0
 #define SG_MODE_INVERSE 1
+/* SG_MODE_BILGER (the paper's network inputs, Sec. 4.1-4.2): as
+ * SG_MODE_INVERSE (inputs h*, p, Y; outputs T, rho, psi, mu, alpha, cp;
+ * FP64 fallback outside the hull), but the network sees only
+ * [h* - h_f(Y), p, BoxCox(Z)], Z Bilger's mixture fraction of Y (the
+ * context's pr_set_bilger table, required before selecting the mode) and
+ * BoxCox(Z) = ((Z + shift)^lambda - 1) / lambda (log at lambda = 0) with the
+ * parameters of surrogate_set_boxcox (default lambda = 1, shift = 1e-3: Z
+ * itself, shifted).  Set mode and Box-Cox parameters before fitting and
+ * training. */
+#define SG_MODE_BILGER 2
 pr_status surrogate_set_option(sg_model *m, int option, int value);
+
+/* Box-Cox parameters of Bilger's mixture fraction in SG_MODE_BILGER (the
+ * paper applies the transform to the mixture fraction, Sec. 4.2): lambda in
+ * [-10, 10], shift in (0, 1].  Stored in checkpoints (format 4). */
+pr_status surrogate_set_boxcox(sg_model *m, double lambda, double shift);
 
 /* Synchronise the device and report PR_ETIMEOUT if a tensor-core kernel gave
  * up waiting on one of its barriers since the last call (the flag is then

@@ -78,6 +78,10 @@ def lib():
             L.pr_species_props.restype = i32
             L.pr_set_diffusion_correction.argtypes = [vp, vp]
             L.pr_set_diffusion_correction.restype = i32
+            L.pr_set_bilger.argtypes = [vp, vp, vp, vp]
+            L.pr_set_bilger.restype = i32
+            L.pr_bilger_z.argtypes = [vp, i32, i64, vp, i64, vp, vp]
+            L.pr_bilger_z.restype = i32
             L.pr_measure_peak.argtypes = [i32, vp]
             L.pr_measure_peak.restype = i32
             L.pr_T_from_h.argtypes = [vp, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, i32, d, vp]
@@ -219,6 +223,30 @@ class PropertyContext:
                                      n, _ptr(status), _stream(stream)), "pr_species_props")
         return hk_t, dk_t, status
 
+    def set_bilger(self, atoms, Y_fuel, Y_ox):
+        """Element table ([N, 3] C, H, O atoms) and the fuel / oxidiser streams of
+        Bilger's mixture fraction."""
+        a = np.ascontiguousarray(atoms, dtype=np.int32).reshape(self.n_species, 3)
+        yf = np.ascontiguousarray(Y_fuel, dtype=np.float64)
+        yo = np.ascontiguousarray(Y_ox, dtype=np.float64)
+        if yf.size != self.n_species or yo.size != self.n_species:
+            raise PrError("stream compositions must have one entry per species")
+        check(lib().pr_set_bilger(self.handle, a.ctypes.data, yf.ctypes.data, yo.ctypes.data), "pr_set_bilger")
+
+    def bilger_z(self, Y, precision="fp64", out=None, stream=None):
+        """Bilger's mixture fraction of the cells of Y [N, n]."""
+        import torch
+        prec = _prec(precision)
+        if not isinstance(Y, torch.Tensor) or not Y.is_cuda or Y.dtype != _dtype_of(prec) or Y.dim() != 2 \
+                or Y.shape[0] != self.n_species or Y.stride(1) != 1:
+            raise PrError(f"Y must be a CUDA [{self.n_species}, n] {_dtype_of(prec)} tensor with unit cell stride")
+        n = Y.shape[1]
+        if out is None:
+            out = torch.empty(n, dtype=Y.dtype, device=Y.device)
+        check(lib().pr_bilger_z(self.handle, prec, n, _ptr(Y), Y.stride(0), _ptr(out), _stream(stream)),
+              "pr_bilger_z")
+        return out
+
     def set_diffusion_correction(self, Tr=None, pr=None, f=None):
         """High-pressure factor f(T_r, p_r) of the binary diffusion coefficients
         as a table (Tr rows, pr columns); no arguments remove it."""
@@ -259,7 +287,7 @@ class _SgConfig(ctypes.Structure):
 
 SG_NORM_FLOATS = 64
 SG_OPT_FUSED_INFER = 1
-SG_OPT_MODE, SG_MODE_FORWARD, SG_MODE_INVERSE = 2, 0, 1
+SG_OPT_MODE, SG_MODE_FORWARD, SG_MODE_INVERSE, SG_MODE_BILGER = 2, 0, 1, 2
 SG_OPT_WAIT_LIMIT_KCYCLES, SG_OPT_TEST_STALL = 3, 4
 SG_OPT_LOSS, SG_LOSS_REL_MSE, SG_LOSS_L1 = 5, 0, 1
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
@@ -291,6 +319,8 @@ def _sg_lib():
         L.surrogate_infer.restype = i32
         L.surrogate_set_option.argtypes = [vp, i32, i32]
         L.surrogate_set_option.restype = i32
+        L.surrogate_set_boxcox.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+        L.surrogate_set_boxcox.restype = i32
         L.surrogate_sync_status.argtypes = [vp]
         L.surrogate_sync_status.restype = i32
         L.surrogate_save.argtypes = [vp, ctypes.c_char_p]
@@ -318,11 +348,17 @@ class Surrogate:
         self.width, self.hidden_layers, self.max_batch = width, hidden_layers, max_batch
 
     def set_mode(self, mode: str):
-        """'forward' (T, p, Y -> rho, Z, h, cp, mu, lambda) or 'inverse' (h*, p, Y
-        -> T, rho, psi, mu, alpha, cp); set before fitting and training."""
-        v = {"forward": SG_MODE_FORWARD, "inverse": SG_MODE_INVERSE}[mode]
+        """'forward' (T, p, Y -> rho, Z, h, cp, mu, lambda), 'inverse' (h*, p, Y
+        -> T, rho, psi, mu, alpha, cp) or 'bilger' (as inverse, the network
+        seeing h*, p and Bilger's mixture fraction of Y; needs the context's
+        set_bilger); set before fitting and training."""
+        v = {"forward": SG_MODE_FORWARD, "inverse": SG_MODE_INVERSE, "bilger": SG_MODE_BILGER}[mode]
         check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_MODE, v), "surrogate_set_option")
         self.mode = mode
+
+    def set_boxcox(self, lam: float, shift: float = 1e-3):
+        """Box-Cox parameters of Bilger's mixture fraction (bilger mode)."""
+        check(_sg_lib().surrogate_set_boxcox(self.handle, float(lam), float(shift)), "surrogate_set_boxcox")
 
     def set_fused_infer(self, on: bool):
         """All layers of an inference chunk in one persistent launch (True,

@@ -61,6 +61,11 @@ struct pr_ctx {
     float *d_corr32;
     int corr_nT, corr_nP;
     int occ_species[2];  // [FP64, FP32]
+    // Bilger's mixture fraction: per-species coefficients b_k of the coupling
+    // function, then beta_ox and 1 / (beta_fuel - beta_ox) ([n_species + 2])
+    double *d_bilger64;
+    float *d_bilger32;
+    int has_bilger;
 };
 
 namespace prgb {
@@ -69,5 +74,5 @@ pr_status species_tables_init(pr_ctx *c, const pr_species_table *tbl);
 void species_tables_free(pr_ctx *c);
 }  // namespace prgb
 
-// SG_MODE_FORWARD or SG_MODE_INVERSE of a surrogate (surrogate.cu).
+// SG_MODE_FORWARD, SG_MODE_INVERSE or SG_MODE_BILGER of a surrogate (surrogate.cu).
 int sg_mode_of(const sg_model *m);

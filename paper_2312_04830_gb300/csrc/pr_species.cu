@@ -206,6 +206,20 @@ __global__ void __launch_bounds__(kSpBlock) species_kernel(const SpArgs<Real> a)
     }
 }
 
+// Bilger's mixture fraction per cell: Z = (sum_k b_k Y_k - beta_ox) / (beta_fuel - beta_ox).
+template <typename Real>
+__global__ void __launch_bounds__(kSpBlock) bilger_kernel(int64_t n, const Real *__restrict__ Y, int64_t ldY,
+                                                          int N, const Real *__restrict__ coef, Real *Z)
+{
+    const Real bo = coef[N], ir = coef[N + 1];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Real beta = 0;
+        for (int k = 0; k < N; ++k) beta = M<Real>::fma(__ldg(coef + k), __ldg(Y + (int64_t)k * ldY + i), beta);
+        Z[i] = (beta - bo) * ir;
+    }
+}
+
 template <typename Real, int NS>
 void launch_species(const SpArgs<Real> &a, int occ, int sms, cudaStream_t st)
 {
@@ -255,6 +269,9 @@ pr_status species_tables_init(pr_ctx *c, const pr_species_table *tbl)
     PR_CUDA_TRY(cudaMalloc(&c->d_dtab32, t.size() * sizeof(float)));
     PR_CUDA_TRY(cudaMalloc(&c->d_corr64, kCorrFloats * sizeof(double)));
     PR_CUDA_TRY(cudaMalloc(&c->d_corr32, kCorrFloats * sizeof(float)));
+    PR_CUDA_TRY(cudaMalloc(&c->d_bilger64, (N + 2) * sizeof(double)));
+    PR_CUDA_TRY(cudaMalloc(&c->d_bilger32, (N + 2) * sizeof(float)));
+    c->has_bilger = 0;
     PR_CUDA_TRY(cudaMemcpy(c->d_dtab64, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
     PR_CUDA_TRY(cudaMemcpy(c->d_dtab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
     c->corr_nT = c->corr_nP = 0;
@@ -269,6 +286,8 @@ void species_tables_free(pr_ctx *c)
     cudaFree(c->d_dtab32);
     cudaFree(c->d_corr64);
     cudaFree(c->d_corr32);
+    cudaFree(c->d_bilger64);
+    cudaFree(c->d_bilger32);
 }
 
 }  // namespace prgb
@@ -307,6 +326,63 @@ pr_status pr_set_diffusion_correction(pr_ctx *ctx, const pr_diffusion_correction
     PR_CUDA_TRY(cudaMemcpy(ctx->d_corr32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
     ctx->corr_nT = nT;
     ctx->corr_nP = nP;
+    return PR_OK;
+}
+
+pr_status pr_set_bilger(pr_ctx *ctx, const int32_t *atoms, const double *Y_fuel, const double *Y_ox)
+{
+    PR_CHECK_ARG(ctx != nullptr && atoms != nullptr && Y_fuel != nullptr && Y_ox != nullptr,
+                 "pr_set_bilger: null argument");
+    const int N = ctx->n_species;
+    // species molar masses back from the device records (1 / inv_W, kg -> g)
+    std::vector<prk::SpeciesRec<double>> sp(ctx->ns_pad);
+    PR_CUDA_TRY(cudaMemcpy(sp.data(), ctx->d_sp64, sp.size() * sizeof(sp[0]), cudaMemcpyDeviceToHost));
+    // [N] coefficients b_k, then beta_ox and 1 / (beta_fuel - beta_ox)
+    std::vector<double> packed(N + 2, 0.0);
+    double bf = 0.0, bo = 0.0;
+    for (int k = 0; k < N; ++k) {
+        PR_CHECK_ARG(atoms[3 * k] >= 0 && atoms[3 * k + 1] >= 0 && atoms[3 * k + 2] >= 0,
+                     "pr_set_bilger: negative atom count for species %d", k);
+        PR_CHECK_ARG(std::isfinite(Y_fuel[k]) && std::isfinite(Y_ox[k]), "pr_set_bilger: stream not finite");
+        const double Wg = 1e3 / sp[k].inv_W;
+        // beta = 2 n_C + n_H / 2 - n_O, n_e = sum_k a_ek Y_k / W_k (moles of element per gram)
+        packed[k] = (2.0 * atoms[3 * k] + 0.5 * atoms[3 * k + 1] - 1.0 * atoms[3 * k + 2]) / Wg;
+        bf += packed[k] * Y_fuel[k];
+        bo += packed[k] * Y_ox[k];
+    }
+    PR_CHECK_ARG(bf != bo, "pr_set_bilger: fuel and oxidiser streams have the same coupling function");
+    packed[N] = bo;
+    packed[N + 1] = 1.0 / (bf - bo);
+    std::vector<float> p32(packed.begin(), packed.end());
+    PR_CUDA_TRY(cudaDeviceSynchronize());
+    PR_CUDA_TRY(cudaMemcpy(ctx->d_bilger64, packed.data(), packed.size() * sizeof(double), cudaMemcpyHostToDevice));
+    PR_CUDA_TRY(cudaMemcpy(ctx->d_bilger32, p32.data(), p32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    ctx->has_bilger = 1;
+    return PR_OK;
+}
+
+pr_status pr_bilger_z(pr_ctx *ctx, pr_precision prec, int64_t n, const void *Y, int64_t ldY, void *Z, void *stream)
+{
+    PR_CHECK_ARG(ctx != nullptr, "pr_bilger_z: null context");
+    PR_CHECK_ARG(ctx->has_bilger, "pr_bilger_z: no element table set (pr_set_bilger)");
+    PR_CHECK_ARG(prec == PR_FP64 || prec == PR_FP32 || prec == PR_MIXED, "pr_bilger_z: bad precision %d", (int)prec);
+    PR_CHECK_ARG(n >= 0, "pr_bilger_z: n < 0");
+    if (n == 0) return PR_OK;
+    PR_CHECK_ARG(ldY >= n, "pr_bilger_z: ldY < n");
+    const size_t esz = (prec == PR_FP64) ? 8 : 4;
+    PR_CHECK_ARG(Y != nullptr && Z != nullptr, "pr_bilger_z: null array");
+    PR_CHECK_ARG(prgb::aligned(Y, esz) && prgb::aligned(Z, esz), "pr_bilger_z: array not aligned to %zu bytes", esz);
+    int64_t need = (n + kSpBlock - 1) / kSpBlock;
+    const int64_t cap = (int64_t)ctx->num_sms * 16;
+    const int g = (int)(need < cap ? need : cap);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == PR_FP64)
+        bilger_kernel<double><<<g, kSpBlock, 0, st>>>(n, (const double *)Y, ldY, ctx->n_species, ctx->d_bilger64,
+                                                      (double *)Z);
+    else
+        bilger_kernel<float><<<g, kSpBlock, 0, st>>>(n, (const float *)Y, ldY, ctx->n_species, ctx->d_bilger32,
+                                                     (float *)Z);
+    PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
 }
 

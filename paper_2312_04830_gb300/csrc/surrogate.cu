@@ -74,14 +74,44 @@ __device__ __forceinline__ void derived_features(float T, const float *Y, const 
 
 __device__ __forceinline__ float h_ideal(float T, const float (&Y)[9], const void *sp32);
 
+// Box-Cox transform ((x + shift)^lambda - 1) / lambda (log(x + shift) at
+// lambda = 0); NaN where x + shift <= 0, which the hull check turns into a
+// fallback.
+__device__ __forceinline__ float box_cox(float x, float lambda, float shift)
+{
+    const float u = x + shift;
+    if (!(u > 0.f)) return __int_as_float(0x7fc00000);
+    return (lambda == 0.f) ? logf(u) : (powf(u, lambda) - 1.f) / lambda;
+}
+
 // Features of one cell from its first raw input v0, p and Y (in f[1..10]):
 //   forward model (v0 = T):  [log T, p, Y_1..Y_9, T_pc / T, log W];
 //   inverse model (v0 = h*): [h* - h_f(Y), p, Y_1..Y_9, log T_pc, log W], where
 //   h_f(Y) = sum_k Y_k h_k(298.15 K) / W_k removes the formation enthalpies, so
-//   that the first input is the sensible-plus-departure enthalpy.
-__device__ __forceinline__ void cell_features(int mode, float v0, const void *sp32, float (&f)[NIN])
+//   that the first input is the sensible-plus-departure enthalpy;
+//   Bilger model (v0 = h*): [h* - h_f(Y), p, BoxCox(Z)] with Bilger's mixture
+//   fraction Z of Y (the paper's network inputs, Sec. 4.1-4.2), the other
+//   slots zero.
+__device__ __forceinline__ void cell_features(const SgDev &d, float v0, float (&f)[NIN])
 {
+    const int mode = d.mode;
+    const void *sp32 = d.sp32;
     float tpc_over_T, logW;
+    if (mode == SG_MODE_BILGER) {
+        float Yk[9];
+        float beta = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            Yk[k] = f[2 + k];
+            beta = fmaf(__ldg(d.bilger + k), Yk[k], beta);
+        }
+        const float z = (beta - __ldg(d.bilger + 9)) * __ldg(d.bilger + 10);
+        f[0] = v0 - h_ideal(298.15f, Yk, sp32);
+        f[2] = box_cox(z, d.bc_lambda, d.bc_shift);
+#pragma unroll
+        for (int k = 3; k < NIN; ++k) f[k] = 0.f;
+        return;
+    }
     if (mode == SG_MODE_INVERSE) {
         float Yk[9];
 #pragma unroll
@@ -98,13 +128,12 @@ __device__ __forceinline__ void cell_features(int mode, float v0, const void *sp
 }
 
 // Features of pool row i, x = [v0, p, Y_1..Y_9] (v0 = T, or h* for the inverse model).
-__device__ __forceinline__ void features(const float *x, int64_t ldx, int64_t i, const void *sp32, int mode,
-                                         float (&f)[NIN])
+__device__ __forceinline__ void features(const float *x, int64_t ldx, int64_t i, const SgDev &d, float (&f)[NIN])
 {
     f[1] = __ldg(x + ldx + i);
 #pragma unroll
     for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
-    cell_features(mode, __ldg(x + i), sp32, f);
+    cell_features(d, __ldg(x + i), f);
 }
 
 // Mass-specific ideal-gas enthalpy sum_k Y_k h_k(T) / W_k [J/kg] from the
@@ -132,17 +161,17 @@ constexpr int kLogMaskInverse = 0x3F;   // all six
 // Targets from raw properties and inputs x = [T, p, Y_1..Y_9]:
 //   forward model, y = [rho, Z, h, cp, mu, lambda]:
 //     [log rho, Z, h - h_ig(T, Y), log cp, log mu, log lambda];
-//   inverse model, y = [T, rho, psi, mu, alpha, cp]: the six logarithms.
+//   inverse and Bilger models, y = [T, rho, psi, mu, alpha, cp]: the six logarithms.
 __device__ __forceinline__ void targets(const float *x, int64_t ldx, const float *y, int64_t ldy, int64_t i,
                                         const void *sp32, int mode, float (&q)[NOUT])
 {
-    const int lm = (mode == SG_MODE_INVERSE) ? kLogMaskInverse : kLogMaskForward;
+    const int lm = (mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
 #pragma unroll
     for (int j = 0; j < NOUT; ++j) {
         const float v = __ldg(y + (int64_t)j * ldy + i);
         q[j] = ((lm >> j) & 1) ? logf(v) : v;
     }
-    if (mode == SG_MODE_INVERSE) return;
+    if (mode != SG_MODE_FORWARD) return;
     float Yk[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Yk[k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
@@ -188,7 +217,7 @@ __global__ void refresh_bf16_kernel(SgDev d)
 // Per-block partial sums (FP64) of the 17 features / targets: sum, sum of
 // squares, min, max.
 __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, const float *y, int64_t ldy,
-                                    const void *sp32, int mode, double *part)
+                                    const SgDev d, double *part)
 {
     double s[NSTAT], s2[NSTAT], mn[NSTAT], mx[NSTAT];
     double cnt = 0;
@@ -196,8 +225,8 @@ __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, cons
     for (int k = 0; k < NSTAT; ++k) { s[k] = 0; s2[k] = 0; mn[k] = 1e300; mx[k] = -1e300; }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float f[NIN], q[NOUT];
-        features(x, ldx, i, sp32, mode, f);
-        targets(x, ldx, y, ldy, i, sp32, mode, q);
+        features(x, ldx, i, d, f);
+        targets(x, ldx, y, ldy, i, d.sp32, d.mode, q);
         bool fin = true;
 #pragma unroll
         for (int k = 0; k < NSTAT; ++k) fin = fin && isfinite((k < NIN) ? f[k] : q[k - NIN]);
@@ -283,7 +312,7 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
         int64_t src = r;
         if (sample_seed != 0 || n_pool != B) src = (int64_t)(splitmix64(sample_seed ^ ((uint64_t)r * 0xD1B54A32D192ED03ull)) % (uint64_t)n_pool);
         float f[NIN], q[NOUT];
-        features(x, ldx, src, d.sp32, d.mode, f);
+        features(x, ldx, src, d, f);
         targets(x, ldx, y, ldy, src, d.sp32, d.mode, q);
         float v[16];
 #pragma unroll
@@ -310,7 +339,7 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
         f[1] = __ldg(p + i);
 #pragma unroll
         for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(Y + (int64_t)k * ldY + i);
-        cell_features(d.mode, Ti, d.sp32, f);
+        cell_features(d, Ti, f);
         bool out = false;
         float v[16];
 #pragma unroll
@@ -323,10 +352,12 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
             }
         }
         store_row16_bf16(d.xi + r * KIN, v);
-        float Yk[9];
+        if (d.mode == SG_MODE_FORWARD) {
+            float Yk[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Yk[k] = f[2 + k];
-        if (d.mode != SG_MODE_INVERSE) d.hig[r] = h_ideal(Ti, Yk, d.sp32);
+            for (int k = 0; k < 9; ++k) Yk[k] = f[2 + k];
+            d.hig[r] = h_ideal(Ti, Yk, d.sp32);
+        }
         if (flags) flags[i] = out ? 1 : 0;
         if (out) list[atomicAdd(count, 1u)] = (int32_t)r;
     }
@@ -777,6 +808,9 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     d.hidden = m->hidden;
     d.max_batch = m->max_batch;
     d.sp32 = ctx->d_sp32;
+    d.bilger = ctx->d_bilger32;
+    d.bc_lambda = 1.0f;      // Box-Cox of Bilger's Z: linear until surrogate_set_boxcox
+    d.bc_shift = 1e-3f;
     const int W = m->width, L = m->hidden;
     const int64_t B = m->max_batch, C = m->chunk;
     cudaError_t e = cudaSuccess;
@@ -956,8 +990,7 @@ pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, in
 {
     PR_CHECK_ARG(m && x && y && n > 0 && ldx >= n && ldy >= n, "surrogate_fit_normalization: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->dev.sp32, m->dev.mode,
-                                                         m->d_normpart);
+    norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->dev, m->d_normpart);
     norm_final_kernel<<<1, 32, 0, st>>>(m->norm_blocks, m->d_normpart, m->dev.norm);
     PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
@@ -1102,8 +1135,8 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             fa.total = (long long)(fa.R + (long long)L * fa.D) * fa.ips;
             fa.out6 = out + r0; fa.ld6 = ldo;
             fa.out_mean = d.norm + 2 * NIN; fa.out_std = d.norm + 2 * NIN + NOUT;
-            fa.add_h = (d.mode == SG_MODE_INVERSE) ? nullptr : d.hig;
-            fa.log_mask = (d.mode == SG_MODE_INVERSE) ? kLogMaskInverse : kLogMaskForward;
+            fa.add_h = (d.mode != SG_MODE_FORWARD) ? nullptr : d.hig;
+            fa.log_mask = (d.mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
             fa.done = m->d_done; fa.err = m->d_err;
             fa.wait_cycles = m->wait_cycles > 0 ? m->wait_cycles : 4000000000LL;
             fa.stall_test = m->stall_test;
@@ -1125,14 +1158,14 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.bias = d.master + d.lay[L].b_off;
             a.out6 = out + r0; a.ld6 = ldo;
             a.out_mean = d.norm + 2 * NIN; a.out_std = d.norm + 2 * NIN + NOUT;
-            a.add_h = (d.mode == SG_MODE_INVERSE) ? nullptr : d.hig;
-            a.log_mask = (d.mode == SG_MODE_INVERSE) ? kLogMaskInverse : kLogMaskForward;
+            a.add_h = (d.mode != SG_MODE_FORWARD) ? nullptr : d.hig;
+            a.log_mask = (d.mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
             PR_CUDA_TRY((launch_gemm<16, kEpiOutPhys>(m->tm_hi[(L - 1) & 1], m->tm_w[L], a, mt, 1, 1, st)));
         }
         // FP64 Peng-Robinson for the cells outside the training hull
         const int fb = ctx->num_sms * 4;
         const SpeciesRec<double> *sp64 = (const SpeciesRec<double> *)ctx->d_sp64;
-        if (d.mode == SG_MODE_INVERSE) {
+        if (d.mode != SG_MODE_FORWARD) {
             if (ctx->has_kij)
                 fallback_inverse_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
                                                                      ldo, sp64, ctx->d_pair64, ctx->d_kij64,
@@ -1182,14 +1215,27 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
         m->loss_l1 = value == SG_LOSS_L1;
         return PR_OK;
     case SG_OPT_MODE:
-        PR_CHECK_ARG(value == SG_MODE_FORWARD || value == SG_MODE_INVERSE, "surrogate_set_option: bad mode %d",
-                     value);
+        PR_CHECK_ARG(value == SG_MODE_FORWARD || value == SG_MODE_INVERSE || value == SG_MODE_BILGER,
+                     "surrogate_set_option: bad mode %d", value);
+        PR_CHECK_ARG(value != SG_MODE_BILGER || m->ctx->has_bilger,
+                     "surrogate_set_option: SG_MODE_BILGER needs the context's element table (pr_set_bilger)");
         m->dev.mode = value;
+        m->dev.bilger = m->ctx->d_bilger32;
         return PR_OK;
     default:
         PR_CHECK_ARG(false, "surrogate_set_option: unknown option %d", option);
     }
     return PR_EINVAL;
+}
+
+pr_status surrogate_set_boxcox(sg_model *m, double lambda, double shift)
+{
+    PR_CHECK_ARG(m != nullptr, "surrogate_set_boxcox: null model");
+    PR_CHECK_ARG(std::isfinite(lambda) && std::fabs(lambda) <= 10.0, "surrogate_set_boxcox: lambda outside [-10, 10]");
+    PR_CHECK_ARG(std::isfinite(shift) && shift > 0.0 && shift <= 1.0, "surrogate_set_boxcox: shift outside (0, 1]");
+    m->dev.bc_lambda = (float)lambda;
+    m->dev.bc_shift = (float)shift;
+    return PR_OK;
 }
 
 pr_status surrogate_sync_status(sg_model *m)
@@ -1220,12 +1266,14 @@ pr_status surrogate_save(const sg_model *m, const char *path)
     FILE *f = fopen(path, "wb");
     if (!f) { prgb::set_error("surrogate_save: cannot open %s", path); return PR_EINVAL; }
     const char magic[4] = {'P', 'R', 'S', 'G'};
-    // format 3: 13 inputs (with T_pc / T and log W); the enthalpy output is the
-    // departure from the ideal-gas enthalpy
-    const int32_t hdr[4] = {3, m->width, m->hidden, m->dev.mode};
+    // format 4: 13 inputs (with T_pc / T and log W); the enthalpy output is the
+    // departure from the ideal-gas enthalpy; the Box-Cox parameters of
+    // Bilger's Z follow the counts
+    const int32_t hdr[4] = {4, m->width, m->hidden, m->dev.mode};
     const int64_t step = m->step;
+    const float bc[2] = {m->dev.bc_lambda, m->dev.bc_shift};
     bool ok = fwrite(magic, 1, 4, f) == 4 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&step, 8, 1, f) == 1 &&
-              fwrite(&n, 8, 1, f) == 1 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+              fwrite(&n, 8, 1, f) == 1 && fwrite(bc, 4, 2, f) == 2 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
     ok = (fclose(f) == 0) && ok;
     if (!ok) { prgb::set_error("surrogate_save: write failed"); return PR_EINVAL; }
     return PR_OK;
@@ -1241,8 +1289,10 @@ pr_status surrogate_load(sg_model *m, const char *path)
     int64_t step = 0, n = 0;
     bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "PRSG", 4) == 0 && fread(hdr, 4, 4, f) == 4 &&
               fread(&step, 8, 1, f) == 1 && fread(&n, 8, 1, f) == 1;
-    ok = ok && hdr[0] == 3 && hdr[1] == m->width && hdr[2] == m->hidden && hdr[3] == m->dev.mode &&
+    ok = ok && (hdr[0] == 3 || hdr[0] == 4) && hdr[1] == m->width && hdr[2] == m->hidden && hdr[3] == m->dev.mode &&
          n == m->dev.n_master;
+    float bc[2] = {m->dev.bc_lambda, m->dev.bc_shift};   // format 3 carries none
+    if (ok && hdr[0] == 4) ok = fread(bc, 4, 2, f) == 2;
     std::vector<float> buf;
     if (ok) {
         buf.resize(3 * n + SG_NORM_FLOATS);
@@ -1255,6 +1305,8 @@ pr_status surrogate_load(sg_model *m, const char *path)
     PR_CUDA_TRY(cudaMemcpy(m->dev.adam_m, buf.data() + n, n * 4, cudaMemcpyHostToDevice));
     PR_CUDA_TRY(cudaMemcpy(m->dev.adam_v, buf.data() + 2 * n, n * 4, cudaMemcpyHostToDevice));
     PR_CUDA_TRY(cudaMemcpy(m->dev.norm, buf.data() + 3 * n, SG_NORM_FLOATS * 4, cudaMemcpyHostToDevice));
+    m->dev.bc_lambda = bc[0];
+    m->dev.bc_shift = bc[1];
     refresh_bf16_kernel<<<256, 256>>>(m->dev);
     PR_CUDA_TRY(cudaDeviceSynchronize());
     m->step = step;

@@ -44,8 +44,10 @@ struct SgDev {
     // inference chunk buffers
     __nv_bfloat16 *xi, *hi[2];
     float *hig;                             // ideal-gas enthalpy of the chunk's cells [chunk]
-    int mode;                               // SG_MODE_FORWARD or SG_MODE_INVERSE
+    int mode;                               // SG_MODE_FORWARD, SG_MODE_INVERSE or SG_MODE_BILGER
     const void *sp32;                       // the context's FP32 species records (NASA-7 data)
+    const float *bilger;                    // SG_MODE_BILGER: the context's b_k [9], beta_ox, 1/range
+    float bc_lambda, bc_shift;              // SG_MODE_BILGER: Box-Cox of Z, ((Z + shift)^lambda - 1) / lambda
 };
 
 struct ParamRef {

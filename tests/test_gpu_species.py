@@ -201,3 +201,18 @@ def test_species_full_field_sampled(ctx, orc, species, cuda):
     g = (hk[:, idx_t].cpu().numpy(), dk[:, idx_t].cpu().numpy())
     o = orc.species_props(species, T[idx], p[idx], Y[:, idx])
     assert_parity(g, o[:2], st[idx_t].cpu().numpy(), o[2], "128^3 sample")
+
+
+def test_bilger_z_matches_oracle(ctx, orc, species, cuda):
+    """pr_bilger_z against the oracle's element-mass-fraction form: the
+    flame-vortex field and random compositions, FP64 and FP32."""
+    import torch
+    ctx.set_bilger(W.ATOMS_CHO, W.Y_FUEL, W.Y_OX)
+    _, _, Yf = W.flame_vortex_field(24)
+    Yr = W.dirichlet_half(np.random.default_rng(3), 9, 5000)
+    for Y in (Yf, Yr):
+        ref = orc.bilger_z(species, W.ATOMS_CHO, W.Y_FUEL, W.Y_OX, Y)
+        z64 = ctx.bilger_z(dev(Y, torch.float64, cuda)).cpu().numpy()
+        assert np.allclose(z64, ref, rtol=0, atol=1e-14)
+        z32 = ctx.bilger_z(dev(Y, torch.float32, cuda), precision="fp32").cpu().numpy().astype(np.float64)
+        assert np.allclose(z32, ref, rtol=0, atol=2e-6)

@@ -513,3 +513,121 @@ def test_inverse_surrogate_gain_on_flame_field(ctx, cuda):
     assert rms["mu"] < 0.05 and rms["alpha"] < 0.15 and rms["cp"] < 0.08
     assert t_sg < t_pr                 # measured 3.9x
     sg.close()
+
+
+# ------------------------------------------------ Bilger-mixture-fraction model
+def bilger_ctx(ctx):
+    ctx.set_bilger(W.ATOMS_CHO, W.Y_FUEL, W.Y_OX)
+    return ctx
+
+
+def make_pool_manifold(orc, species, n, seed):
+    """Bilger-model pool: flame-sheet states with noisy T (exact compositions),
+    x = [h, p, Y], y = [T, rho, psi, mu, alpha, cp] from the oracle."""
+    T, p, Y = W.manifold_states(n, seed=seed, exact_frac=1.0)
+    o, st = orc.props_ext(species, T, p, Y)
+    ok = (st == 0) & np.all(np.isfinite(o), axis=0) & np.all(o[[0, 3, 4, 5, 6, 7]] > 0, axis=0)
+    x = np.vstack([o[2], p, Y])[:, ok].astype(np.float32)
+    y = np.vstack([T, o[0], o[6], o[4], o[7], o[3]])[:, ok].astype(np.float32)
+    return x, y
+
+
+def features_bilger(x, species, lam, shift):
+    """[h - h_f(Y), p, BoxCox(Z), 0 ...] of raw states x = [h, p, Y] (float64),
+    Z the oracle's Bilger mixture fraction."""
+    import oracle
+    h, p, Y = x[0].astype(np.float64), x[1].astype(np.float64), x[2:].astype(np.float64)
+    hf = oracle.h_ideal(species, np.full(h.size, 298.15), Y)
+    Z = oracle.bilger_z(species, W.ATOMS_CHO, W.Y_FUEL, W.Y_OX, Y)
+    bc = np.log(Z + shift) if lam == 0 else ((Z + shift) ** lam - 1.0) / lam
+    f = np.zeros((13, h.size))
+    f[0], f[1], f[2] = h - hf, p, bc
+    return f
+
+
+def test_bilger_inference_matches_oracle_forward(ctx, orc, species, cuda):
+    """The paper's network inputs (enthalpy, pressure, Box-Cox of Bilger's
+    mixture fraction; Sec. 4.1-4.2): the fused tensor-core path against the
+    float64 forward pass with the same weights, on flame-sheet states."""
+    from paper_2312_04830_gb300 import binding
+    bilger_ctx(ctx)
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=1024, seed=31)
+    sg.set_mode("bilger")
+    sg.set_boxcox(0.3, 1e-3)
+    x, y = make_pool_manifold(orc, species, 6000, seed=32)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    n = 2500
+    out, fb = sg.infer(to_dev(x[0, :n], cuda), to_dev(x[1, :n], cuda), to_dev(x[2:, :n], cuda))
+    sg.sync_status()
+    out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy()
+    assert fb.sum() == 0
+    norm = sg.get_normalization().astype(np.float64)
+    assert np.all(norm[16:26] == 1.0)          # the unused input slots: zero variance, unit scale
+    params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 6])
+    s_in = (features_bilger(x[:, :n], species, 0.3, 1e-3).T - norm[0:13]) / norm[13:26]
+    yhat, _ = omlp.forward(params, s_in, "tanh")
+    s_gpu = (np.log(out).T - norm[26:32]) / norm[32:38]
+    err = np.abs(s_gpu - yhat)
+    print("bilger standardised output error: median", np.median(err), "max", err.max())
+    assert np.median(err) < 0.01 and err.max() < 0.1
+    sg.close()
+
+
+def test_bilger_fallback_and_checkpoint(ctx, orc, species, cuda, tmp_path):
+    """Cells that are no mixture of the two streams (H2-rich, Bilger Z > 1) leave
+    the hull and take the FP64 inversion; a format-4 checkpoint carries the
+    Box-Cox parameters (same outputs after reloading into a fresh model)."""
+    from paper_2312_04830_gb300 import binding
+    bilger_ctx(ctx)
+    sg = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=512, seed=33)
+    sg.set_mode("bilger")
+    sg.set_boxcox(0.5, 2e-3)
+    x, y = make_pool_manifold(orc, species, 4000, seed=34)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    rng = np.random.default_rng(35)
+    n = 400
+    T = rng.uniform(400.0, 2500.0, n)
+    p = np.full(n, 1e7)
+    Y = np.zeros((9, n))
+    Y[W.SPECIES.index("H2"), :200] = 1.0                   # Z > 1: outside the hull
+    _, Ym = W.flame_sheet_state(rng.uniform(0.0, 1.0, n - 200))
+    Y[:, 200:] = Ym
+    o, _ = orc.props_ext(species, T, p, Y)
+    x32 = np.vstack([o[2], p, Y]).astype(np.float32)
+    args = [to_dev(x32[0], cuda), to_dev(x32[1], cuda), to_dev(x32[2:], cuda)]
+    out, fb = sg.infer(*args)
+    sg.sync_status()
+    out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy().astype(bool)
+    assert np.all(fb[:200])
+    x64 = x32.astype(np.float64)
+    To, sto, _ = orc.T_from_h(species, x64[0, :200], x64[1, :200], x64[2:, :200], np.full(200, 1000.0))
+    oo, sto2 = orc.props_ext(species, To, x64[1, :200], x64[2:, :200])
+    ref = np.vstack([To, oo[0], oo[6], oo[4], oo[7], oo[3]])
+    m = (sto == 0) & (sto2 == 0)
+    assert m.sum() > 150
+    e = np.abs(out[:, :200][:, m] - ref[:, m]) / np.abs(ref[:, m])
+    assert e.max() < 1e-6
+    path = tmp_path / "bilger.ckpt"
+    sg.save(path)
+    sg2 = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=512, seed=99)
+    sg2.set_mode("bilger")
+    sg2.load(path)
+    out2, _ = sg2.infer(*args)
+    sg2.sync_status()
+    assert np.array_equal(out2.cpu().numpy(), out.astype(np.float32), equal_nan=True)
+    with pytest.raises(binding.PrError):
+        sg2.set_boxcox(0.5, 0.0)
+    sg.close()
+    sg2.close()
+
+
+def test_bilger_mode_needs_the_element_table(prlib, species, cuda):
+    from paper_2312_04830_gb300 import binding
+    c = binding.PropertyContext(species)
+    sg = binding.Surrogate(c, width=128, hidden_layers=2, max_batch=256, infer_chunk=512, seed=1)
+    with pytest.raises(binding.PrError):
+        sg.set_mode("bilger")
+    with pytest.raises(binding.PrError):
+        c.bilger_z(to_dev(np.full((9, 4), 1.0 / 9), cuda).double())
+    sg.close()
+    c.close()
