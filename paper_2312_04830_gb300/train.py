@@ -83,15 +83,66 @@ def make_pool_inverse(ctx, n, seed, device):
     return label_pool_inverse(ctx, T, p, Y, device)
 
 
-def make_pool(ctx, n, seed, device, data="mixed", a2=20.0):
-    """Labelled pool of n states: "mixed" (half uniform cells, half noisy
-    flame-sheet states) or "augmented" (the paper's augmentation around the
-    cells of a flame-vortex field, W.augmented_field_states)."""
+def pool_states(n, seed, data="mixed", a2=20.0):
+    """n states: "mixed" (half uniform cells, half noisy flame-sheet states),
+    "manifold" (flame-sheet compositions with noisy T) or "augmented" (the
+    paper's augmentation around the cells of a flame-vortex field)."""
     if data == "augmented":
-        T, p, Y = W.augmented_field_states(n, seed=seed, a2=a2)
-    else:
-        T, p, Y = W.training_states(n, seed=seed)
+        return W.augmented_field_states(n, seed=seed, a2=a2)
+    if data == "manifold":
+        return W.manifold_states(n, seed=seed, exact_frac=1.0)
+    return W.training_states(n, seed=seed)
+
+
+def make_pool(ctx, n, seed, device, data="mixed", a2=20.0):
+    """Labelled forward-model pool of n states (see pool_states)."""
+    T, p, Y = pool_states(n, seed, data, a2)
     return label_pool(ctx, T, p, Y, device)
+
+
+def boxcox_lambda(z, shift, lo=-3.0, hi=3.0, iters=60):
+    """Maximum-likelihood Box-Cox exponent of the values z + shift (golden
+    section on the profile log-likelihood (lam - 1) sum log u - n/2 log var(BC))."""
+    u = np.asarray(z, dtype=np.float64) + shift
+    u = u[u > 0]
+    lu = np.log(u)
+    slu = lu.sum()
+
+    def llf(lam):
+        bc = lu if abs(lam) < 1e-12 else np.expm1(lam * lu) / lam
+        return (lam - 1.0) * slu - 0.5 * u.size * np.log(bc.var())
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+    a, b = lo, hi
+    c, d = b - g * (b - a), a + g * (b - a)
+    fc, fd = llf(c), llf(d)
+    for _ in range(iters):
+        if fc > fd:
+            b, d, fd = d, c, fc
+            c = b - g * (b - a)
+            fc = llf(c)
+        else:
+            a, c, fc = c, d, fd
+            d = a + g * (b - a)
+            fd = llf(d)
+    return 0.5 * (a + b)
+
+
+def evaluate_field_inverse(sg, ctx, grid, device):
+    """Errors of an inverse-type surrogate (h, p, Y in; T, rho, psi, mu, alpha,
+    cp out) on the flame-vortex field against the FP64 path at the field's T."""
+    import torch
+    T, p, Y = W.flame_vortex_field(grid)
+    d64 = lambda v: torch.as_tensor(v, dtype=torch.float64, device=device)
+    T64, p64, Y64 = d64(T), d64(p), d64(Y)
+    o8, st = ctx.props_ext(T64, p64, Y64, precision="fp64")
+    dil, _ = ctx.props(T64, torch.ones_like(p64), Y64, precision="fp64", outputs=("mu", "lambda"))
+    out, fb = sg.infer(o8[2].float(), p64.float(), Y64.float())
+    ref = torch.stack([T64, o8[0], o8[6], o8[4], o8[7], o8[3]])
+    ok = (st == 0) & torch.all(torch.isfinite(ref), dim=0)
+    phys = ok & (o8[4] >= DILUTE_FLOOR * dil[4]) & (o8[5] >= DILUTE_FLOOR * dil[5])
+    return {"cells": int(ok.sum()), "physical_cells": int(phys.sum()),
+            "physical": relative_rms(out[:, phys], ref[:, phys].float(), INVERSE_OUT_NAMES),
+            "fallback_fraction": float(fb.float().mean())}
 
 
 def evaluate_field(sg, ctx, grid, device):
@@ -170,18 +221,33 @@ def main():
     ap.add_argument("--save", default=None)
     ap.add_argument("--loss", choices=("mse", "l1"), default="mse",
                     help="relative MSE on standardised targets, or the paper's L1 norm")
-    ap.add_argument("--data", choices=("mixed", "augmented"), default="mixed",
-                    help="uniform + flame-sheet states, or the paper's augmentation around a field")
+    ap.add_argument("--data", choices=("mixed", "manifold", "augmented"), default="mixed",
+                    help="uniform + flame-sheet states, flame-sheet states, or the paper's augmentation around a field")
     ap.add_argument("--a2", type=float, default=20.0, help="divisor a2 of the augmentation")
     ap.add_argument("--eval-field", type=int, default=128, help="flame-vortex field edge for the field error")
+    ap.add_argument("--model", choices=("forward", "inverse", "bilger"), default="forward",
+                    help="T,p,Y -> properties; h,p,Y -> T and properties; or the same from h, p and Bilger's Z")
+    ap.add_argument("--bc-shift", type=float, default=1e-3, help="Box-Cox shift of Bilger's Z")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     ctx = binding.PropertyContext(W.species_table())
+    ctx.set_bilger(W.ATOMS_CHO, W.Y_FUEL, W.Y_OX)
     t0 = time.perf_counter()
-    x, y = make_pool(ctx, a.pool, a.seed, dev, a.data, a.a2)
-    xh, yh = make_pool(ctx, a.heldout, a.seed + 1, dev)
+    if a.model == "forward":
+        x, y = make_pool(ctx, a.pool, a.seed, dev, a.data, a.a2)
+        xh, yh = make_pool(ctx, a.heldout, a.seed + 1, dev)
+    else:
+        x, y = label_pool_inverse(ctx, *pool_states(a.pool, a.seed, a.data, a.a2), dev)
+        xh, yh = label_pool_inverse(ctx, *pool_states(a.heldout, a.seed + 1, a.data, a.a2), dev)
     t_data = time.perf_counter() - t0
     sg = binding.Surrogate(ctx, width=a.width, hidden_layers=a.layers, max_batch=a.batch)
+    bc = None
+    if a.model != "forward":
+        sg.set_mode(a.model)
+    if a.model == "bilger":
+        z = ctx.bilger_z(x[2:, :1 << 20].contiguous(), precision="fp32").double().cpu().numpy()
+        bc = boxcox_lambda(z, a.bc_shift)
+        sg.set_boxcox(bc, a.bc_shift)
     sg.set_loss(a.loss)
     sg.fit_normalization(x, y)
     steps = int(round(a.epochs * x.shape[1] / a.batch))
@@ -190,10 +256,13 @@ def main():
     flops = 3 * 2 * (13 * a.width + (a.layers - 1) * a.width ** 2 + a.width * 6) * a.batch * steps
     rep = {"pool": int(x.shape[1]), "steps": steps, "batch": a.batch, "train_seconds": secs,
            "samples_per_s": steps * a.batch / secs, "train_tflops": flops / secs / 1e12,
-           "data_seconds": t_data, "losses": losses, "loss": a.loss, "data": a.data,
-           "heldout": evaluate(sg, xh, yh)}
+           "data_seconds": t_data, "losses": losses, "loss": a.loss, "data": a.data, "model": a.model,
+           "boxcox_lambda": bc}
+    if a.model == "forward":
+        rep["heldout"] = evaluate(sg, xh, yh)
     if a.eval_field > 0:
-        rep["field"] = evaluate_field(sg, ctx, a.eval_field, dev)
+        rep["field"] = (evaluate_field(sg, ctx, a.eval_field, dev) if a.model == "forward"
+                        else evaluate_field_inverse(sg, ctx, a.eval_field, dev))
     if a.save:
         sg.save(a.save)
     print(json.dumps(rep))

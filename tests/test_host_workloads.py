@@ -42,3 +42,17 @@ def test_augmentation_is_seeded():
     c = W.augmented_field_states(1000, seed=8, grid=8)
     assert all(np.array_equal(u, v) for u, v in zip(a, b))
     assert not np.array_equal(a[0], c[0])
+
+
+def test_boxcox_lambda_is_the_maximum_likelihood_exponent():
+    """The Box-Cox exponent fitted for Bilger's Z (train.boxcox_lambda)
+    against SciPy's maximum-likelihood estimate, and the log-normal case whose
+    exponent is 0."""
+    import pytest
+    ss = pytest.importorskip("scipy.stats")
+    from paper_2312_04830_gb300 import train
+    rng = np.random.default_rng(0)
+    z = rng.beta(0.3, 2.0, 100000)
+    assert train.boxcox_lambda(z, 1e-3) == pytest.approx(ss.boxcox_normmax(z + 1e-3, method="mle"), abs=1e-6)
+    x = rng.lognormal(0.0, 0.5, 100000)
+    assert abs(train.boxcox_lambda(x, 0.0)) < 0.02
