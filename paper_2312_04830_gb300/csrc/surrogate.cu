@@ -39,6 +39,15 @@ namespace {
 
 constexpr int NIN = 13, NOUT = 6;
 constexpr int KIN = 64;      // padded input width (one 64-wide k-block)
+// Each standardised input enters the first layer as two BF16 numbers, its
+// rounding hi = bf16(v) in column k and the remainder lo = bf16(v - hi) in
+// column kLoOff + k, both multiplied by the same weight (the FP32
+// accumulation adds them): the network sees its inputs to about 16 bits
+// instead of BF16's 8, at no tensor-core cost since K = 64 is one k-block
+// either way.  (A BF16 log T alone is off by up to 0.35 % in T, which moves
+// the viscosity of liquid oxygen by over 1 %.)
+constexpr int kLoOff = 16;
+static_assert(NIN <= 16 && kLoOff >= 16 && kLoOff + 16 <= KIN, "hi and lo input blocks must fit the padded K");
 constexpr int NOP = 16;      // padded output width
 constexpr int MOP = 128;     // padded output rows of the last layer's weight gradient
 constexpr int NSTAT = NIN + NOUT;
@@ -200,8 +209,12 @@ __global__ void init_params_kernel(SgDev d, uint64_t seed)
 __device__ __forceinline__ void write_bf16_copies(const SgDev &d, const ParamRef &r, float v)
 {
     if (r.bias) return;
+    // layer 0: padding columns from kLoOff on hold the lo-part weights,
+    // written only by the valid weights' own copies below
+    if (r.layer == 0 && !r.valid && r.i >= kLoOff) return;
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
     d.wb[r.layer][(int64_t)r.o * r.in_pad + r.i] = b;
+    if (r.layer == 0 && r.valid) d.wb[0][(int64_t)r.o * r.in_pad + kLoOff + r.i] = b;   // weight of the input's lo part
     if (r.layer > 0) d.wt[r.layer][(int64_t)r.i * r.out_pad_k + r.o] = b;
 }
 
@@ -302,6 +315,14 @@ __global__ void norm_final_kernel(int nblocks, const double *part, float *norm)
 }
 
 // ------------------------------------------------------------ prep kernels
+// lo[k] = v[k] - bf16(v[k]): the part of each input that BF16 drops (exact in
+// FP32; stored as BF16 it keeps the input to about 16 significant bits).
+__device__ __forceinline__ void split_hi_lo(const float (&v)[16], float (&lo)[16])
+{
+#pragma unroll
+    for (int k = 0; k < 16; ++k) lo[k] = v[k] - __bfloat162float(__float2bfloat16_rn(v[k]));
+}
+
 // Training batch: row r takes pool row src (in order when sample_seed == 0 and
 // the pool is the batch, else uniformly at random with replacement).
 __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const float *x, int64_t ldx, const float *y,
@@ -314,12 +335,17 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
         float f[NIN], q[NOUT];
         features(x, ldx, src, d, f);
         targets(x, ldx, y, ldy, src, d.sp32, d.mode, q);
-        float v[16];
+        float v[16], lo[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = (k < NIN) ? (f[k] - nm[k]) / nm[NIN + k] : 0.f;
+        split_hi_lo(v, lo);
         store_row16_bf16(d.x0 + r * KIN, v);
+        store_row16_bf16(d.x0 + r * KIN + kLoOff, lo);
 #pragma unroll
-        for (int k = 0; k < NIN; ++k) d.x0t[(int64_t)k * d.max_batch + r] = __float2bfloat16_rn(v[k]);
+        for (int k = 0; k < NIN; ++k) {
+            d.x0t[(int64_t)k * d.max_batch + r] = __float2bfloat16_rn(v[k]);
+            d.x0t[(int64_t)(kLoOff + k) * d.max_batch + r] = __float2bfloat16_rn(lo[k]);
+        }
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) d.tgt[(int64_t)j * d.max_batch + r] = (q[j] - nm[2 * NIN + j]) / nm[2 * NIN + NOUT + j];
     }
@@ -341,7 +367,7 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
         for (int k = 0; k < 9; ++k) f[2 + k] = __ldg(Y + (int64_t)k * ldY + i);
         cell_features(d, Ti, f);
         bool out = false;
-        float v[16];
+        float v[16], vlo[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             if (k < NIN) {
@@ -351,7 +377,9 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
                 v[k] = 0.f;
             }
         }
+        split_hi_lo(v, vlo);
         store_row16_bf16(d.xi + r * KIN, v);
+        store_row16_bf16(d.xi + r * KIN + kLoOff, vlo);
         if (d.mode == SG_MODE_FORWARD) {
             float Yk[9];
 #pragma unroll
@@ -494,7 +522,10 @@ __global__ void adam_kernel(SgDev d, float lr, float b1, float b2, float eps, in
         } else {
             const float *pp = d.partial[r.layer];
             const int64_t plane = (int64_t)d.dw_mpad[r.layer] * r.in_pad;
-            for (int s = 0; s < d.dw_splits[r.layer]; ++s) g += pp[s * plane + (int64_t)r.o * r.in_pad + r.i];
+            for (int s = 0; s < d.dw_splits[r.layer]; ++s) {
+                g += pp[s * plane + (int64_t)r.o * r.in_pad + r.i];
+                if (r.layer == 0) g += pp[s * plane + (int64_t)r.o * r.in_pad + kLoOff + r.i];   // tied lo weight
+            }
         }
         if (export_only) {
             grad_out[r.flat] = g;
