@@ -70,6 +70,8 @@ BYTES_PER_CELL = {
     # per-species outputs: T, p, Y in; h_k/(R T) and D_k for every species + status out
     "species_fp64": (2 + N_SPECIES) * 8 + 2 * N_SPECIES * 8 + 4,
     "species_fp32": (2 + N_SPECIES) * 4 + 2 * N_SPECIES * 4 + 4,
+    "props_mixed": (2 + N_SPECIES) * 4 + 6 * 4 + 4,
+    "newton_mixed": (3 + N_SPECIES) * 4 + 4 + 4 + 4,
 }
 
 
@@ -463,9 +465,15 @@ def run_ours(args):
     if not args.no_species:
         hk64, dk64 = (torch.empty((9, n), dtype=torch.float64, device=dev) for _ in range(2))
         hk32, dk32 = (torch.empty((9, n), dtype=torch.float32, device=dev) for _ in range(2))
+        outm = torch.empty((6, n), dtype=torch.float32, device=dev)
+        Tnm = torch.empty_like(T32)
         sp_calls = {
             "species_fp64": lambda: ctx.species_props(T64, p64, Y64, "fp64", hk=hk64, Dk=dk64, status=st),
             "species_fp32": lambda: ctx.species_props(T32, p32, Y32, "fp32", hk=hk32, Dk=dk32, status=st),
+            # the mixed-precision pattern: FP32 arithmetic, FP64 where the root selection or
+            # the pseudo-boiling inversion needs it
+            "props_mixed": lambda: ctx.props(T32, p32, Y32, "mixed", out=outm, status=st),
+            "newton_mixed": lambda: ctx.T_from_h(hs32, p32, Y32, T32, "mixed", T_out=Tnm, status=st, iters=it),
         }
         next_rows = {}
         for nm, fn in sp_calls.items():
@@ -489,7 +497,10 @@ def run_ours(args):
         rel = lambda a, b: float(((a.double() - b).abs() / b.abs().clamp_min(1.0)).max())
         next_rows["species_fp32_max_rel_err_vs_fp64"] = {"hk_RT": rel(hk32, hk64),
                                                          "Dk": float(((dk32.double() - dk64).abs() / dk64).max())}
-        del hk64, dk64, hk32, dk32
+        from paper_2312_04830_gb300 import train as TR
+        ok6 = torch.all(torch.isfinite(out64), dim=0) & torch.all(torch.isfinite(outm), dim=0)
+        next_rows["props_mixed_error_vs_fp64"] = TR.relative_rms(outm[:, ok6], out64[:, ok6].float())
+        del hk64, dk64, hk32, dk32, outm, Tnm
 
     # error of the reduced-precision paths on the field against the FP64 PR
     # path's outputs of the last timed step (rel RMS, p99, max per property)

@@ -55,6 +55,11 @@ typedef int pr_status;
 #define PR_CELL_BAD_INPUT   4  /* non-finite / non-positive T or p, negative Y, |sum Y - 1| > 1e-6 */
 #define PR_CELL_AMBIGUOUS   5  /* two physical roots with |Delta g_res| < 1e-9 (larger Z kept) */
 
+/* PR_MIXED: FP32 arithmetic throughout, FP64 for the cubic's root selection:
+ * a cell whose FP32 cubic has one physical root, clear of the three-root
+ * boundary (discriminant above 1e-4 of its terms' scale), keeps that root;
+ * cells with several physical roots (the residual-Gibbs choice between them)
+ * or a near-degenerate cubic are solved and selected in FP64. */
 typedef enum { PR_FP64 = 0, PR_FP32 = 1, PR_MIXED = 2 } pr_precision;
 
 /* Flags of pr_species_table.flags */
@@ -193,8 +198,8 @@ pr_status pr_measure_peak(int kind, double *ops_per_s);
  * the FP32 steps fail or do not settle; the FP64 iteration alone decides
  * convergence, so the result meets the same FP64 tolerance
  * (PR_FLAG_NEWTON_FP64_ONLY turns the warm start off).  iters counts the
- * FP64 iterations.  PR_MIXED iterates on the FP32 thermodynamics (FP64 cubic
- * root) and re-solves in FP64, from that root, the cells where it failed and
+ * FP64 iterations.  PR_MIXED iterates on the mixed thermodynamics (FP64 root
+ * selection, above) and re-solves in FP64, from that root, the cells where it failed and
  * those in the pseudo-boiling band (cp above 3 x the ideal-gas cp), where
  * the FP32 iteration is least reliable; there its T is the FP64 solution
  * rounded to FP32.  iters then counts both iterations.

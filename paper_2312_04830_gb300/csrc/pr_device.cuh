@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "prgb300.h"
 
 namespace prk {
@@ -198,14 +200,17 @@ __device__ __forceinline__ RZ cubic_polish(RZ z, RZ c2, RZ c1, RZ c0)
     return z;
 }
 
+// *clear (optional): the cubic has a single real root by a margin its
+// rounding cannot close, disc > 1e-4 (hq^2 + |tp^3|).
 template <typename RZ>
-__device__ __forceinline__ int cubic_phys_roots(RZ c2, RZ c1, RZ c0, RZ B, RZ z[3])
+__device__ __forceinline__ int cubic_phys_roots(RZ c2, RZ c1, RZ c0, RZ B, RZ z[3], bool *clear = nullptr)
 {
     const RZ c23 = c2 * RZ(1.0 / 3.0);
     const RZ P = M<RZ>::fma(-c2, c23, c1);                         // c1 - c2^2/3
     const RZ Q = M<RZ>::fma(c23, M<RZ>::fma(RZ(2) * c23, c23, -c1), c0);
     const RZ hq = RZ(0.5) * Q, tp = P * RZ(1.0 / 3.0);
     const RZ disc = M<RZ>::fma(hq, hq, tp * tp * tp);
+    if (clear) *clear = disc > RZ(1e-4) * (hq * hq + M<RZ>::fabs(tp * tp * tp));
     float seed[3];
     int ns;
     if (disc > RZ(0)) {
@@ -295,16 +300,42 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
     mix_a<Real, NS, KIJ>(c, T, sp, kij1m, am, dam, d2am);
     const Real bm = c.bm;
     const Real RT = Real(kR) * T;
-    const RZ A = (RZ)am * (RZ)p / ((RZ)RT * (RZ)RT);
-    const RZ B = (RZ)bm * (RZ)p / (RZ)RT;
-    const RZ c2 = B - RZ(1);
-    const RZ c1 = A - B * M<RZ>::fma(RZ(3), B, RZ(2));
-    const RZ c0 = B * (B + M<RZ>::fma(B, B, -A));
-    RZ zr[3];
-    const int nr = cubic_phys_roots<RZ>(c2, c1, c0, B, zr);
     RZ Zz;
-    o.status = select_root<RZ>(zr, nr, A, B, Zz);
-    if (o.status == kNoRoot) return;
+    RZ larg;   // 2 sqrt 2 B / (Z + (1 - sqrt 2) B), the departure logarithm's argument
+    bool need_rz = true;
+    if constexpr (!std::is_same<Real, RZ>::value) {
+        // Mixed precision: the FP32 cubic decides where FP64 is needed.  A
+        // single physical root clear of the three-root boundary is taken as it
+        // is: its coefficients are FP32 numbers, so an FP64 polish would not
+        // make it more accurate.  Several physical roots (the Gibbs selection
+        // between them) or a near-degenerate cubic go through the FP64 solve.
+        const Real Af = am * p / (RT * RT);
+        const Real Bf = bm * p / RT;
+        const Real c2f = Bf - Real(1);
+        const Real c1f = Af - Bf * M<Real>::fma(Real(3), Bf, Real(2));
+        const Real c0f = Bf * (Bf + M<Real>::fma(Bf, Bf, -Af));
+        Real zf[3];
+        bool clear = false;
+        const int nf = cubic_phys_roots<Real>(c2f, c1f, c0f, Bf, zf, &clear);
+        if (nf == 1 && clear) {
+            o.status = kOk;
+            Zz = (RZ)zf[0];
+            larg = (RZ)(Real(2.0 * kSqrt2) * Bf / (zf[0] + Real(1.0 - kSqrt2) * Bf));
+            need_rz = false;
+        }
+    }
+    if (need_rz) {
+        const RZ A = (RZ)am * (RZ)p / ((RZ)RT * (RZ)RT);
+        const RZ B = (RZ)bm * (RZ)p / (RZ)RT;
+        const RZ c2 = B - RZ(1);
+        const RZ c1 = A - B * M<RZ>::fma(RZ(3), B, RZ(2));
+        const RZ c0 = B * (B + M<RZ>::fma(B, B, -A));
+        RZ zr[3];
+        const int nr = cubic_phys_roots<RZ>(c2, c1, c0, B, zr);
+        o.status = select_root<RZ>(zr, nr, A, B, Zz);
+        if (o.status == kNoRoot) return;
+        larg = RZ(2.0 * kSqrt2) * B / (Zz + RZ(1.0 - kSqrt2) * B);
+    }
 
     // ideal-gas part (NASA-7)
     Real cp_ig = 0, h_ig = 0;
@@ -321,11 +352,9 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
     const Real iW = Real(1) / c.Wbar;
 
     // departures (in RZ where the root enters, then Real)
-    const RZ dm = RZ(1.0 - kSqrt2);
     // ln[(Z + (1 + sqrt 2) B)/(Z + (1 - sqrt 2) B)] = log1p(2 sqrt 2 B / (Z + (1 - sqrt 2) B)):
-    // the argument from the root's precision; the logarithm at the outputs'
-    // (the mixed path keeps FP64 for the root alone)
-    const RZ larg = RZ(2.0 * kSqrt2) * B / (Zz + dm * B);
+    // the argument (larg, above) from the root's precision; the logarithm at
+    // the outputs'
     const Real Z = (Real)Zz;
     const Real Lr = M<Real>::log1p((Real)larg);
     const Real inv2s2b = Real(1) / (Real(2.0 * kSqrt2) * bm);
