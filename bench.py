@@ -206,10 +206,19 @@ def cpu_baseline(T, p, Y, Ttrue, species, budget_cells_props=1 << 24, budget_cel
     oracle.T_from_h(tb, hs[2], p[s2], Y[:, s2], T[s2])
     t3 = time.perf_counter()
     secs = (t1 - t0) + (t3 - t2)
+    # one core on a 1/64 subsample of the same cells (per-core rate of the oracle)
+    m1, m2 = s1[::64], s2[::64]
+    t4 = time.perf_counter()
+    oracle.props(tb, T[m1], p[m1], Y[:, m1], threads=1)
+    t5 = time.perf_counter()
+    oracle.T_from_h(tb, hs[2][::64], p[m2], Y[:, m2], T[m2], threads=1)
+    t6 = time.perf_counter()
     return {"value": (n1 + n2) / secs, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"FP64 oracle: props on {n1} and T-from-h on {n2} cells spread evenly over the "
                       f"{T.size}-cell field; one cell-eval per cell per path",
-            "seconds": secs}
+            "seconds": secs,
+            "single_core": {"value": (m1.size + m2.size) / (t6 - t4), "unit": UNIT, "cores": 1,
+                            "sample": f"every 64th cell of the same samples ({m1.size} props, {m2.size} T-from-h)"}}
 
 
 # ----------------------------------------------------------- reference arm

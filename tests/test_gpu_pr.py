@@ -369,3 +369,31 @@ def test_measured_pipe_peaks(prlib, cuda):
     assert ex2 > 1e12
     with pytest.raises(binding.PrError):
         binding.check(prlib.pr_measure_peak(9, None), "pr_measure_peak")
+
+
+def test_mixed_selects_roots_in_fp64(ctx, orc, species, cuda):
+    """Subcritical O2 and CH4 (3 MPa, across their saturation temperatures),
+    where the cubic has liquid and vapour roots and the residual Gibbs energy
+    picks one: the mixed path's FP64 selection keeps the FP64 path's phase on
+    every cell (Z within 1e-5), including the cells closest to the switch."""
+    import torch
+    cells = []
+    for name, lo, hi in (("O2", 120.0, 150.0), ("CH4", 150.0, 188.0)):
+        k = W.SPECIES.index(name)
+        T = np.linspace(lo, hi, 4001)
+        Y = np.zeros((9, T.size))
+        Y[k] = 1.0
+        cells.append((T, Y))
+    T = np.concatenate([c[0] for c in cells]).astype(np.float32).astype(np.float64)
+    Y = np.concatenate([c[1] for c in cells], axis=1)
+    p = np.full(T.size, 3e6)
+    _, _, d = orc.diagnose(species, T, p, Y)
+    three = np.array([di["n_phys"] for di in d]) >= 2
+    assert three.sum() > 1000                   # the FP64 selection is exercised
+    g64, s64 = run_props(ctx, T, p, Y, cuda, precision="fp64")
+    gm, sm = run_props(ctx, T, p, Y, cuda, precision="mixed")
+    ok = (s64 == 0) & (sm == 0)
+    assert ok.sum() > 0.99 * T.size
+    dz = np.abs(gm[1, ok] - g64[1, ok]) / g64[1, ok]
+    print("mixed vs FP64 Z on two-root cells: max", dz[three[ok]].max())
+    assert dz.max() < 1e-5
