@@ -70,6 +70,11 @@ struct GemmArgs {
     // swizzle); tm_out / tm_gd map those matrices with that box
     int tma_out;
     CUtensorMap tm_out, tm_gd;
+    // kEpiDx with tma_out and tma_outT: `outT` goes out through the warp's
+    // second 4 KB box as [64 features][32 rows] (unswizzled) and a TMA store
+    // of that box (tm_outT: outT with 32 x 64 boxes)
+    int tma_outT;
+    CUtensorMap tm_outT;
 };
 
 constexpr int kEpiWarps = 8;
@@ -237,6 +242,7 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
     // one bulk group per 64 columns; the next group first waits until the
     // previous boxes have been read out of shared memory
     const bool tma = (EPI == kEpiHidden || EPI == kEpiDx) && a.tma_out && (HALF % 64 == 0);
+    const bool tmaT = tma && EPI == kEpiDx && a.tma_outT;   // the transposed copy through `sg`
     uint8_t *sh = stg, *sg = stg + 4096;
     float lsum = 0.f;
     if (active && !fail) {
@@ -329,11 +335,19 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) v[jj] = mval ? v[jj] * g[jj] : 0.f;
                 if (tma) stage_row16_bf16(sh, lane, c & 3, v);
+                if (tmaT) {
+                    // column jj of this chunk is row (c % 4) * 16 + jj of the box, this lane's element of it
+                    __nv_bfloat16 *bt = reinterpret_cast<__nv_bfloat16 *>(sg) + (c & 3) * 16 * 32 + lane;
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) bt[jj * 32] = __float2bfloat16_rn(v[jj]);
+                }
                 if (mval) {
                     if (!tma) store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+                    if (!tmaT) {
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj)
-                        a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                        for (int jj = 0; jj < 16; ++jj)
+                            a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                    }
                 }
             } else {  // kEpiDw
                 if (m < a.Mpad) {
@@ -349,6 +363,7 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                 if (lane == 0) {
                     umma::tma_store_2d(&a.tm_out, sh, nb - 48, m0 + q * 32);
                     if (EPI == kEpiHidden && a.gd) umma::tma_store_2d(&a.tm_gd, sg, nb - 48, m0 + q * 32);
+                    if (tmaT) umma::tma_store_2d(&a.tm_outT, sg, m0 + q * 32, nb - 48);   // (row, feature)
                     umma::bulk_commit();
                 }
             }

@@ -507,8 +507,26 @@ __global__ void __launch_bounds__(128) fallback_inverse_kernel(const int32_t *li
 }
 
 // ------------------------------------------------------------------- Adam
-__global__ void adam_kernel(SgDev d, float lr, float b1, float b2, float eps, int t, int64_t nct_bias,
-                            int export_only, float *grad_out)
+// Bias gradients: one warp per (layer, output) sums the per-M-tile column sums
+// of dz (nct of them), lanes striding over the tiles.
+__global__ void bias_grad_kernel(SgDev d, int64_t nct)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int l = (int)(wid / d.width), o = (int)(wid % d.width);
+    if (l > d.hidden) return;
+    const int ncol = d.lay[l].out_pad;
+    if (o >= ncol) return;
+    const float *cs = d.colsum[l];
+    float g = 0.f;
+    for (int64_t c = lane; c < nct; c += 32) g += cs[c * ncol + o];
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) g += __shfl_xor_sync(0xffffffffu, g, k);
+    if (lane == 0) d.bgrad[(int64_t)l * d.width + o] = g;
+}
+
+__global__ void adam_kernel(SgDev d, float lr, float b1, float b2, float eps, int t, int export_only,
+                            float *grad_out)
 {
     const float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.n_master; e += (int64_t)gridDim.x * blockDim.x) {
@@ -516,16 +534,26 @@ __global__ void adam_kernel(SgDev d, float lr, float b1, float b2, float eps, in
         if (!r.valid) continue;
         float g = 0.f;
         if (r.bias) {
-            const float *cs = d.colsum[r.layer];
-            const int ncol = r.out_pad_n;
-            for (int64_t c = 0; c < nct_bias; ++c) g += cs[c * ncol + r.o];
+            g = d.bgrad[(int64_t)r.layer * d.width + r.o];
         } else {
-            const float *pp = d.partial[r.layer];
+            // split-K partials; four independent sums keep four loads in flight
+            const float *pp = d.partial[r.layer] + (int64_t)r.o * r.in_pad + r.i;
             const int64_t plane = (int64_t)d.dw_mpad[r.layer] * r.in_pad;
-            for (int s = 0; s < d.dw_splits[r.layer]; ++s) {
-                g += pp[s * plane + (int64_t)r.o * r.in_pad + r.i];
-                if (r.layer == 0) g += pp[s * plane + (int64_t)r.o * r.in_pad + kLoOff + r.i];   // tied lo weight
+            const int ns = d.dw_splits[r.layer];
+            float g4[4] = {0.f, 0.f, 0.f, 0.f};
+            int s = 0;
+            for (; s + 4 <= ns; s += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    g4[u] += pp[(s + u) * plane];
+                    if (r.layer == 0) g4[u] += pp[(s + u) * plane + kLoOff];   // tied lo weight
+                }
             }
+            for (; s < ns; ++s) {
+                g4[0] += pp[s * plane];
+                if (r.layer == 0) g4[0] += pp[s * plane + kLoOff];
+            }
+            g = (g4[0] + g4[1]) + (g4[2] + g4[3]);
         }
         if (export_only) {
             grad_out[r.flat] = g;
@@ -540,6 +568,9 @@ __global__ void adam_kernel(SgDev d, float lr, float b1, float b2, float eps, in
         write_bf16_copies(d, r, w);
     }
 }
+
+// one thread per master element (n_master ~ 10^6: a few thousand blocks)
+inline int adam_blocks(const SgDev &d) { return (int)((d.n_master + 255) / 256); }
 
 __global__ void loss_final_kernel(const float *part, int64_t nct, float scale, float *loss_out)
 {
@@ -596,6 +627,23 @@ bool make_map(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, ui
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Unswizzled map of a feature-major matrix [rows][pitch] (BF16) with boxes of
+// 32 x 64: the TMA-store target of the transposed copies (32 batch rows of 64
+// features per box, 64-byte box rows).
+bool make_map_t(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, uint64_t pitch)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {pitch * 2};
+    cuuint32_t box[2] = {32, 64};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -783,6 +831,7 @@ static pr_status build_maps(sg_model *m)
         ok = ok && make_map(&m->ts_h[l], d.h[l], W, B, W, 32);
         ok = ok && make_map(&m->ts_g[l], d.g[l], W, B, W, 32);
         ok = ok && make_map(&m->ts_dz[l], d.dz[l], W, B, W, 32);
+        ok = ok && make_map_t(&m->tsT_dz[l], d.dzt[l], B, W, B);
     }
     ok = ok && make_map(&m->ts_hi[0], d.hi[0], W, C, W, 32);
     ok = ok && make_map(&m->ts_hi[1], d.hi[1], W, C, W, 32);
@@ -904,6 +953,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
         alloc((void **)&d.partial[l], (size_t)splits * mp * np * 4);
         const int ncol = (l == L) ? NOP : W;
         alloc((void **)&d.colsum[l], (size_t)(B / 128) * ncol * 4);
+        if (l == 0) alloc((void **)&d.bgrad, (size_t)(L + 1) * W * 4);
     }
     alloc((void **)&d.loss_part, (B / 128) * 4);
     alloc((void **)&m->d_loss, 4);
@@ -1066,6 +1116,7 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         a.gd = d.g[l - 1]; a.ldg = W;
         a.out = d.dz[l - 1]; a.ldo = W; a.outT = d.dzt[l - 1]; a.ldoT = d.max_batch;
         a.tma_out = 1; a.tm_out = m->ts_dz[l - 1];
+        a.tma_outT = 1; a.tm_outT = m->tsT_dz[l - 1];
         a.colsum = d.colsum[l - 1];
         const CUtensorMap &ta = (l == L) ? m->tm_dzo : m->tm_dz[l];
         e = launch_gemm_n<kEpiDx>(ta, m->tm_wt[l], a, mt, W, 1, st);
@@ -1106,10 +1157,12 @@ static pr_status train_common(sg_model *m, int64_t batch, int64_t n_pool, const 
     if (s) return s;
     const int64_t nct = batch / 128;
     if (grad_out) {
-        adam_kernel<<<512, 256, 0, st>>>(d, 0.f, 0.9f, 0.999f, 1e-8f, 1, nct, 1, grad_out);
+        bias_grad_kernel<<<(int)(((int64_t)(m->hidden + 1) * m->width * 32 + 255) / 256), 256, 0, st>>>(d, nct);
+        adam_kernel<<<adam_blocks(d), 256, 0, st>>>(d, 0.f, 0.9f, 0.999f, 1e-8f, 1, 1, grad_out);
     } else {
         m->step += 1;
-        adam_kernel<<<512, 256, 0, st>>>(d, lr, 0.9f, 0.999f, 1e-8f, (int)m->step, nct, 0, nullptr);
+        bias_grad_kernel<<<(int)(((int64_t)(m->hidden + 1) * m->width * 32 + 255) / 256), 256, 0, st>>>(d, nct);
+        adam_kernel<<<adam_blocks(d), 256, 0, st>>>(d, lr, 0.9f, 0.999f, 1e-8f, (int)m->step, 0, nullptr);
     }
     float *lo = loss_out ? loss_out : m->d_loss;
     loss_final_kernel<<<1, 256, 0, st>>>(d.loss_part, nct, 1.0f / (float)(batch * NOUT), lo);

@@ -40,6 +40,7 @@ struct SgDev {
     float *partial[SG_MAX_HIDDEN + 1];      // weight-gradient partials [split][Mpad][in_pad]
     int dw_splits[SG_MAX_HIDDEN + 1], dw_kps[SG_MAX_HIDDEN + 1], dw_mpad[SG_MAX_HIDDEN + 1];
     float *colsum[SG_MAX_HIDDEN + 1];       // per-CTA column sums of dz [B/128][out_pad]
+    float *bgrad;                           // bias gradients [hidden + 1][width] (reduced colsum)
     float *loss_part;                       // [B/128]
     // inference chunk buffers
     __nv_bfloat16 *xi, *hi[2];
@@ -103,6 +104,7 @@ struct sg_model {
         tm_dzt[SG_MAX_HIDDEN], tm_dzo, tm_dzot, tm_xi, tm_hi[2];
     // epilogue TMA-store maps (32-row boxes): h, GeLU'(z), dz, inference h
     CUtensorMap ts_h[SG_MAX_HIDDEN], ts_g[SG_MAX_HIDDEN], ts_dz[SG_MAX_HIDDEN], ts_hi[2];
+    CUtensorMap tsT_dz[SG_MAX_HIDDEN];      // dz^T [W][B] as the TMA-store target of 32 x 64 boxes
     // fused inference (mlp_fused.cuh): activation ring, its maps, the weight
     // maps with 256-row boxes, per-(row block, layer) arrival counters
     int fused_ok, fused_on, fused_D, fused_ring;
