@@ -27,6 +27,15 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
               "-Xcompiler", "-Wall", "-I", INCLUDE, "-I", CSRC]
 
 
+# Per-unit flags.  The FP32 property kernels and the mixed-precision kernels
+# take the fast single-precision forms (approximate division and square root,
+# hardware exp / log, flush of FP32 denormals): their results are stated to
+# FP32 accuracy against the FP64 oracle, and FP64 arithmetic, including the
+# mixed path's FP64 root selection and re-solves, is untouched by these flags.
+# The FP32 inversion (pr_inst_fp32_newton.cu) keeps the IEEE forms.
+UNIT_FLAGS = {"pr_inst_fp32.cu": ["--use_fast_math"], "pr_inst_mixed.cu": ["--use_fast_math"]}
+
+
 def nvcc() -> str:
     for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -49,7 +58,8 @@ def _compile(src: str, verbose: bool, ptxas_v: bool) -> str:
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not ptxas_v:
         return obj
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_v else []) + ["-c", src, "-o", obj]
+    cmd = ([nvcc()] + ARCH + NVCC_FLAGS + UNIT_FLAGS.get(os.path.basename(src), []) +
+           (["-Xptxas", "-v"] if ptxas_v else []) + ["-c", src, "-o", obj])
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)

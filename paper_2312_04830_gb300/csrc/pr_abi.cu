@@ -121,10 +121,13 @@ __global__ void setup_species_kernel(const HostTable *__restrict__ t, int N, int
 template <typename Real, typename RZ>
 void fill_occ(int NS, int occ_p[2], int occ_n[2])
 {
-    int o[4];
-    if (NS == 9) occupancy<Real, RZ, 9>(o);
-    else occupancy<Real, RZ, 32>(o);
-    occ_p[0] = o[0]; occ_p[1] = o[1]; occ_n[0] = o[2]; occ_n[1] = o[3];
+    if (NS == 9) {
+        occupancy_props<Real, RZ, 9>(occ_p);
+        occupancy_newton<Real, RZ, 9>(occ_n);
+    } else {
+        occupancy_props<Real, RZ, 32>(occ_p);
+        occupancy_newton<Real, RZ, 32>(occ_n);
+    }
 }
 
 bool bad_double(double v) { return !std::isfinite(v); }

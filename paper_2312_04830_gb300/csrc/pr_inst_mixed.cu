@@ -1,4 +1,5 @@
-// Instantiation of the property kernels for float arithmetic with a double cubic solve.
+// Instantiation of the property kernels for float arithmetic with a double cubic solve (compiled with
+// the fast single-precision forms: see build.py UNIT_FLAGS).
 #include "pr_kernels.cuh"
 
 namespace prk {

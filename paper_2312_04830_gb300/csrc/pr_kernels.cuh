@@ -347,21 +347,32 @@ void launch_newton(const NewtonArgs<Real> &a, bool kij, int occ, int sms, cudaSt
     else newton_kernel<Real, RZ, NS, false><<<g, kBlock, 0, st>>>(a);
 }
 
-// resident CTAs per SM of the four kernels of one (Real, RZ, NS):
-// occ[0..1] props (kij off/on), occ[2..3] Newton (kij off/on)
+// resident CTAs per SM of the property kernels (occ[0..1]: kij off/on) and of
+// the inversion kernels of one (Real, RZ, NS)
 template <typename Real, typename RZ, int NS>
-void occupancy(int occ[4])
+void occupancy_props(int occ[2])
 {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], props_kernel<Real, RZ, NS, false>, kBlock, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], props_kernel<Real, RZ, NS, true>, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], newton_kernel<Real, RZ, NS, false>, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], newton_kernel<Real, RZ, NS, true>, kBlock, 0);
-    for (int k = 0; k < 4; ++k) occ[k] = occ[k] > 0 ? occ[k] : 1;
+    for (int k = 0; k < 2; ++k) occ[k] = occ[k] > 0 ? occ[k] : 1;
 }
 
-#define PRK_DECLARE(Real, RZ, NS, EXT)                                                                    \
+template <typename Real, typename RZ, int NS>
+void occupancy_newton(int occ[2])
+{
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], newton_kernel<Real, RZ, NS, false>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], newton_kernel<Real, RZ, NS, true>, kBlock, 0);
+    for (int k = 0; k < 2; ++k) occ[k] = occ[k] > 0 ? occ[k] : 1;
+}
+
+// Explicit instantiations, one translation unit per (precision, kernel kind) so
+// that each can take its own compiler flags.
+#define PRK_DECLARE_PROPS(Real, RZ, NS, EXT)                                                              \
     EXT template void launch_props<Real, RZ, NS>(const PropsArgs<Real> &, bool, int, int, cudaStream_t);   \
+    EXT template void occupancy_props<Real, RZ, NS>(int *);
+#define PRK_DECLARE_NEWTON(Real, RZ, NS, EXT)                                                             \
     EXT template void launch_newton<Real, RZ, NS>(const NewtonArgs<Real> &, bool, int, int, cudaStream_t); \
-    EXT template void occupancy<Real, RZ, NS>(int *);
+    EXT template void occupancy_newton<Real, RZ, NS>(int *);
+#define PRK_DECLARE(Real, RZ, NS, EXT) PRK_DECLARE_PROPS(Real, RZ, NS, EXT) PRK_DECLARE_NEWTON(Real, RZ, NS, EXT)
 
 }  // namespace prk
