@@ -309,8 +309,9 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
         // is: its coefficients are FP32 numbers, so an FP64 polish would not
         // make it more accurate.  Several physical roots (the Gibbs selection
         // between them) or a near-degenerate cubic go through the FP64 solve.
-        const Real Af = am * p / (RT * RT);
-        const Real Bf = bm * p / RT;
+        const Real iRTf = Real(1) / RT;
+        const Real Bf = bm * p * iRTf;
+        const Real Af = am * p * iRTf * iRTf;
         const Real c2f = Bf - Real(1);
         const Real c1f = Af - Bf * M<Real>::fma(Real(3), Bf, Real(2));
         const Real c0f = Bf * (Bf + M<Real>::fma(Bf, Bf, -Af));
@@ -325,8 +326,12 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
         }
     }
     if (need_rz) {
-        const RZ A = (RZ)am * (RZ)p / ((RZ)RT * (RZ)RT);
-        const RZ B = (RZ)bm * (RZ)p / (RZ)RT;
+        // pairs of quotients below share one reciprocal (an FP64 division is
+        // several FP64-pipe instructions)
+        const RZ iRT = RZ(1) / (RZ)RT;
+        const RZ pRT = (RZ)p * iRT;
+        const RZ B = (RZ)bm * pRT;
+        const RZ A = (RZ)am * pRT * iRT;
         const RZ c2 = B - RZ(1);
         const RZ c1 = A - B * M<RZ>::fma(RZ(3), B, RZ(2));
         const RZ c0 = B * (B + M<RZ>::fma(B, B, -A));
@@ -349,7 +354,9 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
         cp_ig = M<Real>::fma(c.x[k], cpk, cp_ig);     // molar
         h_ig = M<Real>::fma(c.x[k], hk, h_ig);
     }
-    const Real iW = Real(1) / c.Wbar;
+    const Real rWb = Real(1) / (c.Wbar * bm);
+    const Real iW = bm * rWb;                                         // 1 / Wbar
+    const Real inv2s2b = Real(1.0 / (2.0 * kSqrt2)) * c.Wbar * rWb;   // 1 / (2 sqrt 2 bm)
 
     // departures (in RZ where the root enters, then Real)
     // ln[(Z + (1 + sqrt 2) B)/(Z + (1 - sqrt 2) B)] = log1p(2 sqrt 2 B / (Z + (1 - sqrt 2) B)):
@@ -357,18 +364,21 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
     // the outputs'
     const Real Z = (Real)Zz;
     const Real Lr = M<Real>::log1p((Real)larg);
-    const Real inv2s2b = Real(1) / (Real(2.0 * kSqrt2) * bm);
     const Real h_dep = M<Real>::fma(RT, (Real)(Zz - RZ(1)), M<Real>::fma(T, dam, -am) * inv2s2b * Lr);
     const Real cv_dep = T * d2am * inv2s2b * Lr;
-    const Real V = Z * RT / p;
+    const Real ZRT = Z * RT;
+    const Real rzp = Real(1) / (ZRT * p);
+    const Real V = ZRT * ZRT * rzp;                                   // Z R T / p
+    const Real rho_mol = p * p * rzp;                                 // p / (Z R T)
     const Real Vmb = V - bm;
     const Real den = M<Real>::fma(V, V + Real(2) * bm, -bm * bm);
-    const Real iden = Real(1) / den;
-    const Real dpdT = Real(kR) / Vmb - dam * iden;
-    const Real dpdV = -RT / (Vmb * Vmb) + Real(2) * am * (V + bm) * iden * iden;
+    const Real rvd = Real(1) / (Vmb * den);
+    const Real iVmb = den * rvd, iden = Vmb * rvd;
+    const Real dpdT = Real(kR) * iVmb - dam * iden;
+    const Real dpdV = -RT * iVmb * iVmb + Real(2) * am * (V + bm) * iden * iden;
     const Real cp_dep = cv_dep - T * dpdT * dpdT / dpdV - Real(kR);
     o.Z = Z;
-    o.rho_mol = p / (Z * RT);
+    o.rho_mol = rho_mol;
     o.h = (h_ig + h_dep) * iW;
     o.cp = (cp_ig + cp_dep) * iW;
     o.cv_ig_molar = cp_ig - Real(kR);
@@ -437,10 +447,12 @@ template <typename Real>
 __device__ __forceinline__ void chung_dense(Real Tc, Real Vc, Real cVc, Real omega, Real Mg, Real mur4, Real kap,
                                             Real T, Real rho_mol, Real cv_molar, Real &mu, Real &lam)
 {
-    const Real Tr = T / Tc;
+    // pairs of quotients share one reciprocal (FP64 divisions are costly)
+    const Real rTM = Real(1) / (Tc * Mg);
+    const Real Tr = T * Mg * rTM;                  // T / Tc
+    const Real iMg = Tc * rTM;                     // 1 / M
     const Real sTr = M<Real>::sqrt(Tr);
     const Real sMTc = M<Real>::sqrt(Mg * Tc);
-    const Real iMg = Real(1) / Mg;
     const Real Ts = Real(1.2593) * Tr;
     const Real Fc = Real(1) - Real(0.2756) * omega + Real(0.059035) * mur4 + kap;
     const Real lnTs = M<Real>::log(Ts);
@@ -448,20 +460,32 @@ __device__ __forceinline__ void chung_dense(Real Tc, Real Vc, Real cVc, Real ome
                     + Real(2.16178) * M<Real>::exp(Real(-2.43787) * Ts);
     const Real y = rho_mol * Real(1e-6) * Vc * Real(1.0 / 6.0);
     const Real omy = Real(1) - y;
-    const Real G1 = (Real(1) - Real(0.5) * y) / (omy * omy * omy);
+    const Real omy3 = omy * omy * omy;
+    const Real yp = (y > Real(0)) ? y : Real(1);   // y = 0 only for p = 0, kept finite
+    const Real ryo = Real(1) / (omy3 * yp);
+    const Real G1 = (Real(1) - Real(0.5) * y) * yp * ryo;   // (1 - y/2) / (1 - y)^3
     Real E[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i)
         E[i] = chung_visc<Real>(i, 0) + chung_visc<Real>(i, 1) * omega + chung_visc<Real>(i, 2) * mur4 + chung_visc<Real>(i, 3) * kap;
-    const Real iy = Real(1) / y;
+    const Real iy = omy3 * ryo;                    // 1 / y
     const Real fy4 = (y > Real(0)) ? -M<Real>::expm1(-E[3] * y) * iy : E[3];
-    const Real G2 = (E[0] * fy4 + E[1] * G1 * M<Real>::exp(E[4] * y) + E[2] * G1) / (E[0] * E[3] + E[1] + E[2]);
-    const Real iTs = Real(1) / Ts;
+    const Real nG = E[0] * fy4 + E[1] * G1 * M<Real>::exp(E[4] * y) + E[2] * G1;
+    const Real dG = E[0] * E[3] + E[1] + E[2];
+    const Real rG = Real(1) / (nG * dG);
+    const Real G2 = nG * nG * rG, iG2 = dG * dG * rG;
+    const Real rTO = Real(1) / (Ts * Ov);
+    const Real iTs = Ov * rTO, iOv = Ts * rTO;
     const Real etass = E[6] * y * y * G2 * M<Real>::exp(E[7] + iTs * (E[8] + E[9] * iTs));
     const Real sqTs = Real(1.1221853679316978) * sTr;   // sqrt(1.2593) sqrt(Tr)
-    const Real iOv = Real(1) / Ov;
-    const Real etas = sqTs * iOv * Fc * (Real(1) / G2 + E[5] * y) + etass;
-    const Real iVc23 = Real(1) / (cVc * cVc);
+    const Real etas = sqTs * iOv * Fc * (iG2 + E[5] * y) + etass;
+    const Real cVc2 = cVc * cVc;
+    const Real al = cv_molar * Real(1.0 / kR) - Real(1.5);
+    const Real be = Real(0.7862) - Real(0.7109) * omega + Real(1.3168) * omega * omega;
+    const Real Zp = Real(2.0) + Real(10.5) * Tr * Tr;
+    const Real dPsi = Real(0.6366) + be * Zp + Real(1.061) * al * be;
+    const Real rPV = Real(1) / (dPsi * cVc2);
+    const Real iVc23 = dPsi * rPV;                 // Vc^(-2/3)
     mu = etas * Real(36.344e-7) * sMTc * iVc23;
     const Real eta0 = Real(40.785e-7) * Fc * (sMTc * sTr) * iVc23 * iOv;   // sqrt(M T)
     Real Bc[7];
@@ -469,15 +493,15 @@ __device__ __forceinline__ void chung_dense(Real Tc, Real Vc, Real cVc, Real ome
     for (int i = 0; i < 7; ++i)
         Bc[i] = chung_cond<Real>(i, 0) + chung_cond<Real>(i, 1) * omega + chung_cond<Real>(i, 2) * mur4 + chung_cond<Real>(i, 3) * kap;
     const Real fyb4 = (y > Real(0)) ? -M<Real>::expm1(-Bc[3] * y) * iy : Bc[3];
-    const Real H2 = (Bc[0] * fyb4 + Bc[1] * G1 * M<Real>::exp(Bc[4] * y) + Bc[2] * G1) / (Bc[0] * Bc[3] + Bc[1] + Bc[2]);
-    const Real al = cv_molar * Real(1.0 / kR) - Real(1.5);
-    const Real be = Real(0.7862) - Real(0.7109) * omega + Real(1.3168) * omega * omega;
-    const Real Zp = Real(2.0) + Real(10.5) * Tr * Tr;
-    const Real Psi = Real(1) + al * ((Real(0.215) + Real(0.28288) * al - Real(1.061) * be + Real(0.26665) * Zp) /
-                                     (Real(0.6366) + be * Zp + Real(1.061) * al * be));
+    const Real nH = Bc[0] * fyb4 + Bc[1] * G1 * M<Real>::exp(Bc[4] * y) + Bc[2] * G1;
+    const Real dH = Bc[0] * Bc[3] + Bc[1] + Bc[2];
+    const Real rH = Real(1) / (nH * dH);
+    const Real H2 = nH * nH * rH, iH2 = dH * dH * rH;
+    const Real Psi = Real(1) + al * (Real(0.215) + Real(0.28288) * al - Real(1.061) * be + Real(0.26665) * Zp) *
+                                   cVc2 * rPV;
     const Real iMkg = Real(1e3) * iMg;
     const Real q = Real(3.586e-3) * (Real(31.622776601683793) * sMTc * iMg) * iVc23;   // sqrt(Tc / M[kg/mol])
-    lam = Real(31.2) * eta0 * Psi * iMkg * (Real(1) / H2 + Bc[5] * y) + q * Bc[6] * y * y * sTr * H2;
+    lam = Real(31.2) * eta0 * Psi * iMkg * (iH2 + Bc[5] * y) + q * Bc[6] * y * y * sTr * H2;
 }
 
 // Chung's mixture rules.  With the combining rules sigma_ij = sqrt(sigma_i
