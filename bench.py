@@ -48,7 +48,10 @@ FP64_FLOPS_PER_CELL = {"props_fp64": 1582.7, "newton_fp64": 1363.5,
                        "species_fp64": 4117.0}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
 # / cells) of the same capture; a full launch moves this x its cells
-TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 107.8}
+TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 107.8,
+                          # fused inference kernel, DRAM bytes per row of a chunk launch
+                          # (profiles/fused_mlp_infer_flame_vortex_128.md)
+                          "surrogate_bf16": 260.9, "surrogate_inverse_bf16": 531.7}
 # surrogate: 2 x (13*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
@@ -583,7 +586,9 @@ def run_ours(args):
                                    "; nominal 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
     elif "tensor_tflops" in d:
         roofline = {"bound": "tensor", "kernel": dom, "achieved": d["tensor_tflops"], "peak": bf16_peak,
-                    "unit": "TFLOP/s", "frac": d["tensor_frac"], "traffic": None,
+                    "unit": "TFLOP/s", "frac": d["tensor_frac"],
+                    "traffic": (TRAFFIC_BYTES_PER_CELL[dom] * min(SG_CHUNK, n)
+                                if dom in TRAFFIC_BYTES_PER_CELL else None),
                     "peak_source": f"{pk_kind} bf16 sustained"}
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": d["algorithmic_GBps"], "peak": pk["hbm_gbs"],
