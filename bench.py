@@ -283,6 +283,9 @@ def train_surrogate(ctx, dev, args):
     sg.close()
     sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=SG_CHUNK)
     sg.fit_normalization(x, y)
+    # low-confidence cells (predicted rho and Z off the equation of state by more than 1 %)
+    # take the FP64 fallback like cells outside the training hull
+    sg.set_confidence(0.01)
     steps = args.sg_steps if args.sg_steps > 0 else int(round(args.sg_epochs * x.shape[1] / 65536))
     losses, secs = TR.train(sg, x, y, steps, 65536, 1e-3, log_every=max(1, steps // 10))
     sg.sync_status()
@@ -430,7 +433,7 @@ def run_ours(args):
         paths.append("surrogate_bf16")
         calls["surrogate_bf16"] = lambda: sg.infer(T32, p32, Y32, out=outsg, used_fallback=fb)
         n_chunks = (n + SG_CHUNK - 1) // SG_CHUNK
-        launches["surrogate_bf16"] = n_chunks * (1 + 1 + 1)     # prep, fused MLP, fallback per chunk
+        launches["surrogate_bf16"] = n_chunks * (1 + 1 + 1 + 1)   # prep, fused MLP, confidence test, fallback
         # the inverse model: h*, p, Y -> T, rho, psi, mu, alpha, cp (the paper's arrangement)
         paths.append("surrogate_inverse_bf16")
         calls["surrogate_inverse_bf16"] = lambda: sgi.infer(hi32, p32, Y32, out=outsi, used_fallback=fbi)

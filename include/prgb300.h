@@ -328,6 +328,12 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * logarithms or scaled values); SG_LOSS_L1: the paper's L1 norm (Sec. 4.3),
  * mean |y - target|, output gradient sign(y - target) / (batch * 6) with
  * sign(0) = 0.  Non-finite targets are masked in both. */
+/* SG_OPT_CONFIDENCE_PPM: low-confidence test of the forward model, in parts
+ * per million (0: off).  The network predicts rho and Z separately while the
+ * equation of state ties them (rho Z R T = p W, W the mean molar mass of Y);
+ * a cell with |rho Z R T / (p W) - 1| above the tolerance takes the FP64
+ * fallback like a cell outside the hull (and is flagged in used_fallback). */
+#define SG_OPT_CONFIDENCE_PPM 6
 #define SG_OPT_LOSS 5
 #define SG_LOSS_REL_MSE 0
 #define SG_LOSS_L1 1

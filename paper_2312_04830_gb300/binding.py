@@ -290,6 +290,7 @@ SG_OPT_FUSED_INFER = 1
 SG_OPT_MODE, SG_MODE_FORWARD, SG_MODE_INVERSE, SG_MODE_BILGER = 2, 0, 1, 2
 SG_OPT_WAIT_LIMIT_KCYCLES, SG_OPT_TEST_STALL = 3, 4
 SG_OPT_LOSS, SG_LOSS_REL_MSE, SG_LOSS_L1 = 5, 0, 1
+SG_OPT_CONFIDENCE_PPM = 6
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
@@ -371,6 +372,13 @@ class Surrogate:
         v = {"mse": SG_LOSS_REL_MSE, "l1": SG_LOSS_L1}[kind]
         check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_LOSS, v), "surrogate_set_option")
         self.loss_kind = kind
+
+    def set_confidence(self, tol: float):
+        """Forward model: cells whose predicted rho and Z disagree with the
+        equation of state (|rho Z R T / (p W) - 1| > tol) take the FP64
+        fallback; 0 turns the test off."""
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_CONFIDENCE_PPM, int(round(tol * 1e6))),
+              "surrogate_set_option")
 
     def set_wait_limit(self, kcycles: int):
         """Limit, in thousands of SM clock cycles, of every bounded wait in the

@@ -354,7 +354,7 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
 // Inference chunk: standardised inputs, training-hull test, compaction of the
 // cells outside the hull into `list` (chunk-local indices).
 __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *T, const float *p, const float *Y,
-                                  int64_t ldY, uint8_t *flags, int32_t *list, unsigned int *count)
+                                  int64_t ldY, uint8_t *flags, uint8_t *cflags, int32_t *list, unsigned int *count)
 {
     const float *nm = d.norm;
     const float *lo = nm + 2 * NIN + 2 * NOUT, *hi = lo + NIN;
@@ -387,7 +387,32 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
             d.hig[r] = h_ideal(Ti, Yk, d.sp32);
         }
         if (flags) flags[i] = out ? 1 : 0;
+        cflags[r] = out ? 1 : 0;
         if (out) list[atomicAdd(count, 1u)] = (int32_t)r;
+    }
+}
+
+// Low-confidence cells of the forward model: the network predicts rho and Z
+// separately, while the equation of state ties them, rho Z R T = p W; a cell
+// whose two outputs disagree by more than `tol` joins the fallback list (cells
+// already on it are skipped through the chunk's flags).
+__global__ void confidence_kernel(SgDev d, int64_t r0, int64_t mc, const float *T, const float *p, const float *Y,
+                                  int64_t ldY, const float *out, int64_t ldo, float tol, uint8_t *flags,
+                                  uint8_t *cflags, int32_t *list, unsigned int *count)
+{
+    const SpeciesRec<float> *sp = static_cast<const SpeciesRec<float> *>(d.sp32);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < mc; r += (int64_t)gridDim.x * blockDim.x) {
+        if (cflags[r]) continue;
+        const int64_t i = r0 + r;
+        float s = 0.f;   // moles per kg = 1 / W
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s = fmaf(__ldg(Y + (int64_t)k * ldY + i), __ldg(&sp[k].inv_W), s);
+        const float c = out[i] * out[ldo + i] * float(prk::kR) * __ldg(T + i) * s / __ldg(p + i);
+        if (!(fabsf(c - 1.f) <= tol)) {
+            cflags[r] = 1;
+            if (flags) flags[i] = 1;
+            list[atomicAdd(count, 1u)] = (int32_t)r;
+        }
     }
 }
 
@@ -1203,8 +1228,8 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
         const int mt = ceil_div(mc, 128);
         PR_CUDA_TRY(cudaMemsetAsync(m->d_count, 0, 4, st));
         const int pb = ceil_div(mc, 256);
-        prep_infer_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, used_fallback, m->d_list,
-                                                                 m->d_count);
+        prep_infer_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, used_fallback,
+                                                                 m->d_flags, m->d_list, m->d_count);
         PR_CUDA_TRY(cudaGetLastError());
         if (m->fused_on) {
             // every layer in one cooperative launch (mlp_fused.cuh)
@@ -1246,7 +1271,12 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.log_mask = (d.mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
             PR_CUDA_TRY((launch_gemm<16, kEpiOutPhys>(m->tm_hi[(L - 1) & 1], m->tm_w[L], a, mt, 1, 1, st)));
         }
-        // FP64 Peng-Robinson for the cells outside the training hull
+        if (d.mode == SG_MODE_FORWARD && m->conf_tol > 0.f) {
+            confidence_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, out, ldo, m->conf_tol,
+                                                                     used_fallback, m->d_flags, m->d_list, m->d_count);
+            PR_CUDA_TRY(cudaGetLastError());
+        }
+        // FP64 Peng-Robinson for the cells outside the training hull (and the low-confidence ones)
         const int fb = ctx->num_sms * 4;
         const SpeciesRec<double> *sp64 = (const SpeciesRec<double> *)ctx->d_sp64;
         if (d.mode != SG_MODE_FORWARD) {
@@ -1293,6 +1323,10 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
         return PR_OK;
     case SG_OPT_TEST_STALL:
         m->stall_test = value != 0;
+        return PR_OK;
+    case SG_OPT_CONFIDENCE_PPM:
+        PR_CHECK_ARG(value >= 0, "surrogate_set_option: confidence tolerance must be >= 0");
+        m->conf_tol = 1e-6f * (float)value;
         return PR_OK;
     case SG_OPT_LOSS:
         PR_CHECK_ARG(value == SG_LOSS_REL_MSE || value == SG_LOSS_L1, "surrogate_set_option: bad loss %d", value);

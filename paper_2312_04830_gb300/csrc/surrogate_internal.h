@@ -111,6 +111,7 @@ struct sg_model {
     long long wait_cycles;                  // bounded-wait limit of the fused kernel
     int stall_test;                         // SG_OPT_TEST_STALL
     int loss_l1;                            // SG_OPT_LOSS == SG_LOSS_L1
+    float conf_tol;                         // SG_OPT_CONFIDENCE_PPM / 1e6; 0: off
     __nv_bfloat16 *ring;                    // [L][fused_ring * 128][W]
     uint32_t *d_done;
     CUtensorMap tmf_w[SG_MAX_HIDDEN + 1], tmf_ring_ld, tmf_ring_st;

@@ -631,3 +631,32 @@ def test_bilger_mode_needs_the_element_table(prlib, species, cuda):
         c.bilger_z(to_dev(np.full((9, 4), 1.0 / 9), cuda).double())
     sg.close()
     c.close()
+
+
+def test_low_confidence_cells_take_the_fallback(ctx, orc, species, cuda):
+    """The forward model's equation-of-state test (SG_OPT_CONFIDENCE_PPM): an
+    untrained network's rho and Z disagree with rho Z R T = p W everywhere, so
+    with the test on every in-hull cell is flagged and carries the FP64 PR
+    values (the library's own FP64 path, rounded to FP32); with it off none is."""
+    import torch
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=1024, seed=41)
+    x, y = make_pool(orc, species, 4000, seed=42)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    n = 1500
+    T, p, Y = to_dev(x[0, :n], cuda), to_dev(x[1, :n], cuda), to_dev(x[2:, :n], cuda)
+    out0, fb0 = sg.infer(T, p, Y)
+    sg.set_confidence(0.01)
+    out1, fb1 = sg.infer(T, p, Y)
+    sg.set_confidence(0.0)
+    sg.sync_status()
+    assert int(fb0.sum()) == 0
+    flagged = fb1.bool()
+    assert flagged.float().mean().item() > 0.95
+    ref, _ = ctx.props(T.double(), p.double(), Y.double(), "fp64")
+    got = out1[:, flagged].double()
+    exp = ref[:, flagged].float().double()
+    assert torch.equal(torch.nan_to_num(got, nan=-1.0), torch.nan_to_num(exp, nan=-1.0))
+    with pytest.raises(binding.PrError):
+        sg.set_confidence(-0.5)
+    sg.close()
