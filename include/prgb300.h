@@ -240,7 +240,8 @@ typedef struct {
     int32_t infer_chunk;    /* rows per inference chunk; multiple of 128 */
 } sg_config;
 
-#define SG_NORM_FLOATS 64  /* in_mean[13] in_std[13] out_mean[6] out_std[6] hull_lo[13] hull_hi[13] */
+#define SG_NORM_FLOATS 84  /* in_mean[13] in_std[13] out_mean[0..5] out_std[0..5] hull_lo[13] hull_hi[13]
+                              out_mean[6..15] out_std[6..15] */
 
 /* Create a model bound to `ctx` (which must hold exactly 9 species; it is
  * used for the Peng-Robinson fallback).  Weights ~ U(-1/sqrt(fan_in),
@@ -334,6 +335,20 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * a cell with |rho Z R T / (p W) - 1| above the tolerance takes the FP64
  * fallback like a cell outside the hull (and is flagged in used_fallback). */
 #define SG_OPT_CONFIDENCE_PPM 6
+/* SG_OPT_OUTPUTS (the paper's per-species networks, Sec. 4.1): with
+ * SG_MODE_INVERSE or SG_MODE_BILGER inputs, the network predicts
+ *   SG_OUT_PROPS  (default) T, rho, psi, mu, alpha, cp;
+ *   SG_OUT_DK     the 9 mixture-averaged diffusion coefficients D_k [m^2/s]
+ *                 (pr_species_props; learned as logarithms);
+ *   SG_OUT_HK     the 9 standard-state enthalpies h_k / (R T).
+ * surrogate_infer then writes [9][ldo]; training targets y are [9][ldy] of
+ * the same quantity; cells outside the hull take the FP64 inversion and the
+ * FP64 per-species values at its T (with the context's correction table).
+ * Selecting outputs re-initialises the weights (set before fitting). */
+#define SG_OPT_OUTPUTS 7
+#define SG_OUT_PROPS 0
+#define SG_OUT_DK 1
+#define SG_OUT_HK 2
 #define SG_OPT_LOSS 5
 #define SG_LOSS_REL_MSE 0
 #define SG_LOSS_L1 1

@@ -285,12 +285,13 @@ class _SgConfig(ctypes.Structure):
                 ("infer_chunk", ctypes.c_int32)]
 
 
-SG_NORM_FLOATS = 64
+SG_NORM_FLOATS = 84
 SG_OPT_FUSED_INFER = 1
 SG_OPT_MODE, SG_MODE_FORWARD, SG_MODE_INVERSE, SG_MODE_BILGER = 2, 0, 1, 2
 SG_OPT_WAIT_LIMIT_KCYCLES, SG_OPT_TEST_STALL = 3, 4
 SG_OPT_LOSS, SG_LOSS_REL_MSE, SG_LOSS_L1 = 5, 0, 1
 SG_OPT_CONFIDENCE_PPM = 6
+SG_OPT_OUTPUTS, SG_OUT_PROPS, SG_OUT_DK, SG_OUT_HK = 7, 0, 1, 2
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
@@ -425,10 +426,22 @@ class Surrogate:
         assert a.size == SG_NORM_FLOATS
         check(_sg_lib().surrogate_set_normalization(self.handle, a.ctypes.data), "surrogate_set_normalization")
 
-    @staticmethod
-    def _pool(x, y):
+    @property
+    def n_out(self) -> int:
+        return getattr(self, "_n_out", N_OUT)
+
+    def set_outputs(self, kind: str):
+        """'props' (the mode's six outputs), 'dk' (the 9 mixture-averaged
+        diffusion coefficients) or 'hk' (the 9 standard-state h_k / (R T));
+        per-species outputs need the inverse or Bilger mode.  Re-initialises
+        the weights."""
+        v = {"props": SG_OUT_PROPS, "dk": SG_OUT_DK, "hk": SG_OUT_HK}[kind]
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_OUTPUTS, v), "surrogate_set_option")
+        self._n_out = N_OUT if v == SG_OUT_PROPS else 9
+
+    def _pool(self, x, y):
         import torch
-        for nm, t, rows in (("x", x, N_RAW), ("y", y, N_OUT)):
+        for nm, t, rows in (("x", x, N_RAW), ("y", y, self.n_out)):
             if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
                 raise PrError(f"{nm} must be a float32 CUDA tensor")
             if t.dim() != 2 or t.shape[0] != rows or t.stride(1) != 1:
@@ -461,7 +474,7 @@ class Surrogate:
         import torch
         n, ldY = self.ctx._cells(PR_FP32, T, p, Y)
         if out is None:
-            out = torch.empty((6, n), dtype=torch.float32, device=T.device)
+            out = torch.empty((self.n_out, n), dtype=torch.float32, device=T.device)
         if used_fallback is None:
             used_fallback = torch.empty(n, dtype=torch.uint8, device=T.device)
         check(_sg_lib().surrogate_infer(self.handle, n, _ptr(T), _ptr(p), _ptr(Y), ldY, _ptr(out), out.stride(0),

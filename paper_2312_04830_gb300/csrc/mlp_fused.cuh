@@ -63,9 +63,10 @@ struct FusedArgs {
     int n_t;                              // N-tiles per hidden layer (W / 256)
     int ips;                              // items per slot, L n_t + 1
     long long total;                      // items, (R + L D) ips
-    float *out6;                          // [6][ld6] physical outputs of the chunk's rows
+    float *out6;                          // [nout][ld6] physical outputs of the chunk's rows
     long long ld6;
-    const float *out_mean, *out_std;      // [6] de-standardisation
+    const float *out_mean, *out_std;      // [nout] de-standardisation
+    int nout;                             // outputs in use (<= 16)
     const float *add_h;                   // per-row term added to output 2 (h), or NULL
     int log_mask;                         // bit j set = output j was learned as its logarithm
     uint32_t *done;                       // [R][L + 1] arrival counters, zero at launch
@@ -379,7 +380,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                     if (m < a.M) {
                         const float *sb = sbias + L * W;
 #pragma unroll
-                        for (int jj = 0; jj < 6; ++jj) {
+                        for (int jj = 0; jj < 16; ++jj) {
+                            if (jj >= a.nout) break;
                             float qv = (__uint_as_float(rr[jj]) + sb[jj]) * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
                             if (jj == 2 && a.add_h) qv += __ldg(a.add_h + m);
                             a.out6[(long long)jj * a.ld6 + m] = ((a.log_mask >> jj) & 1) ? __expf(qv) : qv;

@@ -33,7 +33,7 @@ constexpr int BK = 64;
 
 enum Epi : int {
     kEpiHidden = 0,    // h = GeLU(acc + b) -> out; (train) h^T -> outT, GeLU'(acc + b) -> gd
-    kEpiOutPhys = 1,   // y = acc + b (n < 6) -> de-standardise -> physical properties out6[6][ld6]
+    kEpiOutPhys = 1,   // y = acc + b (n < nout) -> de-standardise -> physical values out6[nout][ld6]
     kEpiOutLoss = 2,   // y = acc + b; d = y - target (0 where the target is not finite); loss += d^2 (or |d|);
                        // dz = scale d -> out, outT, colsum
     kEpiDx = 3,        // dz = acc * gd -> out, outT, colsum
@@ -54,16 +54,17 @@ struct GemmArgs {
     float *partial;           // kEpiDw: [split][Mpad][N]
     int Mpad;
     float *colsum;            // [m_tiles][N] per-M-tile column sums of dz (bias gradients)
-    float *out6;              // kEpiOutPhys: [6][ld6]
+    float *out6;              // kEpiOutPhys: [nout][ld6]
     int64_t ld6;
-    const float *out_mean, *out_std;   // [6] de-standardisation
+    const float *out_mean, *out_std;   // [nout] de-standardisation
     const float *add_h;       // kEpiOutPhys: per-row term added to output 2 (h) after de-standardisation
     int log_mask;             // kEpiOutPhys: bit j set = output j was learned as its logarithm
-    const float *target;      // kEpiOutLoss: standardised targets [6][ldt]
+    const float *target;      // kEpiOutLoss: standardised targets [nout][ldt]
     int64_t ldt;
     float loss_scale;         // d loss / d y = loss_scale * (y - target), or loss_scale * sign(y - target) (l1)
     float *loss_part;         // [m_tiles] per-M-tile sum of squared (l1: absolute) errors
     int l1;                   // kEpiOutLoss: 1 = L1 loss, 0 = squared error
+    int nout;                 // kEpiOutPhys / kEpiOutLoss: outputs in use (<= 16)
     int *err;                 // set to 1 when a bounded wait runs out
     // kEpiHidden / kEpiDx with tma_out != 0: `out` (and `gd` when written) go
     // out through shared memory and TMA stores of 32 x 64 boxes (128-byte
@@ -302,7 +303,8 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
             } else if (EPI == kEpiOutPhys) {
                 if (mval && nb == 0) {
 #pragma unroll
-                    for (int jj = 0; jj < 6; ++jj) {
+                    for (int jj = 0; jj < 16; ++jj) {
+                        if (jj >= a.nout) break;
                         const float sv = v[jj] + bias[jj];
                         float qv = sv * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
                         if (jj == 2 && a.add_h) qv += __ldg(a.add_h + m);
@@ -313,7 +315,7 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
                     float d = 0.f;
-                    if (mval && nb == 0 && jj < 6) {
+                    if (mval && nb == 0 && jj < a.nout) {
                         const float tv = __ldg(a.target + (int64_t)jj * a.ldt + m);
                         d = isfinite(tv) ? v[jj] + bias[jj] - tv : 0.f;   // non-finite targets are masked
                     }

@@ -34,22 +34,19 @@
 
 #include "pr_device.cuh"
 #include "pr_internal.h"
+#include "pr_species.cuh"
 
 namespace {
 
 using prk::M;
 using prk::SpeciesRec;
+using prs::corr_factor;
+using prs::dtab_len;
+using prs::omega_d;
 
 constexpr int kSpBlock = 128;
 constexpr int kCorrMax = 64;
 constexpr int kCorrFloats = 2 * kCorrMax + kCorrMax * kCorrMax;
-
-// Neufeld et al. (1972) fit of the Lennard-Jones Omega^(1,1)*.
-constexpr double kNA = 1.06036, kNB = 0.15610, kNC = 0.19300, kND = 0.47635;
-constexpr double kNE = 1.03587, kNF = 1.52996, kNG = 1.76474, kNH = 3.89411;
-
-// Flat per-context table: tc[NS], pc[NS], ie[NS*NS], epsB[NS*NS], ic[NS*NS].
-inline size_t dtab_len(int NS) { return 2 * (size_t)NS + 3 * (size_t)NS * NS; }
 
 template <typename Real>
 struct SpArgs {
@@ -62,35 +59,6 @@ struct SpArgs {
     const Real *corr;     // Tr[cT], pr[cP], f[cT][cP]; cT = 0: no correction
     int N, cT, cP;
 };
-
-// Omega_D at T* = Ts, with pw = T*^-B given.
-template <typename Real>
-__device__ __forceinline__ Real omega_d(Real Ts, Real pw)
-{
-    Real om = Real(kNA) * pw;
-    if (Ts < Real(40.0 / kND)) om = M<Real>::fma(Real(kNC), M<Real>::exp(Real(-kND) * Ts), om);
-    if (Ts < Real(40.0 / kNF)) om = M<Real>::fma(Real(kNE), M<Real>::exp(Real(-kNF) * Ts), om);
-    if (Ts < Real(40.0 / kNH)) om = M<Real>::fma(Real(kNG), M<Real>::exp(Real(-kNH) * Ts), om);
-    return om;
-}
-
-// Bilinear, clamped to the table's edges.
-template <typename Real>
-__device__ __forceinline__ Real corr_factor(const Real *__restrict__ c, int cT, int cP, Real x, Real y)
-{
-    const Real *Tr = c, *pr = c + cT, *f = c + cT + cP;
-    x = fmin(fmax(x, Tr[0]), Tr[cT - 1]);
-    y = fmin(fmax(y, pr[0]), pr[cP - 1]);
-    int i = 0, j = 0;
-    while (i < cT - 2 && x > Tr[i + 1]) ++i;
-    while (j < cP - 2 && y > pr[j + 1]) ++j;
-    const Real tx = (x - Tr[i]) / (Tr[i + 1] - Tr[i]);
-    const Real ty = (y - pr[j]) / (pr[j + 1] - pr[j]);
-    const Real *r0 = f + i * cP + j, *r1 = r0 + cP;
-    const Real g0 = M<Real>::fma(ty, r0[1] - r0[0], r0[0]);
-    const Real g1 = M<Real>::fma(ty, r1[1] - r1[0], r1[0]);
-    return M<Real>::fma(tx, g1 - g0, g0);
-}
 
 template <typename Real, int NS>
 __global__ void __launch_bounds__(kSpBlock) species_kernel(const SpArgs<Real> a)
@@ -109,7 +77,6 @@ __global__ void __launch_bounds__(kSpBlock) species_kernel(const SpArgs<Real> a)
     }
     for (int e = threadIdx.x; e < 2 * NS + 3 * NS * NS; e += blockDim.x) s_tab[e] = a.dtab[e];
     __syncthreads();
-    const Real *tc = s_tab, *pc = s_tab + NS, *ie = s_tab + 2 * NS, *epsB = ie + NS * NS, *ic = epsB + NS * NS;
 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
@@ -140,67 +107,19 @@ __global__ void __launch_bounds__(kSpBlock) species_kernel(const SpArgs<Real> a)
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
                 if (k >= a.N) break;
-                const Real *e = s_h[T < s_tmid[k] ? 0 : 1][k];
-                const Real h = M<Real>::fma(
-                    M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(e[4], T, e[3]), T, e[2]), T, e[1]), T, e[0]),
-                    T, e[5]);
-                a.hk[(int64_t)k * a.ldo + i] = h * iRT;
+                a.hk[(int64_t)k * a.ldo + i] = prs::h_over_RT<Real>(s_h[T < s_tmid[k] ? 0 : 1][k], T, iRT);
             }
         }
         if (a.Dk) {
             const Real inv_s = Real(1) / s;
-            Real Tpc = 0, ppc = 0;
 #pragma unroll
-            for (int k = 0; k < NS; ++k) {
-                x[k] *= inv_s;
-                Tpc = M<Real>::fma(x[k], tc[k], Tpc);
-                ppc = M<Real>::fma(x[k], pc[k], ppc);
-            }
-            const Real f = (a.cT > 0) ? corr_factor<Real>(a.corr, a.cT, a.cP, T / Tpc, p / ppc) : Real(1);
-            const Real TmB = M<Real>::exp(Real(-kNB) * M<Real>::log(T));   // T^-B
-            Real acc[NS];
-#pragma unroll
-            for (int k = 0; k < NS; ++k) acc[k] = 0;
-#pragma unroll
-            for (int k = 0; k < NS - 1; ++k) {
-                if (k >= a.N - 1) break;
-#pragma unroll
-                for (int j = k + 1; j < NS; ++j) {
-                    if (j >= a.N) break;
-                    const int q = k * NS + j;
-                    const Real om = omega_d<Real>(T * ie[q], TmB * epsB[q]);
-                    const Real w = om * ic[q];
-                    acc[k] = M<Real>::fma(x[j], w, acc[k]);
-                    acc[j] = M<Real>::fma(x[k], w, acc[j]);
-                }
-            }
-            const Real scale = f * T * M<Real>::sqrt(T) / p;   // f T^(3/2) / p
-            // sum_{j != k} y_j from prefix and suffix sums
-            Real others[NS];
-            Real run = 0;
-#pragma unroll
-            for (int k = 0; k < NS; ++k) {
-                others[k] = run;
-                run += y[k];
-            }
-            run = 0;
-#pragma unroll
-            for (int k = NS - 1; k >= 0; --k) {
-                others[k] += run;
-                run += y[k];
-            }
-            const Real iys = Real(1) / ysum;
+            for (int k = 0; k < NS; ++k) x[k] *= inv_s;
+            Real D[NS];
+            prs::diffusion_cell<Real, NS>(y, x, ysum, T, p, a.N, s_tab, a.corr, a.cT, a.cP, D);
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
                 if (k >= a.N) break;
-                Real d;
-                if (acc[k] > Real(0)) {
-                    d = others[k] * iys * scale / acc[k];
-                } else {   // alone in the cell: self-diffusion
-                    const int q = k * NS + k;
-                    d = scale / (omega_d<Real>(T * ie[q], TmB * epsB[q]) * ic[q]);
-                }
-                a.Dk[(int64_t)k * a.ldo + i] = d;
+                a.Dk[(int64_t)k * a.ldo + i] = D[k];
             }
         }
     }
@@ -260,7 +179,7 @@ pr_status species_tables_init(pr_ctx *c, const pr_species_table *tbl)
             const double Mkj = 2.0 / (1.0 / tbl->W[k] + 1.0 / tbl->W[j]);
             const double ckj = 0.0266 / (std::sqrt(Mkj) * sig * sig);
             ie[k * NS + j] = 1.0 / eps;
-            epsB[k * NS + j] = std::pow(eps, kNB);
+            epsB[k * NS + j] = std::pow(eps, prs::kNB);
             ic[k * NS + j] = 1.0 / ckj;
         }
     std::vector<float> t32(t.size());

@@ -30,6 +30,7 @@
 #include "pr_device.cuh"
 #include "pr_internal.h"
 #include "pr_kernels.cuh"
+#include "pr_species.cuh"
 #include "surrogate_internal.h"
 
 using namespace mlp;
@@ -37,7 +38,9 @@ using prk::SpeciesRec;
 
 namespace {
 
-constexpr int NIN = 13, NOUT = 6;
+constexpr int NIN = 13;
+constexpr int NOUT6 = 6;       // outputs of the property models (forward, inverse, Bilger)
+constexpr int NOUT_MAX = 16;   // output rows of the padded last layer: up to 16 outputs
 constexpr int KIN = 64;      // padded input width (one 64-wide k-block)
 // Each standardised input enters the first layer as two BF16 numbers, its
 // rounding hi = bf16(v) in column k and the remainder lo = bf16(v - hi) in
@@ -50,7 +53,14 @@ constexpr int kLoOff = 16;
 static_assert(NIN <= 16 && kLoOff >= 16 && kLoOff + 16 <= KIN, "hi and lo input blocks must fit the padded K");
 constexpr int NOP = 16;      // padded output width
 constexpr int MOP = 128;     // padded output rows of the last layer's weight gradient
-constexpr int NSTAT = NIN + NOUT;
+constexpr int NSTAT = NIN + NOUT_MAX;
+
+// Normalisation vector (SG_NORM_FLOATS = 84): in_mean[13] in_std[13]
+// out_mean[0..5] out_std[0..5] hull_lo[13] hull_hi[13], then out_mean[6..15]
+// and out_std[6..15] of the per-species outputs.
+__host__ __device__ constexpr int out_mean_idx(int j) { return j < NOUT6 ? 2 * NIN + j : 64 + (j - NOUT6); }
+__host__ __device__ constexpr int out_std_idx(int j) { return j < NOUT6 ? 2 * NIN + NOUT6 + j : 74 + (j - NOUT6); }
+static_assert(SG_NORM_FLOATS == 84, "normalisation layout");
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
@@ -166,21 +176,32 @@ __device__ __forceinline__ float h_ideal(float T, const float (&Y)[9], const voi
 // Outputs learned as logarithms (bit j: output j).
 constexpr int kLogMaskForward = 0x39;   // rho, cp, mu, lambda
 constexpr int kLogMaskInverse = 0x3F;   // all six
+constexpr int kLogMaskDk = 0x1FF;       // the nine diffusion coefficients
+
+__host__ __device__ inline int log_mask_of(int mode, int outputs)
+{
+    if (outputs == SG_OUT_DK) return kLogMaskDk;
+    if (outputs == SG_OUT_HK) return 0;
+    return (mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
+}
 
 // Targets from raw properties and inputs x = [T, p, Y_1..Y_9]:
 //   forward model, y = [rho, Z, h, cp, mu, lambda]:
 //     [log rho, Z, h - h_ig(T, Y), log cp, log mu, log lambda];
-//   inverse and Bilger models, y = [T, rho, psi, mu, alpha, cp]: the six logarithms.
+//   inverse and Bilger models, y = [T, rho, psi, mu, alpha, cp]: the six logarithms;
+//   per-species outputs (inverse or Bilger inputs), y = D_k [9]: their logarithms,
+//   or y = h_k / (R T) [9] as they are.
 __device__ __forceinline__ void targets(const float *x, int64_t ldx, const float *y, int64_t ldy, int64_t i,
-                                        const void *sp32, int mode, float (&q)[NOUT])
+                                        const SgDev &d, float (&q)[NOUT_MAX])
 {
-    const int lm = (mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
+    const int lm = log_mask_of(d.mode, d.outputs);
 #pragma unroll
-    for (int j = 0; j < NOUT; ++j) {
-        const float v = __ldg(y + (int64_t)j * ldy + i);
+    for (int j = 0; j < NOUT_MAX; ++j) {
+        const float v = (j < d.nout) ? __ldg(y + (int64_t)j * ldy + i) : 0.f;
         q[j] = ((lm >> j) & 1) ? logf(v) : v;
     }
-    if (mode != SG_MODE_FORWARD) return;
+    const void *sp32 = d.sp32;
+    if (d.mode != SG_MODE_FORWARD) return;
     float Yk[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Yk[k] = __ldg(x + (int64_t)(2 + k) * ldx + i);
@@ -237,12 +258,12 @@ __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, cons
 #pragma unroll
     for (int k = 0; k < NSTAT; ++k) { s[k] = 0; s2[k] = 0; mn[k] = 1e300; mx[k] = -1e300; }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float f[NIN], q[NOUT];
+        float f[NIN], q[NOUT_MAX];
         features(x, ldx, i, d, f);
-        targets(x, ldx, y, ldy, i, d.sp32, d.mode, q);
+        targets(x, ldx, y, ldy, i, d, q);
         bool fin = true;
 #pragma unroll
-        for (int k = 0; k < NSTAT; ++k) fin = fin && isfinite((k < NIN) ? f[k] : q[k - NIN]);
+        for (int k = 0; k < NSTAT; ++k) fin = fin && (k >= NIN + d.nout || isfinite((k < NIN) ? f[k] : q[k - NIN]));
         if (!fin) continue;   // rows with a non-finite feature or target are left out
         cnt += 1;
 #pragma unroll
@@ -285,8 +306,7 @@ __global__ void norm_partial_kernel(int64_t n, const float *x, int64_t ldx, cons
 }
 
 // Mean, standard deviation and the training hull (min/max widened by 1 % of
-// the range) from the block partials.  norm layout: in_mean[11] in_std[11]
-// out_mean[6] out_std[6] hull_lo[11] hull_hi[11].
+// the range) from the block partials, in the normalisation layout above.
 __global__ void norm_final_kernel(int nblocks, const double *part, float *norm)
 {
     const int k = threadIdx.x;
@@ -306,11 +326,22 @@ __global__ void norm_final_kernel(int nblocks, const double *part, float *norm)
         norm[k] = (float)mean;
         norm[NIN + k] = (float)sd;
         const double w = 0.01 * (e - c);
-        norm[2 * NIN + 2 * NOUT + k] = (float)(c - w);
-        norm[3 * NIN + 2 * NOUT + k] = (float)(e + w);
+        norm[2 * NIN + 2 * NOUT6 + k] = (float)(c - w);
+        norm[3 * NIN + 2 * NOUT6 + k] = (float)(e + w);
     } else {
-        norm[2 * NIN + (k - NIN)] = (float)mean;
-        norm[2 * NIN + NOUT + (k - NIN)] = (float)sd;
+        norm[out_mean_idx(k - NIN)] = (float)mean;
+        norm[out_std_idx(k - NIN)] = (float)sd;
+    }
+}
+
+// The output statistics gathered into one array, mean[16] then std[16], for
+// the epilogues and the training targets.
+__global__ void outstat_kernel(const float *norm, float *outstat)
+{
+    const int j = threadIdx.x;
+    if (j < NOUT_MAX) {
+        outstat[j] = norm[out_mean_idx(j)];
+        outstat[NOUT_MAX + j] = norm[out_std_idx(j)];
     }
 }
 
@@ -332,9 +363,9 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < B; r += (int64_t)gridDim.x * blockDim.x) {
         int64_t src = r;
         if (sample_seed != 0 || n_pool != B) src = (int64_t)(splitmix64(sample_seed ^ ((uint64_t)r * 0xD1B54A32D192ED03ull)) % (uint64_t)n_pool);
-        float f[NIN], q[NOUT];
+        float f[NIN], q[NOUT_MAX];
         features(x, ldx, src, d, f);
-        targets(x, ldx, y, ldy, src, d.sp32, d.mode, q);
+        targets(x, ldx, y, ldy, src, d, q);
         float v[16], lo[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = (k < NIN) ? (f[k] - nm[k]) / nm[NIN + k] : 0.f;
@@ -347,7 +378,8 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
             d.x0t[(int64_t)(kLoOff + k) * d.max_batch + r] = __float2bfloat16_rn(lo[k]);
         }
 #pragma unroll
-        for (int j = 0; j < NOUT; ++j) d.tgt[(int64_t)j * d.max_batch + r] = (q[j] - nm[2 * NIN + j]) / nm[2 * NIN + NOUT + j];
+        for (int j = 0; j < NOUT_MAX; ++j)
+            if (j < d.nout) d.tgt[(int64_t)j * d.max_batch + r] = (q[j] - d.outstat[j]) / d.outstat[NOUT_MAX + j];
     }
 }
 
@@ -357,7 +389,7 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
                                   int64_t ldY, uint8_t *flags, uint8_t *cflags, int32_t *list, unsigned int *count)
 {
     const float *nm = d.norm;
-    const float *lo = nm + 2 * NIN + 2 * NOUT, *hi = lo + NIN;
+    const float *lo = nm + 2 * NIN + 2 * NOUT6, *hi = lo + NIN;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < mc; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = r0 + r;
         float f[NIN];
@@ -528,6 +560,65 @@ __global__ void __launch_bounds__(128) fallback_inverse_kernel(const int32_t *li
         }
 #pragma unroll
         for (int q = 0; q < 6; ++q) out[(int64_t)q * ldo + i] = o[q];
+    }
+}
+
+// Per-species outputs of cells outside the hull: the FP64 inversion T(h, p, Y)
+// started from the network's own T estimate is not available here (the
+// outputs are per-species quantities), so it starts from 1000 K, then the
+// FP64 per-species values at that T: D_k (with the context's correction
+// table) or h_k / (R T).  NaN where the inversion fails.
+template <int NS, bool KIJ>
+__global__ void __launch_bounds__(128) fallback_species_kernel(const int32_t *list, const unsigned int *count,
+                                                               int64_t r0, const float *H, const float *p,
+                                                               const float *Y, int64_t ldY, float *out, int64_t ldo,
+                                                               const SpeciesRec<double> *sp, const double *kij,
+                                                               const double *dtab, const double *corr, int cT,
+                                                               int cP, int N, int outputs)
+{
+    __shared__ SpeciesRec<double> s_sp[NS];
+    __shared__ double s_kij[NS * NS];
+    __shared__ double s_tab[2 * NS + 3 * NS * NS];
+    {
+        const double *src = reinterpret_cast<const double *>(sp);
+        double *dst = reinterpret_cast<double *>(s_sp);
+        for (int j = threadIdx.x; j < (int)(NS * sizeof(SpeciesRec<double>) / 8); j += blockDim.x) dst[j] = src[j];
+        for (int j = threadIdx.x; j < NS * NS; j += blockDim.x) s_kij[j] = kij[j];
+        for (int j = threadIdx.x; j < 2 * NS + 3 * NS * NS; j += blockDim.x) s_tab[j] = dtab[j];
+    }
+    __syncthreads();
+    const unsigned int n = *count;
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int64_t i = r0 + list[t];
+        const double hv = (double)__ldg(H + i), pv = (double)__ldg(p + i);
+        prk::Comp<double, NS> c;
+        bool ok = prk::comp_fp64_of_fp32<NS>(c, Y, ldY, i, N, s_sp) && (pv > 0) && isfinite(hv) && isfinite(pv);
+        double o[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) o[k] = __longlong_as_double(0x7ff8000000000000ULL);
+        if (ok) {
+            double T, cpl;
+            int it;
+            const int st = prk::newton_solve<double, double, NS, KIJ>(c, hv, pv, 1000.0, s_sp, s_kij, 60, 1e-12, 1e-6,
+                                                                     T, it, cpl);
+            if (st == prk::kOk) {
+                if (outputs == SG_OUT_HK) {
+                    const double iRT = 1.0 / (prk::kR * T);
+#pragma unroll
+                    for (int k = 0; k < NS; ++k)
+                        if (k < N) o[k] = prs::h_over_RT<double>(T < s_sp[k].T_mid ? s_sp[k].h_lo : s_sp[k].h_hi, T, iRT);
+                } else {
+                    double y[NS], ysum = 0.0;
+#pragma unroll
+                    for (int k = 0; k < NS; ++k) {
+                        y[k] = (k < N) ? (double)__ldg(Y + (int64_t)k * ldY + i) : 0.0;
+                        ysum += y[k];
+                    }
+                    prs::diffusion_cell<double, NS>(y, c.x, ysum, T, pv, N, s_tab, corr, cT, cP, o);
+                }
+            }
+        }
+        for (int k = 0; k < N; ++k) out[(int64_t)k * ldo + i] = (float)o[k];
     }
 }
 
@@ -901,6 +992,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     sg_model *m = new (std::nothrow) sg_model();
     if (!m) { prgb::set_error("surrogate_create: host allocation failed"); return PR_ENOMEM; }
     m->ctx = ctx;
+    m->seed = seed;
     m->width = cfg->width;
     m->hidden = cfg->hidden_layers;
     m->max_batch = cfg->max_batch;
@@ -916,6 +1008,8 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     d.bilger = ctx->d_bilger32;
     d.bc_lambda = 1.0f;      // Box-Cox of Bilger's Z: linear until surrogate_set_boxcox
     d.bc_shift = 1e-3f;
+    d.nout = NOUT6;
+    d.outputs = SG_OUT_PROPS;
     const int W = m->width, L = m->hidden;
     const int64_t B = m->max_batch, C = m->chunk;
     cudaError_t e = cudaSuccess;
@@ -931,7 +1025,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     int64_t off = 0, flat = 0;
     for (int l = 0; l <= L; ++l) {
         const int in = (l == 0) ? NIN : W, in_pad = (l == 0) ? KIN : W;
-        const int out = (l == L) ? NOUT : W, out_pad = (l == L) ? NOP : W;
+        const int out = (l == L) ? NOUT6 : W, out_pad = (l == L) ? NOP : W;
         d.lay[l] = {off, off + (int64_t)out_pad * in_pad, in, in_pad, out, out_pad, flat};
         off += (int64_t)out_pad * in_pad + out_pad;
         flat += (int64_t)out * in + out;
@@ -948,10 +1042,11 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
             alloc((void **)&d.wt[l], (size_t)d.lay[l].in_pad * out_pad_k * 2);
         }
     }
-    alloc((void **)&d.norm, 64 * 4);
+    alloc((void **)&d.norm, SG_NORM_FLOATS * 4);
+    alloc((void **)&d.outstat, 2 * NOUT_MAX * 4);
     alloc((void **)&d.x0, B * KIN * 2);
     alloc((void **)&d.x0t, (int64_t)KIN * B * 2);
-    alloc((void **)&d.tgt, (int64_t)NOUT * B * 4);
+    alloc((void **)&d.tgt, (int64_t)NOUT_MAX * B * 4);
     for (int l = 0; l < L; ++l) {
         alloc((void **)&d.h[l], B * W * 2);
         alloc((void **)&d.ht[l], B * W * 2);
@@ -1009,11 +1104,15 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     alloc((void **)&m->d_flags, C);
     if (e == cudaSuccess) {
         // default normalisation: identity, unbounded hull
-        float nm[64];
-        for (int k = 0; k < 64; ++k) nm[k] = 0.f;
-        for (int k = 0; k < NIN; ++k) { nm[NIN + k] = 1.f; nm[2 * NIN + 2 * NOUT + k] = -3e38f; nm[3 * NIN + 2 * NOUT + k] = 3e38f; }
-        for (int j = 0; j < NOUT; ++j) nm[2 * NIN + NOUT + j] = 1.f;
+        float nm[SG_NORM_FLOATS];
+        for (int k = 0; k < SG_NORM_FLOATS; ++k) nm[k] = 0.f;
+        for (int k = 0; k < NIN; ++k) { nm[NIN + k] = 1.f; nm[2 * NIN + 2 * NOUT6 + k] = -3e38f; nm[3 * NIN + 2 * NOUT6 + k] = 3e38f; }
+        for (int j = 0; j < NOUT_MAX; ++j) nm[out_std_idx(j)] = 1.f;
         e = cudaMemcpy(d.norm, nm, sizeof(nm), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            outstat_kernel<<<1, 32>>>(d.norm, d.outstat);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess) {
         init_params_kernel<<<256, 256>>>(d, seed ? seed : 1);
@@ -1084,10 +1183,12 @@ pr_status surrogate_set_normalization(sg_model *m, const float *host_src)
     PR_CHECK_ARG(m && host_src, "surrogate_set_normalization: null argument");
     for (int k = 0; k < NIN; ++k)
         PR_CHECK_ARG(host_src[NIN + k] > 0, "surrogate_set_normalization: input std must be > 0");
-    for (int j = 0; j < NOUT; ++j)
-        PR_CHECK_ARG(host_src[2 * NIN + NOUT + j] > 0, "surrogate_set_normalization: output std must be > 0");
+    for (int j = 0; j < m->dev.nout; ++j)
+        PR_CHECK_ARG(host_src[out_std_idx(j)] > 0, "surrogate_set_normalization: output std must be > 0");
     PR_CUDA_TRY(cudaDeviceSynchronize());
     PR_CUDA_TRY(cudaMemcpy(m->dev.norm, host_src, SG_NORM_FLOATS * 4, cudaMemcpyHostToDevice));
+    outstat_kernel<<<1, 32>>>(m->dev.norm, m->dev.outstat);
+    PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
 }
 
@@ -1098,6 +1199,7 @@ pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, in
     cudaStream_t st = (cudaStream_t)stream;
     norm_partial_kernel<<<m->norm_blocks, 256, 0, st>>>(n, x, ldx, y, ldy, m->dev, m->d_normpart);
     norm_final_kernel<<<1, 32, 0, st>>>(m->norm_blocks, m->d_normpart, m->dev.norm);
+    outstat_kernel<<<1, 32, 0, st>>>(m->dev.norm, m->dev.outstat);
     PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
 }
@@ -1128,7 +1230,8 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         a.bias = d.master + d.lay[L].b_off;
         a.target = d.tgt; a.ldt = d.max_batch;
         a.l1 = m->loss_l1;
-        a.loss_scale = (m->loss_l1 ? 1.0f : 2.0f) / (float)(B * NOUT);
+        a.loss_scale = (m->loss_l1 ? 1.0f : 2.0f) / (float)(B * d.nout);
+        a.nout = d.nout;
         a.out = d.dzo; a.ldo = KIN; a.outT = d.dzot; a.ldoT = d.max_batch;
         a.colsum = d.colsum[L]; a.loss_part = d.loss_part;
         e = launch_gemm<16, kEpiOutLoss>(m->tm_h[L - 1], m->tm_w[L], a, mt, 1, 1, st);
@@ -1190,7 +1293,7 @@ static pr_status train_common(sg_model *m, int64_t batch, int64_t n_pool, const 
         adam_kernel<<<adam_blocks(d), 256, 0, st>>>(d, lr, 0.9f, 0.999f, 1e-8f, (int)m->step, 0, nullptr);
     }
     float *lo = loss_out ? loss_out : m->d_loss;
-    loss_final_kernel<<<1, 256, 0, st>>>(d.loss_part, nct, 1.0f / (float)(batch * NOUT), lo);
+    loss_final_kernel<<<1, 256, 0, st>>>(d.loss_part, nct, 1.0f / (float)(batch * d.nout), lo);
     PR_CUDA_TRY(cudaGetLastError());
     return PR_OK;
 }
@@ -1243,9 +1346,10 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             fa.n_t = W / kFusedBN; fa.ips = L * fa.n_t + 1;
             fa.total = (long long)(fa.R + (long long)L * fa.D) * fa.ips;
             fa.out6 = out + r0; fa.ld6 = ldo;
-            fa.out_mean = d.norm + 2 * NIN; fa.out_std = d.norm + 2 * NIN + NOUT;
+            fa.out_mean = d.outstat; fa.out_std = d.outstat + NOUT_MAX;
             fa.add_h = (d.mode != SG_MODE_FORWARD) ? nullptr : d.hig;
-            fa.log_mask = (d.mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
+            fa.log_mask = log_mask_of(d.mode, d.outputs);
+            fa.nout = d.nout;
             fa.done = m->d_done; fa.err = m->d_err;
             fa.wait_cycles = m->wait_cycles > 0 ? m->wait_cycles : 4000000000LL;
             fa.stall_test = m->stall_test;
@@ -1266,9 +1370,10 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.M = (int)mc; a.N = NOP; a.K = W; a.kb_per_split = W / 64;
             a.bias = d.master + d.lay[L].b_off;
             a.out6 = out + r0; a.ld6 = ldo;
-            a.out_mean = d.norm + 2 * NIN; a.out_std = d.norm + 2 * NIN + NOUT;
+            a.out_mean = d.outstat; a.out_std = d.outstat + NOUT_MAX;
             a.add_h = (d.mode != SG_MODE_FORWARD) ? nullptr : d.hig;
-            a.log_mask = (d.mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
+            a.log_mask = log_mask_of(d.mode, d.outputs);
+            a.nout = d.nout;
             PR_CUDA_TRY((launch_gemm<16, kEpiOutPhys>(m->tm_hi[(L - 1) & 1], m->tm_w[L], a, mt, 1, 1, st)));
         }
         if (d.mode == SG_MODE_FORWARD && m->conf_tol > 0.f) {
@@ -1279,7 +1384,18 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
         // FP64 Peng-Robinson for the cells outside the training hull (and the low-confidence ones)
         const int fb = ctx->num_sms * 4;
         const SpeciesRec<double> *sp64 = (const SpeciesRec<double> *)ctx->d_sp64;
-        if (d.mode != SG_MODE_FORWARD) {
+        if (d.outputs != SG_OUT_PROPS) {
+            if (ctx->has_kij)
+                fallback_species_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
+                                                                     ldo, sp64, ctx->d_kij64, ctx->d_dtab64,
+                                                                     ctx->d_corr64, ctx->corr_nT, ctx->corr_nP,
+                                                                     ctx->n_species, d.outputs);
+            else
+                fallback_species_kernel<9, false><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
+                                                                      ldo, sp64, ctx->d_kij64, ctx->d_dtab64,
+                                                                      ctx->d_corr64, ctx->corr_nT, ctx->corr_nP,
+                                                                      ctx->n_species, d.outputs);
+        } else if (d.mode != SG_MODE_FORWARD) {
             if (ctx->has_kij)
                 fallback_inverse_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
                                                                      ldo, sp64, ctx->d_pair64, ctx->d_kij64,
@@ -1324,6 +1440,26 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
     case SG_OPT_TEST_STALL:
         m->stall_test = value != 0;
         return PR_OK;
+    case SG_OPT_OUTPUTS: {
+        PR_CHECK_ARG(value == SG_OUT_PROPS || value == SG_OUT_DK || value == SG_OUT_HK,
+                     "surrogate_set_option: bad outputs %d", value);
+        PR_CHECK_ARG(value == SG_OUT_PROPS || m->dev.mode != SG_MODE_FORWARD,
+                     "surrogate_set_option: per-species outputs need the inverse or Bilger inputs (h, p, Y)");
+        SgDev &d = m->dev;
+        d.outputs = value;
+        d.nout = (value == SG_OUT_PROPS) ? NOUT6 : m->ctx->n_species;
+        // the last layer's output count changes the exported parameter count;
+        // start the weights afresh
+        LayerLayout &LL = d.lay[d.hidden];
+        d.n_flat = LL.flat_off + (int64_t)d.nout * LL.in + d.nout;
+        LL.out = d.nout;
+        PR_CUDA_TRY(cudaDeviceSynchronize());
+        init_params_kernel<<<256, 256>>>(d, m->seed ? m->seed : 1);
+        refresh_bf16_kernel<<<256, 256>>>(d);
+        PR_CUDA_TRY(cudaDeviceSynchronize());
+        m->step = 0;
+        return PR_OK;
+    }
     case SG_OPT_CONFIDENCE_PPM:
         PR_CHECK_ARG(value >= 0, "surrogate_set_option: confidence tolerance must be >= 0");
         m->conf_tol = 1e-6f * (float)value;
@@ -1337,6 +1473,8 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
                      "surrogate_set_option: bad mode %d", value);
         PR_CHECK_ARG(value != SG_MODE_BILGER || m->ctx->has_bilger,
                      "surrogate_set_option: SG_MODE_BILGER needs the context's element table (pr_set_bilger)");
+        PR_CHECK_ARG(value != SG_MODE_FORWARD || m->dev.outputs == SG_OUT_PROPS,
+                     "surrogate_set_option: the forward model has no per-species outputs");
         m->dev.mode = value;
         m->dev.bilger = m->ctx->d_bilger32;
         return PR_OK;
@@ -1384,10 +1522,11 @@ pr_status surrogate_save(const sg_model *m, const char *path)
     FILE *f = fopen(path, "wb");
     if (!f) { prgb::set_error("surrogate_save: cannot open %s", path); return PR_EINVAL; }
     const char magic[4] = {'P', 'R', 'S', 'G'};
-    // format 4: 13 inputs (with T_pc / T and log W); the enthalpy output is the
-    // departure from the ideal-gas enthalpy; the Box-Cox parameters of
-    // Bilger's Z follow the counts
-    const int32_t hdr[4] = {4, m->width, m->hidden, m->dev.mode};
+    // format 5: 13 inputs (with T_pc / T and log W); the enthalpy output is the
+    // departure from the ideal-gas enthalpy; the mode word carries the output
+    // set in its second byte; the Box-Cox parameters of Bilger's Z follow the
+    // counts; the normalisation has SG_NORM_FLOATS entries (64 before format 5)
+    const int32_t hdr[4] = {5, m->width, m->hidden, m->dev.mode | (m->dev.outputs << 8)};
     const int64_t step = m->step;
     const float bc[2] = {m->dev.bc_lambda, m->dev.bc_shift};
     bool ok = fwrite(magic, 1, 4, f) == 4 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&step, 8, 1, f) == 1 &&
@@ -1407,14 +1546,21 @@ pr_status surrogate_load(sg_model *m, const char *path)
     int64_t step = 0, n = 0;
     bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "PRSG", 4) == 0 && fread(hdr, 4, 4, f) == 4 &&
               fread(&step, 8, 1, f) == 1 && fread(&n, 8, 1, f) == 1;
-    ok = ok && (hdr[0] == 3 || hdr[0] == 4) && hdr[1] == m->width && hdr[2] == m->hidden && hdr[3] == m->dev.mode &&
+    const int32_t mode_word = m->dev.mode | (m->dev.outputs << 8);
+    ok = ok && hdr[0] >= 3 && hdr[0] <= 5 && hdr[1] == m->width && hdr[2] == m->hidden && hdr[3] == mode_word &&
          n == m->dev.n_master;
     float bc[2] = {m->dev.bc_lambda, m->dev.bc_shift};   // format 3 carries none
-    if (ok && hdr[0] == 4) ok = fread(bc, 4, 2, f) == 2;
+    if (ok && hdr[0] >= 4) ok = fread(bc, 4, 2, f) == 2;
+    const int norm_floats = (hdr[0] >= 5) ? SG_NORM_FLOATS : 64;
     std::vector<float> buf;
     if (ok) {
         buf.resize(3 * n + SG_NORM_FLOATS);
-        ok = fread(buf.data(), 4, buf.size(), f) == buf.size();
+        ok = fread(buf.data(), 4, 3 * n + norm_floats, f) == (size_t)(3 * n + norm_floats);
+        // older formats: the statistics of outputs 6..15 as the identity
+        for (int j = NOUT6; j < NOUT_MAX && norm_floats < SG_NORM_FLOATS; ++j) {
+            buf[3 * n + out_mean_idx(j)] = 0.f;
+            buf[3 * n + out_std_idx(j)] = 1.f;
+        }
     }
     fclose(f);
     if (!ok) { prgb::set_error("surrogate_load: %s is not a checkpoint of this model", path); return PR_EINVAL; }
@@ -1425,6 +1571,7 @@ pr_status surrogate_load(sg_model *m, const char *path)
     PR_CUDA_TRY(cudaMemcpy(m->dev.norm, buf.data() + 3 * n, SG_NORM_FLOATS * 4, cudaMemcpyHostToDevice));
     m->dev.bc_lambda = bc[0];
     m->dev.bc_shift = bc[1];
+    outstat_kernel<<<1, 32>>>(m->dev.norm, m->dev.outstat);
     refresh_bf16_kernel<<<256, 256>>>(m->dev);
     PR_CUDA_TRY(cudaDeviceSynchronize());
     m->step = step;

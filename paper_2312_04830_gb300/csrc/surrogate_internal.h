@@ -31,6 +31,9 @@ struct SgDev {
     __nv_bfloat16 *wb[SG_MAX_HIDDEN + 1];   // W [out_pad][in_pad]
     __nv_bfloat16 *wt[SG_MAX_HIDDEN + 1];   // W^T [in][K of the input-gradient GEMM]
     float *norm;                            // SG_NORM_FLOATS
+    float *outstat;                         // output mean[16] then std[16], gathered from norm
+    int nout;                               // outputs of the model: 6, or 9 per-species ones
+    int outputs;                            // SG_OUT_PROPS, SG_OUT_DK or SG_OUT_HK
     // training activations (batch-major X [B][.] and feature-major X^T [.][B])
     __nv_bfloat16 *x0, *x0t;
     float *tgt;                             // standardised targets [6][B]
@@ -87,6 +90,7 @@ __device__ __forceinline__ ParamRef decode_param(const SgDev &d, int64_t e)
 
 struct sg_model {
     pr_ctx *ctx;
+    uint64_t seed;                          // of the initial weights
     int width, hidden;
     int64_t max_batch, chunk;
     int64_t step;

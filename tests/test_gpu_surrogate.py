@@ -660,3 +660,134 @@ def test_low_confidence_cells_take_the_fallback(ctx, orc, species, cuda):
     with pytest.raises(binding.PrError):
         sg.set_confidence(-0.5)
     sg.close()
+
+
+# ------------------------------------------------ per-species output networks
+def out_stats(norm, nout):
+    """Output means and standard deviations from the 84-float normalisation
+    (outputs 0..5 at 26..37, outputs 6..15 appended at 64..83)."""
+    mean = np.array([norm[26 + j] if j < 6 else norm[64 + j - 6] for j in range(nout)])
+    std = np.array([norm[32 + j] if j < 6 else norm[74 + j - 6] for j in range(nout)])
+    return mean, std
+
+
+def make_pool_species(orc, species, n, seed, kind):
+    """Pool of a per-species network: x = [h, p, Y] of physical states, y = the
+    oracle's D_k [m^2/s] or h_k / (R T) at their T (float32)."""
+    T, p, Y = W.training_states(n, seed=seed)
+    o, st = orc.props_ext(species, T, p, Y)
+    hk, dk, sst = orc.species_props(species, T, p, Y)
+    ok = (st == 0) & (sst == 0) & np.all(np.isfinite(o), axis=0) & np.all(o[[0, 3, 4, 5, 6, 7]] > 0, axis=0)
+    x = np.vstack([o[2], p, Y])[:, ok].astype(np.float32)
+    y = (dk if kind == "dk" else hk)[:, ok].astype(np.float32)
+    return x, y, T[ok]
+
+
+@pytest.mark.parametrize("kind", ["dk", "hk"])
+def test_species_network_matches_oracle_forward(ctx, orc, species, cuda, kind):
+    """A network with the paper's per-species outputs (9 diffusion coefficients
+    as logarithms, or 9 standard-state enthalpies) through the fused kernel,
+    against the float64 forward pass with the same weights."""
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=1024, seed=51)
+    sg.set_mode("inverse")
+    sg.set_outputs(kind)
+    assert sg.num_params == 13 * 512 + 512 + 3 * (512 * 512 + 512) + 512 * 9 + 9
+    x, y, _ = make_pool_species(orc, species, 6000, 52, kind)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    n = 2500
+    out, fb = sg.infer(to_dev(x[0, :n], cuda), to_dev(x[1, :n], cuda), to_dev(x[2:, :n], cuda))
+    sg.sync_status()
+    out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy()
+    assert out.shape == (9, n) and fb.sum() == 0
+    norm = sg.get_normalization().astype(np.float64)
+    mean, std = out_stats(norm, 9)
+    params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 9])
+    s_in = (features_inverse(x[:, :n], species).T - norm[0:13]) / norm[13:26]
+    yhat, _ = omlp.forward(params, s_in, "tanh")
+    q = np.log(out) if kind == "dk" else out
+    err = np.abs((q.T - mean) / std - yhat)
+    print(kind, "standardised output error: median", np.median(err), "max", err.max())
+    assert np.median(err) < 0.01 and err.max() < 0.1
+    sg.close()
+
+
+def test_species_network_gradients_match_oracle(ctx, orc, species, cuda):
+    """Training of a 9-output network: loss and every gradient against the
+    float64 oracle MLP (relative MSE on the standardised log D_k)."""
+    from paper_2312_04830_gb300 import binding
+    width, layers, batch = 128, 2, 512
+    sg = binding.Surrogate(ctx, width=width, hidden_layers=layers, max_batch=batch, infer_chunk=1024, seed=53)
+    sg.set_mode("inverse")
+    sg.set_outputs("dk")
+    x, y, _ = make_pool_species(orc, species, batch + 200, 54, "dk")
+    x, y = np.ascontiguousarray(x[:, :batch]), np.ascontiguousarray(y[:, :batch])
+    xd, yd = to_dev(x, cuda), to_dev(y, cuda)
+    sg.fit_normalization(xd, yd)
+    loss, grad = sg.loss_grad(xd, yd, batch)
+    sg.sync_status()
+    norm = sg.get_normalization().astype(np.float64)
+    mean, std = out_stats(norm, 9)
+    params = unflatten(sg.get_params(), [13] + [width] * layers + [9])
+    s_in = (features_inverse(x, species).T - norm[0:13]) / norm[13:26]
+    s_out = (np.log(y.astype(np.float64)).T - mean) / std
+    yhat, cache = omlp.forward(params, s_in, "tanh")
+    assert float(loss.item()) == pytest.approx(omlp.loss(yhat, s_out), rel=2e-2)
+    grads = omlp.backward(params, cache, yhat, s_out, "tanh")
+    g_gpu = grad.cpu().numpy().astype(np.float64)
+    off = 0
+    for li, (gW, gb) in enumerate(grads):
+        for name, go in (("W", gW.ravel()), ("b", gb)):
+            gg = g_gpu[off:off + go.size]
+            off += go.size
+            rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
+            cos = float(gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go)))
+            assert rel < 3e-2 and cos > 0.999, (li, name, rel, cos)
+    assert off == g_gpu.size
+    sg.close()
+
+
+@pytest.mark.parametrize("kind", ["dk", "hk"])
+def test_species_network_fallback_and_checkpoint(ctx, orc, species, cuda, tmp_path, kind):
+    """Cells outside the hull take the FP64 inversion and the FP64 per-species
+    values at its T: the oracle's T(h, p, Y) and species outputs, rounded to
+    FP32; a format-5 checkpoint restores the model (same outputs)."""
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=512, seed=55)
+    sg.set_mode("inverse")
+    sg.set_outputs(kind)
+    x, y, _ = make_pool_species(orc, species, 4000, 56, kind)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    T, p, Y = W.uniform_cells(400, seed=57)
+    T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
+    p[:200] = 2e7                                  # outside the pool's 10 MPa +- 5 %: out of the hull
+    o, _ = orc.props_ext(species, T, p, Y)
+    x32 = np.vstack([o[2], p, Y]).astype(np.float32)
+    args = [to_dev(x32[0], cuda), to_dev(x32[1], cuda), to_dev(x32[2:], cuda)]
+    out, fb = sg.infer(*args)
+    sg.sync_status()
+    out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy().astype(bool)
+    assert np.all(fb[:200])
+    x64 = x32.astype(np.float64)
+    To, sto, _ = orc.T_from_h(species, x64[0, :200], x64[1, :200], x64[2:, :200], np.full(200, 1000.0))
+    hk, dk, sts = orc.species_props(species, To, x64[1, :200], x64[2:, :200])
+    ref = dk if kind == "dk" else hk
+    m = (sto == 0) & (sts == 0)
+    assert m.sum() > 150
+    scale = np.abs(ref[:, m]) if kind == "dk" else np.maximum(np.abs(ref[:, m]), 1.0)
+    e = np.abs(out[:, :200][:, m] - ref[:, m]) / scale
+    print(kind, "fallback max rel err", e.max())
+    assert e.max() < 1e-6
+    path = tmp_path / f"species_{kind}.ckpt"
+    sg.save(path)
+    sg2 = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=512, seed=99)
+    sg2.set_mode("inverse")
+    sg2.set_outputs(kind)
+    sg2.load(path)
+    out2, _ = sg2.infer(*args)
+    sg2.sync_status()
+    assert np.array_equal(out2.cpu().numpy(), out.astype(np.float32), equal_nan=True)
+    with pytest.raises(binding.PrError):
+        sg2.set_mode("forward")                   # no per-species outputs for the forward model
+    sg.close()
+    sg2.close()
