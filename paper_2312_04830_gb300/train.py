@@ -78,6 +78,47 @@ def label_pool_inverse(ctx, T, p, Y, device, chunk=1 << 23):
     return torch.cat(xs, dim=1).contiguous(), torch.cat(ys, dim=1).contiguous()
 
 
+def label_pool_species(ctx, T, p, Y, device, kind, chunk=1 << 23):
+    """Pool of a per-species network (the paper's diffusion and enthalpy
+    networks, Sec. 4.1): x = [h, p, Y] from pr_props_ext in FP64, y = the 9
+    D_k [m^2/s] (kind "dk") or h_k / (R T) ("hk") from pr_species_props at
+    the states' T, float32; the same physical-outcome filter as label_pool."""
+    import torch
+    xs, ys = [], []
+    for a in range(0, T.size, chunk):
+        b = min(T.size, a + chunk)
+        d = lambda v: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device=device)
+        Td, pd, Yd = d(T[a:b]), d(p[a:b]), d(Y[:, a:b])
+        o, st = ctx.props_ext(Td, pd, Yd, precision="fp64")
+        dil, _ = ctx.props(Td, torch.ones_like(pd), Yd, precision="fp64", outputs=("mu", "lambda"))
+        hk, dk, sst = ctx.species_props(Td, pd, Yd, precision="fp64")
+        keep = (st == 0) & (sst == 0) & torch.all(torch.isfinite(o), dim=0) & torch.all(o[[0, 3, 4, 5, 6, 7]] > 0, dim=0)
+        keep &= (o[4] >= DILUTE_FLOOR * dil[4]) & (o[5] >= DILUTE_FLOOR * dil[5])
+        xs.append(torch.cat([o[2][None], pd[None], Yd], dim=0)[:, keep].float())
+        ys.append((dk if kind == "dk" else hk)[:, keep].float())
+    return torch.cat(xs, dim=1).contiguous(), torch.cat(ys, dim=1).contiguous()
+
+
+def evaluate_field_species(sg, ctx, grid, device, kind):
+    """Errors of a per-species network on the flame-vortex field against the
+    FP64 per-species path at the field's T (relative RMS per species; h_k/(R T)
+    relative to max(|h_k/(R T)|, 1))."""
+    import torch
+    T, p, Y = W.flame_vortex_field(grid)
+    d64 = lambda v: torch.as_tensor(v, dtype=torch.float64, device=device)
+    T64, p64, Y64 = d64(T), d64(p), d64(Y)
+    o8, st = ctx.props_ext(T64, p64, Y64, precision="fp64")
+    hk, dk, sst = ctx.species_props(T64, p64, Y64, precision="fp64")
+    ref = dk if kind == "dk" else hk
+    out, fb = sg.infer(o8[2].float(), p64.float(), Y64.float())
+    ok = (st == 0) & (sst == 0)
+    scale = ref.abs() if kind == "dk" else ref.abs().clamp_min(1.0)
+    e = ((out.double() - ref) / scale)[:, ok]
+    return {"cells": int(ok.sum()), "fallback_fraction": float(fb.float().mean()),
+            "rel_rms": {nm: float(torch.sqrt(torch.mean(e[k] ** 2))) for k, nm in enumerate(W.SPECIES)},
+            "p99": {nm: float(torch.quantile(e[k].abs()[:1 << 24].float(), 0.99)) for k, nm in enumerate(W.SPECIES)}}
+
+
 def make_pool_inverse(ctx, n, seed, device):
     T, p, Y = W.training_states(n, seed=seed)
     return label_pool_inverse(ctx, T, p, Y, device)
@@ -228,6 +269,8 @@ def main():
     ap.add_argument("--model", choices=("forward", "inverse", "bilger"), default="forward",
                     help="T,p,Y -> properties; h,p,Y -> T and properties; or the same from h, p and Bilger's Z")
     ap.add_argument("--bc-shift", type=float, default=1e-3, help="Box-Cox shift of Bilger's Z")
+    ap.add_argument("--outputs", choices=("props", "dk", "hk"), default="props",
+                    help="inverse / Bilger models: the six properties, or the 9 D_k or h_k/(R T)")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     ctx = binding.PropertyContext(W.species_table())
@@ -236,6 +279,9 @@ def main():
     if a.model == "forward":
         x, y = make_pool(ctx, a.pool, a.seed, dev, a.data, a.a2)
         xh, yh = make_pool(ctx, a.heldout, a.seed + 1, dev)
+    elif a.outputs != "props":
+        x, y = label_pool_species(ctx, *pool_states(a.pool, a.seed, a.data, a.a2), dev, a.outputs)
+        xh, yh = None, None
     else:
         x, y = label_pool_inverse(ctx, *pool_states(a.pool, a.seed, a.data, a.a2), dev)
         xh, yh = label_pool_inverse(ctx, *pool_states(a.heldout, a.seed + 1, a.data, a.a2), dev)
@@ -244,6 +290,10 @@ def main():
     bc = None
     if a.model != "forward":
         sg.set_mode(a.model)
+    if a.outputs != "props":
+        if a.model == "forward":
+            raise SystemExit("per-species outputs need --model inverse or bilger")
+        sg.set_outputs(a.outputs)
     if a.model == "bilger":
         z = ctx.bilger_z(x[2:, :1 << 20].contiguous(), precision="fp32").double().cpu().numpy()
         bc = boxcox_lambda(z, a.bc_shift)
@@ -253,7 +303,7 @@ def main():
     steps = int(round(a.epochs * x.shape[1] / a.batch))
     losses, secs = train(sg, x, y, steps, a.batch, a.lr, seed=a.seed)
     sg.sync_status()
-    flops = 3 * 2 * (13 * a.width + (a.layers - 1) * a.width ** 2 + a.width * 6) * a.batch * steps
+    flops = 3 * 2 * (13 * a.width + (a.layers - 1) * a.width ** 2 + a.width * sg.n_out) * a.batch * steps
     rep = {"pool": int(x.shape[1]), "steps": steps, "batch": a.batch, "train_seconds": secs,
            "samples_per_s": steps * a.batch / secs, "train_tflops": flops / secs / 1e12,
            "data_seconds": t_data, "losses": losses, "loss": a.loss, "data": a.data, "model": a.model,
@@ -261,8 +311,13 @@ def main():
     if a.model == "forward":
         rep["heldout"] = evaluate(sg, xh, yh)
     if a.eval_field > 0:
-        rep["field"] = (evaluate_field(sg, ctx, a.eval_field, dev) if a.model == "forward"
-                        else evaluate_field_inverse(sg, ctx, a.eval_field, dev))
+        if a.outputs != "props":
+            rep["field"] = evaluate_field_species(sg, ctx, a.eval_field, dev, a.outputs)
+        elif a.model == "forward":
+            rep["field"] = evaluate_field(sg, ctx, a.eval_field, dev)
+        else:
+            rep["field"] = evaluate_field_inverse(sg, ctx, a.eval_field, dev)
+    rep["outputs"] = a.outputs
     if a.save:
         sg.save(a.save)
     print(json.dumps(rep))
