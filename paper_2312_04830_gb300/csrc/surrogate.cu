@@ -225,8 +225,9 @@ __global__ void init_params_kernel(SgDev d, uint64_t seed)
     }
 }
 
-// BF16 copies of the weights: W [out][in_pad] (forward B operand) and W^T
-// [in][out_pad] (input-gradient B operand).
+// BF16 copy of the weights, W [out][in_pad] (the forward B operand); the
+// transposed copies W^T [in][out_pad] (input-gradient B operands) are made from
+// it by transpose_w_kernel.
 __device__ __forceinline__ void write_bf16_copies(const SgDev &d, const ParamRef &r, float v)
 {
     if (r.bias) return;
@@ -236,7 +237,34 @@ __device__ __forceinline__ void write_bf16_copies(const SgDev &d, const ParamRef
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
     d.wb[r.layer][(int64_t)r.o * r.in_pad + r.i] = b;
     if (r.layer == 0 && r.valid) d.wb[0][(int64_t)r.o * r.in_pad + kLoOff + r.i] = b;   // weight of the input's lo part
-    if (r.layer > 0) d.wt[r.layer][(int64_t)r.i * r.out_pad_k + r.o] = b;
+}
+
+// W^T [in][out_pad_k] of layers 1..L from their BF16 W [out_pad][in_pad], by
+// 32 x 32 tiles through shared memory (both sides coalesced).  grid: (in / 32,
+// max out_pad / 32, L), block 32 x 8.
+__global__ void transpose_w_kernel(SgDev d)
+{
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int l = blockIdx.z + 1;
+    const LayerLayout &Ly = d.lay[l];
+    const int o0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+    if (o0 >= Ly.out_pad || i0 >= Ly.in_pad) return;
+    const int out_pad_k = (l == d.hidden) ? KIN : d.width;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int o = o0 + r;
+        tile[r][threadIdx.x] = (o < Ly.out_pad) ? d.wb[l][(int64_t)o * Ly.in_pad + i0 + threadIdx.x]
+                                                 : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int o = o0 + threadIdx.x;
+        if (o < Ly.out_pad) d.wt[l][(int64_t)(i0 + r) * out_pad_k + o] = tile[threadIdx.x][r];
+    }
+}
+
+void launch_transpose_w(const SgDev &d, cudaStream_t st)
+{
+    transpose_w_kernel<<<dim3(d.width / 32, d.width / 32, d.hidden), dim3(32, 8), 0, st>>>(d);
 }
 
 __global__ void refresh_bf16_kernel(SgDev d)
@@ -1117,6 +1145,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     if (e == cudaSuccess) {
         init_params_kernel<<<256, 256>>>(d, seed ? seed : 1);
         refresh_bf16_kernel<<<256, 256>>>(d);
+        launch_transpose_w(d, 0);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -1163,6 +1192,7 @@ pr_status surrogate_set_params(sg_model *m, const float *host_src, int64_t n)
     if (e == cudaSuccess) {
         copy_params_kernel<<<256, 256>>>(m->dev, tmp, 0);
         refresh_bf16_kernel<<<256, 256>>>(m->dev);
+        launch_transpose_w(m->dev, 0);
         e = cudaDeviceSynchronize();
     }
     cudaFree(tmp);
@@ -1291,6 +1321,7 @@ static pr_status train_common(sg_model *m, int64_t batch, int64_t n_pool, const 
         m->step += 1;
         bias_grad_kernel<<<(int)(((int64_t)(m->hidden + 1) * m->width * 32 + 255) / 256), 256, 0, st>>>(d, nct);
         adam_kernel<<<adam_blocks(d), 256, 0, st>>>(d, lr, 0.9f, 0.999f, 1e-8f, (int)m->step, 0, nullptr);
+        launch_transpose_w(d, st);
     }
     float *lo = loss_out ? loss_out : m->d_loss;
     loss_final_kernel<<<1, 256, 0, st>>>(d.loss_part, nct, 1.0f / (float)(batch * d.nout), lo);
@@ -1456,6 +1487,7 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
         PR_CUDA_TRY(cudaDeviceSynchronize());
         init_params_kernel<<<256, 256>>>(d, m->seed ? m->seed : 1);
         refresh_bf16_kernel<<<256, 256>>>(d);
+        launch_transpose_w(d, 0);
         PR_CUDA_TRY(cudaDeviceSynchronize());
         m->step = 0;
         return PR_OK;
@@ -1573,6 +1605,7 @@ pr_status surrogate_load(sg_model *m, const char *path)
     m->dev.bc_shift = bc[1];
     outstat_kernel<<<1, 32>>>(m->dev.norm, m->dev.outstat);
     refresh_bf16_kernel<<<256, 256>>>(m->dev);
+    launch_transpose_w(m->dev, 0);
     PR_CUDA_TRY(cudaDeviceSynchronize());
     m->step = step;
     return PR_OK;
