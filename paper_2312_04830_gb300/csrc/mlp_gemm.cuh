@@ -136,6 +136,21 @@ __device__ __forceinline__ float2 gelu2(float2 a, float2 b)
     return __ffma2_rn(hz, t, hz);
 }
 
+// gelu_and_grad of z = a + b on two lanes at once (packed FP32): the same
+// operations in the same order as the scalar form, so the same bits.
+__device__ __forceinline__ void gelu_and_grad2(float2 a, float2 b, float2 &g, float2 &dg)
+{
+    const float2 z = __fadd2_rn(a, b);
+    const float2 z2 = __fmul2_rn(z, z);
+    const float2 u = __fmul2_rn(z, __ffma2_rn(make_float2(kGeluKC, kGeluKC), z2, make_float2(kGeluK, kGeluK)));
+    const float2 t = make_float2(tanh_approx(u.x), tanh_approx(u.y));
+    const float2 hz = __fmul2_rn(make_float2(0.5f, 0.5f), z);
+    g = __ffma2_rn(hz, t, hz);
+    const float2 dk = __ffma2_rn(make_float2(3.0f * kGeluKC, 3.0f * kGeluKC), z2, make_float2(kGeluK, kGeluK));
+    const float2 omt = __ffma2_rn(make_float2(-t.x, -t.y), t, make_float2(1.0f, 1.0f));
+    dg = __ffma2_rn(__fmul2_rn(hz, omt), dk, __ffma2_rn(make_float2(0.5f, 0.5f), t, make_float2(0.5f, 0.5f)));
+}
+
 __device__ __forceinline__ void gelu_and_grad(float z, float &g, float &dg)
 {
     const float z2 = z * z;
@@ -249,6 +264,14 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
     if (active && !fail) {
         uint32_t rnext[16];
         umma::tmem_ld16(taddr, rnext);
+        // kEpiDx: GeLU'(z) of this lane's row, one chunk ahead (a global load
+        // whose latency would otherwise stall every chunk)
+        uint4 gq0 = make_uint4(0, 0, 0, 0), gq1 = gq0;
+        const __nv_bfloat16 *grow = (EPI == kEpiDx && mval) ? a.gd + (int64_t)m * a.ldg + n0 + hcol : nullptr;
+        if (grow) {
+            gq0 = reinterpret_cast<const uint4 *>(grow)[0];
+            gq1 = reinterpret_cast<const uint4 *>(grow)[1];
+        }
 #pragma unroll 1
         for (int c = 0; c < HALF / 16; ++c) {
             umma::tmem_ld_wait(rnext);
@@ -258,6 +281,11 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
             // next chunk's load is in flight while this one is processed
             if (c + 1 < HALF / 16) umma::tmem_ld16(taddr + (c + 1) * 16, rnext);
             const int nb = n0 + hcol + c * 16;
+            uint4 gc0 = gq0, gc1 = gq1;
+            if (grow && c + 1 < HALF / 16) {
+                gq0 = reinterpret_cast<const uint4 *>(grow + (c + 1) * 16)[0];
+                gq1 = reinterpret_cast<const uint4 *>(grow + (c + 1) * 16)[1];
+            }
             if (tma && (c & 3) == 0) {
                 if (lane == 0) umma::bulk_wait_read0();
                 __syncwarp();
@@ -272,7 +300,15 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                 }
             }
             float g[16];
-            if (EPI == kEpiDx && mval) load_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, g);
+            if (EPI == kEpiDx) {
+                const uint32_t w[8] = {gc0.x, gc0.y, gc0.z, gc0.w, gc1.x, gc1.y, gc1.z, gc1.w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[k]));
+                    g[2 * k] = f.x;
+                    g[2 * k + 1] = f.y;
+                }
+            }
             float v[16];
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) v[jj] = __uint_as_float(rr[jj]);
@@ -280,7 +316,12 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                 float gg[16];
                 if (a.gd) {
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) gelu_and_grad(v[jj] + bias[jj], v[jj], gg[jj]);
+                    for (int jj = 0; jj < 16; jj += 2) {
+                        float2 g2, d2;
+                        gelu_and_grad2(make_float2(v[jj], v[jj + 1]), make_float2(bias[jj], bias[jj + 1]), g2, d2);
+                        v[jj] = g2.x; v[jj + 1] = g2.y;
+                        gg[jj] = d2.x; gg[jj + 1] = d2.y;
+                    }
                 } else {
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) v[jj] = gelu_f(v[jj] + bias[jj]);
