@@ -265,8 +265,8 @@ pr_status surrogate_set_normalization(sg_model *m, const float *host_src);
 
 /* Fit the normalisation and the training hull (per-input [min, max] widened
  * by 1 % of the range) to a pool of n states.  x: DEVICE [11][ldx] raw inputs
- * (T, p, Y_1..Y_9); y: DEVICE [6][ldy] raw properties (rho, Z, h, cp, mu,
- * lambda).  Rows whose features or log-targets are not finite (e.g. a
+ * (T, p, Y_1..Y_9); y: DEVICE [n_out][ldy] raw targets (rho, Z, h, cp, mu,
+ * lambda for the property networks; see SG_OPT_MODE and SG_OPT_OUTPUTS).  Rows whose features or log-targets are not finite (e.g. a
  * non-positive property) are left out.  Asynchronous on `stream`. */
 pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, int64_t ldx, const float *y,
                                       int64_t ldy, void *stream);
@@ -274,7 +274,7 @@ pr_status surrogate_fit_normalization(sg_model *m, int64_t n, const float *x, in
 /* One training step (Sec. 4.3, with the squared error on the standardised
  * log / scaled targets, i.e. a relative-MSE loss, and Adam with beta =
  * (0.9, 0.999), eps = 1e-8): batch rows (a multiple of 128, <= max_batch)
- * are drawn from the pool x [11][ldx], y [6][ldy] (DEVICE, n_pool rows):
+ * are drawn from the pool x [11][ldx], y [n_out][ldy] (DEVICE, n_pool rows):
  * rows 0..batch-1 in order when sample_seed == 0 and n_pool == batch, else
  * uniformly with replacement by a counter-based hash of (sample_seed, row).
  * Outputs whose target is not finite contribute neither loss nor gradient.
@@ -288,8 +288,9 @@ pr_status surrogate_train_step(sg_model *m, int64_t batch, int64_t n_pool, const
 pr_status surrogate_loss_grad(sg_model *m, int64_t batch, const float *x, int64_t ldx, const float *y, int64_t ldy,
                               float *loss_out, float *grad_out, void *stream);
 
-/* Inference (FP32 I/O): T, p [n], Y [9][ldY] DEVICE inputs; out [6][ldo]
- * DEVICE outputs rho, Z, h, cp, mu, lambda.  Cells with any input outside
+/* Inference (FP32 I/O): T, p [n], Y [9][ldY] DEVICE inputs; out [n_out][ldo]
+ * DEVICE outputs (rho, Z, h, cp, mu, lambda for the forward property network;
+ * n_out = 6, or 9 with SG_OPT_OUTPUTS = SG_OUT_DK or SG_OUT_HK).  Cells with any input outside
  * the training hull are evaluated by the FP64 Peng-Robinson path instead and
  * flagged in used_fallback [n] (DEVICE uint8, NULL allowed). */
 pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p, const float *Y, int64_t ldY,
@@ -310,7 +311,7 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  *           cp] (pr_props_ext's units; alpha = lambda / cp);
  *   inputs: [h* - h_f(Y), p, Y_1..Y_9, log T_pc, log W] with h_f(Y) = sum_k
  *           Y_k h_k(298.15 K) / W_k (formation enthalpies removed);
- *   surrogate_infer: the T argument holds h*, and out [6][ldo] receives
+ *   surrogate_infer: the T argument holds h*, and out [n_out][ldo] receives
  *           [T, rho, psi, mu, alpha, cp]; cells outside the training hull get
  *           the FP64 inversion started from the network's T, then
  *           pr_props_ext's values at that T (NaN where the inversion fails). */
