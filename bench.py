@@ -51,7 +51,7 @@ FP64_FLOPS_PER_CELL = {"props_fp64": 1582.7, "newton_fp64": 1363.5,
 TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 107.8,
                           # fused inference kernel, DRAM bytes per row of a chunk launch
                           # (profiles/fused_mlp_infer_flame_vortex_128.md)
-                          "surrogate_bf16": 260.9, "surrogate_inverse_bf16": 531.7}
+                          "surrogate_bf16": 353.9, "surrogate_inverse_bf16": 446.4}
 # surrogate: 2 x (13*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)

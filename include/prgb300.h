@@ -299,8 +299,12 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
 /* Model options.  SG_OPT_FUSED_INFER (default 1 when available): run all
  * layers of an inference chunk in one persistent cooperative launch whose
  * activations stay in L2-sized rings (widths that are multiples of 256, up
- * to 1024, hidden_layers x width <= 4560); 0 runs one GEMM launch per layer.  Both give identical outputs.
- * PR_EINVAL for an unknown option or a value the model cannot take. */
+ * to 1024, hidden_layers x width <= 4528).  1: 128 x 256 tiles, one CTA
+ * each; 2: 256 x 256 tiles on CTA pairs (clusters of two, tcgen05 pair MMA,
+ * each CTA holding half of every weight tile), falling back to 1 when the
+ * device refuses that launch; 0: one GEMM launch per layer.  All give
+ * identical outputs.  PR_EINVAL for an unknown option or a value the model
+ * cannot take. */
 #define SG_OPT_FUSED_INFER 1
 /* SG_OPT_MODE: SG_MODE_FORWARD (default) or SG_MODE_INVERSE, the paper's own
  * arrangement (Sec. 4.1: the networks take enthalpy, pressure and composition
@@ -366,6 +370,11 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * training. */
 #define SG_MODE_BILGER 2
 pr_status surrogate_set_option(sg_model *m, int option, int value);
+
+/* Current value of an option (host int *value).  For SG_OPT_FUSED_INFER it
+ * is the kernel the next inference runs: 0 per-layer launches, 1 single
+ * CTAs, 2 CTA pairs.  PR_EINVAL for an unknown option or a null pointer. */
+pr_status surrogate_get_option(const sg_model *m, int option, int *value);
 
 /* Box-Cox parameters of Bilger's mixture fraction in SG_MODE_BILGER (the
  * paper applies the transform to the mixture fraction, Sec. 4.2): lambda in

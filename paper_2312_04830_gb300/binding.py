@@ -321,6 +321,8 @@ def _sg_lib():
         L.surrogate_infer.restype = i32
         L.surrogate_set_option.argtypes = [vp, i32, i32]
         L.surrogate_set_option.restype = i32
+        L.surrogate_get_option.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int)]
+        L.surrogate_get_option.restype = i32
         L.surrogate_set_boxcox.argtypes = [vp, ctypes.c_double, ctypes.c_double]
         L.surrogate_set_boxcox.restype = i32
         L.surrogate_sync_status.argtypes = [vp]
@@ -362,10 +364,26 @@ class Surrogate:
         """Box-Cox parameters of Bilger's mixture fraction (bilger mode)."""
         check(_sg_lib().surrogate_set_boxcox(self.handle, float(lam), float(shift)), "surrogate_set_boxcox")
 
-    def set_fused_infer(self, on: bool):
+    def set_fused_infer(self, on):
         """All layers of an inference chunk in one persistent launch (True,
-        the default where the width allows it) or one launch per layer."""
-        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_FUSED_INFER, int(bool(on))), "surrogate_set_option")
+        the default where the width allows it: 128 x 256 tiles, one CTA
+        each), 'pair' for the same with 256 x 256 tiles on CTA pairs (where
+        the device takes their launch), or one launch per layer (False)."""
+        v = 2 if on == "pair" else int(bool(on))
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_FUSED_INFER, v), "surrogate_set_option")
+
+    def get_option(self, option: int) -> int:
+        """Current value of a model option (SG_OPT_*); for SG_OPT_FUSED_INFER
+        the kernel the next inference runs: 0 per layer, 1 single CTAs, 2
+        CTA pairs."""
+        v = ctypes.c_int(0)
+        check(_sg_lib().surrogate_get_option(self.handle, int(option), ctypes.byref(v)), "surrogate_get_option")
+        return v.value
+
+    @property
+    def fused_kind(self) -> str:
+        """'pair', 'single' or 'per-layer': the inference kernel in use."""
+        return {0: "per-layer", 1: "single", 2: "pair"}[self.get_option(SG_OPT_FUSED_INFER)]
 
     def set_loss(self, kind: str):
         """Training loss: 'mse' (relative MSE on the standardised targets, the

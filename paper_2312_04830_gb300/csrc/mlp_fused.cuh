@@ -22,12 +22,15 @@
 // Dependencies, through per-(row block, layer) arrival counters in global
 // memory: each epilogue warp adds 1 when its part of an item is complete and
 // visible (hidden items: after its TMA stores have completed, released at gpu
-// scope; output items: once the accumulator has been read).  Before loading,
-// the producer of (r, l) waits until layer l - 1 of block r has all its
-// arrivals (its input) and, for a hidden layer, until layer l + 1 of block
-// r - RING has all of its arrivals (the readers of the ring row block it is
-// about to overwrite).  Both are items of earlier slots.  Every wait is
-// bounded and gives up early once any CTA has failed.
+// scope; output items: once the accumulator has been read).  Item (r, l) may
+// start once layer l - 1 of block r has all its arrivals (its input) and, for
+// a hidden layer, layer l + 1 of block r - RING has all of its arrivals (the
+// readers of the ring row block it is about to overwrite).  Both are items of
+// earlier slots.  A dependency warp walks the CTA's items ahead of the TMA
+// producer, takes these acquire round trips and the proxy fence, and
+// publishes how many items are ready in shared memory, so the producer never
+// stalls on a global-memory round trip.  Every wait is bounded and gives up
+// early once any CTA has failed.
 //
 // Progress.  The launch is cooperative (all CTAs resident) and every item
 // waits only on strictly earlier items.  An epilogue warp releases a hidden
@@ -45,7 +48,8 @@ constexpr int kFusedMaxLayers = 9;   // up to 8 hidden layers + the output layer
 constexpr int kFusedBN = 256;        // N-tile of the hidden layers
 constexpr int kFusedOutBN = 16;      // padded output width
 constexpr int kFusedEpiWarps = 16;   // four per TMEM lane quarter, 64 columns each
-constexpr int kFusedThreads = 64 + 32 * kFusedEpiWarps;
+constexpr int kFusedDepWarp = 2 + kFusedEpiWarps;   // after the producer, the MMA issuer and the epilogue
+constexpr int kFusedThreads = 64 + 32 * kFusedEpiWarps + 32;
 constexpr int kFusedCols = kFusedBN * 4 / kFusedEpiWarps;   // columns of a hidden tile per epilogue warp
 
 struct FusedArgs {
@@ -75,13 +79,18 @@ struct FusedArgs {
     int stall_test;                       // test hook: layer 1 of row block 0 waits for one arrival too many
 };
 
+// Shared-memory plan.  Single CTAs: stages of a 128 x 64 input tile and a
+// 256 x 64 weight tile.  CTA pairs: each CTA's stage holds its 128 input rows
+// and half (128 rows) of the weight tile, the pair's MMA reading both CTAs'
+// stages; a stage is two thirds the size, so four fit.
+template <bool PAIR>
 struct FusedCfg {
-    static constexpr int A_BYTES = BM * BK * 2;           // 16 KB
-    static constexpr int B_BYTES = kFusedBN * BK * 2;     // 32 KB
+    static constexpr int A_BYTES = BM * BK * 2;                          // 16 KB
+    static constexpr int B_BYTES = (PAIR ? kFusedBN / 2 : kFusedBN) * BK * 2;   // 16 or 32 KB
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int S = 3;
+    static constexpr int S = PAIR ? 4 : 3;
     static constexpr int STG_BYTES = kFusedEpiWarps * 4096;   // one 32 x 64 BF16 box per epilogue warp
-    static constexpr int BAR_BYTES = 128;
+    static constexpr int BAR_BYTES = 256;   // 2 S + 4 mbarriers, the TMEM address, the ready count
     static constexpr uint32_t TMEM_COLS = 2 * kFusedBN;   // two accumulator buffers
     static constexpr int kMaxSmem = 232448;               // 227 KB opt-in per CTA
     static int smem_bytes(int L, int W) { return 1024 + S * STAGE + STG_BYTES + BAR_BYTES + (L * W + 16) * 4; }
@@ -147,6 +156,22 @@ __device__ __forceinline__ bool wait_count(const uint32_t *p, uint32_t target, c
     }
 }
 
+// Wait until the dependency warp has cleared `n` items (false after
+// ~max_cycles, or at once when it reported a failed wait).
+__device__ __forceinline__ bool wait_ready(const uint32_t *dep_ready, uint32_t n, long long max_cycles)
+{
+    uint32_t v = umma::ld_acquire_cta_shared(dep_ready);
+    if (v >= n) return v != ~0u;
+    const long long t0 = clock64();
+    while (true) {
+        v = umma::ld_acquire_cta_shared(dep_ready);
+        if (v >= n) return v != ~0u;
+        const long long dt = clock64() - t0;
+        if (dt > max_cycles) return false;
+        if (dt > 20000) __nanosleep(32);
+    }
+}
+
 // One 16-column chunk of a hidden item's epilogue for this lane's row: GeLU of
 // accumulator + bias, BF16, into the warp's staging box (chunk c % 4 of it;
 // the box must be free again at c % 4 == 0).
@@ -173,9 +198,11 @@ __device__ __forceinline__ void hidden_chunk(const uint32_t (&r)[16], const floa
     stage_row16_bf16(stg, lane, c & 3, v);
 }
 
+template <bool PAIR>
 __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __grid_constant__ FusedArgs a)
 {
-    using C = FusedCfg;
+    using C = FusedCfg<PAIR>;
+    constexpr int CT = PAIR ? 2 : 1;   // CTAs per unit of 128 CT rows
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *stg_base = smem + C::S * C::STAGE;
@@ -184,10 +211,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
     uint64_t *acc_full = empty + C::S;     // [2]
     uint64_t *acc_empty = acc_full + 2;    // [2]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    uint32_t *dep_ready = tmem_slot + 1;   // items whose dependencies hold; ~0u after a failed wait
     float *sbias = reinterpret_cast<float *>(stg_base + C::STG_BYTES + C::BAR_BYTES);   // [L W + 16]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = a.L, W = a.W;
+    const uint32_t rank = PAIR ? umma::cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
+    const long long g0 = PAIR ? (blockIdx.x >> 1) : blockIdx.x;   // this CTA's (pair's) first item
+    const long long gs = PAIR ? (gridDim.x >> 1) : gridDim.x;     // item stride
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::S; ++s) {
@@ -196,8 +228,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
         }
         for (int b = 0; b < 2; ++b) {
             umma::mbar_init(&acc_full[b], 1);
-            umma::mbar_init(&acc_empty[b], kFusedEpiWarps);
+            umma::mbar_init(&acc_empty[b], CT * kFusedEpiWarps);
         }
+        *tmem_slot = 0u;
+        *dep_ready = 0u;
         umma::fence_mbar_init();
         umma::tma_prefetch_desc(&a.tm_x);
     }
@@ -207,12 +241,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
         const int n = (e < L * W) ? e - l * W : e - L * W;
         sbias[e] = __ldg(a.bias[l] + n);
     }
+    __syncthreads();
     if (warp == 1) {
-        umma::tmem_alloc(tmem_slot, C::TMEM_COLS);
-        umma::tmem_relinquish();
+        if constexpr (PAIR) {
+            umma::tmem_alloc_pair(tmem_slot, C::TMEM_COLS);
+            umma::tmem_relinquish_pair();
+        } else {
+            umma::tmem_alloc(tmem_slot, C::TMEM_COLS);
+            umma::tmem_relinquish();
+        }
     }
     umma::tc_fence_before();
     __syncthreads();
+    // the peer signals this CTA's barriers: they must be initialised before
+    // either CTA of the pair issues a load
+    if constexpr (PAIR) umma::cluster_sync();
     umma::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     bool fail = false;
@@ -223,24 +266,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
     if (warp == 0) {
         // ------------------------------------------------------- TMA producer
         if (lane == 0) {
-            uint32_t it = 0;
-            for (long long i = blockIdx.x; i < a.total && !fail; i += gridDim.x) {
+            uint32_t it = 0, nready = 0;
+            for (long long i = g0; i < a.total && !fail; i += gs) {
                 const FusedItem t = fused_item(a, i);
                 if (!t.valid) continue;
-                bool ok = true;
-                if (t.l > 0)   // the input: layer l - 1 of this block
-                    ok = wait_count(done + (long long)t.r * stride_l + (t.l - 1),
-                                    fused_target(a, t.l - 1) + ((a.stall_test && t.r == 0 && t.l == 1) ? 1u : 0u),
-                                    a.err, a.wait_cycles);
-                if (ok && t.l < L && t.r >= a.ring)   // the ring row block's previous readers
-                    ok = wait_count(done + (long long)(t.r - a.ring) * stride_l + (t.l + 1), fused_target(a, t.l + 1),
-                                    a.err, a.wait_cycles);
-                if (!ok) { fail = true; break; }
-                umma::fence_proxy_async_global();   // the producers' stores, seen by this CTA's TMA loads
+                // the dependency warp has acquired this item's inputs (and
+                // fenced them for the TMA loads)
+                if (!wait_ready(dep_ready, ++nready, a.wait_cycles)) { fail = true; break; }
                 const bool out_l = t.l == L;
                 const int nkb = (t.l == 0) ? 1 : W / BK;
-                const uint32_t bytes = C::A_BYTES + (out_l ? kFusedOutBN : kFusedBN) * BK * 2;
-                const int arow = (t.l == 0) ? t.r * BM : (t.r % a.ring) * BM;
+                const int bn = (out_l ? kFusedOutBN : kFusedBN) / CT;   // weight rows this CTA loads
+                const uint32_t bytes = CT * (C::A_BYTES + bn * BK * 2);  // the pair's (or CTA's) stage
+                const int unit_blk = (t.l == 0) ? t.r : (t.r % a.ring);
+                const int arow = (unit_blk * CT + (int)rank) * BM;
+                const int brow = (out_l ? 0 : t.j * kFusedBN) + (int)rank * bn;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % C::S;
                     const uint32_t ph = (it / C::S) & 1u;
@@ -249,29 +288,53 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                         break;
                     }
                     uint8_t *st = smem + s * C::STAGE;
-                    umma::mbar_arrive_expect_tx(&full[s], bytes);
-                    if (t.l == 0)
-                        umma::tma_load_2d(st, &a.tm_x, &full[s], kb * BK, arow);
-                    else
-                        umma::tma_load_3d(st, &a.tm_ring_ld, &full[s], kb * BK, arow, t.l - 1);
-                    umma::tma_load_2d(st + C::A_BYTES, &a.tm_w[t.l], &full[s], kb * BK, t.j * kFusedBN);
+                    if (leader) umma::mbar_arrive_expect_tx(&full[s], bytes);
+                    if constexpr (PAIR) {
+                        // both CTAs' tiles complete on the leader's barrier
+                        const uint32_t fb = umma::mapa_shared(umma::smem_u32(&full[s]), 0u);
+                        if (t.l == 0)
+                            umma::tma_load_2d_pair(st, &a.tm_x, fb, kb * BK, arow);
+                        else
+                            umma::tma_load_3d_pair(st, &a.tm_ring_ld, fb, kb * BK, arow, t.l - 1);
+                        umma::tma_load_2d_pair(st + C::A_BYTES, &a.tm_w[t.l], fb, kb * BK, brow);
+                    } else {
+                        if (t.l == 0)
+                            umma::tma_load_2d(st, &a.tm_x, &full[s], kb * BK, arow);
+                        else
+                            umma::tma_load_3d(st, &a.tm_ring_ld, &full[s], kb * BK, arow, t.l - 1);
+                        umma::tma_load_2d(st + C::A_BYTES, &a.tm_w[t.l], &full[s], kb * BK, brow);
+                    }
                 }
             }
+            if constexpr (PAIR) {
+                // the leader's MMAs read this CTA's stages: every use must be
+                // released before the CTA may exit
+                if (!fail)
+                    for (uint32_t k = it; k < it + (uint32_t)C::S; ++k)
+                        if (k >= (uint32_t)C::S &&
+                            !umma::mbar_wait(&empty[k % C::S], ((k / C::S) & 1u) ^ 1u, 200000000LL)) {
+                            fail = true;
+                            break;
+                        }
+            }
             // no copy may still be landing in shared memory when the CTA exits
-            for (uint32_t k = (it > (uint32_t)C::S ? it - C::S : 0u); k < it; ++k)
-                if (!umma::mbar_wait(&full[k % C::S], (k / C::S) & 1u, 200000000LL)) fail = true;
+            // (the peer's copies complete on the leader's barriers)
+            if (leader)
+                for (uint32_t k = (it > (uint32_t)C::S ? it - C::S : 0u); k < it; ++k)
+                    if (!umma::mbar_wait(&full[k % C::S], (k / C::S) & 1u, 200000000LL)) fail = true;
             if (fail) atomicExch(a.err, 1);
         }
     } else if (warp == 1) {
         // -------------------------------------------------------- MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             uint32_t it = 0, jacc = 0;
-            for (long long i = blockIdx.x; i < a.total && !fail; i += gridDim.x) {
+            for (long long i = g0; i < a.total && !fail; i += gs) {
                 const FusedItem t = fused_item(a, i);
                 if (!t.valid) continue;
                 const bool out_l = t.l == L;
                 const int nkb = (t.l == 0) ? 1 : W / BK;
-                const uint32_t idesc = out_l ? umma::idesc_bf16_f32(BM, kFusedOutBN) : umma::idesc_bf16_f32(BM, kFusedBN);
+                const uint32_t idesc = out_l ? umma::idesc_bf16_f32(CT * BM, kFusedOutBN)
+                                             : umma::idesc_bf16_f32(CT * BM, kFusedBN);
                 const uint32_t buf = jacc & 1u;
                 if (jacc >= 2 && !umma::mbar_wait(&acc_empty[buf], ((jacc >> 1) & 1u) ^ 1u, a.wait_cycles)) {
                     fail = true;
@@ -287,16 +350,51 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                     const uint32_t sa = umma::smem_u32(smem + s * C::STAGE);
                     const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        umma::mma_bf16(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
-                                       umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
-                    umma::mma_commit(&empty[s]);
+                    for (int k = 0; k < BK / 16; ++k) {
+                        if constexpr (PAIR)
+                            umma::mma_bf16_pair(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
+                                                umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        else
+                            umma::mma_bf16(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
+                                           umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    }
+                    if constexpr (PAIR)
+                        umma::mma_commit_pair_mc(&empty[s], (uint16_t)0x3);
+                    else
+                        umma::mma_commit(&empty[s]);
                 }
                 if (fail) break;
-                umma::mma_commit(&acc_full[buf]);
+                if constexpr (PAIR)
+                    umma::mma_commit_pair_mc(&acc_full[buf], (uint16_t)0x3);
+                else
+                    umma::mma_commit(&acc_full[buf]);
                 ++jacc;
             }
             if (fail) atomicExch(a.err, 1);
+        }
+    } else if (warp == kFusedDepWarp) {
+        // ------------------------------------------------- dependency warp
+        if (lane == 0) {
+            uint32_t nready = 0;
+            for (long long i = g0; i < a.total; i += gs) {
+                const FusedItem t = fused_item(a, i);
+                if (!t.valid) continue;
+                bool ok = true;
+                if (t.l > 0)   // the input: layer l - 1 of this unit
+                    ok = wait_count(done + (long long)t.r * stride_l + (t.l - 1),
+                                    CT * fused_target(a, t.l - 1) + ((a.stall_test && t.r == 0 && t.l == 1) ? 1u : 0u),
+                                    a.err, a.wait_cycles);
+                if (ok && t.l < L && t.r >= a.ring)   // the ring unit's previous readers
+                    ok = wait_count(done + (long long)(t.r - a.ring) * stride_l + (t.l + 1), CT * fused_target(a, t.l + 1),
+                                    a.err, a.wait_cycles);
+                if (!ok) {
+                    umma::st_release_cta_shared(dep_ready, ~0u);
+                    atomicExch(a.err, 1);
+                    break;
+                }
+                umma::fence_proxy_async_global();   // the producers' stores, seen by this CTA's TMA loads
+                umma::st_release_cta_shared(dep_ready, ++nready);
+            }
         }
     } else {
         // ---------------------------------------------------------- epilogue
@@ -306,7 +404,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
         uint8_t *stg = stg_base + ew * 4096;
         uint32_t *pending = nullptr;   // arrival counter of a hidden item whose release is deferred
         uint32_t jacc = 0;
-        for (long long i = blockIdx.x; i < a.total; i += gridDim.x) {
+        for (long long i = g0; i < a.total; i += gs) {
             const FusedItem t = fused_item(a, i);
             if (!t.valid) continue;
             const uint32_t buf = jacc & 1u;
@@ -324,12 +422,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                 }
                 pending = nullptr;
             }
-            const int m0 = t.r * BM;
+            const int m0 = (t.r * CT + (int)rank) * BM;
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * kFusedBN;
+            // the accumulator buffer is free once every epilogue warp of the
+            // pair (or CTA) has read it
+            const uint32_t acc_empty_c = PAIR ? umma::mapa_shared(umma::smem_u32(&acc_empty[buf]), 0u) : 0u;
             if (t.l < L) {
                 // hidden layer: GeLU(acc + b) -> BF16 -> swizzled box -> TMA store into the ring
                 const float *sb = sbias + t.l * W + t.j * kFusedBN + hcol;
-                const int ring_row = (t.r % a.ring) * BM + q * 32;
+                const int ring_row = ((t.r % a.ring) * CT + (int)rank) * BM + q * 32;
                 if (!fail) {
                     // 4 chunks of 16 columns; TMEM loads double-buffered in ra / rb
                     uint32_t ra[16], rb[16];
@@ -352,13 +453,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                 }
                 umma::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) umma::mbar_arrive(&acc_empty[buf]);   // the next item's MMAs may start
-                // defer the release when the CTA's next item waits on nothing at or after this one
+                if (lane == 0) {   // the next item's MMAs may start
+                    if constexpr (PAIR)
+                        umma::mbar_arrive_cluster(acc_empty_c);
+                    else
+                        umma::mbar_arrive(&acc_empty[buf]);
+                }
+                // defer the release when the next item waits on nothing at or after this one
                 uint32_t *ctr = done_w + (long long)t.r * stride_l + t.l;
-                long long nx = i + gridDim.x;
+                long long nx = i + gs;
                 FusedItem tn;
                 tn.valid = false;
-                for (; nx < a.total; nx += gridDim.x) {
+                for (; nx < a.total; nx += gs) {
                     tn = fused_item(a, nx);
                     if (tn.valid) break;
                 }
@@ -391,7 +497,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
                 umma::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    umma::mbar_arrive(&acc_empty[buf]);
+                    if constexpr (PAIR)
+                        umma::mbar_arrive_cluster(acc_empty_c);
+                    else
+                        umma::mbar_arrive(&acc_empty[buf]);
                     umma::red_release_gpu_add(done_w + (long long)t.r * stride_l + L, 1u);
                 }
             }
@@ -407,10 +516,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(const __gri
     __syncwarp();
     umma::tc_fence_before();
     __syncthreads();
+    // the pair's MMAs, barrier signals and remote arrivals are all done before
+    // either CTA frees its tensor memory or exits
+    if constexpr (PAIR) umma::cluster_sync();
     if (warp == 1) {
         __syncwarp();
         umma::tc_fence_after();
-        umma::tmem_dealloc(tmem, C::TMEM_COLS);
+        if constexpr (PAIR)
+            umma::tmem_dealloc_pair(tmem, C::TMEM_COLS);
+        else
+            umma::tmem_dealloc(tmem, C::TMEM_COLS);
     }
 }
 

@@ -894,37 +894,86 @@ cudaError_t launch_gemm_n(const CUtensorMap &ta, const CUtensorMap &tb, const Ge
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // One cooperative launch of the fused inference kernel (all CTAs resident:
-// they wait on one another's arrival counters).
-cudaError_t launch_fused(const FusedArgs &fa, cudaStream_t st)
+// they wait on one another's arrival counters) over `units` CTAs or, for
+// PAIR, CTA pairs (clusters of two).
+template <bool PAIR>
+cudaError_t launch_fused(const FusedArgs &fa, int units, cudaStream_t st)
 {
     static int dev_ready[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    const int smem_max = FusedCfg::kMaxSmem;
     if (!dev_ready[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+        cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel<PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             FusedCfg<PAIR>::kMaxSmem);
         if (e != cudaSuccess) return e;
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_fused_kernel, kFusedThreads, smem_max);
-        if (e != cudaSuccess) return e;
-        if (occ < 1) return cudaErrorInvalidConfiguration;
+        if (!PAIR) {
+            int occ = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_fused_kernel<PAIR>, kFusedThreads,
+                                                              FusedCfg<PAIR>::kMaxSmem);
+            if (e != cudaSuccess) return e;
+            if (occ < 1) return cudaErrorInvalidConfiguration;
+        }
         dev_ready[dev] = 1;
     }
-    const int sms = num_sms_current();
-    const long long g = fa.total < sms ? fa.total : sms;
+    const long long g = fa.total < units ? fa.total : units;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = 2;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)((PAIR ? 2 : 1) * g), 1, 1);
+    cfg.blockDim = dim3(kFusedThreads, 1, 1);
+    cfg.dynamicSmemBytes = FusedCfg<PAIR>::smem_bytes(fa.L, fa.W);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = PAIR ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, mlp_fused_kernel<PAIR>, fa);
+}
+
+// CTA pairs of the fused kernel that the device holds at once (0: none, or
+// cluster launches unavailable).
+int fused_pair_clusters(int L, int W)
+{
+    if (cudaFuncSetAttribute(mlp_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             FusedCfg<true>::kMaxSmem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.gridDim = dim3((unsigned)g, 1, 1);
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * num_sms_current(), 1, 1);
     cfg.blockDim = dim3(kFusedThreads, 1, 1);
-    cfg.dynamicSmemBytes = FusedCfg::smem_bytes(fa.L, fa.W);
-    cfg.stream = st;
+    cfg.dynamicSmemBytes = FusedCfg<true>::smem_bytes(L, W);
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, mlp_fused_kernel, fa);
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, mlp_fused_kernel<true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+// Slot lag D between consecutive layers, about three rounds of G concurrent
+// units (an item's inputs are released about two rounds after its producer
+// item's turn), and the ring size 2 D + 4 (a ring unit is rewritten about
+// three rounds after its readers' turn).
+void fused_lag(int G, int ips, int &D, int &ring)
+{
+    const int lagmin = (G + 2 * ips + ips - 1) / ips;   // slots with D ips > G + ips
+    const int three_rounds = (3 * G + ips - 1) / ips;
+    D = three_rounds > lagmin + 4 ? three_rounds : lagmin + 4;
+    ring = 2 * D + 4;
 }
 
 GemmArgs base_args(sg_model *m)
@@ -984,7 +1033,12 @@ static pr_status build_maps(sg_model *m)
         ok = ok && make_map(&m->tmf_w[0], d.wb[0], KIN, W, KIN, kFusedBN);
         for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tmf_w[l], d.wb[l], W, W, W, kFusedBN);
         m->tmf_w[L] = m->tm_w[L];
-        const int64_t rr = (int64_t)m->fused_ring * 128;
+        if (m->fused_pair_ok) {   // each CTA of a pair loads half of every weight tile
+            ok = ok && make_map(&m->tmp_w[0], d.wb[0], KIN, W, KIN, kFusedBN / 2);
+            for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tmp_w[l], d.wb[l], W, W, W, kFusedBN / 2);
+            ok = ok && make_map(&m->tmp_w[L], d.wb[L], W, NOP, W, kFusedOutBN / 2);
+        }
+        const int64_t rr = (int64_t)m->fused_ring_rows * 128;
         ok = ok && make_map_3d(&m->tmf_ring_ld, m->ring, W, rr, L, 128);
         ok = ok && make_map_3d(&m->tmf_ring_st, m->ring, W, rr, L, 32);
     }
@@ -1109,19 +1163,20 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     alloc((void **)&m->d_normpart, (size_t)m->norm_blocks * (NSTAT + 1) * 4 * 8);
     alloc((void **)&d.xi, C * KIN * 2);
     alloc((void **)&d.hig, C * 4);
-    // fused inference (mlp_fused.cuh): consecutive layers D slots apart, about
-    // three rounds of the grid (an item's inputs are released about two rounds
-    // after its producer item's turn); a ring row block is rewritten about
-    // three rounds after its readers' turn
+    // fused inference (mlp_fused.cuh), with single-CTA tiles or CTA pairs
     m->fused_ok = (W % kFusedBN == 0) && W <= 1024 && L <= SG_MAX_HIDDEN &&
-                  FusedCfg::smem_bytes(L, W) <= FusedCfg::kMaxSmem;
+                  FusedCfg<false>::smem_bytes(L, W) <= FusedCfg<false>::kMaxSmem;
     if (m->fused_ok) {
-        const int G = ctx->num_sms, n_t = W / kFusedBN, ips = L * n_t + 1;
-        const int lagmin = (G + 2 * ips + ips - 1) / ips;   // slots with D ips > G + ips
-        const int three_rounds = (3 * G + ips - 1) / ips;
-        m->fused_D = three_rounds > lagmin + 4 ? three_rounds : lagmin + 4;
-        m->fused_ring = 2 * m->fused_D + 4;
-        alloc((void **)&m->ring, (size_t)L * m->fused_ring * 128 * W * 2);
+        const int ips = L * (W / kFusedBN) + 1;
+        fused_lag(ctx->num_sms, ips, m->fused_D, m->fused_ring);
+        m->fused_ring_rows = m->fused_ring;
+        m->fused_clusters = (FusedCfg<true>::smem_bytes(L, W) <= FusedCfg<true>::kMaxSmem) ? fused_pair_clusters(L, W) : 0;
+        m->fused_pair_ok = m->fused_clusters > 0;
+        if (m->fused_pair_ok) {
+            fused_lag(m->fused_clusters, ips, m->fused_D2, m->fused_ring2);
+            if (2 * m->fused_ring2 > m->fused_ring_rows) m->fused_ring_rows = 2 * m->fused_ring2;
+        }
+        alloc((void **)&m->ring, (size_t)L * m->fused_ring_rows * 128 * W * 2);
         alloc((void **)&m->d_done, (size_t)ceil_div(C, 128) * (L + 1) * 4);
     }
     m->fused_on = m->fused_ok;
@@ -1366,16 +1421,17 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
                                                                  m->d_flags, m->d_list, m->d_count);
         PR_CUDA_TRY(cudaGetLastError());
         if (m->fused_on) {
-            // every layer in one cooperative launch (mlp_fused.cuh)
+            // every layer in one cooperative launch (mlp_fused.cuh): single
+            // CTAs, or CTA pairs when asked for and the device takes them
+            bool pair = m->fused_on == 2 && m->fused_pair_ok;
             FusedArgs fa;
             memset(&fa, 0, sizeof(fa));
             fa.tm_x = m->tm_xi;
             fa.tm_ring_ld = m->tmf_ring_ld;
             fa.tm_ring_st = m->tmf_ring_st;
-            for (int l = 0; l <= L; ++l) { fa.tm_w[l] = m->tmf_w[l]; fa.bias[l] = d.master + d.lay[l].b_off; }
-            fa.M = (int)mc; fa.R = mt; fa.L = L; fa.W = W; fa.D = m->fused_D; fa.ring = m->fused_ring;
+            for (int l = 0; l <= L; ++l) fa.bias[l] = d.master + d.lay[l].b_off;
+            fa.M = (int)mc; fa.L = L; fa.W = W;
             fa.n_t = W / kFusedBN; fa.ips = L * fa.n_t + 1;
-            fa.total = (long long)(fa.R + (long long)L * fa.D) * fa.ips;
             fa.out6 = out + r0; fa.ld6 = ldo;
             fa.out_mean = d.outstat; fa.out_std = d.outstat + NOUT_MAX;
             fa.add_h = (d.mode != SG_MODE_FORWARD) ? nullptr : d.hig;
@@ -1385,7 +1441,25 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             fa.wait_cycles = m->wait_cycles > 0 ? m->wait_cycles : 4000000000LL;
             fa.stall_test = m->stall_test;
             PR_CUDA_TRY(cudaMemsetAsync(m->d_done, 0, (size_t)mt * (L + 1) * 4, st));
-            PR_CUDA_TRY(launch_fused(fa, st));
+            cudaError_t e = cudaSuccess;
+            if (pair) {
+                for (int l = 0; l <= L; ++l) fa.tm_w[l] = m->tmp_w[l];
+                fa.R = ceil_div(mt, 2); fa.D = m->fused_D2; fa.ring = m->fused_ring2;
+                fa.total = (long long)(fa.R + (long long)L * fa.D) * fa.ips;
+                e = launch_fused<true>(fa, m->fused_clusters, st);
+                if (e != cudaSuccess) {   // a configuration the device refuses: single CTAs from now on
+                    cudaGetLastError();
+                    m->fused_pair_ok = 0;
+                    pair = false;
+                }
+            }
+            if (!pair) {
+                for (int l = 0; l <= L; ++l) fa.tm_w[l] = m->tmf_w[l];
+                fa.R = mt; fa.D = m->fused_D; fa.ring = m->fused_ring;
+                fa.total = (long long)(fa.R + (long long)L * fa.D) * fa.ips;
+                e = launch_fused<false>(fa, num_sms_current(), st);
+            }
+            PR_CUDA_TRY(e);
         }
         for (int l = 0; l < L && !m->fused_on; ++l) {
             GemmArgs a = base_args(m);
@@ -1454,12 +1528,29 @@ int sg_mode_of(const sg_model *m) { return m->dev.mode; }
 
 extern "C" {
 
+pr_status surrogate_get_option(const sg_model *m, int option, int *value)
+{
+    PR_CHECK_ARG(m != nullptr && value != nullptr, "surrogate_get_option: null argument");
+    switch (option) {
+    case SG_OPT_FUSED_INFER: *value = !m->fused_on ? 0 : (m->fused_on == 2 && m->fused_pair_ok) ? 2 : 1; return PR_OK;
+    case SG_OPT_MODE: *value = m->dev.mode; return PR_OK;
+    case SG_OPT_WAIT_LIMIT_KCYCLES: *value = (int)(m->wait_cycles / 1000); return PR_OK;
+    case SG_OPT_TEST_STALL: *value = m->stall_test; return PR_OK;
+    case SG_OPT_LOSS: *value = m->loss_l1 ? SG_LOSS_L1 : SG_LOSS_REL_MSE; return PR_OK;
+    case SG_OPT_CONFIDENCE_PPM: *value = (int)(m->conf_tol * 1e6f + 0.5f); return PR_OK;
+    case SG_OPT_OUTPUTS: *value = m->dev.outputs; return PR_OK;
+    default: break;
+    }
+    PR_CHECK_ARG(false, "surrogate_get_option: unknown option %d", option);
+    return PR_EINVAL;
+}
+
 pr_status surrogate_set_option(sg_model *m, int option, int value)
 {
     PR_CHECK_ARG(m != nullptr, "surrogate_set_option: null model");
     switch (option) {
     case SG_OPT_FUSED_INFER:
-        PR_CHECK_ARG(value == 0 || (value == 1 && m->fused_ok),
+        PR_CHECK_ARG(value == 0 || ((value == 1 || value == 2) && m->fused_ok),
                      "surrogate_set_option: fused inference needs a width that is a multiple of 256, <= 1024, "
                      "and its biases within shared memory");
         m->fused_on = value;

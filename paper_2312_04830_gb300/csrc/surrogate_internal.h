@@ -111,13 +111,17 @@ struct sg_model {
     CUtensorMap tsT_dz[SG_MAX_HIDDEN];      // dz^T [W][B] as the TMA-store target of 32 x 64 boxes
     // fused inference (mlp_fused.cuh): activation ring, its maps, the weight
     // maps with 256-row boxes, per-(row block, layer) arrival counters
-    int fused_ok, fused_on, fused_D, fused_ring;
+    int fused_ok, fused_on, fused_D, fused_ring;   // single-CTA tiles: slot lag, ring row blocks
+    int fused_pair_ok, fused_D2, fused_ring2;      // CTA-pair tiles: slot lag, ring units of two row blocks
+    int fused_clusters;                     // CTA pairs resident at once
+    int fused_ring_rows;                    // row blocks per layer of the ring buffer
     long long wait_cycles;                  // bounded-wait limit of the fused kernel
     int stall_test;                         // SG_OPT_TEST_STALL
     int loss_l1;                            // SG_OPT_LOSS == SG_LOSS_L1
     float conf_tol;                         // SG_OPT_CONFIDENCE_PPM / 1e6; 0: off
-    __nv_bfloat16 *ring;                    // [L][fused_ring * 128][W]
+    __nv_bfloat16 *ring;                    // [L][fused_ring_rows * 128][W]
     uint32_t *d_done;
     CUtensorMap tmf_w[SG_MAX_HIDDEN + 1], tmf_ring_ld, tmf_ring_st;
+    CUtensorMap tmp_w[SG_MAX_HIDDEN + 1];  // CTA pairs: half-height weight boxes
     std::vector<void *> allocs;
 };

@@ -193,9 +193,11 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
                                                    (512, 1, 1024, 300)])
 def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers, chunk, n):
     """All layers of a chunk in one persistent launch (activation ring in L2,
-    cross-CTA arrival counters) give the same bits as one launch per layer:
-    chunks longer than the ring (ring slots reused), a ragged last chunk, and
-    a chunk shorter than the grid."""
+    cross-CTA arrival counters), with 128 x 256 tiles on single CTAs (the
+    default) or 256 x 256 tiles on CTA pairs, give the same bits as one launch
+    per layer: chunks longer than the ring (ring slots reused), a ragged last
+    chunk, an odd number of row blocks (the last pair's second half empty),
+    and a chunk shorter than the grid."""
     import torch
     from paper_2312_04830_gb300 import binding
     sg = binding.Surrogate(ctx, width=width, hidden_layers=layers, max_batch=1024, infer_chunk=chunk, seed=21)
@@ -205,22 +207,27 @@ def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers
     T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=cuda)
     Td, pd, Yd = d(T), d(p), d(Y)
+    assert sg.fused_kind == "single"
     outs = []
-    for fused in (True, False):
+    for fused, kind in ((True, "single"), ("pair", "pair"), (False, "per-layer")):
         sg.set_fused_infer(fused)
+        assert sg.fused_kind == kind
         o, fb = sg.infer(Td, pd, Yd)
         sg.sync_status()
         outs.append(o.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1], equal_nan=True)
+    assert np.array_equal(outs[0], outs[2], equal_nan=True)
+    assert np.array_equal(outs[1], outs[2], equal_nan=True)
     assert np.isfinite(outs[0]).mean() > 0.9
     sg.close()
 
 
-def test_fused_inference_wait_timeout_is_reported(ctx, orc, species, cuda):
-    """Failure detection of the persistent kernel: with one arrival counter
-    made unreachable and a short wait limit (20M cycles, ~10 ms), the waits
-    run out, the kernel finishes, the host gets PR_ETIMEOUT, and the context
-    stays usable: the next launches give the per-layer result bit for bit."""
+@pytest.mark.parametrize("kind", [True, "pair"])
+def test_fused_inference_wait_timeout_is_reported(ctx, orc, species, cuda, kind):
+    """Failure detection of the persistent kernel (single CTAs and CTA pairs):
+    with one arrival counter made unreachable and a short wait limit (20M
+    cycles, ~10 ms), the waits run out, the kernel finishes, the host gets
+    PR_ETIMEOUT, and the context stays usable: the next launches give the
+    per-layer result bit for bit."""
     import torch
     from paper_2312_04830_gb300 import binding
     sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=32768, seed=31)
@@ -230,6 +237,7 @@ def test_fused_inference_wait_timeout_is_reported(ctx, orc, species, cuda):
     T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=cuda)
     Td, pd, Yd = d(T), d(p), d(Y)
+    sg.set_fused_infer(kind)
     sg.set_wait_limit(20000)
     sg.set_test_stall(True)
     sg.infer(Td, pd, Yd)
@@ -239,7 +247,7 @@ def test_fused_inference_wait_timeout_is_reported(ctx, orc, species, cuda):
     sg.set_test_stall(False)
     sg.set_wait_limit(0)
     outs = []
-    for fused in (True, False):
+    for fused in (kind, False):
         sg.set_fused_infer(fused)
         o, _ = sg.infer(Td, pd, Yd)
         sg.sync_status()
