@@ -43,12 +43,12 @@ FP64_PEAK_TFLOPS = FP64_PEAK_NOMINAL_TFLOPS
 # FP64 flops per cell of the FP64 kernels, from ncu instruction counts
 # (2 x DFMA + DADD + DMUL per launch / cells) on the 128^3 flame-vortex field
 # (profiles/fp64_kernels_counts_flame_vortex_128.md)
-FP64_FLOPS_PER_CELL = {"props_fp64": 1582.7, "newton_fp64": 1363.5,
+FP64_FLOPS_PER_CELL = {"props_fp64": 1582.7, "newton_fp64": 1309.0,
                        # per-species outputs (profiles/species_kernel_fp64_flame_vortex_128.md)
                        "species_fp64": 4117.0}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
 # / cells) of the same capture; a full launch moves this x its cells
-TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 107.8,
+TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 108.0,
                           # fused inference kernel, DRAM bytes per row of a chunk launch
                           # (profiles/fused_mlp_infer_flame_vortex_128.md)
                           "surrogate_bf16": 353.9, "surrogate_inverse_bf16": 446.4}

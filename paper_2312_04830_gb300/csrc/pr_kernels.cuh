@@ -135,10 +135,26 @@ __device__ __noinline__ int eval_h(const Comp<Real, NS> &c, double T, Real p, co
     return kOk;
 }
 
+// h(T) and cp(T) in FP32 with FP32 arguments (the warm start's evaluations).
+template <int NS, bool KIJ>
+__device__ __noinline__ int eval_h_f32(const Comp<float, NS> &c, float T, float p, const SpeciesRec<float> *sp,
+                                       const float *kij, float &h, float &cp)
+{
+    Thermo<float> th;
+    thermo<float, float, NS, KIJ>(c, T, p, sp, kij, th);
+    if (th.status == kNoRoot) return kNoRoot;
+    h = th.h;
+    cp = th.cp;
+    return kOk;
+}
+
 // Warm start of the FP64 inversion: plain Newton on the FP32 thermodynamics
 // from T0 until a step is below 1e-5 T (at most 8 steps).  Returns the FP32
 // root, or T0 when a step fails, leaves [kTLo, kTHi] or does not settle (the
-// FP64 iteration then starts from T0 as it would without a warm start).
+// FP64 iteration then starts from T0 as it would without a warm start).  The
+// update runs in FP32 as well (h* rounded to FP32 moves the root by less than
+// the FP32 enthalpy's own error), so the FP64 pipe only does the final
+// conversion.
 template <int NS, bool KIJ>
 __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, double T0, double hs, double p,
                                                const SpeciesRec<float> *sp, const float *kij)
@@ -148,16 +164,17 @@ __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, doub
     for (int k = 0; k < NS; ++k) c.x[k] = (float)c64.x[k];
     c.Wbar = (float)c64.Wbar;
     c.bm = (float)c64.bm;
-    double T = T0;
+    const float hsf = (float)hs, pf = (float)p;
+    float T = (float)T0;
 #pragma unroll 1
     for (int k = 0; k < 8; ++k) {
-        double h, cp;
-        if (eval_h<float, float, NS, KIJ>(c, T, (float)p, sp, kij, h, cp) || !(cp > 0)) return T0;
-        const double Tn = T - (h - hs) / cp;
-        if (!(Tn > kTLo && Tn < kTHi)) return T0;
-        const bool done = fabs(Tn - T) <= 1e-5 * Tn;
+        float h, cp;
+        if (eval_h_f32<NS, KIJ>(c, T, pf, sp, kij, h, cp) || !(cp > 0.f)) return T0;
+        const float Tn = T - (h - hsf) / cp;
+        if (!(Tn > (float)kTLo && Tn < (float)kTHi)) return T0;
+        const bool done = fabsf(Tn - T) <= 1e-5f * Tn;
         T = Tn;
-        if (done) return T;
+        if (done) return (double)T;
     }
     return T0;
 }
