@@ -96,6 +96,44 @@ template <> struct M<float> {
 
 // -------------------------------------------------------- composition
 // T-independent part of a cell: mole fractions, mean molar mass, b_m.
+// Per-species branch decisions of the FP64 path on the integer pipe (an FP64
+// compare takes an FP64-pipe slot, the scarce resource of these kernels).
+// For a positive finite a and a non-NaN b, a < b exactly when a's bit pattern
+// is below b's as a signed integer: positive numbers order like their
+// patterns, and every negative b (-0 included) has a negative pattern.
+template <typename Real>
+__device__ __forceinline__ bool lt_pos(Real a, Real b)
+{
+    if constexpr (sizeof(Real) == 8)
+        return __double_as_longlong(a) < __double_as_longlong(b);
+    else
+        return a < b;
+}
+
+// y >= 0 and finite (-0 included): on the bit pattern for FP64.
+template <typename Real>
+__device__ __forceinline__ bool nonneg_finite(Real y)
+{
+    if constexpr (sizeof(Real) == 8) {
+        const long long b = __double_as_longlong(y);
+        return (b >= 0 && b < 0x7FF0000000000000LL) || b == (long long)0x8000000000000000ULL;
+    } else {
+        return (y >= Real(0)) && M<Real>::finite(y);
+    }
+}
+
+// u >= 0 for a non-NaN u (-0 counts as 0): sign bit clear, or magnitude 0.
+template <typename Real>
+__device__ __forceinline__ bool nonneg(Real u)
+{
+    if constexpr (sizeof(Real) == 8) {
+        const long long b = __double_as_longlong(u);
+        return b >= 0 || (b << 1) == 0;
+    } else {
+        return u >= Real(0);
+    }
+}
+
 template <typename Real, int NS>
 struct Comp {
     Real x[NS];     // mole fractions
@@ -112,7 +150,7 @@ __device__ __forceinline__ bool load_comp(Comp<Real, NS> &c, const Real *__restr
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         Real y = (k < N) ? __ldg(Y + (int64_t)k * ldY + i) : Real(0);
-        ok = ok && (y >= Real(0)) && M<Real>::finite(y);
+        ok = ok && nonneg_finite(y);
         ysum += y;
         c.x[k] = y * sp[k].inv_W;            // moles per kg, normalised below
         s += c.x[k];
@@ -144,7 +182,7 @@ __device__ __forceinline__ void mix_a(const Comp<Real, NS> &c, Real T, const Spe
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
             const Real u = M<Real>::fma(-sp[k].kq, sqT, Real(1) + sp[k].kappa);
-            const Real g = (u >= Real(0)) ? sp[k].sqrt_ac : -sp[k].sqrt_ac;  // sqrt(ac) sgn(u)
+            const Real g = nonneg(u) ? sp[k].sqrt_ac : -sp[k].sqrt_ac;  // sqrt(ac) sgn(u)
             const Real xg = c.x[k] * g;
             S0 = M<Real>::fma(xg, u, S0);              // x sqrt(ac) |u|
             const Real xgq = xg * sp[k].kq;
@@ -161,13 +199,13 @@ __device__ __forceinline__ void mix_a(const Comp<Real, NS> &c, Real T, const Spe
 #pragma unroll 1
         for (int i = 0; i < NS; ++i) {
             const Real ui = M<Real>::fma(-sp[i].kq, sqT, Real(1) + sp[i].kappa);
-            const Real gi = c.x[i] * ((ui >= Real(0)) ? sp[i].sqrt_ac : -sp[i].sqrt_ac);
+            const Real gi = c.x[i] * (nonneg(ui) ? sp[i].sqrt_ac : -sp[i].sqrt_ac);
             const Real ri = gi * ui, dri = gi * sp[i].kq * h1, d2ri = gi * sp[i].kq * h2;
             Real t0 = 0, t1 = 0;
 #pragma unroll
             for (int j = 0; j < NS; ++j) {
                 const Real uj = M<Real>::fma(-sp[j].kq, sqT, Real(1) + sp[j].kappa);
-                const Real gj = c.x[j] * kij1m[i * NS + j] * ((uj >= Real(0)) ? sp[j].sqrt_ac : -sp[j].sqrt_ac);
+                const Real gj = c.x[j] * kij1m[i * NS + j] * (nonneg(uj) ? sp[j].sqrt_ac : -sp[j].sqrt_ac);
                 t0 = M<Real>::fma(gj, uj, t0);
                 t1 = M<Real>::fma(gj * sp[j].kq, h1, t1);
             }
@@ -346,7 +384,7 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
     Real cp_ig = 0, h_ig = 0;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        const bool lo = T < sp[k].T_mid;
+        const bool lo = lt_pos(T, sp[k].T_mid);   // T > 0 here
         const Real *a = lo ? sp[k].cp_lo : sp[k].cp_hi;
         const Real *e = lo ? sp[k].h_lo : sp[k].h_hi;
         const Real cpk = M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(a[4], T, a[3]), T, a[2]), T, a[1]), T, a[0]);
