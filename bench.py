@@ -48,7 +48,7 @@ FP64_FLOPS_PER_CELL = {"props_fp64": 1582.7, "newton_fp64": 1309.0,
                        "species_fp64": 4117.0}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
 # / cells) of the same capture; a full launch moves this x its cells
-TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 108.0,
+TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 107.6,
                           # fused inference kernel, DRAM bytes per row of a chunk launch
                           # (profiles/fused_mlp_infer_flame_vortex_128.md)
                           "surrogate_bf16": 353.9, "surrogate_inverse_bf16": 446.4}
