@@ -1,0 +1,130 @@
+"""Parity at the full benchmark size (GPU): the 256^3 flame-vortex field
+(16,777,216 cells, N = 9) in the launch configuration the benchmark times.
+
+The property evaluation and the inversion run over the whole field in one
+call each; sampled cells are checked against the oracle, which the oracle can
+compute one by one.  The surrogate runs the whole field in 4 Mi-row chunks;
+the fused kernel's outputs equal the per-layer launches bit for bit on every
+row, and sampled rows match the float64 forward of the oracle MLP.  Inputs
+come from the seeded generators; expected values from the oracle only.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2312_04830_gb300 import workloads as W
+
+from .parity import assert_fp64_parity, cond_numbers, input_condition
+from .test_gpu_surrogate import h_ig_of, make_pool, standardise, unflatten
+
+pytestmark = pytest.mark.gpu
+
+GRID = 256
+N_SAMPLE = 20000
+CHUNK = 1 << 22   # rows per fused-inference launch, as in the benchmark
+
+
+@pytest.fixture(scope="module")
+def ctx(prlib, cuda, species):
+    from paper_2312_04830_gb300 import binding
+    c = binding.PropertyContext(species)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def field():
+    T, p, Y = W.flame_vortex_field(GRID)
+    Ttrue = W.newton_targets(T)
+    idx = np.sort(np.random.default_rng(31).choice(T.size, N_SAMPLE, replace=False))
+    return T, p, Y, Ttrue, idx
+
+
+def dev(a, dtype, cuda):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=cuda)
+
+
+def test_props_fp64_full_field_sampled(ctx, orc, species, cuda, field):
+    """pr_props in FP64 over all 16.8 M cells in one call; 20000 sampled cells
+    against the oracle (1e-10, with the oracle's sensitivity allowance)."""
+    import torch
+    T, p, Y, _, idx = field
+    out, st = ctx.props(dev(T, torch.float64, cuda), dev(p, torch.float64, cuda), dev(Y, torch.float64, cuda),
+                        precision="fp64")
+    torch.cuda.synchronize()
+    it = torch.as_tensor(idx, device=cuda)
+    g, gs = out[:, it].cpu().numpy(), st[it].cpu().numpy()
+    assert np.all(st.cpu().numpy() >= 0)
+    Ts, ps, Ys = T[idx], p[idx], Y[:, idx]
+    o, os_, d = orc.diagnose(species, Ts, ps, Ys)
+    tb = orc.Table(species)
+    rep = assert_fp64_parity(g, gs, o, os_, Ts, cond_numbers(d), label="256^3 sample",
+                             kappa_fn=lambda k: input_condition(orc, tb, Ts, ps, Ys, k))
+    assert rep["n_ok"] > 0.99 * N_SAMPLE
+
+
+def test_T_from_h_fp64_full_field_sampled(ctx, orc, species, cuda, field):
+    """pr_T_from_h in FP64 over all 16.8 M cells in one call, as the benchmark
+    runs it (h* = h(T_true) of the FP64 path, start at the field's T); on
+    20000 sampled cells the result equals the oracle's own inversion of its
+    own h(T_true) and T_true (1e-10)."""
+    import torch
+    T, p, Y, Ttrue, idx = field
+    T64, p64, Y64 = dev(T, torch.float64, cuda), dev(p, torch.float64, cuda), dev(Y, torch.float64, cuda)
+    hs, _ = ctx.props(dev(Ttrue, torch.float64, cuda), p64, Y64, precision="fp64", outputs=("h",))
+    hstar = hs[2].clone()
+    del hs
+    Tg, stg, itg = ctx.T_from_h(hstar, p64, Y64, T64)
+    torch.cuda.synchronize()
+    it = torch.as_tensor(idx, device=cuda)
+    Tg, stg, itg = Tg[it].cpu().numpy(), stg[it].cpu().numpy(), itg[it].cpu().numpy()
+    Ts, ps, Ys = T[idx], p[idx], Y[:, idx]
+    ho, sth = orc.props(species, Ttrue[idx], ps, Ys)
+    To, sto, _ = orc.T_from_h(species, ho[2], ps, Ys, Ts)
+    ok = (sto == 0) & (sth == 0)
+    assert ok.sum() > 0.99 * N_SAMPLE
+    assert np.all(stg[ok] == 0)
+    np.testing.assert_allclose(Tg[ok], To[ok], rtol=1e-10)
+    np.testing.assert_allclose(Tg[ok], Ttrue[idx][ok], rtol=1e-10)
+    assert itg[ok].max() <= 60
+
+
+def test_surrogate_full_field_fused_equals_layerwise_and_oracle(ctx, orc, species, cuda, field):
+    """surrogate_infer over all 16.8 M rows in 4 Mi-row chunks (width 512, 4
+    hidden layers): the fused kernel equals the per-layer launches bit for bit
+    on every row, and sampled rows inside the training hull match the float64
+    forward of the same weights."""
+    import torch
+    from paper_2312_04830_gb300 import binding
+    T, p, Y, _, idx = field
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=CHUNK, seed=41)
+    x, y = make_pool(orc, species, 8000, seed=42)
+    sg.fit_normalization(dev(x, torch.float32, cuda), dev(y, torch.float32, cuda))
+    Td, pd, Yd = dev(T, torch.float32, cuda), dev(p, torch.float32, cuda), dev(Y, torch.float32, cuda)
+    assert sg.fused_kind == "single"
+    out_f, fb_f = sg.infer(Td, pd, Yd)
+    sg.sync_status()
+    sg.set_fused_infer(False)
+    out_l, fb_l = sg.infer(Td, pd, Yd)
+    sg.sync_status()
+    assert torch.equal(fb_f, fb_l)
+    assert torch.equal(out_f.isnan(), out_l.isnan())
+    same = (out_f == out_l) | (out_f.isnan() & out_l.isnan())
+    assert bool(same.all())
+    it = torch.as_tensor(idx, device=cuda)
+    o, fb = out_f[:, it].double().cpu().numpy(), fb_f[it].cpu().numpy()
+    keep = fb == 0
+    assert keep.mean() > 0.5
+    xs = np.vstack([T[idx], p[idx], Y[:, idx]]).astype(np.float32)[:, keep]
+    norm = sg.get_normalization().astype(np.float64)
+    params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 6])
+    s_in, _ = standardise(xs, np.ones((6, xs.shape[1]), np.float32), norm, species)
+    yhat, _ = omlp.forward(params, s_in, "tanh")
+    s_gpu = (omlp.output_targets(o[:, keep], h_ig_of(species, xs)) - norm[26:32]) / norm[32:38]
+    err = np.abs(s_gpu - yhat)
+    print("full field: fallback fraction", 1 - keep.mean(), "standardised error median", np.median(err),
+          "max", err.max())
+    assert np.median(err) < 0.01
+    assert err.max() < 0.1
+    sg.close()
