@@ -128,3 +128,34 @@ def test_surrogate_full_field_fused_equals_layerwise_and_oracle(ctx, orc, specie
     assert np.median(err) < 0.01
     assert err.max() < 0.1
     sg.close()
+
+
+def test_props_fp64_64bit_indexing(ctx, orc, species, cuda):
+    """Maximum-size edge case: 2^28 + 77 cells in one pr_props call (FP64,
+    about 37 GB on the device), so that the species-major mass fractions'
+    element index k ldY + i passes 2^31.  The cells tile a seeded set of
+    32768; sampled cells near the end and across the range equal the oracle
+    on their base cells (1e-10)."""
+    import torch
+    Tb, pb, Yb = W.uniform_cells(32768, seed=51)
+    nb = Tb.size
+    n = (1 << 28) + 77
+    reps = -(-n // nb)
+    Td = dev(Tb, torch.float64, cuda).repeat(reps)[:n].contiguous()
+    pd = dev(pb, torch.float64, cuda).repeat(reps)[:n].contiguous()
+    Yd = dev(Yb, torch.float64, cuda).repeat(1, reps)[:, :n].contiguous()
+    out, st = ctx.props(Td, pd, Yd, precision="fp64")
+    torch.cuda.synchronize()
+    del Td, pd, Yd
+    rng = np.random.default_rng(52)
+    idx = np.unique(np.concatenate([np.arange(n - 2000, n), rng.choice(n, 3000, replace=False)]))
+    assert 8 * n + idx.max() > (1 << 31)
+    it = torch.as_tensor(idx, device=cuda)
+    g, gs = out[:, it].cpu().numpy(), st[it].cpu().numpy()
+    del out, st
+    base = idx % nb
+    o, os_, d = orc.diagnose(species, Tb[base], pb[base], Yb[:, base])
+    tb = orc.Table(species)
+    rep = assert_fp64_parity(g, gs, o, os_, Tb[base], cond_numbers(d), label="2^28 + 77 cells",
+                             kappa_fn=lambda k: input_condition(orc, tb, Tb[base], pb[base], Yb[:, base], k))
+    assert rep["n_ok"] > 0.97 * idx.size
