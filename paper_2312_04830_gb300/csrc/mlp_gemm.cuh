@@ -32,12 +32,15 @@ constexpr int BM = 128;
 constexpr int BK = 64;
 
 enum Epi : int {
-    kEpiHidden = 0,    // h = GeLU(acc + b) -> out; (train) h^T -> outT, GeLU'(acc + b) -> gd
+    kEpiHidden = 0,    // h = GeLU(acc + b) -> out; (train) GeLU'(acc + b) -> gd; h^T -> outT if set
     kEpiOutPhys = 1,   // y = acc + b (n < nout) -> de-standardise -> physical values out6[nout][ld6]
     kEpiOutLoss = 2,   // y = acc + b; d = y - target (0 where the target is not finite); loss += d^2 (or |d|);
                        // dz = scale d -> out, outT, colsum
     kEpiDx = 3,        // dz = acc * gd -> out, outT, colsum
     kEpiDw = 4,        // partial[split][m][n] = acc (FP32)
+    kEpiDwMN = 5,      // as kEpiDw, with A and B read MN-major: A from [K][M], B from [K][N]
+                       // (tmA / tmB with 64 x 64 boxes), e.g. dW = dz^T h from the batch-major dz
+                       // and h; BN >= 64
 };
 
 struct GemmArgs {
@@ -370,9 +373,11 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                 }
                 if (mval) {
                     store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
+                    if (a.outT) {
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj)
-                        a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                        for (int jj = 0; jj < 16; ++jj)
+                            a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
+                    }
                 }
             } else if (EPI == kEpiDx) {
 #pragma unroll
@@ -386,13 +391,13 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                 }
                 if (mval) {
                     if (!tma) store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-                    if (!tmaT) {
+                    if (!tmaT && a.outT) {
 #pragma unroll
                         for (int jj = 0; jj < 16; ++jj)
                             a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
                     }
                 }
-            } else {  // kEpiDw
+            } else {  // kEpiDw, kEpiDwMN
                 if (m < a.Mpad) {
                     float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)split * a.Mpad + m) * a.N + nb);
 #pragma unroll
@@ -451,6 +456,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     float *sbias = red + 4 * BN + 16;                                                // [N] (N <= 1024)
 
     static_assert(MC == 1 || (MC == 2 && BN >= 32), "weight multicast needs two B boxes of BN/2 rows");
+    static_assert(EPI != kEpiDwMN || (BN >= 64 && MC == 1), "MN-major operands come in 64-wide boxes");
+    constexpr bool kMN = EPI == kEpiDwMN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb_total = (a.K + BK - 1) / BK;
     const int total = ((a.m_tiles + MC - 1) / MC) * a.n_tiles * a.splits;   // tile groups
@@ -499,12 +506,22 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
                     if (it >= (uint32_t)C::S && !umma::mbar_wait(&empty[s], ph ^ 1u)) { fail = true; break; }
                     uint8_t *st = smem + s * C::STAGE;
                     umma::mbar_arrive_expect_tx(&full[s], C::STAGE);
-                    umma::tma_load_2d(st, &tmA, &full[s], (kb0 + kb) * BK, m0);
-                    if (MC == 2)   // this CTA's half of the B tile, to both CTAs
-                        umma::tma_load_2d_mc(st + C::A_BYTES + rank * (C::B_BYTES / 2), &tmB, &full[s],
-                                             (kb0 + kb) * BK, n0 + rank * (BN / 2), (uint16_t)0x3);
-                    else
-                        umma::tma_load_2d(st + C::A_BYTES, &tmB, &full[s], (kb0 + kb) * BK, n0);
+                    if constexpr (kMN) {
+                        // 64 k-rows of 64 M (N) columns per box; blocks of 64 columns 8 KB apart
+                        const int kr = (kb0 + kb) * BK;
+#pragma unroll
+                        for (int i = 0; i < BM / 64; ++i) umma::tma_load_2d(st + i * 8192, &tmA, &full[s], m0 + 64 * i, kr);
+#pragma unroll
+                        for (int j = 0; j < BN / 64; ++j)
+                            umma::tma_load_2d(st + C::A_BYTES + j * 8192, &tmB, &full[s], n0 + 64 * j, kr);
+                    } else {
+                        umma::tma_load_2d(st, &tmA, &full[s], (kb0 + kb) * BK, m0);
+                        if (MC == 2)   // this CTA's half of the B tile, to both CTAs
+                            umma::tma_load_2d_mc(st + C::A_BYTES + rank * (C::B_BYTES / 2), &tmB, &full[s],
+                                                 (kb0 + kb) * BK, n0 + rank * (BN / 2), (uint16_t)0x3);
+                        else
+                            umma::tma_load_2d(st + C::A_BYTES, &tmB, &full[s], (kb0 + kb) * BK, n0);
+                    }
                 }
             }
             // with multicast, both CTAs' MMAs must be done with every stage (the
@@ -522,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     } else if (warp == 1) {
         // -------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN);
+            constexpr uint32_t idesc = kMN ? umma::idesc_bf16_f32_mn(BM, BN) : umma::idesc_bf16_f32(BM, BN);
             uint32_t it = 0, j = 0;
             for (int t = t_first; t < total && !fail; t += t_step, ++j) {
                 int split, mt, n0;
@@ -542,8 +559,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
                     const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
                     for (int k = 0; k < BK / 16; ++k) {
-                        umma::mma_bf16(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
-                                       umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        if constexpr (kMN)   // 16 k-rows of 128 B per step
+                            umma::mma_bf16(d_tmem, umma::sdesc_mnmajor_sw128(sa + k * 2048, 8192),
+                                           umma::sdesc_mnmajor_sw128(sb + k * 2048, 8192), idesc,
+                                           (kb > 0 || k > 0) ? 1u : 0u);
+                        else
+                            umma::mma_bf16(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
+                                           umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
                     }
                     if (MC == 2)
                         umma::mma_commit_mc(&empty[s], (uint16_t)0x3);

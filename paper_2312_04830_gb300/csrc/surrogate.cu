@@ -401,11 +401,6 @@ __global__ void prep_train_kernel(SgDev d, int64_t B, int64_t n_pool, const floa
         store_row16_bf16(d.x0 + r * KIN, v);
         store_row16_bf16(d.x0 + r * KIN + kLoOff, lo);
 #pragma unroll
-        for (int k = 0; k < NIN; ++k) {
-            d.x0t[(int64_t)k * d.max_batch + r] = __float2bfloat16_rn(v[k]);
-            d.x0t[(int64_t)(kLoOff + k) * d.max_batch + r] = __float2bfloat16_rn(lo[k]);
-        }
-#pragma unroll
         for (int j = 0; j < NOUT_MAX; ++j)
             if (j < d.nout) d.tgt[(int64_t)j * d.max_batch + r] = (q[j] - d.outstat[j]) / d.outstat[NOUT_MAX + j];
     }
@@ -775,24 +770,6 @@ bool make_map(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, ui
     return r == CUDA_SUCCESS;
 }
 
-// Unswizzled map of a feature-major matrix [rows][pitch] (BF16) with boxes of
-// 32 x 64: the TMA-store target of the transposed copies (32 batch rows of 64
-// features per box, 64-byte box rows).
-bool make_map_t(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, uint64_t pitch)
-{
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {inner, rows};
-    cuuint64_t strides[1] = {pitch * 2};
-    cuuint32_t box[2] = {32, 64};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-// The stack of L rings [L][rows][inner] (BF16), boxes of 64 x box_rows x 1.
 bool make_map_3d(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows, uint64_t depth, uint32_t box_rows)
 {
     EncodeTiledFn fn = encode_fn();
@@ -888,6 +865,18 @@ cudaError_t launch_gemm_n(const CUtensorMap &ta, const CUtensorMap &tb, const Ge
     case 128: return launch_gemm<128, EPI, use_mc(128, EPI) ? 2 : 1>(ta, tb, a, m_tiles, N / 128, splits, st);
     case 64: return launch_gemm<64, EPI>(ta, tb, a, m_tiles, N / 64, splits, st);
     default: return launch_gemm<16, EPI>(ta, tb, a, m_tiles, N / 16, splits, st);
+    }
+}
+
+// Weight-gradient GEMM with MN-major operands: N tiles of 256, 128 or 64.
+cudaError_t launch_gemm_dw_mn(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a, int m_tiles, int N,
+                              int splits, cudaStream_t st)
+{
+    switch (pick_bn(N)) {
+    case 256: return launch_gemm<256, kEpiDwMN>(ta, tb, a, m_tiles, N / 256, splits, st);
+    case 128: return launch_gemm<128, kEpiDwMN>(ta, tb, a, m_tiles, N / 128, splits, st);
+    case 64: return launch_gemm<64, kEpiDwMN>(ta, tb, a, m_tiles, N / 64, splits, st);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -1006,15 +995,15 @@ static pr_status build_maps(sg_model *m)
     ok = ok && make_map(&m->tm_wt[L], d.wt[L], KIN, W, KIN, bwx);
     // training activations
     ok = ok && make_map(&m->tm_x0, d.x0, KIN, B, KIN, 128);
-    ok = ok && make_map(&m->tm_x0t, d.x0t, B, KIN, B, 64);
+    ok = ok && make_map(&m->tmn_x0, d.x0, KIN, B, KIN, 64);
     for (int l = 0; l < L; ++l) {
         ok = ok && make_map(&m->tm_h[l], d.h[l], W, B, W, 128);
-        ok = ok && make_map(&m->tm_ht[l], d.ht[l], B, W, B, bw);
+        ok = ok && make_map(&m->tmn_h[l], d.h[l], W, B, W, 64);
         ok = ok && make_map(&m->tm_dz[l], d.dz[l], W, B, W, 128);
-        ok = ok && make_map(&m->tm_dzt[l], d.dzt[l], B, W, B, 128);
+        ok = ok && make_map(&m->tmn_dz[l], d.dz[l], W, B, W, 64);
     }
     ok = ok && make_map(&m->tm_dzo, d.dzo, KIN, B, KIN, 128);
-    ok = ok && make_map(&m->tm_dzot, d.dzot, B, MOP, B, 128);
+    ok = ok && make_map(&m->tmn_dzo, d.dzo, KIN, B, KIN, 64);
     // inference
     ok = ok && make_map(&m->tm_xi, d.xi, KIN, C, KIN, 128);
     ok = ok && make_map(&m->tm_hi[0], d.hi[0], W, C, W, 128);
@@ -1024,7 +1013,6 @@ static pr_status build_maps(sg_model *m)
         ok = ok && make_map(&m->ts_h[l], d.h[l], W, B, W, 32);
         ok = ok && make_map(&m->ts_g[l], d.g[l], W, B, W, 32);
         ok = ok && make_map(&m->ts_dz[l], d.dz[l], W, B, W, 32);
-        ok = ok && make_map_t(&m->tsT_dz[l], d.dzt[l], B, W, B);
     }
     ok = ok && make_map(&m->ts_hi[0], d.hi[0], W, C, W, 32);
     ok = ok && make_map(&m->ts_hi[1], d.hi[1], W, C, W, 32);
@@ -1127,17 +1115,13 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     alloc((void **)&d.norm, SG_NORM_FLOATS * 4);
     alloc((void **)&d.outstat, 2 * NOUT_MAX * 4);
     alloc((void **)&d.x0, B * KIN * 2);
-    alloc((void **)&d.x0t, (int64_t)KIN * B * 2);
     alloc((void **)&d.tgt, (int64_t)NOUT_MAX * B * 4);
     for (int l = 0; l < L; ++l) {
         alloc((void **)&d.h[l], B * W * 2);
-        alloc((void **)&d.ht[l], B * W * 2);
         alloc((void **)&d.g[l], B * W * 2);
         alloc((void **)&d.dz[l], B * W * 2);
-        alloc((void **)&d.dzt[l], B * W * 2);
     }
     alloc((void **)&d.dzo, B * KIN * 2);
-    alloc((void **)&d.dzot, (int64_t)MOP * B * 2);
     // weight-gradient partials: splits chosen so that tiles x splits ~ SM count
     const int kb = (int)(B / 64);
     for (int l = 0; l <= L; ++l) {
@@ -1301,7 +1285,7 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         GemmArgs a = base_args(m);
         a.M = (int)B; a.N = W; a.K = (l == 0) ? KIN : W; a.kb_per_split = a.K / 64;
         a.bias = d.master + d.lay[l].b_off;
-        a.out = d.h[l]; a.ldo = W; a.outT = d.ht[l]; a.ldoT = d.max_batch; a.gd = d.g[l]; a.ldg = W;
+        a.out = d.h[l]; a.ldo = W; a.gd = d.g[l]; a.ldg = W;
         a.tma_out = 1; a.tm_out = m->ts_h[l]; a.tm_gd = m->ts_g[l];
         const CUtensorMap &ta = (l == 0) ? m->tm_x0 : m->tm_h[l - 1];
         e = launch_gemm_n<kEpiHidden>(ta, m->tm_w[l], a, mt, W, 1, st);
@@ -1317,7 +1301,7 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         a.l1 = m->loss_l1;
         a.loss_scale = (m->loss_l1 ? 1.0f : 2.0f) / (float)(B * d.nout);
         a.nout = d.nout;
-        a.out = d.dzo; a.ldo = KIN; a.outT = d.dzot; a.ldoT = d.max_batch;
+        a.out = d.dzo; a.ldo = KIN;
         a.colsum = d.colsum[L]; a.loss_part = d.loss_part;
         e = launch_gemm<16, kEpiOutLoss>(m->tm_h[L - 1], m->tm_w[L], a, mt, 1, 1, st);
         if (e != cudaSuccess) { prgb::set_error("loss: %s", cudaGetErrorString(e)); return PR_ECUDA; }
@@ -1327,24 +1311,24 @@ static pr_status fwd_bwd(sg_model *m, int64_t B, cudaStream_t st)
         GemmArgs a = base_args(m);
         a.M = (int)B; a.N = W; a.K = (l == L) ? KIN : W; a.kb_per_split = a.K / 64;
         a.gd = d.g[l - 1]; a.ldg = W;
-        a.out = d.dz[l - 1]; a.ldo = W; a.outT = d.dzt[l - 1]; a.ldoT = d.max_batch;
+        a.out = d.dz[l - 1]; a.ldo = W;
         a.tma_out = 1; a.tm_out = m->ts_dz[l - 1];
-        a.tma_outT = 1; a.tm_outT = m->tsT_dz[l - 1];
         a.colsum = d.colsum[l - 1];
         const CUtensorMap &ta = (l == L) ? m->tm_dzo : m->tm_dz[l];
         e = launch_gemm_n<kEpiDx>(ta, m->tm_wt[l], a, mt, W, 1, st);
         if (e != cudaSuccess) { prgb::set_error("dx: %s", cudaGetErrorString(e)); return PR_ECUDA; }
     }
-    // weight gradients: dW_l = dz_l^T h_{l-1}, K = batch, split along K
+    // weight gradients: dW_l = dz_l^T h_{l-1}, K = batch, split along K; both
+    // operands read MN-major from the batch-major dz and h
     for (int l = 0; l <= L; ++l) {
         GemmArgs a = base_args(m);
         const int mp = d.dw_mpad[l], np = d.lay[l].in_pad;
         a.M = mp; a.Mpad = mp; a.N = np; a.K = (int)B; a.kb_per_split = d.dw_kps[l];
         a.partial = d.partial[l];
         const int splits = ceil_div(ceil_div(B, 64), d.dw_kps[l]);
-        const CUtensorMap &ta = (l == L) ? m->tm_dzot : m->tm_dzt[l];
-        const CUtensorMap &tb = (l == 0) ? m->tm_x0t : m->tm_ht[l - 1];
-        e = launch_gemm_n<kEpiDw>(ta, tb, a, mp / 128, np, splits, st);
+        const CUtensorMap &ta = (l == L) ? m->tmn_dzo : m->tmn_dz[l];
+        const CUtensorMap &tb = (l == 0) ? m->tmn_x0 : m->tmn_h[l - 1];
+        e = launch_gemm_dw_mn(ta, tb, a, mp / 128, np, splits, st);
         if (e != cudaSuccess) { prgb::set_error("dw: %s", cudaGetErrorString(e)); return PR_ECUDA; }
         m->last_splits[l] = splits;
     }

@@ -34,12 +34,13 @@ struct SgDev {
     float *outstat;                         // output mean[16] then std[16], gathered from norm
     int nout;                               // outputs of the model: 6, or 9 per-species ones
     int outputs;                            // SG_OUT_PROPS, SG_OUT_DK or SG_OUT_HK
-    // training activations (batch-major X [B][.] and feature-major X^T [.][B])
-    __nv_bfloat16 *x0, *x0t;
+    // training activations, batch-major [B][.] (the weight-gradient GEMMs read
+    // them MN-major, so no transposed copies)
+    __nv_bfloat16 *x0;
     float *tgt;                             // standardised targets [6][B]
-    __nv_bfloat16 *h[SG_MAX_HIDDEN], *ht[SG_MAX_HIDDEN], *g[SG_MAX_HIDDEN];
-    __nv_bfloat16 *dz[SG_MAX_HIDDEN], *dzt[SG_MAX_HIDDEN];
-    __nv_bfloat16 *dzo, *dzot;              // output-layer dz [B][64] and dz^T [128][B]
+    __nv_bfloat16 *h[SG_MAX_HIDDEN], *g[SG_MAX_HIDDEN];
+    __nv_bfloat16 *dz[SG_MAX_HIDDEN];
+    __nv_bfloat16 *dzo;                     // output-layer dz [B][64]
     float *partial[SG_MAX_HIDDEN + 1];      // weight-gradient partials [split][Mpad][in_pad]
     int dw_splits[SG_MAX_HIDDEN + 1], dw_kps[SG_MAX_HIDDEN + 1], dw_mpad[SG_MAX_HIDDEN + 1];
     float *colsum[SG_MAX_HIDDEN + 1];       // per-CTA column sums of dz [B/128][out_pad]
@@ -104,11 +105,11 @@ struct sg_model {
     uint8_t *d_flags;
     int last_splits[SG_MAX_HIDDEN + 1];
     CUtensorMap tm_w[SG_MAX_HIDDEN + 1], tm_wt[SG_MAX_HIDDEN + 1];
-    CUtensorMap tm_x0, tm_x0t, tm_h[SG_MAX_HIDDEN], tm_ht[SG_MAX_HIDDEN], tm_dz[SG_MAX_HIDDEN],
-        tm_dzt[SG_MAX_HIDDEN], tm_dzo, tm_dzot, tm_xi, tm_hi[2];
+    CUtensorMap tm_x0, tm_h[SG_MAX_HIDDEN], tm_dz[SG_MAX_HIDDEN], tm_dzo, tm_xi, tm_hi[2];
+    // weight-gradient operands read MN-major: x0, h, dz, dzo with 64 x 64 boxes
+    CUtensorMap tmn_x0, tmn_h[SG_MAX_HIDDEN], tmn_dz[SG_MAX_HIDDEN], tmn_dzo;
     // epilogue TMA-store maps (32-row boxes): h, GeLU'(z), dz, inference h
     CUtensorMap ts_h[SG_MAX_HIDDEN], ts_g[SG_MAX_HIDDEN], ts_dz[SG_MAX_HIDDEN], ts_hi[2];
-    CUtensorMap tsT_dz[SG_MAX_HIDDEN];      // dz^T [W][B] as the TMA-store target of 32 x 64 boxes
     // fused inference (mlp_fused.cuh): activation ring, its maps, the weight
     // maps with 256-row boxes, per-(row block, layer) arrival counters
     int fused_ok, fused_on, fused_D, fused_ring;   // single-CTA tiles: slot lag, ring row blocks

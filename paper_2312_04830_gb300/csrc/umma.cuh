@@ -376,12 +376,34 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr)
     return d;
 }
 
+// Shared-memory matrix descriptor of an MN-major operand tile written by TMA
+// with 128-byte swizzling: each 128-byte row holds 64 consecutive M (or N)
+// elements of one k, and rows of consecutive k follow one another, so 8-row
+// swizzle atoms of 1024 B are stacked along K (stride offset 1024 B) and
+// blocks of 64 M/N elements lie `lbo` bytes apart (leading offset).
+__device__ __forceinline__ uint64_t sdesc_mnmajor_sw128(uint32_t saddr, uint32_t lbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulator (bits [4,6) = 1), BF16
 // A and B (bits [7,10) and [10,13) = 1), both K-major, N >> 3 at [17,23),
 // M >> 4 at [24,29).
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with A and B MN-major (bits 15 and 16: the operands' major modes).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N)
+{
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
 }  // namespace umma
