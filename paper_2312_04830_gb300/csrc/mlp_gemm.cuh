@@ -32,11 +32,11 @@ constexpr int BM = 128;
 constexpr int BK = 64;
 
 enum Epi : int {
-    kEpiHidden = 0,    // h = GeLU(acc + b) -> out; (train) GeLU'(acc + b) -> gd; h^T -> outT if set
+    kEpiHidden = 0,    // h = GeLU(acc + b) -> out; (train) GeLU'(acc + b) -> gd
     kEpiOutPhys = 1,   // y = acc + b (n < nout) -> de-standardise -> physical values out6[nout][ld6]
     kEpiOutLoss = 2,   // y = acc + b; d = y - target (0 where the target is not finite); loss += d^2 (or |d|);
-                       // dz = scale d -> out, outT, colsum
-    kEpiDx = 3,        // dz = acc * gd -> out, outT, colsum
+                       // dz = scale d -> out, colsum
+    kEpiDx = 3,        // dz = acc * gd -> out, colsum
     kEpiDw = 4,        // partial[split][m][n] = acc (FP32)
     kEpiDwMN = 5,      // as kEpiDw, with A and B read MN-major: A from [K][M], B from [K][N]
                        // (tmA / tmB with 64 x 64 boxes), e.g. dW = dz^T h from the batch-major dz
@@ -50,8 +50,6 @@ struct GemmArgs {
     const float *bias;        // [N]
     __nv_bfloat16 *out;       // [M][ldo] batch-major
     int64_t ldo;
-    __nv_bfloat16 *outT;      // [N][ldoT] feature-major (may be null)
-    int64_t ldoT;
     __nv_bfloat16 *gd;        // [M][ldg] GeLU'(z): written by kEpiHidden (train), read by kEpiDx
     int64_t ldg;
     float *partial;           // kEpiDw: [split][Mpad][N]
@@ -74,11 +72,6 @@ struct GemmArgs {
     // swizzle); tm_out / tm_gd map those matrices with that box
     int tma_out;
     CUtensorMap tm_out, tm_gd;
-    // kEpiDx with tma_out and tma_outT: `outT` goes out through the warp's
-    // second 4 KB box as [64 features][32 rows] (unswizzled) and a TMA store
-    // of that box (tm_outT: outT with 32 x 64 boxes)
-    int tma_outT;
-    CUtensorMap tm_outT;
 };
 
 constexpr int kEpiWarps = 8;
@@ -261,7 +254,6 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
     // one bulk group per 64 columns; the next group first waits until the
     // previous boxes have been read out of shared memory
     const bool tma = (EPI == kEpiHidden || EPI == kEpiDx) && a.tma_out && (HALF % 64 == 0);
-    const bool tmaT = tma && EPI == kEpiDx && a.tma_outT;   // the transposed copy through `sg`
     uint8_t *sh = stg, *sg = stg + 4096;
     float lsum = 0.f;
     if (active && !fail) {
@@ -338,11 +330,6 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                         store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
                         if (a.gd) store_row16_bf16(a.gd + (int64_t)m * a.ldg + nb, gg);
                     }
-                    if (a.outT) {
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj)
-                            a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
-                    }
                 }
             } else if (EPI == kEpiOutPhys) {
                 if (mval && nb == 0) {
@@ -371,32 +358,12 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                         v[jj] = a.loss_scale * d;
                     }
                 }
-                if (mval) {
-                    store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-                    if (a.outT) {
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj)
-                            a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
-                    }
-                }
+                if (mval) store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
             } else if (EPI == kEpiDx) {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) v[jj] = mval ? v[jj] * g[jj] : 0.f;
                 if (tma) stage_row16_bf16(sh, lane, c & 3, v);
-                if (tmaT) {
-                    // column jj of this chunk is row (c % 4) * 16 + jj of the box, this lane's element of it
-                    __nv_bfloat16 *bt = reinterpret_cast<__nv_bfloat16 *>(sg) + (c & 3) * 16 * 32 + lane;
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) bt[jj * 32] = __float2bfloat16_rn(v[jj]);
-                }
-                if (mval) {
-                    if (!tma) store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
-                    if (!tmaT && a.outT) {
-#pragma unroll
-                        for (int jj = 0; jj < 16; ++jj)
-                            a.outT[(int64_t)(nb + jj) * a.ldoT + m] = __float2bfloat16_rn(v[jj]);
-                    }
-                }
+                if (mval && !tma) store_row16_bf16(a.out + (int64_t)m * a.ldo + nb, v);
             } else {  // kEpiDw, kEpiDwMN
                 if (m < a.Mpad) {
                     float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)split * a.Mpad + m) * a.N + nb);
@@ -411,7 +378,6 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
                 if (lane == 0) {
                     umma::tma_store_2d(&a.tm_out, sh, nb - 48, m0 + q * 32);
                     if (EPI == kEpiHidden && a.gd) umma::tma_store_2d(&a.tm_gd, sg, nb - 48, m0 + q * 32);
-                    if (tmaT) umma::tma_store_2d(&a.tm_outT, sg, m0 + q * 32, nb - 48);   // (row, feature)
                     umma::bulk_commit();
                 }
             }
