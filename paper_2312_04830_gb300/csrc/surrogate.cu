@@ -820,8 +820,7 @@ cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a
         gemm_kernel<BN, EPI, MC><<<groups < sms ? groups : sms, kThreads, Cfg<BN>::SMEM, st>>>(ta, tb, a);
         return cudaGetLastError();
     }
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = MC;
@@ -906,8 +905,7 @@ cudaError_t launch_fused(const FusedArgs &fa, int units, cudaStream_t st)
         dev_ready[dev] = 1;
     }
     const long long g = fa.total < units ? fa.total : units;
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
@@ -933,8 +931,7 @@ int fused_pair_clusters(int L, int W)
         cudaGetLastError();
         return 0;
     }
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
