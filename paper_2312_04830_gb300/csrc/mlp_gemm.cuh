@@ -10,13 +10,8 @@
 // the tile's columns).  The accumulator is double-buffered in TMEM (2 x BN
 // columns), so the epilogue of one tile overlaps the main loop of the next.
 // Tiles are visited with the N index fastest, so the CTAs working on the
-// N-tiles of one M-tile run together and share the A tile through L2.
-//
-// With MC = 2 the CTAs run in clusters of two that take adjacent M-tiles with
-// the same N-tile: each CTA loads half of the B (weight) tile and multicasts
-// it to both, so the pair reads each weight tile from L2 once.  A stage may
-// then be refilled only when both CTAs' MMAs have finished with it: every MMA
-// commit arrives on the stage's `empty` barrier in both CTAs (count 2).
+// N-tiles of one M-tile run together and share the A tile through L2; each
+// CTA loads its own full weight (B) tile.
 #pragma once
 
 #include <cuda.h>
@@ -390,20 +385,18 @@ __device__ __forceinline__ float epilogue_tile(const GemmArgs &a, uint32_t taddr
     return lsum;
 }
 
-// Tile `t` of the grid-stride walk, for the CTA of cluster rank `rank`: K
-// split, M-tile index (possibly >= m_tiles for the second CTA of a cluster
-// when m_tiles is odd) and N offset.
-template <int BN, int MC>
-__device__ __forceinline__ void tile_of(const GemmArgs &a, int t, int rank, int &split, int &mt, int &n0)
+// Tile `t` of the grid-stride walk: K split, M-tile index and N offset.
+template <int BN>
+__device__ __forceinline__ void tile_of(const GemmArgs &a, int t, int &split, int &mt, int &n0)
 {
-    const int per_split = ((a.m_tiles + MC - 1) / MC) * a.n_tiles;
+    const int per_split = a.m_tiles * a.n_tiles;
     split = t / per_split;
     const int r = t % per_split;
-    mt = (r / a.n_tiles) * MC + rank;
+    mt = r / a.n_tiles;
     n0 = (r % a.n_tiles) * BN;
 }
 
-template <int BN, int EPI, int MC>
+template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB,
                                                            const __grid_constant__ GemmArgs a)
@@ -421,19 +414,17 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     float *red = reinterpret_cast<float *>(stg_base + C::STG_BYTES + C::BAR_BYTES);   // [4][BN] + 16
     float *sbias = red + 4 * BN + 16;                                                // [N] (N <= 1024)
 
-    static_assert(MC == 1 || (MC == 2 && BN >= 32), "weight multicast needs two B boxes of BN/2 rows");
-    static_assert(EPI != kEpiDwMN || (BN >= 64 && MC == 1), "MN-major operands come in 64-wide boxes");
+    static_assert(EPI != kEpiDwMN || BN >= 64, "MN-major operands come in 64-wide boxes");
     constexpr bool kMN = EPI == kEpiDwMN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb_total = (a.K + BK - 1) / BK;
-    const int total = ((a.m_tiles + MC - 1) / MC) * a.n_tiles * a.splits;   // tile groups
-    const int rank = (MC == 2) ? (int)umma::cluster_ctarank() : 0;
-    const int t_first = blockIdx.x / MC, t_step = gridDim.x / MC;
+    const int total = a.m_tiles * a.n_tiles * a.splits;
+    const int t_first = blockIdx.x, t_step = gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::S; ++s) {
             umma::mbar_init(&full[s], 1);
-            umma::mbar_init(&empty[s], MC);
+            umma::mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             umma::mbar_init(&acc_full[b], 1);
@@ -449,9 +440,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     }
     umma::tc_fence_before();
     __syncthreads();
-    // the peer multicasts into this CTA's stages and barriers: its barriers
-    // must be initialised before either CTA issues a load
-    if (MC == 2) umma::cluster_sync();
     umma::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     bool fail = false;
@@ -462,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             uint32_t it = 0;
             for (int t = t_first; t < total && !fail; t += t_step) {
                 int split, mt, n0;
-                tile_of<BN, MC>(a, t, rank, split, mt, n0);
+                tile_of<BN>(a, t, split, mt, n0);
                 const int m0 = mt * BM;
                 const int kb0 = split * a.kb_per_split;
                 const int nkb = min(a.kb_per_split, kb_total - kb0);
@@ -482,22 +470,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
                             umma::tma_load_2d(st + C::A_BYTES + j * 8192, &tmB, &full[s], n0 + 64 * j, kr);
                     } else {
                         umma::tma_load_2d(st, &tmA, &full[s], (kb0 + kb) * BK, m0);
-                        if (MC == 2)   // this CTA's half of the B tile, to both CTAs
-                            umma::tma_load_2d_mc(st + C::A_BYTES + rank * (C::B_BYTES / 2), &tmB, &full[s],
-                                                 (kb0 + kb) * BK, n0 + rank * (BN / 2), (uint16_t)0x3);
-                        else
-                            umma::tma_load_2d(st + C::A_BYTES, &tmB, &full[s], (kb0 + kb) * BK, n0);
+                        umma::tma_load_2d(st + C::A_BYTES, &tmB, &full[s], (kb0 + kb) * BK, n0);
                     }
                 }
             }
-            // with multicast, both CTAs' MMAs must be done with every stage (the
-            // peer's arrivals have landed here) before this CTA may exit
-            if (MC == 2 && !fail)
-                for (uint32_t k = it; k < it + (uint32_t)C::S; ++k)
-                    if (k >= (uint32_t)C::S && !umma::mbar_wait(&empty[k % C::S], ((k / C::S) & 1u) ^ 1u, 200000000LL)) {
-                        fail = true;
-                        break;
-                    }
             // no copy may still be landing in shared memory when the CTA exits
             for (uint32_t k = (it > (uint32_t)C::S ? it - C::S : 0u); k < it; ++k)
                 if (!umma::mbar_wait(&full[k % C::S], (k / C::S) & 1u, 200000000LL)) fail = true;
@@ -509,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             uint32_t it = 0, j = 0;
             for (int t = t_first; t < total && !fail; t += t_step, ++j) {
                 int split, mt, n0;
-                tile_of<BN, MC>(a, t, rank, split, mt, n0);
+                tile_of<BN>(a, t, split, mt, n0);
                 const int kb0 = split * a.kb_per_split;
                 const int nkb = min(a.kb_per_split, kb_total - kb0);
                 const uint32_t buf = j & 1u;
@@ -533,10 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
                             umma::mma_bf16(d_tmem, umma::sdesc_kmajor_sw128(sa + k * 32),
                                            umma::sdesc_kmajor_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
                     }
-                    if (MC == 2)
-                        umma::mma_commit_mc(&empty[s], (uint16_t)0x3);
-                    else
-                        umma::mma_commit(&empty[s]);
+                    umma::mma_commit(&empty[s]);
                 }
                 umma::mma_commit(&acc_full[buf]);
             }
@@ -555,8 +528,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         uint32_t j = 0;
         for (int t = t_first; t < total; t += t_step, ++j) {
             int split, mt, n0;
-            tile_of<BN, MC>(a, t, rank, split, mt, n0);
-            const bool tile_ok = mt < a.m_tiles;   // false for the idle half of a cluster's last group
+            tile_of<BN>(a, t, split, mt, n0);
+            const bool tile_ok = mt < a.m_tiles;
             const int m0 = mt * BM;
             const int m = m0 + row;
             const bool mval = m < a.M;
@@ -599,7 +572,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         umma::tc_fence_after();
         umma::tmem_dealloc(tmem, C::TMEM_COLS);
     }
-    if (MC == 2) umma::cluster_sync();   // the peer may still address this CTA's barriers until here
 }
 
 

@@ -795,61 +795,28 @@ int num_sms_current()
 }
 
 // Persistent launch: one CTA per SM (or fewer when there are fewer tiles).
-// MC = 2: clusters of two CTAs sharing each weight tile by TMA multicast (the
-// B tensor map's box is then BN/2 rows); as many clusters as fit at once.
-template <int BN, int EPI, int MC = 1>
+template <int BN, int EPI>
 cudaError_t launch_gemm(const CUtensorMap &ta, const CUtensorMap &tb, GemmArgs a, int m_tiles, int n_tiles,
                         int splits, cudaStream_t st)
 {
-    static int dev_ready[64] = {0};   // per device: attribute set, and (MC = 2) clusters that fit at once
+    static int dev_ready[64] = {0};   // per device: shared-memory attribute set
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     a.m_tiles = m_tiles;
     a.n_tiles = n_tiles;
     a.splits = splits;
-    const int groups = ((m_tiles + MC - 1) / MC) * n_tiles * splits;
-    if (MC == 1) {
-        if (!dev_ready[dev]) {
-            cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, EPI, MC>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::SMEM);
-            if (e != cudaSuccess) return e;
-            dev_ready[dev] = 1;
-        }
-        const int sms = num_sms_current();
-        gemm_kernel<BN, EPI, MC><<<groups < sms ? groups : sms, kThreads, Cfg<BN>::SMEM, st>>>(ta, tb, a);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = MC;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = Cfg<BN>::SMEM;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    const int tiles = m_tiles * n_tiles * splits;
     if (!dev_ready[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, EPI, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Cfg<BN>::SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::SMEM);
         if (e != cudaSuccess) return e;
-        cfg.gridDim = dim3(MC * num_sms_current(), 1, 1);
-        int nc = 0;
-        e = cudaOccupancyMaxActiveClusters(&nc, gemm_kernel<BN, EPI, MC>, &cfg);
-        if (e != cudaSuccess) return e;
-        if (nc < 1) return cudaErrorInvalidConfiguration;
-        dev_ready[dev] = nc;
+        dev_ready[dev] = 1;
     }
-    const int clusters = groups < dev_ready[dev] ? groups : dev_ready[dev];
-    cfg.gridDim = dim3(MC * clusters, 1, 1);
-    return cudaLaunchKernelEx(&cfg, gemm_kernel<BN, EPI, MC>, ta, tb, a);
+    const int sms = num_sms_current();
+    gemm_kernel<BN, EPI><<<tiles < sms ? tiles : sms, kThreads, Cfg<BN>::SMEM, st>>>(ta, tb, a);
+    return cudaGetLastError();
 }
-
-// Weight multicast across a cluster of two for the wide-N GEMMs of the
-// hidden layers (forward and input gradients).
-constexpr bool use_mc(int BN, int EPI) { return BN >= 128 && (EPI == kEpiHidden || EPI == kEpiDx); }
 
 // Widest N tile (256, 128, 64 or 16) that divides N.
 inline int pick_bn(int N) { return (N % 256 == 0) ? 256 : (N % 128 == 0) ? 128 : (N % 64 == 0) ? 64 : 16; }
@@ -860,8 +827,8 @@ cudaError_t launch_gemm_n(const CUtensorMap &ta, const CUtensorMap &tb, const Ge
                           int splits, cudaStream_t st)
 {
     switch (pick_bn(N)) {
-    case 256: return launch_gemm<256, EPI, use_mc(256, EPI) ? 2 : 1>(ta, tb, a, m_tiles, N / 256, splits, st);
-    case 128: return launch_gemm<128, EPI, use_mc(128, EPI) ? 2 : 1>(ta, tb, a, m_tiles, N / 128, splits, st);
+    case 256: return launch_gemm<256, EPI>(ta, tb, a, m_tiles, N / 256, splits, st);
+    case 128: return launch_gemm<128, EPI>(ta, tb, a, m_tiles, N / 128, splits, st);
     case 64: return launch_gemm<64, EPI>(ta, tb, a, m_tiles, N / 64, splits, st);
     default: return launch_gemm<16, EPI>(ta, tb, a, m_tiles, N / 16, splits, st);
     }
@@ -979,17 +946,14 @@ static pr_status build_maps(sg_model *m)
     const int W = m->width, L = m->hidden;
     const int64_t B = m->max_batch, C = m->chunk;
     bool ok = true;
-    // weights (forward B operands); the hidden-layer GEMMs (N = W) load them
-    // in two halves of a tile when they multicast them across a cluster
-    const uint32_t bw = (uint32_t)pick_bn(W);   // box rows of B operands with N = W
-    const uint32_t bwm = use_mc((int)bw, kEpiHidden) ? bw / 2 : bw;
-    const uint32_t bwx = use_mc((int)bw, kEpiDx) ? bw / 2 : bw;
-    ok = ok && make_map(&m->tm_w[0], d.wb[0], KIN, W, KIN, bwm);
-    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_w[l], d.wb[l], W, W, W, bwm);
+    // weights (forward B operands): one box holds a whole N tile of the GEMMs with N = W
+    const uint32_t bw = (uint32_t)pick_bn(W);
+    ok = ok && make_map(&m->tm_w[0], d.wb[0], KIN, W, KIN, bw);
+    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_w[l], d.wb[l], W, W, W, bw);
     ok = ok && make_map(&m->tm_w[L], d.wb[L], W, NOP, W, 16);
     // transposed weights (input-gradient B operands)
-    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_wt[l], d.wt[l], W, W, W, bwx);
-    ok = ok && make_map(&m->tm_wt[L], d.wt[L], KIN, W, KIN, bwx);
+    for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tm_wt[l], d.wt[l], W, W, W, bw);
+    ok = ok && make_map(&m->tm_wt[L], d.wt[L], KIN, W, KIN, bw);
     // training activations
     ok = ok && make_map(&m->tm_x0, d.x0, KIN, B, KIN, 128);
     ok = ok && make_map(&m->tmn_x0, d.x0, KIN, B, KIN, 64);

@@ -102,20 +102,6 @@ __device__ __forceinline__ void tma_load_3d(void *smem_dst, const CUtensorMap *t
         : "memory");
 }
 
-// As tma_load_2d, but the box lands at the same shared-memory offset in every
-// CTA of the cluster named in `cta_mask`, and each of those CTAs' mbarrier at
-// `bar`'s offset receives the byte count.
-__device__ __forceinline__ void tma_load_2d_mc(void *smem_dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1,
-                                               uint16_t cta_mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;"
-        ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1),
-        "h"(cta_mask)
-        : "memory");
-}
-
 // ------------------------------------------------------------ clusters
 __device__ __forceinline__ uint32_t cluster_ctarank()
 {
@@ -272,16 +258,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
-}
-
-// As mma_commit, arriving on the mbarrier at `bar`'s offset in every CTA of
-// the cluster named in `cta_mask`.
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t cta_mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-        ::"r"(smem_u32(bar)), "h"(cta_mask)
-        : "memory");
 }
 
 // ------------------------------------------- tcgen05, CTA pairs (cta_group::2)
