@@ -35,22 +35,20 @@ METRIC = "cell-evals/s: PR FP64/FP32 vs BF16 MLP at <=1% rel err; %HBM roofline;
 UNIT = "cell-evals/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS_SUSTAINED = 1700.0
 # FP64 (non-tensor) peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz;
 # the roofline uses the DFMA throughput measured on the device (pr_measure_peak)
 # when that succeeds, this nominal figure otherwise
 FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = FP64_PEAK_NOMINAL_TFLOPS
-# FP64 flops per cell of the FP64 kernels, from ncu instruction counts
-# (2 x DFMA + DADD + DMUL per launch / cells) on the 128^3 flame-vortex field
-# (profiles/fp64_kernels_counts_flame_vortex_128.md)
-FP64_FLOPS_PER_CELL = {"props_fp64": 1582.7, "newton_fp64": 1309.0,
-                       # per-species outputs (profiles/species_kernel_fp64_flame_vortex_128.md)
-                       "species_fp64": 4117.0}
+# FP64 flops per cell the FP64 kernels execute, from ncu instruction counts
+# (2 x DFMA + DADD + DMUL per launch / cells) of one launch on the 128^3
+# flame-vortex field; reported beside the algorithmic count as kernel_flops
+FP64_FLOPS_PER_CELL = {"props_fp64": 1582.7, "newton_fp64": 1309.0, "species_fp64": 4117.0}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
-# / cells) of the same capture; a full launch moves this x its cells
+# / cells) of the same captures; a full launch moves this x its cells (the
+# surrogates: DRAM bytes per row of one fused-inference chunk launch)
 TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 107.6,
-                          # fused inference kernel, DRAM bytes per row of a chunk launch
-                          # (profiles/fused_mlp_infer_flame_vortex_128.md)
                           "surrogate_bf16": 353.9, "surrogate_inverse_bf16": 446.4}
 # surrogate: 2 x (13*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
@@ -201,6 +199,7 @@ def cpu_baseline(T, p, Y, Ttrue, species, budget_cells_props=1 << 24, budget_cel
     s1 = np.linspace(0, T.size - 1, n1).astype(np.int64)
     s2 = np.linspace(0, T.size - 1, n2).astype(np.int64)
     tb = oracle.Table(species)
+    cores = oracle.max_threads()
     t0 = time.perf_counter()
     oracle.props(tb, T[s1], p[s1], Y[:, s1])
     t1 = time.perf_counter()
@@ -216,7 +215,7 @@ def cpu_baseline(T, p, Y, Ttrue, species, budget_cells_props=1 << 24, budget_cel
     t5 = time.perf_counter()
     oracle.T_from_h(tb, hs[2][::64], p[m2], Y[:, m2], T[m2], threads=1)
     t6 = time.perf_counter()
-    return {"value": (n1 + n2) / secs, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    return {"value": (n1 + n2) / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle: props on {n1} and T-from-h on {n2} cells spread evenly over the "
                       f"{T.size}-cell field; one cell-eval per cell per path",
             "seconds": secs,
@@ -277,6 +276,8 @@ def train_surrogate(ctx, dev, args):
     x, y = TR.label_pool(ctx, Tp, pp, Yp, dev)
     xh, yh = TR.label_pool(ctx, Th, ph, Yh, dev)
     t_data = time.perf_counter() - t0
+    pk, _ = peaks()
+    bf16_peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or FALLBACK_BF16_TFLOPS_SUSTAINED
     sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=SG_CHUNK)
     sg.fit_normalization(x, y)
     TR.train(sg, x, y, 20, 65536, 1e-3, log_every=0)          # warm-up steps
@@ -292,7 +293,7 @@ def train_surrogate(ctx, dev, args):
     flops = 3 * mlp_flops_per_cell() * 65536 * steps
     report = {"pool": int(x.shape[1]), "steps": steps, "batch": 65536, "seconds": secs,
               "samples_per_s": 65536 * steps / secs, "tflops": flops / secs / 1e12,
-              "tensor_frac": flops / secs / 1e12 / 1729.3,
+              "tensor_frac": flops / secs / 1e12 / bf16_peak,
               "epochs": 65536 * steps / x.shape[1], "data_seconds": t_data,
               "loss_first_last": [losses[0][1], losses[-1][1]],
               "heldout_error_vs_pr_fp64": TR.evaluate(sg, xh, yh)}
@@ -559,7 +560,7 @@ def run_ours(args):
         return 0
 
     pk, pk_kind = peaks()
-    bf16_peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+    bf16_peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or FALLBACK_BF16_TFLOPS_SUSTAINED
     roof_paths = {}
     for nm in paths:
         sec = per_path_ms[nm] * 1e-3

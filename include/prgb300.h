@@ -482,12 +482,13 @@ pr_status mlp_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t 
  * It allocates nothing: the compacted cell list lives in a fixed scratch array
  * compiled into the library (PR_NOALLOC_MAX_CELLS indices plus a counter,
  * about 4 MB), which every GPU that loads the library holds until the process
- * exits.  n > PR_NOALLOC_MAX_CELLS is rejected with PR_EINVAL.  The first call
- * on each device looks up the scratch array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call shares the one scratch array and clears its counter first; calls whose
- * work overlaps on the GPU (e.g. on two streams at once) race on it.
- * Asynchronous on `stream`. */
+ * exits.  n > PR_NOALLOC_MAX_CELLS is rejected with PR_EINVAL.  pr_create
+ * looks up the scratch array's device address on the context's device, so
+ * this call needs no set-up of its own; it must be made with the context's
+ * device current (PR_EINVAL otherwise).  Every call shares the one scratch
+ * array and clears its counter first; calls whose work overlaps on the GPU
+ * (e.g. on two streams at once, or from two contexts on one device) race on
+ * it.  Asynchronous on `stream`. */
 #define PR_NOALLOC_MAX_CELLS (1 << 20)
 pr_status pr_fallback_props_noalloc(pr_ctx *ctx, int64_t n, const float *T, const float *p, const float *Y,
                                     int64_t ldY, const uint8_t *mask, float *out, int64_t ldo, void *stream);

@@ -39,6 +39,19 @@
 #include <omp.h>
 #endif
 
+/* Threads of one batch call: nthreads when positive, else the OpenMP default.
+ * Given per loop (num_threads clause), so a one-thread call leaves the
+ * default of later calls unchanged. */
+static int orc_threads(int nthreads)
+{
+#ifdef _OPENMP
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
 #define ORC_R 8.314462618 /* J/(mol K) */
 
 /* Species data, all arrays of length N (nasa_*: N x 7, kij: N x N or NULL). */
@@ -481,8 +494,7 @@ void orc_props(const orc_species *sp, int64_t n, const double *T, const double *
                double *out, int32_t *status, int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 256)
+#pragma omp parallel for schedule(dynamic, 256) num_threads(orc_threads(nthreads))
 #endif
     for (int64_t i = 0; i < n; ++i) {
         double o[6];
@@ -505,8 +517,7 @@ void orc_props_ext(const orc_species *sp, int64_t n, const double *T, const doub
                    double *out, int32_t *status, int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 256)
+#pragma omp parallel for schedule(dynamic, 256) num_threads(orc_threads(nthreads))
 #endif
     for (int64_t i = 0; i < n; ++i) {
         double o[6];
@@ -624,8 +635,7 @@ void orc_species_props(const orc_species *sp, const orc_corr *corr, int64_t n, c
                        const double *Y, double *hk_RT, double *Dk, int32_t *status, int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 256)
+#pragma omp parallel for schedule(dynamic, 256) num_threads(orc_threads(nthreads))
 #endif
     for (int64_t i = 0; i < n; ++i) {
         const int N = sp->N;
@@ -785,8 +795,7 @@ void orc_T_from_h(const orc_species *sp, int64_t n, const double *hstar, const d
                   int max_iter, double rtol, int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 256)
+#pragma omp parallel for schedule(dynamic, 256) num_threads(orc_threads(nthreads))
 #endif
     for (int64_t i = 0; i < n; ++i) {
         int it = 0;

@@ -15,8 +15,6 @@
 // until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "pr_device.cuh"
 #include "pr_internal.h"
 
@@ -24,16 +22,10 @@ using prk::SpeciesRec;
 
 namespace {
 
-constexpr int kNoallocMaxDevices = 64;
 constexpr size_t kCounterBytes = 256;   // the counter, padded so that the list stays 256-byte aligned
 
 // File-scope scratch: [counter (uint32) | pad to 256 B | int32 list[PR_NOALLOC_MAX_CELLS]].
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kCounterBytes + 4ull * PR_NOALLOC_MAX_CELLS];
-
-// Device address of g_noalloc_scratch per device (in host code the symbol's
-// name is only a host-side stand-in, never a device address).
-void *g_scratch_ptr[kNoallocMaxDevices] = {};
-std::mutex g_scratch_mu;
 
 __global__ void noalloc_compact_kernel(int64_t n, const uint8_t *__restrict__ mask, unsigned int *count,
                                        int32_t *list)
@@ -42,7 +34,8 @@ __global__ void noalloc_compact_kernel(int64_t n, const uint8_t *__restrict__ ma
         if (mask[i]) list[atomicAdd(count, 1u)] = (int32_t)i;
 }
 
-// FP64 properties of the listed cells; float inputs and outputs.
+// FP64 properties of the listed cells; float inputs and outputs (the same
+// per-cell step as the surrogate's fallback kernel).
 template <int NS, bool KIJ>
 __global__ void __launch_bounds__(128) noalloc_props_kernel(const int32_t *list, const unsigned int *count,
                                                             const float *T, const float *p, const float *Y,
@@ -64,70 +57,8 @@ __global__ void __launch_bounds__(128) noalloc_props_kernel(const int32_t *list,
     }
     __syncthreads();
     const unsigned int m = *count;
-    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
-        const int64_t i = list[t];
-        const double Tv = (double)T[i], pv = (double)p[i];
-        prk::Comp<double, NS> c;
-        double ysum = 0, s = 0;
-        bool ok = (Tv > 0) && (pv > 0) && isfinite(Tv) && isfinite(pv);
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            const double y = (k < N) ? (double)Y[(int64_t)k * ldY + i] : 0.0;
-            ok = ok && (y >= 0) && isfinite(y);
-            ysum += y;
-            c.x[k] = y * s_sp[k].inv_W;
-            s += c.x[k];
-        }
-        ok = ok && fabs(ysum - 1.0) <= 1e-6 && s > 0;
-        const double is = 1.0 / s;
-        double bm = 0;
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            c.x[k] *= is;
-            bm = fma(c.x[k], s_sp[k].b, bm);
-        }
-        c.Wbar = is;
-        c.bm = bm;
-        float o[6];
-        for (int q = 0; q < 6; ++q) o[q] = __int_as_float(0x7fc00000);
-        if (ok) {
-            prk::Thermo<double> th;
-            prk::thermo<double, double, NS, KIJ>(c, Tv, pv, s_sp, s_kij, th);
-            if (th.status != prk::kNoRoot) {
-                double mu, lam;
-                prk::transport<double, NS>(c, Tv, th, s_sp, s_pair, flags, mu, lam);
-                o[0] = (float)(pv * c.Wbar / (th.Z * prk::kR * Tv));
-                o[1] = (float)th.Z;
-                o[2] = (float)th.h;
-                o[3] = (float)th.cp;
-                o[4] = (float)mu;
-                o[5] = (float)lam;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) out[(int64_t)q * ldo + i] = o[q];
-    }
-}
-
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current).
-pr_status scratch_on_current_device(void **ptr)
-{
-    int dev = -1;
-    PR_CUDA_TRY(cudaGetDevice(&dev));
-    PR_CHECK_ARG(dev >= 0 && dev < kNoallocMaxDevices, "pr_fallback_props_noalloc: device %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            prgb::set_error("pr_fallback_props_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            return PR_ECUDA;
-        }
-        g_scratch_ptr[dev] = p;
-    }
-    *ptr = g_scratch_ptr[dev];
-    return PR_OK;
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x)
+        prk::fallback_cell_fp64<NS, KIJ>(list[t], T, p, Y, ldY, out, ldo, s_sp, s_pair, s_kij, N, flags);
 }
 
 template <int NS, bool KIJ>
@@ -140,6 +71,26 @@ void launch_noalloc(const pr_ctx *ctx, const int32_t *list, const unsigned int *
 }
 
 }  // namespace
+
+namespace prgb {
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, never a device address, so
+// the address is looked up here, once per context, by pr_create (with the
+// context's device current) and kept in the context.
+pr_status noalloc_scratch_address(void **ptr)
+{
+    *ptr = nullptr;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();   // not left for a later launch check to report
+        set_error("cudaGetSymbolAddress of the allocation-free scratch failed: %s", cudaGetErrorString(e));
+        return PR_ECUDA;
+    }
+    *ptr = p;
+    return PR_OK;
+}
+}  // namespace prgb
 
 extern "C" pr_status pr_fallback_props_noalloc(pr_ctx *ctx, int64_t n, const float *T, const float *p,
                                                const float *Y, int64_t ldY, const uint8_t *mask, float *out,
@@ -155,9 +106,19 @@ extern "C" pr_status pr_fallback_props_noalloc(pr_ctx *ctx, int64_t n, const flo
     PR_CHECK_ARG(ldY >= n && ldo >= n, "pr_fallback_props_noalloc: ldY/ldo < n");
     PR_CHECK_ARG(prgb::aligned(T, 4) && prgb::aligned(p, 4) && prgb::aligned(Y, 4) && prgb::aligned(out, 4),
                  "pr_fallback_props_noalloc: misaligned array");
-    void *scratch = nullptr;
-    pr_status s = scratch_on_current_device(&scratch);
-    if (s) return s;
+    // the context's tables live on its device, and the scratch address was
+    // taken there: another current device would read memory it cannot reach
+    int dev = -1;
+    PR_CUDA_TRY(cudaGetDevice(&dev));
+    PR_CHECK_ARG(dev == ctx->device,
+                 "pr_fallback_props_noalloc: the current device (%d) is not the context's device (%d)", dev,
+                 ctx->device);
+    void *scratch = ctx->noalloc_scratch;
+    if (!scratch) {
+        prgb::set_error("pr_fallback_props_noalloc: the scratch address could not be looked up when the context "
+                        "was created");
+        return PR_ECUDA;
+    }
     unsigned int *count = reinterpret_cast<unsigned int *>(scratch);
     int32_t *list = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(scratch) + kCounterBytes);
     cudaStream_t st = (cudaStream_t)stream;

@@ -221,6 +221,12 @@ pr_status pr_create(const pr_species_table *tbl, pr_ctx **out)
     fill_occ<double, double>(NS, c->occ_props[PR_FP64], c->occ_newton[PR_FP64]);
     fill_occ<float, float>(NS, c->occ_props[PR_FP32], c->occ_newton[PR_FP32]);
     fill_occ<float, double>(NS, c->occ_props[PR_MIXED], c->occ_newton[PR_MIXED]);
+    // with the context's device current; a failed lookup only disables
+    // pr_fallback_props_noalloc (which then reports it)
+    if (prgb::noalloc_scratch_address(&c->noalloc_scratch) != PR_OK) {
+        c->noalloc_scratch = nullptr;
+        prgb::set_error("");
+    }
     *out = c;
     return PR_OK;
 }

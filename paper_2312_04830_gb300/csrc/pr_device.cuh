@@ -596,4 +596,59 @@ __device__ __forceinline__ void transport(const Comp<Real, NS> &c, Real T, const
     chung_dense<Real>(Tcm, Vcm, sm * Real(1.0 / 0.809), wm, Mm, mur4, km, T, th.rho_mol, th.cv_ig_molar, mu, lam);
 }
 
+// FP64 properties of cell i from FP32 inputs, written as FP32 to
+// out[q * ldo + i] (q = rho, Z, h, cp, mu, lambda): the Peng-Robinson step
+// that replaces the surrogate on a flagged cell.  Inputs are validated as
+// load_comp does (positive finite T and p, non-negative finite Y, |sum Y - 1|
+// <= 1e-6); a bad input or a cubic without a root Z > B gives NaN outputs.
+// sp, pair and kij are the shared-memory copies of the context's tables.
+template <int NS, bool KIJ>
+__device__ __forceinline__ void fallback_cell_fp64(int64_t i, const float *__restrict__ T,
+                                                   const float *__restrict__ p, const float *__restrict__ Y,
+                                                   int64_t ldY, float *out, int64_t ldo, const SpeciesRec<double> *sp,
+                                                   const double *pair, const double *kij, int N, int flags)
+{
+    const double Tv = (double)__ldg(T + i), pv = (double)__ldg(p + i);
+    Comp<double, NS> c;
+    double ysum = 0, s = 0;
+    bool ok = (Tv > 0) && (pv > 0) && isfinite(Tv) && isfinite(pv);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const double y = (k < N) ? (double)__ldg(Y + (int64_t)k * ldY + i) : 0.0;
+        ok = ok && (y >= 0) && isfinite(y);
+        ysum += y;
+        c.x[k] = y * sp[k].inv_W;
+        s += c.x[k];
+    }
+    ok = ok && fabs(ysum - 1.0) <= 1e-6 && s > 0;
+    const double is = 1.0 / s;
+    double bm = 0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        c.x[k] *= is;
+        bm = fma(c.x[k], sp[k].b, bm);
+    }
+    c.Wbar = is;
+    c.bm = bm;
+    float o[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) o[q] = __int_as_float(0x7fc00000);
+    if (ok) {
+        Thermo<double> th;
+        thermo<double, double, NS, KIJ>(c, Tv, pv, sp, kij, th);
+        if (th.status != kNoRoot) {
+            double mu, lam;
+            transport<double, NS>(c, Tv, th, sp, pair, flags, mu, lam);
+            o[0] = (float)(pv * c.Wbar / (th.Z * kR * Tv));
+            o[1] = (float)th.Z;
+            o[2] = (float)th.h;
+            o[3] = (float)th.cp;
+            o[4] = (float)mu;
+            o[5] = (float)lam;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) out[(int64_t)q * ldo + i] = o[q];
+}
+
 }  // namespace prk

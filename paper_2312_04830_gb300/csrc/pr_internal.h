@@ -66,12 +66,17 @@ struct pr_ctx {
     double *d_bilger64;
     float *d_bilger32;
     int has_bilger;
+    // device address of the allocation-free entry point's scratch array on
+    // this context's device (noalloc.cu), or NULL if the lookup failed
+    void *noalloc_scratch;
 };
 
 namespace prgb {
 // Build / release the per-species tables of a context (pr_species.cu).
 pr_status species_tables_init(pr_ctx *c, const pr_species_table *tbl);
 void species_tables_free(pr_ctx *c);
+// Device address of the allocation-free scratch array on the current device (noalloc.cu).
+pr_status noalloc_scratch_address(void **ptr);
 }  // namespace prgb
 
 // SG_MODE_FORWARD, SG_MODE_INVERSE or SG_MODE_BILGER of a surrogate (surrogate.cu).

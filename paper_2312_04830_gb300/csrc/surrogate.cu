@@ -491,42 +491,8 @@ __global__ void __launch_bounds__(128) fallback_kernel(const int32_t *list, cons
     }
     __syncthreads();
     const unsigned int n = *count;
-    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const int64_t i = r0 + list[t];
-        const double Tv = (double)__ldg(T + i), pv = (double)__ldg(p + i);
-        prk::Comp<double, NS> c;
-        double ysum = 0, s = 0;
-        bool ok = (Tv > 0) && (pv > 0) && isfinite(Tv) && isfinite(pv);
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            const double y = (k < N) ? (double)__ldg(Y + (int64_t)k * ldY + i) : 0.0;
-            ok = ok && (y >= 0) && isfinite(y);
-            ysum += y;
-            c.x[k] = y * s_sp[k].inv_W;
-            s += c.x[k];
-        }
-        ok = ok && fabs(ysum - 1.0) <= 1e-6 && s > 0;
-        const double is = 1.0 / s;
-        double bm = 0;
-#pragma unroll
-        for (int k = 0; k < NS; ++k) { c.x[k] *= is; bm = fma(c.x[k], s_sp[k].b, bm); }
-        c.Wbar = is;
-        c.bm = bm;
-        float o[6];
-        for (int q = 0; q < 6; ++q) o[q] = __int_as_float(0x7fc00000);
-        if (ok) {
-            prk::Thermo<double> th;
-            prk::thermo<double, double, NS, KIJ>(c, Tv, pv, s_sp, s_kij, th);
-            if (th.status != prk::kNoRoot) {
-                double mu, lam;
-                prk::transport<double, NS>(c, Tv, th, s_sp, s_pair, flags, mu, lam);
-                o[0] = (float)(pv * c.Wbar / (th.Z * prk::kR * Tv));
-                o[1] = (float)th.Z; o[2] = (float)th.h; o[3] = (float)th.cp; o[4] = (float)mu; o[5] = (float)lam;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) out[(int64_t)q * ldo + i] = o[q];
-    }
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        prk::fallback_cell_fp64<NS, KIJ>(r0 + list[t], T, p, Y, ldY, out, ldo, s_sp, s_pair, s_kij, N, flags);
 }
 
 // FP64 Peng-Robinson fallback of the inverse model for the listed cells: the
