@@ -54,6 +54,10 @@ TRAFFIC_BYTES_PER_CELL = {"props_fp64": 126.2, "newton_fp64": 107.6,
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
 
+# relative tolerance of the surrogates' transport test (mu, lambda against
+# Chung's correlation at the network's own density; beyond it: FP64 fallback)
+TRANSPORT_CONFIDENCE = 0.02
+
 # rows per surrogate inference chunk: all layers of a chunk run in one
 # persistent launch, activations in L2-resident rings
 SG_CHUNK = 1 << 22
@@ -284,9 +288,11 @@ def train_surrogate(ctx, dev, args):
     sg.close()
     sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=SG_CHUNK)
     sg.fit_normalization(x, y)
-    # low-confidence cells (predicted rho and Z off the equation of state by more than 1 %)
-    # take the FP64 fallback like cells outside the training hull
+    # low-confidence cells take the FP64 fallback like cells outside the training hull:
+    # predicted rho and Z off the equation of state by more than 1 %, or mu or lambda
+    # more than 2 % away from Chung's correlation at the network's own density
     sg.set_confidence(0.01)
+    sg.set_transport_confidence(TRANSPORT_CONFIDENCE)
     steps = args.sg_steps if args.sg_steps > 0 else int(round(args.sg_epochs * x.shape[1] / 65536))
     losses, secs = TR.train(sg, x, y, steps, 65536, 1e-3, log_every=max(1, steps // 10))
     sg.sync_status()
@@ -303,6 +309,7 @@ def train_surrogate(ctx, dev, args):
     del Tp, pp, Yp
     sgi = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=65536, infer_chunk=SG_CHUNK)
     sgi.set_mode("inverse")
+    sgi.set_transport_confidence(TRANSPORT_CONFIDENCE)
     sgi.fit_normalization(x, y)
     steps_i = args.sg_steps if args.sg_steps > 0 else int(round(args.sg_epochs * x.shape[1] / 65536))
     losses_i, secs_i = TR.train(sgi, x, y, steps_i, 65536, 1e-3, log_every=max(1, steps_i // 10))
@@ -438,7 +445,7 @@ def run_ours(args):
         # the inverse model: h*, p, Y -> T, rho, psi, mu, alpha, cp (the paper's arrangement)
         paths.append("surrogate_inverse_bf16")
         calls["surrogate_inverse_bf16"] = lambda: sgi.infer(hi32, p32, Y32, out=outsi, used_fallback=fbi)
-        launches["surrogate_inverse_bf16"] = n_chunks * (1 + 1 + 1)
+        launches["surrogate_inverse_bf16"] = n_chunks * (1 + 1 + 1 + 1)   # prep, fused MLP, transport test, fallback
     launches_per_step = sum(launches.values())
 
     def step(ev=None):

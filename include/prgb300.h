@@ -56,10 +56,11 @@ typedef int pr_status;
 #define PR_CELL_AMBIGUOUS   5  /* two physical roots with |Delta g_res| < 1e-9 (larger Z kept) */
 
 /* PR_MIXED: FP32 arithmetic throughout, FP64 for the cubic's root selection:
- * a cell whose FP32 cubic has one physical root, clear of the three-root
- * boundary (discriminant above 1e-4 of its terms' scale), keeps that root;
- * cells with several physical roots (the residual-Gibbs choice between them)
- * or a near-degenerate cubic are solved and selected in FP64. */
+ * a cell whose FP32 cubic has one physical root, with the root count settled
+ * by margins FP32 rounding cannot close (|discriminant| above 1e-4 of its
+ * terms' scale, every other real root below 0.999 B), keeps that root; cells
+ * with several physical roots (the residual-Gibbs choice between them) or a
+ * near-degenerate cubic are solved and selected in FP64. */
 typedef enum { PR_FP64 = 0, PR_FP32 = 1, PR_MIXED = 2 } pr_precision;
 
 /* Flags of pr_species_table.flags */
@@ -340,6 +341,15 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * a cell with |rho Z R T / (p W) - 1| above the tolerance takes the FP64
  * fallback like a cell outside the hull (and is flagged in used_fallback). */
 #define SG_OPT_CONFIDENCE_PPM 6
+/* SG_OPT_TRANSPORT_CONFIDENCE_PPM: low-confidence test of the property models'
+ * transport outputs, in parts per million (0: off).  Chung's correlation
+ * (Sec. 2) is evaluated in FP32 at the network's own density -- and, for the
+ * inverse and Bilger models, its own temperature -- and the cell's
+ * composition; a cell whose predicted mu or lambda (inverse models: alpha cp)
+ * differs from those values by more than the tolerance takes the FP64
+ * fallback like a cell outside the hull (flagged in used_fallback).  No effect
+ * on the per-species networks. */
+#define SG_OPT_TRANSPORT_CONFIDENCE_PPM 8
 /* SG_OPT_OUTPUTS (the paper's per-species networks, Sec. 4.1): with
  * SG_MODE_INVERSE or SG_MODE_BILGER inputs, the network predicts
  *   SG_OUT_PROPS  (default) T, rho, psi, mu, alpha, cp;

@@ -62,7 +62,7 @@ class Diag(ctypes.Structure):
                 ("cond", ctypes.c_double), ("h_ig", ctypes.c_double), ("cp_ig", ctypes.c_double),
                 ("cv_ig_molar", ctypes.c_double), ("h_dep", ctypes.c_double), ("cp_dep", ctypes.c_double),
                 ("dpdT", ctypes.c_double), ("dpdV", ctypes.c_double), ("mu_dilute", ctypes.c_double),
-                ("lambda_dilute", ctypes.c_double)]
+                ("lambda_dilute", ctypes.c_double), ("cancel_mu", ctypes.c_double), ("cancel_lam", ctypes.c_double)]
 
 
 def lib():
@@ -79,6 +79,8 @@ def lib():
             L.orc_h_ideal.restype = None
             L.orc_diagnose.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
             L.orc_diagnose.restype = None
+            L.orc_props_at_Z.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+            L.orc_props_at_Z.restype = None
             L.orc_T_from_h.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32]
             L.orc_T_from_h.restype = None
             L.orc_cubic_real_roots.argtypes = [d, d, d, vp]
@@ -165,6 +167,19 @@ def h_ideal(sp, T, Y, **kw):
     h = np.empty(T.size)
     lib().orc_h_ideal(tb.ref, T.size, _ptr(T), _ptr(Y), _ptr(h))
     return h
+
+
+def props_at_Z(sp, T, p, Y, Z, **kw):
+    """(out[6, n], status[n]) with the root Z[i] in place of the selected one:
+    the derived outputs as functions of the root (a test aid)."""
+    tb = sp if isinstance(sp, Table) else Table(sp, **kw)
+    T, p, Y = _soa(T, p, Y, tb.n)
+    n = T.size
+    Z = np.ascontiguousarray(np.broadcast_to(Z, (n,)), dtype=np.float64)
+    out = np.empty((6, n))
+    st = np.empty(n, dtype=np.int32)
+    lib().orc_props_at_Z(tb.ref, n, _ptr(T), _ptr(p), _ptr(Y), _ptr(Z), _ptr(out), _ptr(st))
+    return out, st
 
 
 def diagnose(sp, T, p, Y, **kw):

@@ -83,6 +83,11 @@ typedef struct {
     double h_dep, cp_dep;        /* J/mol, J/(mol K) */
     double dpdT, dpdV;           /* (dp/dT)_V, (dp/dV)_T */
     double mu_dilute, lambda_dilute; /* Pa s, W/(m K): the y -> 0 limit of the dense forms */
+    /* cancellation ratios sum|t_i| / |sum t_i| of the sums in Chung's dense
+     * viscosity (G2's numerator and denominator, 1/G2 + E6 y, the two eta*
+     * terms) and conductivity (the same of H2, 1/H2 + B6 y, the two lambda
+     * terms): the factor by which rounding errors of the terms grow in them */
+    double cancel_mu, cancel_lam;
 } orc_diag;
 
 enum { ORC_OK = 0, ORC_NEWTON_MAXIT = 1, ORC_H_OUT_OF_RANGE = 2, ORC_NO_ROOT = 3,
@@ -252,8 +257,14 @@ typedef struct {
 /* Chung dense-fluid viscosity [Pa s] and conductivity [W/(m K)] of a fluid
  * with corresponding-states parameters cs at temperature T, molar density
  * rho_mol [mol/m^3] and ideal-gas molar cv (for the conductivity). */
+/* sum|t_i| / |sum t_i| of a three-term sum (1 without cancellation) */
+static double cancel3(double a, double b, double c)
+{
+    return (fabs(a) + fabs(b) + fabs(c)) / fabs(a + b + c);
+}
+
 static void chung_dense(const chung_cs *cs, double T, double rho_mol, double cv_molar,
-                        double *mu, double *lam, double *mu0, double *lam0)
+                        double *mu, double *lam, double *mu0, double *lam0, double *cmu, double *clam)
 {
     double Ts = 1.2593 * T / cs->Tc;
     double Fc = 1.0 - 0.2756 * cs->omega + 0.059035 * cs->mur4 + cs->kappa;
@@ -291,13 +302,27 @@ static void chung_dense(const chung_cs *cs, double T, double rho_mol, double cv_
     double q = 3.586e-3 * sqrt(cs->Tc / Mkg) / Vc23;
     *lam = 31.2 * eta0 * Psi / Mkg * (1.0 / H2 + Bc[5] * y) + q * Bc[6] * y * y * sqrt(Tr) * H2;
     *lam0 = 31.2 * eta0 * Psi / Mkg;
+    if (cmu) {
+        double c = cancel3(E[0] * fy4, E[1] * G1 * exp(E[4] * y), E[2] * G1);
+        c = fmax(c, cancel3(E[0] * E[3], E[1], E[2]));
+        c = fmax(c, cancel3(1.0 / G2, E[5] * y, 0.0));
+        c = fmax(c, cancel3(sqrt(Ts) / Ov * Fc * (1.0 / G2 + E[5] * y), etass, 0.0));
+        *cmu = c;
+    }
+    if (clam) {
+        double c = cancel3(Bc[0] * fyb4, Bc[1] * G1 * exp(Bc[4] * y), Bc[2] * G1);
+        c = fmax(c, cancel3(Bc[0] * Bc[3], Bc[1], Bc[2]));
+        c = fmax(c, cancel3(1.0 / H2, Bc[5] * y, 0.0));
+        c = fmax(c, cancel3(31.2 * eta0 * Psi / Mkg * (1.0 / H2 + Bc[5] * y), q * Bc[6] * y * y * sqrt(Tr) * H2, 0.0));
+        *clam = c;
+    }
 }
 
 /* ---------------------------------------------------------------------- */
 /* Thermodynamic part of one cell: everything up to h and cp.  Returns the
  * status (0, 3, 4 or 5).  Output arrays may be NULL except d. */
 static int cell_thermo(const orc_species *sp, double T, double p, const double *Y, ptrdiff_t ystride,
-                       double *X, orc_diag *d)
+                       double *X, orc_diag *d, const double *Z_given)
 {
     const int N = sp->N;
     memset(d, 0, sizeof(*d));
@@ -371,6 +396,9 @@ static int cell_thermo(const orc_species *sp, double T, double p, const double *
     d->gres_gap = (nphys > 1) ? fabs(gsecond - gbest) : INFINITY;
     if (nphys == 0) return ORC_NO_ROOT;
     double Z = best;
+    /* a caller-given Z in place of the selected root: the derived outputs as
+     * functions of Z (their sensitivity to the root, for the tests) */
+    if (Z_given) Z = *Z_given;
     d->Z = Z;
     {
         double dP = (3.0 * Z + 2.0 * c2) * Z + c1;
@@ -407,8 +435,10 @@ static int cell_thermo(const orc_species *sp, double T, double p, const double *
 
 /* Chung transport for a thermodynamic state already evaluated. */
 static void cell_transport(const orc_species *sp, double T, double p, const double *X, const orc_diag *d,
-                           double *mu, double *lam, double *mu0, double *lam0)
+                           double *mu, double *lam, double *mu0, double *lam0, double *cmu, double *clam)
 {
+    if (cmu) *cmu = 1.0;
+    if (clam) *clam = 1.0;
     const int N = sp->N;
     double rho_mol = p / (d->Z * ORC_R * T);            /* mol/m^3 */
     if (sp->transport_rule == 1) {
@@ -420,8 +450,11 @@ static void cell_transport(const orc_species *sp, double T, double p, const doub
             double mur = 131.3 * sp->dipole[k] / sqrt(sp->Vc[k] * sp->Tc[k]);
             cs.mur4 = mur * mur * mur * mur; cs.kappa = sp->kappa[k];
             double mk, lk, m0k, l0k;
-            chung_dense(&cs, T, rho_mol, d->cv_ig_molar, &mk, &lk, &m0k, &l0k);
+            double cmk, clk;
+            chung_dense(&cs, T, rho_mol, d->cv_ig_molar, &mk, &lk, &m0k, &l0k, &cmk, &clk);
             m += X[k] * mk; l += X[k] * lk; m0 += X[k] * m0k; l0 += X[k] * l0k;
+            if (cmu) *cmu = fmax(*cmu, cmk);
+            if (clam) *clam = fmax(*clam, clk);
         }
         *mu = m; *lam = l; *mu0 = m0; *lam0 = l0;
         return;
@@ -461,17 +494,18 @@ static void cell_transport(const orc_species *sp, double T, double p, const doub
     double mum = sqrt(sqrt(mum4));
     double mur = 131.3 * mum / sqrt(cs.Vc * cs.Tc);
     cs.mur4 = mur * mur * mur * mur;
-    chung_dense(&cs, T, rho_mol, d->cv_ig_molar, mu, lam, mu0, lam0);
+    chung_dense(&cs, T, rho_mol, d->cv_ig_molar, mu, lam, mu0, lam0, cmu, clam);
 }
 
-/* One cell, all outputs.  out = {rho, Z, h, cp, mu, lambda}. */
-int orc_cell(const orc_species *sp, double T, double p, const double *Y, ptrdiff_t ystride,
-             double out[6], orc_diag *diag)
+/* One cell, all outputs.  out = {rho, Z, h, cp, mu, lambda}.  Z_given (NULL
+ * for the method itself) replaces the selected root. */
+static int orc_cell_z(const orc_species *sp, double T, double p, const double *Y, ptrdiff_t ystride,
+                      double out[6], orc_diag *diag, const double *Z_given)
 {
     double X[64];
     orc_diag dl;
     orc_diag *d = diag ? diag : &dl;
-    int st = cell_thermo(sp, T, p, Y, ystride, X, d);
+    int st = cell_thermo(sp, T, p, Y, ystride, X, d, Z_given);
     if (st != ORC_OK && st != ORC_AMBIGUOUS) {
         for (int q = 0; q < 6; ++q) out[q] = NAN;
         return st;
@@ -482,9 +516,30 @@ int orc_cell(const orc_species *sp, double T, double p, const double *Y, ptrdiff
     out[2] = d->h_ig + d->h_dep / d->Wbar;
     out[3] = d->cp_ig + d->cp_dep / d->Wbar;
     double mu0, lam0;
-    cell_transport(sp, T, p, X, d, &out[4], &out[5], &mu0, &lam0);
+    cell_transport(sp, T, p, X, d, &out[4], &out[5], &mu0, &lam0, &d->cancel_mu, &d->cancel_lam);
     d->mu_dilute = mu0; d->lambda_dilute = lam0;
     return st;
+}
+
+int orc_cell(const orc_species *sp, double T, double p, const double *Y, ptrdiff_t ystride,
+             double out[6], orc_diag *diag)
+{
+    return orc_cell_z(sp, T, p, Y, ystride, out, diag, NULL);
+}
+
+/* The outputs of n cells with the root Z[i] substituted for the selected one
+ * (out[6*n] as orc_props; status as orc_props').  A test aid: how the derived
+ * outputs move with the root, at the oracle's own root and near it. */
+void orc_props_at_Z(const orc_species *sp, int64_t n, const double *T, const double *p, const double *Y,
+                    const double *Z, double *out, int32_t *status)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double o[6];
+        orc_diag d;
+        int st = orc_cell_z(sp, T[i], p[i], Y + i, (ptrdiff_t)n, o, &d, &Z[i]);
+        for (int q = 0; q < 6; ++q) out[q * n + i] = o[q];
+        if (status) status[i] = st;
+    }
 }
 
 /* Batch over n cells, SoA: T[n], p[n], Y[N*n] species-major; out[6*n] as
@@ -740,7 +795,7 @@ static int cell_h(const orc_species *sp, double T, double p, const double *Y, pt
 {
     double X[64];
     orc_diag d;
-    int st = cell_thermo(sp, T, p, Y, ys, X, &d);
+    int st = cell_thermo(sp, T, p, Y, ys, X, &d, NULL);
     if (st != ORC_OK && st != ORC_AMBIGUOUS) return st;
     *h = d.h_ig + d.h_dep / d.Wbar;
     *cp = d.cp_ig + d.cp_dep / d.Wbar;

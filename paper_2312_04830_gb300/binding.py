@@ -292,6 +292,7 @@ SG_OPT_WAIT_LIMIT_KCYCLES, SG_OPT_TEST_STALL = 3, 4
 SG_OPT_LOSS, SG_LOSS_REL_MSE, SG_LOSS_L1 = 5, 0, 1
 SG_OPT_CONFIDENCE_PPM = 6
 SG_OPT_OUTPUTS, SG_OUT_PROPS, SG_OUT_DK, SG_OUT_HK = 7, 0, 1, 2
+SG_OPT_TRANSPORT_CONFIDENCE_PPM = 8
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
@@ -397,6 +398,14 @@ class Surrogate:
         equation of state (|rho Z R T / (p W) - 1| > tol) take the FP64
         fallback; 0 turns the test off."""
         check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_CONFIDENCE_PPM, int(round(tol * 1e6))),
+              "surrogate_set_option")
+
+    def set_transport_confidence(self, tol: float):
+        """Property models: cells whose predicted mu or lambda differ by more
+        than tol (relative) from Chung's correlation evaluated at the
+        network's own density (and temperature, for the inverse models) take
+        the FP64 fallback; 0 turns the test off."""
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_TRANSPORT_CONFIDENCE_PPM, int(round(tol * 1e6))),
               "surrogate_set_option")
 
     def set_wait_limit(self, kcycles: int):

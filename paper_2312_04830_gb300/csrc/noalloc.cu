@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(128) noalloc_props_kernel(const int32_t *list,
                                                             const float *T, const float *p, const float *Y,
                                                             int64_t ldY, float *out, int64_t ldo,
                                                             const SpeciesRec<double> *sp, const double *pair,
-                                                            const double *kij, int N, int flags)
+                                                            const double *kij, int N, int flags, double tmid_u)
 {
     __shared__ SpeciesRec<double> s_sp[NS];
     __shared__ double s_pair[NS * NS];
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(128) noalloc_props_kernel(const int32_t *list,
     __syncthreads();
     const unsigned int m = *count;
     for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x)
-        prk::fallback_cell_fp64<NS, KIJ>(list[t], T, p, Y, ldY, out, ldo, s_sp, s_pair, s_kij, N, flags);
+        prk::fallback_cell_fp64<NS, KIJ>(list[t], T, p, Y, ldY, out, ldo, s_sp, s_pair, s_kij, N, flags, tmid_u);
 }
 
 template <int NS, bool KIJ>
@@ -67,7 +67,7 @@ void launch_noalloc(const pr_ctx *ctx, const int32_t *list, const unsigned int *
 {
     noalloc_props_kernel<NS, KIJ><<<ctx->num_sms * 4, 128, 0, st>>>(
         list, count, T, p, Y, ldY, out, ldo, (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64,
-        ctx->n_species, ctx->flags);
+        ctx->n_species, ctx->flags, ctx->tmid_u);
 }
 
 }  // namespace

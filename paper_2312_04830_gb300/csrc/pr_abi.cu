@@ -207,6 +207,24 @@ pr_status pr_create(const pr_species_table *tbl, pr_ctx **out)
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && NS == 9) {
+        HostTab9<double> *t64 = new (std::nothrow) HostTab9<double>();
+        HostTab9<float> *t32 = new (std::nothrow) HostTab9<float>();
+        c->h_tab64 = t64;
+        c->h_tab32 = t32;
+        if (!t64 || !t32) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMemcpy(t64->sp, c->d_sp64, sizeof(t64->sp), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(t64->pair, c->d_pair64, sizeof(t64->pair), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(t64->kij, c->d_kij64, sizeof(t64->kij), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(t32->sp, c->d_sp32, sizeof(t32->sp), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(t32->pair, c->d_pair32, sizeof(t32->pair), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(t32->kij, c->d_kij32, sizeof(t32->kij), cudaMemcpyDeviceToHost);
+    }
+    // one NASA-7 switch temperature for every species: the ideal-gas sums then
+    // take one range test per cell
+    c->tmid_u = h->T_mid[0] > 0 ? h->T_mid[0] : 0.0;
+    for (int k = 1; k < N; ++k)
+        if (h->T_mid[k] != h->T_mid[0]) c->tmid_u = 0.0;
     if (d_tab) cudaFree(d_tab);
     delete h;
     if (e != cudaSuccess) {
@@ -242,6 +260,8 @@ void pr_destroy(pr_ctx *c)
     cudaFree(c->d_kij64);
     cudaFree(c->d_kij32);
     prgb::species_tables_free(c);
+    delete static_cast<HostTab9<double> *>(c->h_tab64);
+    delete static_cast<HostTab9<float> *>(c->h_tab32);
     delete c;
 }
 
@@ -277,20 +297,20 @@ static pr_status props_impl(pr_ctx *ctx, pr_precision prec, int64_t n, const voi
         PropsArgs<double> a{n, ldY, (const double *)T, (const double *)p, (const double *)Y, (double *)rho,
                             (double *)Z, (double *)h, (double *)cp, (double *)mu, (double *)lambda, cell_status,
                             (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64,
-                            ctx->n_species, ctx->flags, (double *)psi, (double *)alpha};
-        if (ctx->ns_pad == 9) launch_props<double, double, 9>(a, kij, occ, ctx->num_sms, st);
-        else launch_props<double, double, 32>(a, kij, occ, ctx->num_sms, st);
+                            ctx->n_species, ctx->flags, (double *)psi, (double *)alpha, ctx->tmid_u};
+        if (ctx->ns_pad == 9) launch_props<double, double, 9>(a, ctx->h_tab64, kij, occ, ctx->num_sms, st);
+        else launch_props<double, double, 32>(a, nullptr, kij, occ, ctx->num_sms, st);
     } else {
         PropsArgs<float> a{n, ldY, (const float *)T, (const float *)p, (const float *)Y, (float *)rho,
                            (float *)Z, (float *)h, (float *)cp, (float *)mu, (float *)lambda, cell_status,
                            (const SpeciesRec<float> *)ctx->d_sp32, ctx->d_pair32, ctx->d_kij32,
-                           ctx->n_species, ctx->flags, (float *)psi, (float *)alpha};
+                           ctx->n_species, ctx->flags, (float *)psi, (float *)alpha, (float)ctx->tmid_u};
         if (prec == PR_FP32) {
-            if (ctx->ns_pad == 9) launch_props<float, float, 9>(a, kij, occ, ctx->num_sms, st);
-            else launch_props<float, float, 32>(a, kij, occ, ctx->num_sms, st);
+            if (ctx->ns_pad == 9) launch_props<float, float, 9>(a, ctx->h_tab32, kij, occ, ctx->num_sms, st);
+            else launch_props<float, float, 32>(a, nullptr, kij, occ, ctx->num_sms, st);
         } else {
-            if (ctx->ns_pad == 9) launch_props<float, double, 9>(a, kij, occ, ctx->num_sms, st);
-            else launch_props<float, double, 32>(a, kij, occ, ctx->num_sms, st);
+            if (ctx->ns_pad == 9) launch_props<float, double, 9>(a, ctx->h_tab32, kij, occ, ctx->num_sms, st);
+            else launch_props<float, double, 32>(a, nullptr, kij, occ, ctx->num_sms, st);
         }
     }
     PR_CUDA_TRY(cudaGetLastError());
@@ -336,7 +356,7 @@ pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n, const void *hst
                              (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64,
                              ctx->n_species, ctx->flags, max_iter, rtol,
                              (const SpeciesRec<float> *)ctx->d_sp32, ctx->d_pair32, ctx->d_kij32,
-                             nullptr, nullptr, nullptr};
+                             nullptr, nullptr, nullptr, ctx->tmid_u};
         if (ctx->ns_pad == 9) launch_newton<double, double, 9>(a, kij, occ, ctx->num_sms, st);
         else launch_newton<double, double, 32>(a, kij, occ, ctx->num_sms, st);
     } else {
@@ -344,7 +364,7 @@ pr_status pr_T_from_h(pr_ctx *ctx, pr_precision prec, int64_t n, const void *hst
                             (float *)T_out, cell_status, iters, (const SpeciesRec<float> *)ctx->d_sp32,
                             ctx->d_pair32, ctx->d_kij32, ctx->n_species, ctx->flags, max_iter, rtol,
                             nullptr, nullptr, nullptr,
-                            (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64};
+                            (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64, ctx->d_kij64, ctx->tmid_u};
         if (prec == PR_FP32) {
             if (ctx->ns_pad == 9) launch_newton<float, float, 9>(a, kij, occ, ctx->num_sms, st);
             else launch_newton<float, float, 32>(a, kij, occ, ctx->num_sms, st);

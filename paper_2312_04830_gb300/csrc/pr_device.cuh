@@ -198,8 +198,11 @@ __device__ __forceinline__ void mix_a(const Comp<Real, NS> &c, Real T, const Spe
         Real a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll 1
         for (int i = 0; i < NS; ++i) {
+            Real xi = 0;   // x_i by selects (no dynamic index into the registers)
+#pragma unroll
+            for (int j = 0; j < NS; ++j) xi = (j == i) ? c.x[j] : xi;
             const Real ui = M<Real>::fma(-sp[i].kq, sqT, Real(1) + sp[i].kappa);
-            const Real gi = c.x[i] * (nonneg(ui) ? sp[i].sqrt_ac : -sp[i].sqrt_ac);
+            const Real gi = xi * (nonneg(ui) ? sp[i].sqrt_ac : -sp[i].sqrt_ac);
             const Real ri = gi * ui, dri = gi * sp[i].kq * h1, d2ri = gi * sp[i].kq * h2;
             Real t0 = 0, t1 = 0;
 #pragma unroll
@@ -238,8 +241,10 @@ __device__ __forceinline__ RZ cubic_polish(RZ z, RZ c2, RZ c1, RZ c0)
     return z;
 }
 
-// *clear (optional): the cubic has a single real root by a margin its
-// rounding cannot close, disc > 1e-4 (hq^2 + |tp^3|).
+// *clear (optional): the count of physical roots is settled by margins its
+// rounding cannot close: the cubic is away from the one-/three-real-root
+// boundary, |disc| > 1e-4 (hq^2 + |tp^3|), and at most one root lies above
+// 0.999 B (the others, if any, below it by more than FP32 rounding moves them).
 template <typename RZ>
 __device__ __forceinline__ int cubic_phys_roots(RZ c2, RZ c1, RZ c0, RZ B, RZ z[3], bool *clear = nullptr)
 {
@@ -248,47 +253,57 @@ __device__ __forceinline__ int cubic_phys_roots(RZ c2, RZ c1, RZ c0, RZ B, RZ z[
     const RZ Q = M<RZ>::fma(c23, M<RZ>::fma(RZ(2) * c23, c23, -c1), c0);
     const RZ hq = RZ(0.5) * Q, tp = P * RZ(1.0 / 3.0);
     const RZ disc = M<RZ>::fma(hq, hq, tp * tp * tp);
-    if (clear) *clear = disc > RZ(1e-4) * (hq * hq + M<RZ>::fabs(tp * tp * tp));
-    float seed[3];
-    int ns;
+    const bool far = M<RZ>::fabs(disc) > RZ(1e-4) * (hq * hq + M<RZ>::fabs(tp * tp * tp));
+    // seeds: one real root (Cardano), or three (trigonometric form, ascending)
+    float seed0, seed1 = 0.f, seed2 = 0.f;
+    bool three = false;
     if (disc > RZ(0)) {
         const float sq = sqrtf((float)disc);
         const float hqf = (float)hq;
         const float u = cbrtf(-hqf - copysignf(sq, hqf));
-        seed[0] = ((u != 0.f) ? (u - (float)P / (3.f * u)) : 0.f) - (float)c23;
-        ns = 1;
+        seed0 = ((u != 0.f) ? (u - (float)P / (3.f * u)) : 0.f) - (float)c23;
     } else {
         const float m = 2.f * sqrtf(fmaxf(-(float)tp, 0.f));
         float arg = (m > 0.f) ? (3.f * (float)Q) / ((float)P * m) : 0.f;
         arg = fminf(1.f, fmaxf(-1.f, arg));
         const float th = acosf(arg) * (1.f / 3.f);
         const float c23f = (float)c23;
-        seed[0] = m * cosf(th + 2.09439510239320f) - c23f;   // smallest
-        seed[1] = m * cosf(th + 4.18879020478639f) - c23f;   // middle
-        seed[2] = m * cosf(th) - c23f;                      // largest
-        ns = 3;
+        seed0 = m * cosf(th + 2.09439510239320f) - c23f;   // smallest
+        seed1 = m * cosf(th + 4.18879020478639f) - c23f;   // middle
+        seed2 = m * cosf(th) - c23f;                      // largest
+        three = true;
     }
-    int n = 0;
-    const float Bf = (float)B;
+    // polish the seeds above B; every array below is indexed by constants
+    // only, so it stays in registers
+    const float Bcut = (float)B * (1.f - 1e-3f);
+    RZ r[3] = {RZ(0), RZ(0), RZ(0)};
+    bool v[3];
+    v[0] = seed0 > Bcut;
+    v[1] = three && seed1 > Bcut;
+    v[2] = three && seed2 > Bcut;
+    if (clear) *clear = far && ((int)v[0] + (int)v[1] + (int)v[2]) <= 1;
+    if (v[0]) r[0] = cubic_polish<RZ>((RZ)seed0, c2, c1, c0);
+    if (v[1]) r[1] = cubic_polish<RZ>((RZ)seed1, c2, c1, c0);
+    if (v[2]) r[2] = cubic_polish<RZ>((RZ)seed2, c2, c1, c0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (k >= ns) break;
-        if (seed[k] <= Bf * (1.f - 1e-3f)) continue;
-        RZ r = cubic_polish<RZ>((RZ)seed[k], c2, c1, c0);
-        if (r > B) {
-            // keep ascending, drop duplicates produced by converging seeds
-            bool dup = false;
-            for (int j = 0; j < n; ++j) dup = dup || (M<RZ>::fabs(r - z[j]) <= RZ(64) * M<RZ>::eps * M<RZ>::fabs(r));
-            if (!dup) z[n++] = r;
-        }
-    }
-    // ascending order (at most three entries)
-    if (n >= 2 && z[1] < z[0]) { RZ t = z[0]; z[0] = z[1]; z[1] = t; }
-    if (n == 3) {
-        if (z[2] < z[1]) { RZ t = z[1]; z[1] = z[2]; z[2] = t; }
-        if (z[1] < z[0]) { RZ t = z[0]; z[0] = z[1]; z[1] = t; }
-    }
-    return n;
+    for (int k = 0; k < 3; ++k) v[k] = v[k] && r[k] > B;
+    // drop duplicates produced by converging seeds (against the roots kept)
+    const RZ dtol = RZ(64) * M<RZ>::eps;
+    if (v[1] && v[0] && M<RZ>::fabs(r[1] - r[0]) <= dtol * M<RZ>::fabs(r[1])) v[1] = false;
+    if (v[2] && ((v[0] && M<RZ>::fabs(r[2] - r[0]) <= dtol * M<RZ>::fabs(r[2])) ||
+                 (v[1] && M<RZ>::fabs(r[2] - r[1]) <= dtol * M<RZ>::fabs(r[2]))))
+        v[2] = false;
+    // ascending, the dropped ones last
+    const RZ big = RZ(3e38);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = v[k] ? r[k] : big;
+    RZ t;
+    if (r[1] < r[0]) { t = r[0]; r[0] = r[1]; r[1] = t; }
+    if (r[2] < r[1]) { t = r[1]; r[1] = r[2]; r[2] = t; }
+    if (r[1] < r[0]) { t = r[0]; r[0] = r[1]; r[1] = t; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) z[k] = r[k];
+    return (int)v[0] + (int)v[1] + (int)v[2];
 }
 
 // Residual Gibbs energy G_res/(RT) of the PR fluid at root Z.
@@ -308,7 +323,9 @@ __device__ __forceinline__ int select_root(const RZ *z, int n, RZ A, RZ B, RZ &Z
     Z = z[0];
     if (n == 1) return kOk;
     RZ gbest = pr_gres<RZ>(z[0], A, B), gsecond = RZ(3e38);
-    for (int k = 1; k < n; ++k) {
+#pragma unroll
+    for (int k = 1; k < 3; ++k) {
+        if (k >= n) break;
         const RZ g = pr_gres<RZ>(z[k], A, B);
         const RZ gap = M<RZ>::fabs(g - gbest);
         if (g < gbest - RZ(1e-12) || (gap <= RZ(1e-12) && z[k] > Z)) {
@@ -330,9 +347,29 @@ struct Thermo {
     int status;
 };
 
+// Mole-weighted NASA-7 coefficient sums of one range: A_j = sum_k x_k R a_j,k
+// (j = 0..4, the cp coefficients) and A5 = sum_k x_k R a_6,k.
+template <typename Real, int NS, bool LO>
+__device__ __forceinline__ void nasa_sums(const Comp<Real, NS> &c, const SpeciesRec<Real> *sp, Real (&A)[5], Real &A5)
+{
+#pragma unroll
+    for (int j = 0; j < 5; ++j) A[j] = Real(0);
+    A5 = Real(0);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const Real *a = LO ? sp[k].cp_lo : sp[k].cp_hi;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) A[j] = M<Real>::fma(c.x[k], a[j], A[j]);
+        A5 = M<Real>::fma(c.x[k], LO ? sp[k].h_lo[5] : sp[k].h_hi[5], A5);
+    }
+}
+
+// tmid_u > 0: every species switches NASA-7 range at tmid_u, so the ideal-gas
+// sums are taken over mole-weighted coefficients (one range test per cell,
+// one polynomial each for cp and h); otherwise species by species.
 template <typename Real, typename RZ, int NS, bool KIJ>
 __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, const SpeciesRec<Real> *sp,
-                                       const Real *kij1m, Thermo<Real> &o)
+                                       const Real *kij1m, Thermo<Real> &o, Real tmid_u = Real(0))
 {
     Real am, dam, d2am;
     mix_a<Real, NS, KIJ>(c, T, sp, kij1m, am, dam, d2am);
@@ -343,10 +380,11 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
     bool need_rz = true;
     if constexpr (!std::is_same<Real, RZ>::value) {
         // Mixed precision: the FP32 cubic decides where FP64 is needed.  A
-        // single physical root clear of the three-root boundary is taken as it
-        // is: its coefficients are FP32 numbers, so an FP64 polish would not
-        // make it more accurate.  Several physical roots (the Gibbs selection
-        // between them) or a near-degenerate cubic go through the FP64 solve.
+        // single physical root, with the root count settled by margins FP32
+        // rounding cannot close (see cubic_phys_roots), is taken as it is: its
+        // coefficients are FP32 numbers, so an FP64 polish would not make it
+        // more accurate.  Several physical roots (the Gibbs selection between
+        // them) or a near-degenerate cubic go through the FP64 solve.
         const Real iRTf = Real(1) / RT;
         const Real Bf = bm * p * iRTf;
         const Real Af = am * p * iRTf * iRTf;
@@ -380,17 +418,28 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
         larg = RZ(2.0 * kSqrt2) * B / (Zz + RZ(1.0 - kSqrt2) * B);
     }
 
-    // ideal-gas part (NASA-7)
+    // ideal-gas part (NASA-7), molar
     Real cp_ig = 0, h_ig = 0;
+    if (tmid_u > Real(0)) {
+        Real A[5], A5;
+        if (lt_pos(T, tmid_u)) nasa_sums<Real, NS, true>(c, sp, A, A5);   // T > 0 here
+        else nasa_sums<Real, NS, false>(c, sp, A, A5);
+        cp_ig = M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(A[4], T, A[3]), T, A[2]), T, A[1]), T, A[0]);
+        // h = sum_j A_j T^(j+1) / (j+1) + A5
+        const Real hp = M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(A[4] * Real(0.2), T, A[3] * Real(0.25)), T,
+                                                                A[2] * Real(1.0 / 3.0)), T, A[1] * Real(0.5)), T, A[0]);
+        h_ig = M<Real>::fma(hp, T, A5);
+    } else {
 #pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        const bool lo = lt_pos(T, sp[k].T_mid);   // T > 0 here
-        const Real *a = lo ? sp[k].cp_lo : sp[k].cp_hi;
-        const Real *e = lo ? sp[k].h_lo : sp[k].h_hi;
-        const Real cpk = M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(a[4], T, a[3]), T, a[2]), T, a[1]), T, a[0]);
-        const Real hk = M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(e[4], T, e[3]), T, e[2]), T, e[1]), T, e[0]), T, e[5]);
-        cp_ig = M<Real>::fma(c.x[k], cpk, cp_ig);     // molar
-        h_ig = M<Real>::fma(c.x[k], hk, h_ig);
+        for (int k = 0; k < NS; ++k) {
+            const bool lo = lt_pos(T, sp[k].T_mid);   // T > 0 here
+            const Real *a = lo ? sp[k].cp_lo : sp[k].cp_hi;
+            const Real *e = lo ? sp[k].h_lo : sp[k].h_hi;
+            const Real cpk = M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(a[4], T, a[3]), T, a[2]), T, a[1]), T, a[0]);
+            const Real hk = M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(M<Real>::fma(e[4], T, e[3]), T, e[2]), T, e[1]), T, e[0]), T, e[5]);
+            cp_ig = M<Real>::fma(c.x[k], cpk, cp_ig);
+            h_ig = M<Real>::fma(c.x[k], hk, h_ig);
+        }
     }
     const Real rWb = Real(1) / (c.Wbar * bm);
     const Real iW = bm * rWb;                                         // 1 / Wbar
@@ -556,12 +605,17 @@ __device__ __forceinline__ void transport(const Comp<Real, NS> &c, Real T, const
         Real m = 0, l = 0;
 #pragma unroll 1
         for (int k = 0; k < NS; ++k) {
-            if (c.x[k] == Real(0)) continue;
+            // x_k by selects over constant indices: a dynamic index would put
+            // the mole fractions of every cell in local memory
+            Real xk = 0;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) xk = (j == k) ? c.x[j] : xk;
+            if (xk == Real(0)) continue;
             Real mk, lk;
             chung_dense<Real>(sp[k].Tc, sp[k].Vc, M<Real>::cbrt(sp[k].Vc), sp[k].omega, sp[k].M, sp[k].mur4,
                               sp[k].kap, T, th.rho_mol, th.cv_ig_molar, mk, lk);
-            m = M<Real>::fma(c.x[k], mk, m);
-            l = M<Real>::fma(c.x[k], lk, l);
+            m = M<Real>::fma(xk, mk, m);
+            l = M<Real>::fma(xk, lk, l);
         }
         mu = m;
         lam = l;
@@ -601,12 +655,15 @@ __device__ __forceinline__ void transport(const Comp<Real, NS> &c, Real T, const
 // that replaces the surrogate on a flagged cell.  Inputs are validated as
 // load_comp does (positive finite T and p, non-negative finite Y, |sum Y - 1|
 // <= 1e-6); a bad input or a cubic without a root Z > B gives NaN outputs.
-// sp, pair and kij are the shared-memory copies of the context's tables.
+// sp, pair and kij are the shared-memory copies of the context's tables;
+// tmid_u its common NASA-7 switch temperature (or 0), as pr_props uses it, so
+// that the cell's values are those of the FP64 property path.
 template <int NS, bool KIJ>
 __device__ __forceinline__ void fallback_cell_fp64(int64_t i, const float *__restrict__ T,
                                                    const float *__restrict__ p, const float *__restrict__ Y,
                                                    int64_t ldY, float *out, int64_t ldo, const SpeciesRec<double> *sp,
-                                                   const double *pair, const double *kij, int N, int flags)
+                                                   const double *pair, const double *kij, int N, int flags,
+                                                   double tmid_u)
 {
     const double Tv = (double)__ldg(T + i), pv = (double)__ldg(p + i);
     Comp<double, NS> c;
@@ -635,7 +692,7 @@ __device__ __forceinline__ void fallback_cell_fp64(int64_t i, const float *__res
     for (int q = 0; q < 6; ++q) o[q] = __int_as_float(0x7fc00000);
     if (ok) {
         Thermo<double> th;
-        thermo<double, double, NS, KIJ>(c, Tv, pv, sp, kij, th);
+        thermo<double, double, NS, KIJ>(c, Tv, pv, sp, kij, th, tmid_u);
         if (th.status != kNoRoot) {
             double mu, lam;
             transport<double, NS>(c, Tv, th, sp, pair, flags, mu, lam);

@@ -66,6 +66,11 @@ struct pr_ctx {
     double *d_bilger64;
     float *d_bilger32;
     int has_bilger;
+    // host images of the 9-species tables (HostTab9<double> / <float>), which
+    // the property kernels take by value; NULL for the 32-species kernels
+    void *h_tab64;
+    void *h_tab32;
+    double tmid_u;       // common NASA-7 switch temperature of every species, or 0
     // device address of the allocation-free entry point's scratch array on
     // this context's device (noalloc.cu), or NULL if the lookup failed
     void *noalloc_scratch;

@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <type_traits>
 
 #include "pr_device.cuh"
@@ -41,6 +42,47 @@ __device__ __forceinline__ void stage(Smem<Real, NS, KIJ> &s, const SpeciesRec<R
     __syncthreads();
 }
 
+// ------------------------------------------------ tables in parameter space
+// The property kernels of up to 9 species take the species records and pair
+// tables by value, in the kernel's parameter space (a constant bank): with
+// the species loops unrolled, every table entry becomes a constant operand of
+// the instruction that uses it, with no load instruction (the shared-memory
+// staging above costs one load per entry and use).  Larger tables (the
+// 32-species kernels) stay in shared memory.
+template <typename Real, int NS, bool KIJ>
+struct ParamTab {
+    SpeciesRec<Real> sp[NS];
+    Real pair[NS * NS];
+    Real kij[KIJ ? NS * NS : 1];
+};
+struct NoTab {
+    int unused;
+};
+template <typename Real, int NS, bool KIJ>
+using TabArg = typename std::conditional<NS == 9, ParamTab<Real, 9, KIJ>, NoTab>::type;
+
+// Host image of a 9-species context's tables (pair and (1 - k_ij) [9][9]).
+template <typename Real>
+struct HostTab9 {
+    SpeciesRec<Real> sp[9];
+    Real pair[81];
+    Real kij[81];
+};
+
+template <typename Real, int NS, bool KIJ>
+inline TabArg<Real, NS, KIJ> make_tab(const void *host)
+{
+    TabArg<Real, NS, KIJ> t;
+    memset(&t, 0, sizeof(t));
+    if constexpr (NS == 9) {
+        const HostTab9<Real> *h = static_cast<const HostTab9<Real> *>(host);
+        memcpy(t.sp, h->sp, sizeof(t.sp));
+        memcpy(t.pair, h->pair, sizeof(t.pair));
+        if (KIJ) memcpy(t.kij, h->kij, sizeof(t.kij));
+    }
+    return t;
+}
+
 // ----------------------------------------------------------- props kernel
 template <typename Real>
 struct PropsArgs {
@@ -52,6 +94,7 @@ struct PropsArgs {
     const Real *pair, *kij;
     int N, flags;
     Real *psi, *alpha;   // (d rho/d p)_h [s^2/m^2], lambda/cp [kg/(m s)]; NULL to skip
+    Real tmid_u;         // common NASA-7 switch temperature of every species, or 0
 };
 
 // psi = (d rho / d p) at constant h (Sec. 4.1) from the EOS partials of the
@@ -71,23 +114,36 @@ __device__ __forceinline__ Real psi_h(const Thermo<Real> &th, Real T, Real W)
 }
 
 template <typename Real, typename RZ, int NS, bool KIJ>
-__global__ void __launch_bounds__(kBlock) props_kernel(const PropsArgs<Real> a)
+__global__ void __launch_bounds__(kBlock) props_kernel(const __grid_constant__ PropsArgs<Real> a,
+                                                       const __grid_constant__ TabArg<Real, NS, KIJ> t)
 {
-    __shared__ Smem<Real, NS, KIJ> s;
-    stage<Real, NS, KIJ>(s, a.sp, a.pair, a.kij);
+    constexpr bool kParam = NS == 9;
+    __shared__ typename std::conditional<kParam, char, Smem<Real, NS, KIJ>>::type s_[1];
+    const SpeciesRec<Real> *sp;
+    const Real *pair, *kij;
+    if constexpr (kParam) {
+        sp = t.sp;
+        pair = t.pair;
+        kij = t.kij;
+    } else {
+        stage<Real, NS, KIJ>(s_[0], a.sp, a.pair, a.kij);
+        sp = s_[0].sp;
+        pair = s_[0].pair;
+        kij = s_[0].kij;
+    }
     const bool want_tr = (a.mu != nullptr) || (a.lam != nullptr) || (a.alpha != nullptr);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         const Real T = __ldg(a.T + i), p = __ldg(a.p + i);
         Comp<Real, NS> c;
-        bool ok = load_comp<Real, NS>(c, a.Y, a.ldY, i, a.N, s.sp);
+        bool ok = load_comp<Real, NS>(c, a.Y, a.ldY, i, a.N, sp);
         ok = ok && (T > Real(0)) && (p > Real(0)) && M<Real>::finite(T) && M<Real>::finite(p);
         Thermo<Real> th;
         th.status = kBadInput;
         Real mu = M<Real>::nan(), lam = M<Real>::nan();
         if (ok) {
-            thermo<Real, RZ, NS, KIJ>(c, T, p, s.sp, s.kij, th);
-            if (th.status != kNoRoot && want_tr) transport<Real, NS>(c, T, th, s.sp, s.pair, a.flags, mu, lam);
+            thermo<Real, RZ, NS, KIJ>(c, T, p, sp, kij, th, a.tmid_u);
+            if (th.status != kNoRoot && want_tr) transport<Real, NS>(c, T, th, sp, pair, a.flags, mu, lam);
         }
         const bool good = ok && th.status != kNoRoot;
         const Real nanv = M<Real>::nan();
@@ -120,15 +176,16 @@ struct NewtonArgs {
     // FP64 tables for the FP64 re-solve of the mixed inversion (mixed kernel only)
     const SpeciesRec<double> *sp64;
     const double *pair64, *kij64;
+    double tmid_u;   // common NASA-7 switch temperature of every species, or 0
 };
 
 // h(T) and cp(T) of a cell at fixed p and composition; status 0 or an error.
 template <typename Real, typename RZ, int NS, bool KIJ>
 __device__ __noinline__ int eval_h(const Comp<Real, NS> &c, double T, Real p, const SpeciesRec<Real> *sp,
-                                      const Real *kij, double &h, double &cp)
+                                      const Real *kij, Real tmid_u, double &h, double &cp)
 {
     Thermo<Real> th;
-    thermo<Real, RZ, NS, KIJ>(c, (Real)T, p, sp, kij, th);
+    thermo<Real, RZ, NS, KIJ>(c, (Real)T, p, sp, kij, th, tmid_u);
     if (th.status == kNoRoot) return kNoRoot;
     h = (double)th.h;
     cp = (double)th.cp;
@@ -138,10 +195,10 @@ __device__ __noinline__ int eval_h(const Comp<Real, NS> &c, double T, Real p, co
 // h(T) and cp(T) in FP32 with FP32 arguments (the warm start's evaluations).
 template <int NS, bool KIJ>
 __device__ __noinline__ int eval_h_f32(const Comp<float, NS> &c, float T, float p, const SpeciesRec<float> *sp,
-                                       const float *kij, float &h, float &cp)
+                                       const float *kij, float tmid_u, float &h, float &cp)
 {
     Thermo<float> th;
-    thermo<float, float, NS, KIJ>(c, T, p, sp, kij, th);
+    thermo<float, float, NS, KIJ>(c, T, p, sp, kij, th, tmid_u);
     if (th.status == kNoRoot) return kNoRoot;
     h = th.h;
     cp = th.cp;
@@ -157,7 +214,7 @@ __device__ __noinline__ int eval_h_f32(const Comp<float, NS> &c, float T, float 
 // conversion.
 template <int NS, bool KIJ>
 __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, double T0, double hs, double p,
-                                               const SpeciesRec<float> *sp, const float *kij)
+                                               const SpeciesRec<float> *sp, const float *kij, float tmid_u)
 {
     Comp<float, NS> c;
 #pragma unroll
@@ -169,7 +226,7 @@ __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, doub
 #pragma unroll 1
     for (int k = 0; k < 8; ++k) {
         float h, cp;
-        if (eval_h_f32<NS, KIJ>(c, T, pf, sp, kij, h, cp) || !(cp > 0.f)) return T0;
+        if (eval_h_f32<NS, KIJ>(c, T, pf, sp, kij, tmid_u, h, cp) || !(cp > 0.f)) return T0;
         const float Tn = T - (h - hsf) / cp;
         if (!(Tn > (float)kTLo && Tn < (float)kTHi)) return T0;
         const bool done = fabsf(Tn - T) <= 1e-5f * Tn;
@@ -187,8 +244,8 @@ __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, doub
 // jump of h(T)).  Returns the status; Tres, iters and the last cp out.
 template <typename Real, typename RZ, int NS, bool KIJ>
 __device__ __forceinline__ int newton_solve(const Comp<Real, NS> &c, double hs, Real p, double T,
-                                            const SpeciesRec<Real> *sp, const Real *kij, int max_iter, double rtol,
-                                            double jump_tol, double &Tres, int &iters, double &cp_last)
+                                            const SpeciesRec<Real> *sp, const Real *kij, Real tmid_u, int max_iter,
+                                            double rtol, double jump_tol, double &Tres, int &iters, double &cp_last)
 {
     double lo = kTLo, hi = kTHi;
     bool lo_done = false, hi_done = false;   // endpoint h evaluated (range checked)
@@ -199,7 +256,7 @@ __device__ __forceinline__ int newton_solve(const Comp<Real, NS> &c, double hs, 
 #pragma unroll 1
     for (it = 1; it <= max_iter; ++it) {
         double h, cp;
-        int e = eval_h<Real, RZ, NS, KIJ>(c, T, p, sp, kij, h, cp);
+        int e = eval_h<Real, RZ, NS, KIJ>(c, T, p, sp, kij, tmid_u, h, cp);
         if (e) { st = e; Tres = T; break; }
         cp_last = cp;
         const double f = h - hs;
@@ -212,7 +269,7 @@ __device__ __forceinline__ int newton_solve(const Comp<Real, NS> &c, double hs, 
             const bool use_lo = (lo == kTLo && !lo_done);
             const double Te = use_lo ? kTLo : kTHi;
             double he, cpe;
-            int e2 = eval_h<Real, RZ, NS, KIJ>(c, Te, p, sp, kij, he, cpe);
+            int e2 = eval_h<Real, RZ, NS, KIJ>(c, Te, p, sp, kij, tmid_u, he, cpe);
             if (e2) { st = e2; Tres = T; break; }
             if (use_lo) lo_done = true; else hi_done = true;
             if ((use_lo && hs < he) || (!use_lo && hs > he)) { st = kHRange; Tres = Te; break; }
@@ -221,7 +278,7 @@ __device__ __forceinline__ int newton_solve(const Comp<Real, NS> &c, double hs, 
         if (fabs(Tn - T) <= rtol * T) {
             Tres = Tn;
             double h2, cp2;
-            if (eval_h<Real, RZ, NS, KIJ>(c, Tn, p, sp, kij, h2, cp2)) { st = kNoRoot; break; }
+            if (eval_h<Real, RZ, NS, KIJ>(c, Tn, p, sp, kij, tmid_u, h2, cp2)) { st = kNoRoot; break; }
             cp_last = cp2;
             st = (fabs(h2 - hs) <= jump_tol * fmax(fabs(hs), fabs(cp2) * Tn)) ? kOk : kHRange;
             break;
@@ -310,11 +367,11 @@ __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a
         if (ok) {
             double T = fmin(fmax(Tg, kTLo), kTHi);
             if constexpr (kFp64) {
-                if (warm) T = warm_start_fp32<NS, KIJ>(c, T, hs, (double)p, s32[0].sp, s32[0].kij);
+                if (warm) T = warm_start_fp32<NS, KIJ>(c, T, hs, (double)p, s32[0].sp, s32[0].kij, (float)a.tmid_u);
             }
             double cp_last;
-            st = newton_solve<Real, RZ, NS, KIJ>(c, hs, p, T, s.sp, s.kij, a.max_iter, rtol, jump_tol, Tres, it,
-                                                 cp_last);
+            st = newton_solve<Real, RZ, NS, KIJ>(c, hs, p, T, s.sp, s.kij, (Real)a.tmid_u, a.max_iter, rtol, jump_tol,
+                                                 Tres, it, cp_last);
             if constexpr (kMixed) {
                 // FP64 where FP32 is least reliable: failed cells, and cells in
                 // the pseudo-boiling band, from the FP32 root (or the guess)
@@ -326,7 +383,7 @@ __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a
                         double T64, cp64;
                         int it64;
                         st = newton_solve<double, double, NS, KIJ>(c64, hs, (double)p, T0, s64[0].sp, s64[0].kij,
-                                                                   a.max_iter, a.rtol, 1e-6, T64, it64, cp64);
+                                                                   a.tmid_u, a.max_iter, a.rtol, 1e-6, T64, it64, cp64);
                         Tres = T64;
                         it += it64;
                     }
@@ -348,12 +405,13 @@ inline int grid_for(int64_t n, int occ, int sms)
     return (int)(need < cap ? need : cap);
 }
 
+// htab: the context's HostTab9<Real> (used when NS == 9)
 template <typename Real, typename RZ, int NS>
-void launch_props(const PropsArgs<Real> &a, bool kij, int occ, int sms, cudaStream_t st)
+void launch_props(const PropsArgs<Real> &a, const void *htab, bool kij, int occ, int sms, cudaStream_t st)
 {
     const int g = grid_for(a.n, occ, sms);
-    if (kij) props_kernel<Real, RZ, NS, true><<<g, kBlock, 0, st>>>(a);
-    else props_kernel<Real, RZ, NS, false><<<g, kBlock, 0, st>>>(a);
+    if (kij) props_kernel<Real, RZ, NS, true><<<g, kBlock, 0, st>>>(a, make_tab<Real, NS, true>(htab));
+    else props_kernel<Real, RZ, NS, false><<<g, kBlock, 0, st>>>(a, make_tab<Real, NS, false>(htab));
 }
 
 template <typename Real, typename RZ, int NS>
@@ -385,7 +443,7 @@ void occupancy_newton(int occ[2])
 // Explicit instantiations, one translation unit per (precision, kernel kind) so
 // that each can take its own compiler flags.
 #define PRK_DECLARE_PROPS(Real, RZ, NS, EXT)                                                              \
-    EXT template void launch_props<Real, RZ, NS>(const PropsArgs<Real> &, bool, int, int, cudaStream_t);   \
+    EXT template void launch_props<Real, RZ, NS>(const PropsArgs<Real> &, const void *, bool, int, int, cudaStream_t); \
     EXT template void occupancy_props<Real, RZ, NS>(int *);
 #define PRK_DECLARE_NEWTON(Real, RZ, NS, EXT)                                                             \
     EXT template void launch_newton<Real, RZ, NS>(const NewtonArgs<Real> &, bool, int, int, cudaStream_t); \

@@ -447,23 +447,69 @@ __global__ void prep_infer_kernel(SgDev d, int64_t r0, int64_t mc, const float *
     }
 }
 
-// Low-confidence cells of the forward model: the network predicts rho and Z
-// separately, while the equation of state ties them, rho Z R T = p W; a cell
-// whose two outputs disagree by more than `tol` joins the fallback list (cells
-// already on it are skipped through the chunk's flags).
-__global__ void confidence_kernel(SgDev d, int64_t r0, int64_t mc, const float *T, const float *p, const float *Y,
-                                  int64_t ldY, const float *out, int64_t ldo, float tol, uint8_t *flags,
-                                  uint8_t *cflags, int32_t *list, unsigned int *count)
+// Low-confidence cells, appended to the fallback list (cells already on it
+// are skipped through the chunk's flags):
+//  * equation of state (forward model, tol > 0): the network predicts rho and
+//    Z separately, while the equation of state ties them, rho Z R T = p W; a
+//    cell whose two outputs disagree by more than `tol` is flagged;
+//  * transport (property models, tol_tr > 0): Chung's correlation evaluated
+//    in FP32 at the network's own density (and, for the inverse models, its
+//    own temperature) and the cell's composition gives mu_c and lambda_c; a
+//    cell whose predicted mu or lambda differs from them by more than tol_tr
+//    (relative) is flagged.  The correlation's narrow excursions (the polar
+//    and association terms of water-rich mixtures) are where the network is
+//    least accurate, and a consistent density makes the check sharp there.
+__global__ void __launch_bounds__(256) confidence_kernel(SgDev d, int64_t r0, int64_t mc, const float *T,
+                                                         const float *p, const float *Y, int64_t ldY,
+                                                         const float *out, int64_t ldo, float tol, float tol_tr,
+                                                         uint8_t *flags, uint8_t *cflags, int32_t *list,
+                                                         unsigned int *count)
 {
-    const SpeciesRec<float> *sp = static_cast<const SpeciesRec<float> *>(d.sp32);
+    __shared__ SpeciesRec<float> s_sp[9];
+    __shared__ float s_pair[81];
+    {
+        const float *src = static_cast<const float *>(d.sp32);
+        float *dst = reinterpret_cast<float *>(s_sp);
+        for (int j = threadIdx.x; j < (int)(9 * sizeof(SpeciesRec<float>) / 4); j += blockDim.x) dst[j] = src[j];
+        for (int j = threadIdx.x; j < 81; j += blockDim.x) s_pair[j] = d.pair32[j];
+    }
+    __syncthreads();
+    const bool fwd = d.mode == SG_MODE_FORWARD;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < mc; r += (int64_t)gridDim.x * blockDim.x) {
         if (cflags[r]) continue;
         const int64_t i = r0 + r;
-        float s = 0.f;   // moles per kg = 1 / W
+        bool bad = false;
+        if (fwd && tol > 0.f) {
+            float s = 0.f;   // moles per kg = 1 / W
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s = fmaf(__ldg(Y + (int64_t)k * ldY + i), __ldg(&sp[k].inv_W), s);
-        const float c = out[i] * out[ldo + i] * float(prk::kR) * __ldg(T + i) * s / __ldg(p + i);
-        if (!(fabsf(c - 1.f) <= tol)) {
+            for (int k = 0; k < 9; ++k) s = fmaf(__ldg(Y + (int64_t)k * ldY + i), s_sp[k].inv_W, s);
+            const float c = out[i] * out[ldo + i] * float(prk::kR) * __ldg(T + i) * s / __ldg(p + i);
+            bad = !(fabsf(c - 1.f) <= tol);
+        }
+        if (!bad && tol_tr > 0.f) {
+            prk::Comp<float, 9> c;
+            if (prk::load_comp<float, 9>(c, Y, ldY, i, 9, s_sp)) {
+                const float Tc = fwd ? __ldg(T + i) : out[i];              // the network's T (inverse models)
+                const float rho = fwd ? out[i] : out[ldo + i];
+                const float mu = fwd ? out[4 * ldo + i] : out[3 * ldo + i];
+                const float lam = fwd ? out[5 * ldo + i] : out[4 * ldo + i] * out[5 * ldo + i];   // alpha cp
+                // ideal-gas molar cv (NASA-7) for the conductivity
+                float cpm = 0.f;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const float *a = (Tc < s_sp[k].T_mid) ? s_sp[k].cp_lo : s_sp[k].cp_hi;
+                    const float cpk = fmaf(fmaf(fmaf(fmaf(a[4], Tc, a[3]), Tc, a[2]), Tc, a[1]), Tc, a[0]);
+                    cpm = fmaf(c.x[k], cpk, cpm);
+                }
+                prk::Thermo<float> th;
+                th.rho_mol = rho / c.Wbar;
+                th.cv_ig_molar = cpm - float(prk::kR);
+                float mu_c, lam_c;
+                prk::transport<float, 9>(c, Tc, th, s_sp, s_pair, d.pr_flags, mu_c, lam_c);
+                bad = !(fabsf(mu - mu_c) <= tol_tr * fabsf(mu_c)) || !(fabsf(lam - lam_c) <= tol_tr * fabsf(lam_c));
+            }
+        }
+        if (bad) {
             cflags[r] = 1;
             if (flags) flags[i] = 1;
             list[atomicAdd(count, 1u)] = (int32_t)r;
@@ -478,7 +524,8 @@ template <int NS, bool KIJ>
 __global__ void __launch_bounds__(128) fallback_kernel(const int32_t *list, const unsigned int *count, int64_t r0,
                                                        const float *T, const float *p, const float *Y, int64_t ldY,
                                                        float *out, int64_t ldo, const SpeciesRec<double> *sp,
-                                                       const double *pair, const double *kij, int N, int flags)
+                                                       const double *pair, const double *kij, int N, int flags,
+                                                       double tmid_u)
 {
     __shared__ SpeciesRec<double> s_sp[NS];
     __shared__ double s_pair[NS * NS];
@@ -492,7 +539,8 @@ __global__ void __launch_bounds__(128) fallback_kernel(const int32_t *list, cons
     __syncthreads();
     const unsigned int n = *count;
     for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
-        prk::fallback_cell_fp64<NS, KIJ>(r0 + list[t], T, p, Y, ldY, out, ldo, s_sp, s_pair, s_kij, N, flags);
+        prk::fallback_cell_fp64<NS, KIJ>(r0 + list[t], T, p, Y, ldY, out, ldo, s_sp, s_pair, s_kij, N, flags,
+                                         tmid_u);
 }
 
 // FP64 Peng-Robinson fallback of the inverse model for the listed cells: the
@@ -530,7 +578,7 @@ __global__ void __launch_bounds__(128) fallback_inverse_kernel(const int32_t *li
             T0 = fmin(fmax(T0, prk::kTLo), prk::kTHi);
             double T, cpl;
             int it;
-            const int st = prk::newton_solve<double, double, NS, KIJ>(c, hv, pv, T0, s_sp, s_kij, 60, 1e-12, 1e-6, T,
+            const int st = prk::newton_solve<double, double, NS, KIJ>(c, hv, pv, T0, s_sp, s_kij, 0.0, 60, 1e-12, 1e-6, T,
                                                                      it, cpl);
             if (st == prk::kOk) {
                 prk::Thermo<double> th;
@@ -588,7 +636,7 @@ __global__ void __launch_bounds__(128) fallback_species_kernel(const int32_t *li
         if (ok) {
             double T, cpl;
             int it;
-            const int st = prk::newton_solve<double, double, NS, KIJ>(c, hv, pv, 1000.0, s_sp, s_kij, 60, 1e-12, 1e-6,
+            const int st = prk::newton_solve<double, double, NS, KIJ>(c, hv, pv, 1000.0, s_sp, s_kij, 0.0, 60, 1e-12, 1e-6,
                                                                      T, it, cpl);
             if (st == prk::kOk) {
                 if (outputs == SG_OUT_HK) {
@@ -1002,6 +1050,8 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
     d.hidden = m->hidden;
     d.max_batch = m->max_batch;
     d.sp32 = ctx->d_sp32;
+    d.pair32 = ctx->d_pair32;
+    d.pr_flags = ctx->flags;
     d.bilger = ctx->d_bilger32;
     d.bc_lambda = 1.0f;      // Box-Cox of Bilger's Z: linear until surrogate_set_boxcox
     d.bc_shift = 1e-3f;
@@ -1392,8 +1442,10 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.nout = d.nout;
             PR_CUDA_TRY((launch_gemm<16, kEpiOutPhys>(m->tm_hi[(L - 1) & 1], m->tm_w[L], a, mt, 1, 1, st)));
         }
-        if (d.mode == SG_MODE_FORWARD && m->conf_tol > 0.f) {
-            confidence_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, out, ldo, m->conf_tol,
+        const float ctol = (d.mode == SG_MODE_FORWARD) ? m->conf_tol : 0.f;
+        const float ttol = (d.outputs == SG_OUT_PROPS) ? m->tr_tol : 0.f;
+        if (ctol > 0.f || ttol > 0.f) {
+            confidence_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, out, ldo, ctol, ttol,
                                                                      used_fallback, m->d_flags, m->d_list, m->d_count);
             PR_CUDA_TRY(cudaGetLastError());
         }
@@ -1423,11 +1475,11 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
         } else if (ctx->has_kij)
             fallback_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out, ldo,
                                                          (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64,
-                                                         ctx->d_kij64, ctx->n_species, ctx->flags);
+                                                         ctx->d_kij64, ctx->n_species, ctx->flags, ctx->tmid_u);
         else
             fallback_kernel<9, false><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out, ldo,
                                                           (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64,
-                                                          ctx->d_kij64, ctx->n_species, ctx->flags);
+                                                          ctx->d_kij64, ctx->n_species, ctx->flags, ctx->tmid_u);
         PR_CUDA_TRY(cudaGetLastError());
     }
     return PR_OK;
@@ -1449,6 +1501,7 @@ pr_status surrogate_get_option(const sg_model *m, int option, int *value)
     case SG_OPT_TEST_STALL: *value = m->stall_test; return PR_OK;
     case SG_OPT_LOSS: *value = m->loss_l1 ? SG_LOSS_L1 : SG_LOSS_REL_MSE; return PR_OK;
     case SG_OPT_CONFIDENCE_PPM: *value = (int)(m->conf_tol * 1e6f + 0.5f); return PR_OK;
+    case SG_OPT_TRANSPORT_CONFIDENCE_PPM: *value = (int)(m->tr_tol * 1e6f + 0.5f); return PR_OK;
     case SG_OPT_OUTPUTS: *value = m->dev.outputs; return PR_OK;
     default: break;
     }
@@ -1497,6 +1550,10 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
     case SG_OPT_CONFIDENCE_PPM:
         PR_CHECK_ARG(value >= 0, "surrogate_set_option: confidence tolerance must be >= 0");
         m->conf_tol = 1e-6f * (float)value;
+        return PR_OK;
+    case SG_OPT_TRANSPORT_CONFIDENCE_PPM:
+        PR_CHECK_ARG(value >= 0, "surrogate_set_option: transport confidence tolerance must be >= 0");
+        m->tr_tol = 1e-6f * (float)value;
         return PR_OK;
     case SG_OPT_LOSS:
         PR_CHECK_ARG(value == SG_LOSS_REL_MSE || value == SG_LOSS_L1, "surrogate_set_option: bad loss %d", value);

@@ -51,6 +51,8 @@ struct SgDev {
     float *hig;                             // ideal-gas enthalpy of the chunk's cells [chunk]
     int mode;                               // SG_MODE_FORWARD, SG_MODE_INVERSE or SG_MODE_BILGER
     const void *sp32;                       // the context's FP32 species records (NASA-7 data)
+    const float *pair32;                    // the context's FP32 Chung pair table [9][9]
+    int pr_flags;                           // the context's PR_FLAG_* (transport rule)
     const float *bilger;                    // SG_MODE_BILGER: the context's b_k [9], beta_ox, 1/range
     float bc_lambda, bc_shift;              // SG_MODE_BILGER: Box-Cox of Z, ((Z + shift)^lambda - 1) / lambda
 };
@@ -120,6 +122,7 @@ struct sg_model {
     int stall_test;                         // SG_OPT_TEST_STALL
     int loss_l1;                            // SG_OPT_LOSS == SG_LOSS_L1
     float conf_tol;                         // SG_OPT_CONFIDENCE_PPM / 1e6; 0: off
+    float tr_tol;                           // SG_OPT_TRANSPORT_CONFIDENCE_PPM / 1e6; 0: off
     __nv_bfloat16 *ring;                    // [L][fused_ring_rows * 128][W]
     uint32_t *d_done;
     CUtensorMap tmf_w[SG_MAX_HIDDEN + 1], tmf_ring_ld, tmf_ring_st;

@@ -40,3 +40,17 @@ def cuda():
     if not torch.cuda.is_available():
         pytest.fail("a CUDA device is required for tests marked gpu")
     return torch.device("cuda:0")
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """One line per kind of cell the FP64 parity rule treats apart (tests/parity.py),
+    summed over the parity checks of the run, just above pytest's last line."""
+    parity = sys.modules.get("tests.parity")
+    if parity is None or not parity.REPORTS:
+        return
+    tot = {k: sum(r[k] for _, r in parity.REPORTS) for k in parity.COUNT_KEYS}
+    terminalreporter.write_line(
+        "FP64 parity: %d checks, %d cells: %d at 1e-10, %d ill-conditioned roots, %d ambiguous, "
+        "%d cancellation-bounded, %d input-ill-conditioned" %
+        (len(parity.REPORTS), tot["n_cells"], tot["n_ok"], tot["n_ill"], tot["n_ambiguous"], tot["n_cancel"],
+         tot["n_input_ill_conditioned"]))
