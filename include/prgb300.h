@@ -187,6 +187,15 @@ pr_status pr_bilger_z(pr_ctx *ctx, pr_precision prec, int64_t n, const void *Y, 
 #define PR_PEAK_FP64_FMA 0
 #define PR_PEAK_FP32_FMA 1
 #define PR_PEAK_MUFU_EX2 2
+/* FP64 library calls per second (CUDA's exp, log, division, square root and
+ * cube root, arguments of order one): the FP64 rate over one of these gives
+ * the FP64-pipe slots a call takes, the weight of that call in the FP64
+ * paths' algorithmic work. */
+#define PR_PEAK_FP64_EXP 3
+#define PR_PEAK_FP64_LOG 4
+#define PR_PEAK_FP64_DIV 5
+#define PR_PEAK_FP64_SQRT 6
+#define PR_PEAK_FP64_CBRT 7
 pr_status pr_measure_peak(int kind, double *ops_per_s);
 
 /* Inversion T(h*, p, Y) by safeguarded Newton on f(T) = h(T) - h*, f' = cp,
@@ -403,16 +412,16 @@ pr_status surrogate_load(sg_model *m, const char *path);
 /* ======================================================================
  * Continuous-batching property server (many simulations sharing one GPU).
  * Requests carry FP32 fields in HOST memory (pinned memory keeps the copies
- * asynchronous; pageable memory works but its copies block the worker).  A
- * worker thread admits requests in arrival order while their device buffers
- * fit in the HBM budget, cuts them into `chunk`-cell pieces, fills batches of
- * up to `max_slots` pieces round-robin across every admitted request, and runs
- * each batch by replaying a CUDA graph captured for its (power-of-two) slot
- * count: gather the pieces, evaluate them (forward properties through the
- * surrogate with its FP64 PR fallback -- or FP32 PR when no model is given --
- * and T from h by the PR Newton path), scatter the results.  Results do not
- * depend on batch composition.  The model (if any) must not be used by other
- * calls while the server runs.
+ * asynchronous; pageable memory works but its copies block the worker) and a
+ * precision.  A worker thread admits requests in arrival order while their
+ * device buffers fit in the HBM budget, cuts them into `chunk`-cell pieces,
+ * fills batches of up to `max_slots` pieces of one (kind, precision)
+ * round-robin across every admitted request of that path, and runs each batch
+ * by replaying a CUDA graph captured for its path and (power-of-two) slot
+ * count: gather the pieces, evaluate them, scatter the results.  Results do
+ * not depend on batch composition.  The worker makes its CUDA calls outside
+ * the request lock, so submitting and polling never wait behind a launch.
+ * The model (if any) must not be used by other calls while the server runs.
  * ====================================================================== */
 
 typedef struct sv_server sv_server;
@@ -420,9 +429,24 @@ typedef struct sv_server sv_server;
 #define SV_PROPS     0   /* out [6][n]: rho, Z, h, cp, mu, lambda */
 #define SV_T_FROM_H  1   /* out [n]: T; status [n] per-cell PR_CELL_* codes */
 
+/* Precision of a request.  Inputs and outputs stay FP32; the FP64 paths widen
+ * the inputs, compute in FP64 (pr_props / pr_T_from_h with PR_FP64, inversion
+ * tolerance 1e-12) and round the results.
+ *   SV_PREC_SERVER  the server's own path: SV_PROPS through the surrogate with
+ *                   its FP64 PR fallback (the FP32 PR path when the server has
+ *                   no model); SV_T_FROM_H in sv_config.newton_precision
+ *   SV_PREC_FP64    the FP64 PR path
+ *   SV_PREC_MIXED   PR_MIXED (FP32 with FP64 root selection / band re-solve)
+ *   SV_PREC_FP32    the FP32 PR path
+ * The FP32 and mixed inversions stop at rtol 1e-6. */
+#define SV_PREC_SERVER 0
+#define SV_PREC_FP64   1
+#define SV_PREC_MIXED  2
+#define SV_PREC_FP32   3
+
 typedef struct {
     int32_t kind;        /* SV_PROPS or SV_T_FROM_H */
-    int32_t pad;
+    int32_t precision;   /* SV_PREC_* */
     int64_t n;           /* cells, >= 1 */
     const float *T;      /* SV_PROPS: T [n]; SV_T_FROM_H: initial guess [n] (HOST) */
     const float *p;      /* [n] (HOST) */
@@ -435,7 +459,7 @@ typedef struct {
 typedef struct {
     int32_t chunk;             /* cells per batch slot: multiple of 128 */
     int32_t max_slots;         /* slots per batch, 1..256 */
-    int32_t newton_precision;  /* PR_MIXED or PR_FP32 */
+    int32_t newton_precision;  /* PR_FP64, PR_MIXED or PR_FP32: SV_T_FROM_H requests at SV_PREC_SERVER */
     int32_t pad;
     size_t hbm_budget_bytes;   /* device memory for admitted requests' buffers */
 } sv_config;

@@ -34,12 +34,15 @@ class PrError(RuntimeError):
     pass
 
 
-PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "mufu_ex2": 2}
+PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "mufu_ex2": 2, "fp64_exp": 3, "fp64_log": 4, "fp64_div": 5,
+              "fp64_sqrt": 6, "fp64_cbrt": 7}
 
 
 def measure_peak(kind: str) -> float:
     """Measured throughput of one arithmetic pipe on the current device:
-    flops/s for 'fp64_fma' and 'fp32_fma', exp2/s for 'mufu_ex2'."""
+    flops/s for 'fp64_fma' and 'fp32_fma', exp2/s for 'mufu_ex2', calls/s of
+    CUDA's FP64 exp, log, division, square root and cube root for 'fp64_exp',
+    'fp64_log', 'fp64_div', 'fp64_sqrt', 'fp64_cbrt'."""
     v = ctypes.c_double(0.0)
     check(lib().pr_measure_peak(PEAK_KINDS[kind], ctypes.byref(v)), "pr_measure_peak")
     return v.value

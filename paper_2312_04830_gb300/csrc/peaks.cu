@@ -65,18 +65,50 @@ __global__ void __launch_bounds__(kPeakBlock) ex2_kernel(float *sink, int iters)
     if (s == -1.2345e30f) sink[0] = s;
 }
 
+// FP64 library calls (exp, log, division, square root, cube root) with CUDA's
+// own implementations: calls per second when nothing else runs, i.e. how many
+// FP64-pipe slots one call takes (the DFMA rate over this rate).  Each chain
+// maps [-1.5, -0.4] into itself with the call and at most one FP64 add or FMA
+// besides, so no clamp is needed; arguments are of order one, as in the
+// property kernels.
+template <int OP>
+__device__ __forceinline__ double f64_call(double x)
+{
+    if (OP == 0) return exp(x) - 1.5;          // [-1.277, -0.830]
+    if (OP == 1) return fma(0.5, log(-x), -0.9);   // [-1.358, -0.697]
+    if (OP == 2) return 1.0 / (x - 0.5);       // [-1.111, -0.5]
+    if (OP == 3) return -sqrt(-x);             // [-1.225, -0.632]
+    return -cbrt(-x);                          // [-1.145, -0.737]
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kPeakBlock) f64_call_kernel(double *sink, int iters)
+{
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = -0.6 - 1e-4 * (threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) x[c] = f64_call<OP>(x[c]);
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == -1.2345e300) sink[0] = s;
+}
+
 }  // namespace
 
 extern "C" pr_status pr_measure_peak(int kind, double *ops_per_s)
 {
     PR_CHECK_ARG(ops_per_s != nullptr, "pr_measure_peak: null output");
-    PR_CHECK_ARG(kind == PR_PEAK_FP64_FMA || kind == PR_PEAK_FP32_FMA || kind == PR_PEAK_MUFU_EX2,
-                 "pr_measure_peak: unknown kind %d", kind);
+    PR_CHECK_ARG(kind >= PR_PEAK_FP64_FMA && kind <= PR_PEAK_FP64_CBRT, "pr_measure_peak: unknown kind %d", kind);
     int dev = 0, sms = 0;
     PR_CUDA_TRY(cudaGetDevice(&dev));
     PR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = sms * 8;
-    const int iters = (kind == PR_PEAK_FP64_FMA) ? 2048 : 32768;
+    const bool call = kind >= PR_PEAK_FP64_EXP;
+    const int iters = call ? 128 : (kind == PR_PEAK_FP64_FMA) ? 2048 : 32768;
     void *sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PR_CUDA_TRY(cudaMalloc(&sink, 16));
@@ -89,8 +121,18 @@ extern "C" pr_status pr_measure_peak(int kind, double *ops_per_s)
             dfma_kernel<<<blocks, kPeakBlock>>>((double *)sink, iters, 0.9999999, 1e-7);
         else if (kind == PR_PEAK_FP32_FMA)
             ffma_kernel<<<blocks, kPeakBlock>>>((float *)sink, iters, 0.9999f, 1e-4f);
-        else
+        else if (kind == PR_PEAK_MUFU_EX2)
             ex2_kernel<<<blocks, kPeakBlock>>>((float *)sink, iters);
+        else if (kind == PR_PEAK_FP64_EXP)
+            f64_call_kernel<0><<<blocks, kPeakBlock>>>((double *)sink, iters);
+        else if (kind == PR_PEAK_FP64_LOG)
+            f64_call_kernel<1><<<blocks, kPeakBlock>>>((double *)sink, iters);
+        else if (kind == PR_PEAK_FP64_DIV)
+            f64_call_kernel<2><<<blocks, kPeakBlock>>>((double *)sink, iters);
+        else if (kind == PR_PEAK_FP64_SQRT)
+            f64_call_kernel<3><<<blocks, kPeakBlock>>>((double *)sink, iters);
+        else
+            f64_call_kernel<4><<<blocks, kPeakBlock>>>((double *)sink, iters);
         cudaEventRecord(e1);
         e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -104,7 +146,7 @@ extern "C" pr_status pr_measure_peak(int kind, double *ops_per_s)
         prgb::set_error("pr_measure_peak: %s", cudaGetErrorString(e));
         return PR_ECUDA;
     }
-    const double ops_per_elem = (kind == PR_PEAK_MUFU_EX2) ? 1.0 : 2.0;   // an FMA is two flops
+    const double ops_per_elem = (kind == PR_PEAK_FP64_FMA || kind == PR_PEAK_FP32_FMA) ? 2.0 : 1.0;   // an FMA is two flops
     *ops_per_s = ops_per_elem * (double)blocks * kPeakBlock * kChains * iters / (best_ms * 1e-3);
     return PR_OK;
 }

@@ -13,10 +13,11 @@ import numpy as np
 from . import binding
 
 SV_PROPS, SV_T_FROM_H = 0, 1
+SV_PREC = {"server": 0, "fp64": 1, "mixed": 2, "fp32": 3}
 
 
 class _SvRequest(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("n", ctypes.c_int64),
+    _fields_ = [("kind", ctypes.c_int32), ("precision", ctypes.c_int32), ("n", ctypes.c_int64),
                 ("T", ctypes.c_void_p), ("p", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("h", ctypes.c_void_p),
                 ("out", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
@@ -86,14 +87,15 @@ class Server:
         except Exception:
             pass
 
-    def submit_props(self, T, p, Y, out) -> int:
+    def submit_props(self, T, p, Y, out, precision="server") -> int:
         n = T.shape[0]
-        r = _SvRequest(SV_PROPS, 0, n, _addr(T), _addr(p), _addr(Y), None, _addr(out), None)
+        r = _SvRequest(SV_PROPS, SV_PREC[precision], n, _addr(T), _addr(p), _addr(Y), None, _addr(out), None)
         return self._submit(r, (T, p, Y, out))
 
-    def submit_T_from_h(self, h, p, Y, T_guess, out, status=None) -> int:
+    def submit_T_from_h(self, h, p, Y, T_guess, out, status=None, precision="server") -> int:
         n = h.shape[0]
-        r = _SvRequest(SV_T_FROM_H, 0, n, _addr(T_guess), _addr(p), _addr(Y), _addr(h), _addr(out), _addr(status))
+        r = _SvRequest(SV_T_FROM_H, SV_PREC[precision], n, _addr(T_guess), _addr(p), _addr(Y), _addr(h), _addr(out),
+                       _addr(status))
         return self._submit(r, (h, p, Y, T_guess, out, status))
 
     def _submit(self, r, keep):

@@ -3,26 +3,40 @@
 FP64 rule (per output, per cell whose oracle status is 0):
   * |q_gpu - q_orc| <= 1e-10 |q_orc|   for rho, Z, cp, mu, lambda;
   * |h_gpu - h_orc| <= 1e-10 max(|h|, cp T)   (h crosses zero);
-  * cells whose root condition number c = sum_k |c_k| |Z|^k / (|Z| |P'(Z)|)
+  * mu and lambda come out of sums that cancel for some mixtures far from
+    Chung's fitted range (e.g. G2's denominator E1 E4 + E2 + E3 of H/H2-rich
+    mixtures).  With c the cancellation ratio sum |t_i| / |sum t_i| of the
+    worst such sum (the oracle reports it), terms that carry at most K_CHAIN
+    roundings each (from the inputs through the mixture sums and the E_i, B_i
+    coefficients) and the standard model of floating-point arithmetic, the
+    computed sum is off by at most gamma(K_CHAIN) c of its value (Higham,
+    Accuracy and Stability of Numerical Algorithms, Sec. 3.1 and 4.2); two
+    such evaluations differ by at most twice that, so mu and lambda pass at
+    1e-10 + 2 gamma(K_CHAIN) c;
+  * cells whose root condition number c_Z = sum_k |c_k| |Z|^k / (|Z| |P'(Z)|)
     exceeds 1e4 (near-degenerate cubics: rounding of the coefficients moves
-    the root by ~eps c) instead need |dZ|/Z <= 8 eps c, and rho, h, mu,
-    lambda within 1e-10 + 100 * 8 eps c.  cp is not compared on these cells:
-    it holds 1/(dp/dV)_T, which vanishes at the critical point, so its
-    sensitivity to the root is unbounded there;
-  * an output that misses 1e-10 on a well-conditioned root passes if the
-    oracle shows it ill-conditioned in its inputs: with the componentwise
-    condition number k_q = sum_x |d ln q / d ln x| over x in (T, p, Y_k)
-    (central differences of the oracle), the bound is 1e-10 + 1e3 eps k_q.
-    This covers Chung's correlations far outside their fitted range (e.g.
-    H/H2-rich mixtures, whose G2 denominator E1 E4 + E2 + E3 is a difference
-    of terms a thousand times larger);
+    the root by up to ~eps c_Z) need |dZ|/Z <= 8 eps c_Z, and every derived
+    output is checked at the oracle's own root: it must lie within 1e-10 of
+    its value plus twice the largest change that moving the oracle's root by
+    that bound (8 eps c_Z, either way) causes in it;
   * cells the oracle flags ambiguous (two roots within 1e-9 in g_res) are
     excluded and counted; the GPU must flag them ok or ambiguous.
+Every check reports how many cells each allowance took and asserts a
+ceiling on them (0.1 % of the cells unless a test builds such cells on
+purpose); the counts are summed in the run's terminal summary.
 """
 import numpy as np
 
 EPS = np.finfo(np.float64).eps
+U = EPS / 2                 # unit roundoff of FP64
+K_CHAIN = 35                # roundings per term of Chung's cancelling sums, the sum included
 NAMES = ("rho", "Z", "h", "cp", "mu", "lambda")
+COUNT_KEYS = ("n_cells", "n_ok", "n_ill", "n_ambiguous", "n_cancel")
+REPORTS = []                # (label, counts) of every FP64 parity check of the run
+
+
+def gamma(k):
+    return k * U / (1 - k * U)
 
 
 def cond_numbers(diags):
@@ -43,7 +57,8 @@ def rel_errors(gpu, orc, T):
 
 def input_condition(orc, species, T, p, Y, idx, h=1e-7):
     """Componentwise condition numbers k_q [6, len(idx)] of the oracle's
-    outputs with respect to relative perturbations of T, p and each Y_k."""
+    outputs with respect to relative perturbations of T, p and each Y_k
+    (a diagnostic of where an output is sensitive to its inputs)."""
     idx = np.asarray(idx)
     base, _ = orc.props(species, T[idx], p[idx], Y[:, idx])
     kap = np.zeros((6, idx.size))
@@ -65,8 +80,30 @@ def input_condition(orc, species, T, p, Y, idx, h=1e-7):
     return kap
 
 
-def assert_fp64_parity(gpu, gst, orc, ost, T, cond, rtol=1e-10, label="", kappa_fn=None):
+def root_sensitivity_bound(orc, species, T, p, Y, idx, Z, dz, o):
+    """Largest change of each output [6, len(idx)] (relative, on the rule's
+    scales) when the root of the cells idx moves from Z by dz (relative) either
+    way: the outputs evaluated by the oracle at Z (1 +- dz)."""
+    idx = np.asarray(idx)
+    worst = np.zeros((6, idx.size))
+    for sgn in (1.0, -1.0):
+        q, _ = orc.props_at_Z(species, T[idx], p[idx], Y[:, idx], Z * (1 + sgn * dz))
+        worst = np.maximum(worst, np.nan_to_num(rel_errors(q, o, T[idx]), nan=np.inf))
+    return worst
+
+
+def assert_fp64_parity(gpu, gst, orc_out, ost, T, diags, rtol=1e-10, label="", zsens=None,
+                       max_frac=1e-3, expect_ill=False, expect_ambiguous=False):
+    """FP64 parity by the rule above.  diags: the oracle's per-cell
+    diagnostics (root condition number, Chung cancellation ratios, root);
+    zsens(idx, Z, dz, o): root_sensitivity_bound for the cells idx (required
+    when ill-conditioned roots occur).  Returns the counts."""
     gpu = np.asarray(gpu, dtype=np.float64)
+    n = T.size
+    cond = np.array([d["cond"] for d in diags])
+    cmu = np.array([d["cancel_mu"] for d in diags])
+    clam = np.array([d["cancel_lam"] for d in diags])
+    Zo = np.array([d["Z"] for d in diags])
     ok = ost == 0
     amb = ost == 5
     assert np.all(np.isin(gst[amb], (0, 5))), f"{label}: ambiguous cells got status {np.unique(gst[amb])}"
@@ -74,35 +111,45 @@ def assert_fp64_parity(gpu, gst, orc, ost, T, cond, rtol=1e-10, label="", kappa_
     assert np.array_equal(gst[bad], ost[bad]), f"{label}: error statuses differ"
     assert np.all(np.isnan(gpu[:, bad])), f"{label}: error cells must be NaN"
     assert np.all(gst[ok] == 0), f"{label}: GPU status differs on {np.count_nonzero(gst[ok] != 0)} ok cells"
-    err = rel_errors(gpu, orc, T)
+    err = rel_errors(gpu, orc_out, T)
     ill = cond > 1e4
     well = ok & ~ill
+    tol = np.full(err.shape, rtol)
+    tol[4] += 2 * gamma(K_CHAIN) * np.nan_to_num(cmu, nan=np.inf)
+    tol[5] += 2 * gamma(K_CHAIN) * np.nan_to_num(clam, nan=np.inf)
     worst = {}
-    n_sens = 0
-    if kappa_fn is not None:
-        cand = np.nonzero(well & np.any(err > rtol, axis=0))[0]
-        if cand.size:
-            kap = kappa_fn(cand)
-            tol = rtol + 1e3 * EPS * kap
-            passed = np.all((err[:, cand] <= tol) | ~np.isfinite(tol), axis=0)
-            well = well.copy()
-            well[cand[passed]] = False
-            n_sens = int(passed.sum())
     for q in range(6):
         e = err[q, well]
         worst[NAMES[q]] = float(e.max()) if e.size else 0.0
-        if e.size and e.max() > rtol:
-            i = np.nonzero(well)[0][int(np.argmax(e))]
-            raise AssertionError(f"{label}: {NAMES[q]} rel err {e.max():.3e} > {rtol} at cell {i} "
-                                 f"(T={T[i]}, gpu={gpu[q, i]!r}, orc={orc[q, i]!r}, cond={cond[i]:.3g})")
+        over = well & (err[q] > tol[q])
+        if np.any(over):
+            i = np.nonzero(over)[0][0]
+            raise AssertionError(f"{label}: {NAMES[q]} rel err {err[q, i]:.3e} > {tol[q, i]:.3e} at cell {i} "
+                                 f"(T={T[i]}, gpu={gpu[q, i]!r}, orc={orc_out[q, i]!r}, cond={cond[i]:.3g}, "
+                                 f"cancel mu/lambda={cmu[i]:.3g}/{clam[i]:.3g})")
+    n_cancel = int(np.count_nonzero(well & np.any(err > rtol, axis=0)))
     sel = ok & ill
     if np.any(sel):
-        tolZ = 8 * EPS * cond[sel]
-        assert np.all(err[1, sel] <= np.maximum(tolZ, rtol)), f"{label}: ill-conditioned Z"
-        for q in (0, 2, 4, 5):
-            assert np.all(err[q, sel] <= rtol + 100 * tolZ), f"{label}: ill-conditioned {NAMES[q]}"
-    return {"n_ok": int(well.sum()), "n_ill": int(sel.sum()), "n_ambiguous": int(amb.sum()),
-            "n_input_ill_conditioned": n_sens, "max_rel": worst}
+        idx = np.nonzero(sel)[0]
+        dz = 8 * EPS * cond[idx]
+        assert np.all(err[1, idx] <= np.maximum(dz, rtol)), f"{label}: ill-conditioned Z"
+        assert zsens is not None, f"{label}: ill-conditioned roots need the root-sensitivity bound"
+        move = zsens(idx, Zo[idx], dz, orc_out[:, idx])
+        for q in (0, 2, 3, 4, 5):
+            lim = rtol + 2 * move[q]
+            assert np.all(err[q, idx] <= lim), \
+                f"{label}: ill-conditioned {NAMES[q]}: {err[q, idx].max():.3e} (limit {lim[np.argmax(err[q, idx])]:.3e})"
+    counts = {"n_cells": int(n), "n_ok": int(np.count_nonzero(well)) - n_cancel, "n_ill": int(sel.sum()),
+              "n_ambiguous": int(amb.sum()), "n_cancel": n_cancel}
+    REPORTS.append((label, counts))
+    print(f"FP64 parity {label}: {counts}")
+    cap = max_frac * n
+    assert n_cancel <= cap, f"{label}: {n_cancel} cells needed the cancellation allowance (ceiling {cap:g})"
+    if not expect_ill:
+        assert counts["n_ill"] <= cap, f"{label}: {counts['n_ill']} ill-conditioned roots (ceiling {cap:g})"
+    if not expect_ambiguous:
+        assert counts["n_ambiguous"] <= cap, f"{label}: {counts['n_ambiguous']} ambiguous cells (ceiling {cap:g})"
+    return dict(counts, max_rel=worst)
 
 
 def error_summary(gpu, orc, T, mask):

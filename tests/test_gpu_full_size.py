@@ -14,7 +14,7 @@ import pytest
 from oracle import mlp as omlp
 from paper_2312_04830_gb300 import workloads as W
 
-from .parity import assert_fp64_parity, cond_numbers, input_condition
+from .parity import assert_fp64_parity, root_sensitivity_bound
 from .test_gpu_surrogate import h_ig_of, make_pool, standardise, unflatten
 
 pytestmark = pytest.mark.gpu
@@ -59,8 +59,8 @@ def test_props_fp64_full_field_sampled(ctx, orc, species, cuda, field):
     Ts, ps, Ys = T[idx], p[idx], Y[:, idx]
     o, os_, d = orc.diagnose(species, Ts, ps, Ys)
     tb = orc.Table(species)
-    rep = assert_fp64_parity(g, gs, o, os_, Ts, cond_numbers(d), label="256^3 sample",
-                             kappa_fn=lambda k: input_condition(orc, tb, Ts, ps, Ys, k))
+    rep = assert_fp64_parity(g, gs, o, os_, Ts, d, label="256^3 sample",
+                             zsens=lambda k, Z, dz, oo: root_sensitivity_bound(orc, tb, Ts, ps, Ys, k, Z, dz, oo))
     assert rep["n_ok"] > 0.99 * N_SAMPLE
 
 
@@ -156,6 +156,7 @@ def test_props_fp64_64bit_indexing(ctx, orc, species, cuda):
     base = idx % nb
     o, os_, d = orc.diagnose(species, Tb[base], pb[base], Yb[:, base])
     tb = orc.Table(species)
-    rep = assert_fp64_parity(g, gs, o, os_, Tb[base], cond_numbers(d), label="2^28 + 77 cells",
-                             kappa_fn=lambda k: input_condition(orc, tb, Tb[base], pb[base], Yb[:, base], k))
+    Tq, pq, Yq = Tb[base], pb[base], Yb[:, base]
+    rep = assert_fp64_parity(g, gs, o, os_, Tq, d, label="2^28 + 77 cells",
+                             zsens=lambda k, Z, dz, oo: root_sensitivity_bound(orc, tb, Tq, pq, Yq, k, Z, dz, oo))
     assert rep["n_ok"] > 0.97 * idx.size

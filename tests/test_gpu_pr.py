@@ -8,7 +8,7 @@ import pytest
 
 from paper_2312_04830_gb300 import workloads as W
 
-from .parity import assert_fp64_parity, cond_numbers, error_summary, input_condition
+from .parity import assert_fp64_parity, cond_numbers, error_summary, root_sensitivity_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -39,12 +39,14 @@ def oracle_props(orc, species, T, p, Y, **kw):
     return out, st, cond_numbers(d)
 
 
-def check(orc, species, g, gs, T, p, Y, label, **kw):
-    """FP64 parity with the sensitivity allowance computed by the oracle."""
-    o, os_, cond = oracle_props(orc, species, T, p, Y, **kw)
+def check(orc, species, g, gs, T, p, Y, label, expect_ill=False, expect_ambiguous=False, **kw):
+    """FP64 parity by the rule of tests/parity.py, the allowances computed by
+    the oracle (Chung cancellation ratios, outputs at a moved root)."""
+    o, os_, d = orc.diagnose(species, T, p, Y, **kw)
     tb = orc.Table(species, **kw)
-    return assert_fp64_parity(g, gs, o, os_, T, cond, label=label,
-                              kappa_fn=lambda idx: input_condition(orc, tb, T, p, Y, idx))
+    zs = lambda idx, Z, dz, oo: root_sensitivity_bound(orc, tb, T, p, Y, idx, Z, dz, oo)
+    return assert_fp64_parity(g, gs, o, os_, T, d, label=label, zsens=zs, expect_ill=expect_ill,
+                              expect_ambiguous=expect_ambiguous)
 
 
 # ------------------------------------------------------------------ FP64
@@ -103,7 +105,7 @@ def _edge_states(species):
 def test_props_fp64_edge_cases(ctx, orc, species, cuda):
     T, p, Y = _edge_states(species)
     g, gs = run_props(ctx, T, p, Y, cuda)
-    rep = check(orc, species, g, gs, T, p, Y, "edge")
+    rep = check(orc, species, g, gs, T, p, Y, "edge", expect_ill=True, expect_ambiguous=True)
     o, os_, cond = oracle_props(orc, species, T, p, Y)
     assert rep["n_ill"] + rep["n_ambiguous"] >= 6     # the critical points
     assert np.count_nonzero(os_ == 4) == 6

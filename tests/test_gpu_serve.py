@@ -117,3 +117,72 @@ def test_wait_times_out_then_completes(setup, cuda):
     st, res, lat = srv.wait(t, timeout_ms=120000.0)
     assert st == 0 and res == 0 and lat > 0
     srv.close()
+
+
+def test_request_precisions_match_direct_calls_and_oracle(setup, orc, species, cuda):
+    """Every request precision, both kinds, in one mix: served results equal the
+    direct library call of that precision bit for bit (the FP64 paths on the
+    widened FP32 inputs, rounded to FP32), and a sample of them -- the FP64
+    paths, and the surrogate's FP64 fallback cells outside the hull -- is
+    checked against the FP64 oracle."""
+    import torch
+    from paper_2312_04830_gb300 import serving
+    from .parity import rel_errors
+    ctx, sg = setup
+    srv = serving.Server(ctx, sg, chunk=4096, max_slots=8, budget_bytes=512 << 20)
+    reqs = {}
+    for j, prec in enumerate(("server", "fp64", "mixed", "fp32")):
+        for kind in (0, 1):
+            rq = make_request(ctx, 7000 + 911 * j + 37 * kind, 600 + 10 * j + kind, cuda)
+            if kind == 0 and prec == "server":
+                rq["T"][::5] = 4300.0                   # outside the hull: the FP64 fallback
+            n = rq["T"].size
+            if kind == 0:
+                out = np.zeros((6, n), dtype=np.float32)
+                t = srv.submit_props(rq["T"], rq["p"], rq["Y"], out, precision=prec)
+            else:
+                out = np.zeros(n, dtype=np.float32)
+                st = np.zeros(n, dtype=np.int32)
+                t = srv.submit_T_from_h(rq["h"], rq["p"], rq["Y"], rq["T"], out, st, precision=prec)
+            reqs[(prec, kind)] = (t, rq, out)
+    for t, _, _ in reqs.values():
+        st_, res, _ = srv.wait(t)
+        assert st_ == 0 and res == 0
+    srv.close()
+    d32 = lambda a: torch.as_tensor(a, device=cuda)
+    d64 = lambda a: torch.as_tensor(a.astype(np.float64), device=cuda)
+    for (prec, kind), (t, rq, out) in reqs.items():
+        if kind == 0:
+            if prec == "server":
+                exp, fb = sg.infer(d32(rq["T"]), d32(rq["p"]), d32(rq["Y"]))
+                fb = fb.cpu().numpy().astype(bool)
+                assert fb[::5].all()
+            elif prec == "fp64":
+                exp, _ = ctx.props(d64(rq["T"]), d64(rq["p"]), d64(rq["Y"]), precision="fp64")
+            else:
+                exp, _ = ctx.props(d32(rq["T"]), d32(rq["p"]), d32(rq["Y"]), precision=prec)
+            exp = exp.float().cpu().numpy()
+        else:
+            if prec == "fp64":
+                Tn, _, _ = ctx.T_from_h(d64(rq["h"]), d64(rq["p"]), d64(rq["Y"]), d64(rq["T"]), precision="fp64",
+                                        rtol=1e-12)
+            else:
+                Tn, _, _ = ctx.T_from_h(d32(rq["h"]), d32(rq["p"]), d32(rq["Y"]), d32(rq["T"]),
+                                        precision="mixed" if prec in ("server", "mixed") else "fp32", rtol=1e-6)
+            exp = Tn.float().cpu().numpy()
+        assert np.array_equal(out, exp, equal_nan=True), (prec, kind)
+    # against the oracle (inputs: the FP32 request values, widened)
+    x = lambda rq, k: rq[k].astype(np.float64)
+    for prec, sel in (("fp64", slice(None, None, 7)), ("server", slice(None, None, 5))):
+        t, rq, out = reqs[(prec, 0)]
+        o, ost = orc.props(species, x(rq, "T")[sel], x(rq, "p")[sel], x(rq, "Y")[:, sel])
+        ok = ost == 0
+        assert ok.sum() > 100
+        err = rel_errors(out[:, sel].astype(np.float64)[:, ok], o[:, ok], x(rq, "T")[sel][ok])
+        assert err.max() < 1e-6, (prec, err.max())
+    t, rq, out = reqs[("fp64", 1)]
+    sel = slice(None, None, 7)
+    Tor, ost, _ = orc.T_from_h(species, x(rq, "h")[sel], x(rq, "p")[sel], x(rq, "Y")[:, sel], x(rq, "T")[sel])
+    ok = ost == 0
+    assert ok.sum() > 100
+    assert np.max(np.abs(out[sel][ok] - Tor[ok]) / Tor[ok]) < 1e-6
