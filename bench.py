@@ -556,6 +556,39 @@ def run_ours(args):
         next_rows["props_mixed_error_vs_fp64"] = TR.relative_rms(outm[:, ok6], out64[:, ok6].float())
         del hk64, dk64, hk32, dk32, outm, Tnm
 
+    # the FP64 inversion started from the inverse network's T (the surrogate as
+    # the inversion's warm start), against the benchmark's start at the field's
+    # T: FP64 Newton iterations per cell and time, with and without the FP32
+    # warm start; results within the inversion's tolerance of each other
+    warm = None
+    if sgi is not None:
+        outw = torch.empty((6, n), dtype=torch.float32, device=dev)
+        fbw = torch.empty(n, dtype=torch.uint8, device=dev)
+        sgi.infer(hs32, p32, Y32, out=outw, used_fallback=fbw)      # T from h* = h(T_true)
+        Tnet = outw[0].double().contiguous()
+        del outw
+        ctx64 = binding.PropertyContext(species, newton_fp64_only=True)
+        Tw = torch.empty_like(T64)
+        warm = {"network_fallback_fraction": float(fbw.float().mean())}
+        for name, c, guess in (("field_T_fp32_warm_start", ctx, T64), ("network_T_fp32_warm_start", ctx, Tnet),
+                               ("field_T_fp64_only", ctx64, T64), ("network_T_fp64_only", ctx64, Tnet)):
+            fn = lambda: c.T_from_h(hs64, p64, Y64, guess, "fp64", T_out=Tw, status=st, iters=it)
+            for _ in range(2):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            okw = st == 0
+            warm[name] = {"ms": e0.elapsed_time(e1) / 3, "fp64_iters_per_cell": float(it.double().mean()),
+                          "converged_fraction": float(okw.double().mean()),
+                          "max_rel_diff_vs_field_start": float(((Tw - Tn64).abs() / Tn64)[okw].max())}
+        ctx64.close()
+        del Tnet, Tw, fbw
+
     # error of the reduced-precision paths on the field against the FP64 PR
     # path's outputs of the last timed step (rel RMS, p99, max per property)
     field_err = None
@@ -647,6 +680,7 @@ def run_ours(args):
         "field_error_vs_pr_fp64": field_err,
         "roofline": roofline,
         "next_rows": next_rows,
+        "inversion_from_network_T": warm,
         "pipe_peaks": pipe_peaks,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
