@@ -45,6 +45,14 @@ FP64_PEAK_TFLOPS = FP64_PEAK_NOMINAL_TFLOPS
 # (2 x DFMA + DADD + DMUL per launch / cells) of one launch on the 128^3
 # flame-vortex field; reported beside the algorithmic count as kernel_flops
 FP64_FLOPS_PER_CELL = {"props_fp64": 1582.7, "newton_fp64": 1309.0, "species_fp64": 4117.0}
+# Algorithmic FP64 work per cell of the forward property path, from the
+# oracle's operation counter on the 256^3 flame-vortex field (oracle/count_ops.py,
+# whose record is oracle/op_counts_flame_vortex_256.json): the method's
+# additions and multiplications, with divisions, roots and transcendental calls
+# weighted by the FP64-pipe work of one CUDA call measured on GB300.  The
+# inversion's algorithmic work depends on how many evaluations a method takes,
+# so its roofline stays on the executed count above.
+ALGO_FP64_FLOPS_PER_CELL = {"props_fp64": 1698.6035400390624}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
 # / cells) of the same captures; a full launch moves this x its cells (the
 # surrogates: DRAM bytes per row of one fused-inference chunk launch)
@@ -639,8 +647,14 @@ def run_ours(args):
         r = {"ms": per_path_ms[nm], "cell_evals_per_s": n / sec, "algorithmic_GBps": gbs,
              "hbm_frac": gbs / pk["hbm_gbs"], "bytes_per_cell": BYTES_PER_CELL[nm]}
         if nm in FP64_FLOPS_PER_CELL:
-            tf = FP64_FLOPS_PER_CELL[nm] * n / sec / 1e12
-            r.update({"fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS})
+            fl = ALGO_FP64_FLOPS_PER_CELL.get(nm, FP64_FLOPS_PER_CELL[nm])
+            tf = fl * n / sec / 1e12
+            r.update({"fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS,
+                      "fp64_flops_per_cell": fl,
+                      "fp64_flops_source": "algorithmic (oracle op counter)" if nm in ALGO_FP64_FLOPS_PER_CELL
+                      else "executed (ncu DFMA, DADD, DMUL counts)",
+                      "kernel_flops_per_cell": FP64_FLOPS_PER_CELL[nm],
+                      "kernel_fp64_frac": FP64_FLOPS_PER_CELL[nm] * n / sec / 1e12 / FP64_PEAK_TFLOPS})
         if nm in ("surrogate_bf16", "surrogate_inverse_bf16"):
             ff = fb_frac if nm == "surrogate_bf16" else float(fbi.float().mean())
             tf = mlp_flops_per_cell() * n * (1.0 - ff) / sec / 1e12
@@ -655,7 +669,8 @@ def run_ours(args):
     if "fp64_tflops" in d:
         roofline = {"bound": "alu", "kernel": dom, "achieved": d["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
                     "peak_nominal": FP64_PEAK_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": d["fp64_frac"],
+                    "unit": "TFLOP/s", "frac": d["fp64_frac"], "flops_per_cell": d["fp64_flops_per_cell"],
+                    "flops_source": d["fp64_flops_source"], "kernel_frac": d["kernel_fp64_frac"],
                     "traffic": TRAFFIC_BYTES_PER_CELL[dom] * n if dom in TRAFFIC_BYTES_PER_CELL else None,
                     "peak_source": "FP64 pipe, " + pipe_peaks["fp64_source"] +
                                    "; nominal 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}

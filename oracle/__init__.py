@@ -34,6 +34,62 @@ R = 8.314462618
 STATUS = {0: "ok", 1: "newton_maxit", 2: "h_out_of_range", 3: "no_root", 4: "bad_input", 5: "ambiguous"}
 
 
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_LIB = os.path.join(_HERE, "libopcount.so")
+_opc = None
+
+
+def build_opcount(force: bool = False) -> str:
+    """Compile the operation-counting build of the oracle (opcount.cpp, g++)."""
+    newest = max(os.path.getmtime(_OPC_SRC), os.path.getmtime(_SRC))
+    if force or not os.path.exists(_OPC_LIB) or os.path.getmtime(_OPC_LIB) < newest:
+        tmp = _OPC_LIB + f".tmp{os.getpid()}"
+        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall",
+               "-Wno-class-memaccess", "-Wno-unused-function", "-o", tmp, _OPC_SRC]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _OPC_LIB)
+    return _OPC_LIB
+
+
+OP_KINDS = ("add", "mul", "div", "sqrt", "cbrt", "exp", "expm1", "log", "log1p", "pow", "trig", "cmp")
+OP_STEPS = {0: "diagnostics", 1: "composition", 2: "species EOS terms", 3: "mixing", 4: "cubic roots",
+            5: "root selection", 6: "ideal gas", 7: "departures", 8: "Chung mixture rules",
+            9: "Chung dense correlation", 10: "output assembly"}
+
+
+def op_counts(sp, T, p, Y):
+    """Per-cell operation counts of the oracle (mean over the cells that
+    evaluate with status 0): {"steps": {name: {kind: count}}, "short":
+    {"mixing" | "chung_rules" | "cubic_roots" | "species_terms" | "ideal_gas":
+    {kind: count}}, "check": [max relative difference of the five short forms
+    from the oracle],
+    "cells": n}.  See opcount.cpp for what is counted."""
+    global _opc
+    with _lock:
+        if _opc is None:
+            L = ctypes.CDLL(build_opcount())
+            vp, i64 = ctypes.c_void_p, ctypes.c_int64
+            L.orc_count_ops.argtypes = [vp] * 10 + [ctypes.c_int, i64, vp, vp, vp, vp, vp, vp]
+            L.orc_count_ops.restype = i64
+            _opc = L
+    tb = sp if isinstance(sp, Table) else Table(sp)
+    a = tb.arrays
+    T, p, Y = _soa(T, p, Y, tb.n)
+    n = T.size
+    nk = len(OP_KINDS)
+    counts = np.zeros((16, nk))
+    short = np.zeros((5, nk))
+    check = np.zeros(5)
+    good = _opc.orc_count_ops(*[_ptr(a[k]) for k in ("W", "Tc", "pc", "omega", "Vc", "dipole", "kappa", "nasa_lo",
+                                                      "nasa_hi", "T_mid")], tb.n, n, _ptr(T), _ptr(p), _ptr(Y),
+                              _ptr(counts), _ptr(short), _ptr(check))
+    g = max(int(good), 1)
+    steps = {OP_STEPS[s]: dict(zip(OP_KINDS, (counts[s] / g).tolist())) for s in OP_STEPS}
+    shorts = {nm: dict(zip(OP_KINDS, (short[r] / g).tolist()))
+              for r, nm in enumerate(("mixing", "chung_rules", "cubic_roots", "species_terms", "ideal_gas"))}
+    return {"steps": steps, "short": shorts, "check": check.tolist(), "cells": int(good)}
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (idempotent)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):

@@ -54,6 +54,15 @@ static int orc_threads(int nthreads)
 
 #define ORC_R 8.314462618 /* J/(mol K) */
 
+/* Step markers for the operation-counting build (opcount.cpp includes this
+ * file with ORC_STEP defined); nothing in the oracle's own build.  Steps:
+ * 1 composition, 2 species EOS terms, 3 mixing, 4 cubic roots, 5 root
+ * selection, 6 ideal gas, 7 departures, 8 Chung mixture rules, 9 Chung
+ * dense correlation, 10 output assembly, 0 diagnostics (not the method). */
+#ifndef ORC_STEP
+#define ORC_STEP(s) ((void)0)
+#endif
+
 /* Species data, all arrays of length N (nasa_*: N x 7, kij: N x N or NULL). */
 typedef struct {
     int32_t N;
@@ -301,6 +310,7 @@ static void chung_dense(const chung_cs *cs, double T, double rho_mol, double cv_
     double Mkg = cs->M * 1e-3;
     double q = 3.586e-3 * sqrt(cs->Tc / Mkg) / Vc23;
     *lam = 31.2 * eta0 * Psi / Mkg * (1.0 / H2 + Bc[5] * y) + q * Bc[6] * y * y * sqrt(Tr) * H2;
+    ORC_STEP(0);
     *lam0 = 31.2 * eta0 * Psi / Mkg;
     if (cmu) {
         double c = cancel3(E[0] * fy4, E[1] * G1 * exp(E[4] * y), E[2] * G1);
@@ -336,12 +346,14 @@ static int cell_thermo(const orc_species *sp, double T, double p, const double *
     }
     if (fabs(ysum - 1.0) > 1e-6) return ORC_BAD_INPUT;
     /* 1. mole fractions */
+    ORC_STEP(1);
     for (int k = 0; k < N; ++k) X[k] = (Y[k * ystride] / (sp->W[k] * 1e-3)) / s;
     double Wbar = 0.0;
     for (int k = 0; k < N; ++k) Wbar += X[k] * sp->W[k] * 1e-3;
     d->Wbar = Wbar;
 
     /* 2. pure-species PR parameters and alpha(T, omega) (PR 1976) */
+    ORC_STEP(2);
     double Oa, Ob;
     orc_pr_omegas(sp->printed_constants, &Oa, &Ob);
     double a[64], r[64], dr[64], d2r[64], b[64];
@@ -358,6 +370,7 @@ static int cell_thermo(const orc_species *sp, double T, double p, const double *
         d2r[k] = sg * sqrt(ac) * kap / (4.0 * sqrt(Tc)) * pow(T, -1.5);
     }
     /* 3. van der Waals mixing: plain double sums */
+    ORC_STEP(3);
     double am = 0, dam = 0, d2am = 0, bm = 0;
     for (int i = 0; i < N; ++i) {
         bm += X[i] * b[i];
@@ -372,26 +385,34 @@ static int cell_thermo(const orc_species *sp, double T, double p, const double *
     d->am = am; d->dam = dam; d->d2am = d2am; d->bm = bm;
 
     /* 4. cubic and root selection */
+    ORC_STEP(4);
     double RT = ORC_R * T;
     double A = am * p / (RT * RT), B = bm * p / RT;
     d->A = A; d->B = B;
     double c2 = -(1.0 - B), c1 = A - 3.0 * B * B - 2.0 * B, c0 = -(A * B - B * B - B * B * B);
     d->n_roots = orc_cubic_real_roots(c2, c1, c0, d->roots);
+    ORC_STEP(5);
     double best = NAN, gbest = INFINITY, gsecond = INFINITY;
     int nphys = 0;
-    for (int k = 0; k < d->n_roots; ++k) {
-        double z = d->roots[k];
-        if (!(z > B)) continue;
-        ++nphys;
-        double g = pr_gres(z, A, B);
-        if (nphys == 1) { best = z; gbest = g; continue; }
-        double gap = fabs(g - gbest);
-        if (g < gbest - 1e-12 || (gap <= 1e-12 && z > best)) {
-            gsecond = gbest; gbest = g; best = z;
-        } else if (g < gsecond) {
-            gsecond = g;
+    for (int k = 0; k < d->n_roots; ++k)
+        if (d->roots[k] > B) { if (nphys == 0) best = d->roots[k]; ++nphys; }
+    /* one physical root: it is the root; several: the least residual Gibbs energy */
+    if (nphys > 1) {
+        int seen = 0;
+        for (int k = 0; k < d->n_roots; ++k) {
+            double z = d->roots[k];
+            if (!(z > B)) continue;
+            double g = pr_gres(z, A, B);
+            if (++seen == 1) { best = z; gbest = g; continue; }
+            double gap = fabs(g - gbest);
+            if (g < gbest - 1e-12 || (gap <= 1e-12 && z > best)) {
+                gsecond = gbest; gbest = g; best = z;
+            } else if (g < gsecond) {
+                gsecond = g;
+            }
         }
     }
+    ORC_STEP(0);
     d->n_phys = nphys;
     d->gres_gap = (nphys > 1) ? fabs(gsecond - gbest) : INFINITY;
     if (nphys == 0) return ORC_NO_ROOT;
@@ -407,6 +428,7 @@ static int cell_thermo(const orc_species *sp, double T, double p, const double *
     }
 
     /* 5. ideal-gas part (NASA-7) */
+    ORC_STEP(6);
     double h_ig = 0, cp_ig = 0;
     for (int k = 0; k < N; ++k) {
         double cpR, hRT;
@@ -419,6 +441,7 @@ static int cell_thermo(const orc_species *sp, double T, double p, const double *
     d->cv_ig_molar = cp_ig * Wbar - ORC_R;
 
     /* 6. departures from the PR residual Helmholtz energy */
+    ORC_STEP(7);
     const double s2 = sqrt(2.0);
     double V = Z * RT / p;
     double L = log((Z + (1.0 + s2) * B) / (Z + (1.0 - s2) * B));
@@ -429,6 +452,7 @@ static int cell_thermo(const orc_species *sp, double T, double p, const double *
     double dpdV = -RT / ((V - bm) * (V - bm)) + 2.0 * am * (V + bm) / (den * den);
     double cp_dep = cv_dep - T * dpdT * dpdT / dpdV - ORC_R;
     d->h_dep = h_dep; d->cp_dep = cp_dep; d->dpdT = dpdT; d->dpdV = dpdV;
+    ORC_STEP(0);
     if (nphys > 1 && d->gres_gap < 1e-9) return ORC_AMBIGUOUS;
     return ORC_OK;
 }
@@ -459,6 +483,7 @@ static void cell_transport(const orc_species *sp, double T, double p, const doub
         *mu = m; *lam = l; *mu0 = m0; *lam0 = l0;
         return;
     }
+    ORC_STEP(8);
     /* Chung mixing rules: sigma_i = 0.809 Vc^(1/3) [A], eps_i/k = Tc/1.2593,
      * pair values by geometric/arithmetic/harmonic combining, then
      * sigma_m^3, (eps/k)_m, M_m, omega_m, mu_m^4, kappa_m as double sums. */
@@ -494,6 +519,7 @@ static void cell_transport(const orc_species *sp, double T, double p, const doub
     double mum = sqrt(sqrt(mum4));
     double mur = 131.3 * mum / sqrt(cs.Vc * cs.Tc);
     cs.mur4 = mur * mur * mur * mur;
+    ORC_STEP(9);
     chung_dense(&cs, T, rho_mol, d->cv_ig_molar, mu, lam, mu0, lam0, cmu, clam);
 }
 
@@ -511,6 +537,7 @@ static int orc_cell_z(const orc_species *sp, double T, double p, const double *Y
         return st;
     }
     double Z = d->Z;
+    ORC_STEP(10);
     out[0] = p * d->Wbar / (Z * ORC_R * T);
     out[1] = Z;
     out[2] = d->h_ig + d->h_dep / d->Wbar;
