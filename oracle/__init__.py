@@ -137,6 +137,8 @@ def lib():
             L.orc_diagnose.restype = None
             L.orc_props_at_Z.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
             L.orc_props_at_Z.restype = None
+            L.orc_chung_pure.argtypes = [d] * 9 + [vp]
+            L.orc_chung_pure.restype = None
             L.orc_T_from_h.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, i32, d, i32]
             L.orc_T_from_h.restype = None
             L.orc_cubic_real_roots.argtypes = [d, d, d, vp]
@@ -223,6 +225,14 @@ def h_ideal(sp, T, Y, **kw):
     h = np.empty(T.size)
     lib().orc_h_ideal(tb.ref, T.size, _ptr(T), _ptr(Y), _ptr(h))
     return h
+
+
+def chung_pure(Tc, Vc, omega, M, dipole, kappa, T, rho_mol, cv_molar):
+    """Chung's correlation for one pure fluid at (T, rho_mol): (mu, lambda,
+    mu_dilute, lambda_dilute) [Pa s, W/(m K)]; units as the species table."""
+    out = np.zeros(4)
+    lib().orc_chung_pure(Tc, Vc, omega, M, dipole, kappa, T, rho_mol, cv_molar, _ptr(out))
+    return tuple(out)
 
 
 def props_at_Z(sp, T, p, Y, Z, **kw):

@@ -328,6 +328,22 @@ static void chung_dense(const chung_cs *cs, double T, double rho_mol, double cv_
     }
 }
 
+/* Chung's dense-fluid viscosity and conductivity of one pure fluid at a given
+ * temperature and molar density (a test aid: the correlation alone, on the
+ * state a worked example or a measurement states).  Units as the species
+ * table: Tc [K], Vc [cm^3/mol], M [g/mol], dipole [debye]; rho_mol
+ * [mol/m^3], cv_molar [J/(mol K)].  out = {mu, lambda, mu_dilute,
+ * lambda_dilute} [Pa s, W/(m K)]. */
+void orc_chung_pure(double Tc, double Vc, double omega, double M, double dipole, double kappa, double T,
+                    double rho_mol, double cv_molar, double out[4])
+{
+    chung_cs cs;
+    cs.Tc = Tc; cs.Vc = Vc; cs.omega = omega; cs.M = M; cs.kappa = kappa;
+    const double mur = 131.3 * dipole / sqrt(Vc * Tc);
+    cs.mur4 = mur * mur * mur * mur;
+    chung_dense(&cs, T, rho_mol, cv_molar, &out[0], &out[1], &out[2], &out[3], NULL, NULL);
+}
+
 /* ---------------------------------------------------------------------- */
 /* Thermodynamic part of one cell: everything up to h and cp.  Returns the
  * status (0, 3, 4 or 5).  Output arrays may be NULL except d. */

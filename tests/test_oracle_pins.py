@@ -514,3 +514,48 @@ def test_psi_ideal_gas_limit(orc, species):
     # the other outputs are those of props; alpha is lambda / cp by definition
     o6, _ = orc.props(species, T, p, Y)
     assert np.array_equal(o[:6], o6)
+
+
+REF = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fluid_reference_data.json")))
+
+
+def _cv0_molar(species, k, T):
+    """Ideal-gas molar cv of species k at T (NASA-7 low range, T < T_mid)."""
+    a = species.nasa_lo[k]
+    return R * (a[0] + a[1] * T + a[2] * T ** 2 + a[3] * T ** 3 + a[4] * T ** 4 - 1.0)
+
+
+def test_chung_polar_terms_against_liquid_water(orc, species):
+    """Sec. 2 (Chung's transport model): the polar (mu_r^4) and association
+    (kappa) columns of Chung's viscosity coefficients, checked on dense liquid
+    water at three measured states (IAPWS-2008 viscosity at the IAPWS-95
+    density).  Without water's dipole and association terms the correlation
+    is 90-500 % off there; with them, within 5 %."""
+    k = W.SPECIES.index("H2O")
+    d = REF["water_liquid_viscosity"]
+    for s in d["states"]:
+        rho_mol = s["rho"] / species.W[k] * 1000.0
+        mu, lam, _, _ = orc.chung_pure(species.Tc[k], species.Vc[k], species.omega[k], species.W[k],
+                                       species.dipole[k], species.kappa[k], s["T"], rho_mol,
+                                       _cv0_molar(species, k, s["T"]))
+        assert mu == pytest.approx(s["mu"], rel=d["tol_rel"]), (s, mu)
+        mu0, _, _, _ = orc.chung_pure(species.Tc[k], species.Vc[k], species.omega[k], species.W[k], 0.0, 0.0,
+                                      s["T"], rho_mol, _cv0_molar(species, k, s["T"]))
+        assert abs(mu0 / s["mu"] - 1.0) > 0.5          # the polar terms matter here
+
+
+def test_chung_dense_terms_against_cryogenic_liquids(orc, species):
+    """Sec. 2: the dense-fluid terms of Chung's viscosity (G2 and eta**) and
+    conductivity (H2 and the y^2 term), checked on saturated liquid oxygen and
+    methane at their normal boiling points (y = rho Vc / 6 near 0.45, where
+    these terms carry most of the value)."""
+    d = REF["cryogenic_liquids"]
+    for s in d["states"]:
+        k = W.SPECIES.index(s["species"])
+        rho_mol = s["rho"] / species.W[k] * 1000.0
+        mu, lam, mu0, lam0 = orc.chung_pure(species.Tc[k], species.Vc[k], species.omega[k], species.W[k],
+                                            species.dipole[k], species.kappa[k], s["T"], rho_mol,
+                                            _cv0_molar(species, k, s["T"]))
+        assert mu == pytest.approx(s["mu"], rel=d["tol_rel"]), (s, mu)
+        assert lam == pytest.approx(s["lambda"], rel=d["tol_rel"]), (s, lam)
+        assert mu > 5 * mu0 and lam > 5 * lam0            # the dense terms carry the value
