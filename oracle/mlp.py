@@ -77,6 +77,38 @@ def forward(params, X, form="erf"):
     return h, cache
 
 
+# ------------------------------------------------ BF16 storage (inference)
+def bf16(x):
+    """Round to the nearest BF16 number (ties to even), via float32: the
+    storage format of the tensor-core path's weights and activations."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16_storage(params, X, form="tanh"):
+    """The forward pass with the values rounded where the tensor-core path
+    stores them in BF16: every weight, the inputs as a pair hi = bf16(x),
+    lo = bf16(x - hi) (both multiplied by the same weight) and every hidden
+    activation after GeLU; the arithmetic in float64.  Returns (yhat,
+    cache of (z_l, h_l before rounding, h_l stored))."""
+    x = np.asarray(X, dtype=np.float64)
+    hi = bf16(x)
+    h = hi + bf16(x - hi)
+    cache = [(None, x, h)]
+    for li, (W, b) in enumerate(params):
+        z = h @ bf16(W).T + b
+        if li + 1 < len(params):
+            g = gelu(z, form)
+            h = bf16(g)
+            cache.append((z, g, h))
+        else:
+            h = z
+            cache.append((z, z, z))
+    return h, cache
+
+
 def loss(yhat, s, kind="mse"):
     if kind == "l1":
         return float(np.mean(np.abs(yhat - s)))

@@ -11,6 +11,8 @@ import pytest
 from oracle import mlp as omlp
 from paper_2312_04830_gb300 import workloads as W
 
+from . import mlp_bound as MB
+
 pytestmark = pytest.mark.gpu
 
 
@@ -180,12 +182,26 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
     norm = sg.get_normalization().astype(np.float64)
     params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 6])
     s_in, _ = standardise(x[:, :n], y[:, :n], norm, species)
+    hig = h_ig_of(species, x[:, :n])
+    s_gpu = (omlp.output_targets(out, hig) - norm[26:32]) / norm[32:38]
+    # against the BF16-storage oracle, per sample, within the first-order bound
+    # of what the GPU may add (FP32 accumulation, hardware tanh, rounding-
+    # boundary flips); outputs carry the FP32 de-standardisation and exp
+    f = features(x[:, :n], species).T
+    in_err = 4 * MB.U32 * (np.abs(f) + np.abs(norm[0:13])) / norm[13:26]
+    yb, bound = MB.output_error_bound(params, s_in, in_err)
+    q = omlp.output_targets(out, hig)
+    bound += 16 * MB.U32 * (np.abs(q) + np.abs(norm[26:32]) + 1.0) / norm[32:38]
+    bound[:, 2] += 8 * MB.U32 * np.abs(hig) / norm[34]
+    err = np.abs(s_gpu - yb)
+    ratio = err / bound
+    print("vs BF16-storage oracle: median %.2e max %.2e; bound median %.2e max %.2e; max err/bound %.3f" %
+          (np.median(err), err.max(), np.median(bound), bound.max(), ratio.max()))
+    assert np.all(err <= bound)
+    # against the float64 network: the storage rounding itself
     yhat, _ = omlp.forward(params, s_in, "tanh")
-    s_gpu = (omlp.output_targets(out, h_ig_of(species, x[:, :n])) - norm[26:32]) / norm[32:38]
-    err = np.abs(s_gpu - yhat)
-    print("standardised output error: median", np.median(err), "max", err.max())
-    assert np.median(err) < 0.01
-    assert err.max() < 0.1
+    e64 = np.abs(s_gpu - yhat)
+    assert np.median(e64) < 0.01 and e64.max() < 0.1
     sg.close()
 
 
@@ -416,6 +432,39 @@ def features_inverse(x, species):
     return np.vstack([h - hf, p, Y, np.log(tpc), -np.log(s)])
 
 
+def inverse_input_error(x, species, f, norm):
+    """Bound on the GPU's standardised inputs' distance from the oracle's for
+    the (h, p, Y) input sets: h - h_f(Y) is a difference taken in FP32 of
+    terms up to |h| + |h_f|; the other features as the forward model's."""
+    import oracle
+    h = x[0].astype(np.float64)
+    hf = oracle.h_ideal(species, np.full(h.size, 298.15), x[2:].astype(np.float64))
+    a = np.abs(f.T) + np.abs(norm[0:13])
+    a[:, 0] = np.abs(h) + np.abs(hf) + np.abs(norm[0])
+    return 8 * MB.U32 * a / norm[13:26]
+
+
+def oracle_bilger(x, species):
+    import oracle
+    return oracle.bilger_z(species, W.ATOMS_CHO, W.Y_FUEL, W.Y_OX, x[2:].astype(np.float64))
+
+
+def check_against_bf16_oracle(label, params, s_in, s_gpu, in_err, out_err):
+    """Standardised outputs of the tensor-core path against the BF16-storage
+    oracle MLP, per sample, within the first-order bound of tests/mlp_bound.py
+    (plus the outputs' FP32 conversion out_err), and against the float64
+    network within what the storage rounding itself moves."""
+    yb, bound = MB.output_error_bound(params, s_in, in_err)
+    bound = bound + out_err
+    err = np.abs(s_gpu - yb)
+    print("%s vs BF16-storage oracle: median %.2e max %.2e; bound median %.2e max %.2e; max err/bound %.3f" %
+          (label, np.median(err), err.max(), np.median(bound), bound.max(), (err / bound).max()))
+    assert np.all(err <= bound)
+    yhat, _ = omlp.forward(params, s_in, "tanh")
+    e64 = np.abs(s_gpu - yhat)
+    assert np.median(e64) < 0.01 and e64.max() < 0.1
+
+
 def test_inverse_inference_matches_oracle_forward(ctx, orc, species, cuda):
     """The inverse model (enthalpy, pressure, composition in; T, rho, psi, mu,
     alpha, cp out, all as logarithms) through the fused tensor-core path,
@@ -432,12 +481,12 @@ def test_inverse_inference_matches_oracle_forward(ctx, orc, species, cuda):
     assert fb.sum() == 0
     norm = sg.get_normalization().astype(np.float64)
     params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 6])
-    s_in = (features_inverse(x[:, :n], species).T - norm[0:13]) / norm[13:26]
-    yhat, _ = omlp.forward(params, s_in, "tanh")
+    f = features_inverse(x[:, :n], species)
+    s_in = (f.T - norm[0:13]) / norm[13:26]
     s_gpu = (np.log(out).T - norm[26:32]) / norm[32:38]
-    err = np.abs(s_gpu - yhat)
-    print("inverse standardised output error: median", np.median(err), "max", err.max())
-    assert np.median(err) < 0.01 and err.max() < 0.1
+    in_err = inverse_input_error(x[:, :n], species, f, norm)
+    out_err = 16 * MB.U32 * (np.abs(np.log(out).T) + np.abs(norm[26:32]) + 1.0) / norm[32:38]
+    check_against_bf16_oracle("inverse", params, s_in, s_gpu, in_err, out_err)
     sg.close()
 
 
@@ -595,12 +644,16 @@ def test_bilger_inference_matches_oracle_forward(ctx, orc, species, cuda):
     norm = sg.get_normalization().astype(np.float64)
     assert np.all(norm[16:26] == 1.0)          # the unused input slots: zero variance, unit scale
     params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 6])
-    s_in = (features_bilger(x[:, :n], species, 0.3, 1e-3).T - norm[0:13]) / norm[13:26]
-    yhat, _ = omlp.forward(params, s_in, "tanh")
+    f = features_bilger(x[:, :n], species, 0.3, 1e-3)
+    s_in = (f.T - norm[0:13]) / norm[13:26]
     s_gpu = (np.log(out).T - norm[26:32]) / norm[32:38]
-    err = np.abs(s_gpu - yhat)
-    print("bilger standardised output error: median", np.median(err), "max", err.max())
-    assert np.median(err) < 0.01 and err.max() < 0.1
+    in_err = inverse_input_error(x[:, :n], species, f, norm)
+    # Bilger's Z in FP32 (a difference of coupling functions of order one over their
+    # range), then the Box-Cox power: d BoxCox / dZ = (Z + shift)^(lambda - 1)
+    Zb = np.clip(oracle_bilger(x[:, :n], species), 0.0, None)
+    in_err[:, 2] = (32 * MB.U32 * (Zb + 1e-3) ** (0.3 - 1.0) + 8 * MB.U32 * np.abs(f[2])) / norm[15]
+    out_err = 16 * MB.U32 * (np.abs(np.log(out).T) + np.abs(norm[26:32]) + 1.0) / norm[32:38]
+    check_against_bf16_oracle("bilger", params, s_in, s_gpu, in_err, out_err)
     sg.close()
 
 
@@ -782,12 +835,13 @@ def test_species_network_matches_oracle_forward(ctx, orc, species, cuda, kind):
     norm = sg.get_normalization().astype(np.float64)
     mean, std = out_stats(norm, 9)
     params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 9])
-    s_in = (features_inverse(x[:, :n], species).T - norm[0:13]) / norm[13:26]
-    yhat, _ = omlp.forward(params, s_in, "tanh")
+    f = features_inverse(x[:, :n], species)
+    s_in = (f.T - norm[0:13]) / norm[13:26]
     q = np.log(out) if kind == "dk" else out
-    err = np.abs((q.T - mean) / std - yhat)
-    print(kind, "standardised output error: median", np.median(err), "max", err.max())
-    assert np.median(err) < 0.01 and err.max() < 0.1
+    s_gpu = (q.T - mean) / std
+    in_err = inverse_input_error(x[:, :n], species, f, norm)
+    out_err = 16 * MB.U32 * (np.abs(q.T) + np.abs(mean) + 1.0) / std
+    check_against_bf16_oracle(kind, params, s_in, s_gpu, in_err, out_err)
     sg.close()
 
 
