@@ -198,6 +198,13 @@ pr_status pr_bilger_z(pr_ctx *ctx, pr_precision prec, int64_t n, const void *Y, 
 #define PR_PEAK_FP64_CBRT 7
 pr_status pr_measure_peak(int kind, double *ops_per_s);
 
+/* The FP64 exponential and logarithm the FP64 property paths use (a
+ * diagnostic, for their accuracy tests): y[i] = f(x[i]) for fn = 0 exp,
+ * 1 expm1, 2 log, 3 log1p (the library's table-driven forms: Tang, ACM TOMS
+ * 15 (1989) 144 and 16 (1990) 378), 4..7 the same functions of CUDA's math
+ * library.  x, y: DEVICE arrays of n doubles; asynchronous on `stream`. */
+pr_status pr_eval_math(int fn, int64_t n, const double *x, double *y, void *stream);
+
 /* Inversion T(h*, p, Y) by safeguarded Newton on f(T) = h(T) - h*, f' = cp,
  * inside the bracket [60, 5000] K, starting from T_guess (clipped to the
  * bracket).  A Newton step that leaves the current bracket, or follows a step

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "pr_internal.h"
+#include "pr_math64.cuh"
 
 namespace {
 
@@ -97,7 +98,40 @@ __global__ void __launch_bounds__(kPeakBlock) f64_call_kernel(double *sink, int 
     if (s == -1.2345e300) sink[0] = s;
 }
 
+// The library's FP64 exp, expm1, log, log1p (fn 0..3) and CUDA's (fn 4..7) on
+// an array, for their accuracy tests.
+__global__ void eval_math_kernel(int fn, int64_t n, const double *x, double *y)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        double r;
+        switch (fn) {
+        case 0: r = m64::exp(v); break;
+        case 1: r = m64::expm1(v); break;
+        case 2: r = m64::log(v); break;
+        case 3: r = m64::log1p(v); break;
+        case 4: r = ::exp(v); break;
+        case 5: r = ::expm1(v); break;
+        case 6: r = ::log(v); break;
+        default: r = ::log1p(v); break;
+        }
+        y[i] = r;
+    }
+}
+
 }  // namespace
+
+extern "C" pr_status pr_eval_math(int fn, int64_t n, const double *x, double *y, void *stream)
+{
+    PR_CHECK_ARG(fn >= 0 && fn <= 7, "pr_eval_math: unknown function %d", fn);
+    PR_CHECK_ARG(n >= 0, "pr_eval_math: n < 0");
+    if (n == 0) return PR_OK;
+    PR_CHECK_ARG(x && y && prgb::aligned(x, 8) && prgb::aligned(y, 8), "pr_eval_math: bad array");
+    const int64_t b = (n + 255) / 256;
+    eval_math_kernel<<<(int)(b < 4096 ? b : 4096), 256, 0, (cudaStream_t)stream>>>(fn, n, x, y);
+    PR_CUDA_TRY(cudaGetLastError());
+    return PR_OK;
+}
 
 extern "C" pr_status pr_measure_peak(int kind, double *ops_per_s)
 {

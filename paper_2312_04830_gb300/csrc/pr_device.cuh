@@ -30,6 +30,8 @@
 
 #include "prgb300.h"
 
+#include "pr_math64.cuh"
+
 namespace prk {
 
 constexpr double kR = 8.314462618;                     // J/(mol K)
@@ -69,10 +71,11 @@ template <> struct M<double> {
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
     static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
     static __device__ __forceinline__ double cbrt(double x) { return ::cbrt(x); }
-    static __device__ __forceinline__ double log(double x) { return ::log(x); }
-    static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
-    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
-    static __device__ __forceinline__ double expm1(double x) { return ::expm1(x); }
+    // table-driven forms with fewer FP64-pipe operations (pr_math64.cuh)
+    static __device__ __forceinline__ double log(double x) { return m64::log(x); }
+    static __device__ __forceinline__ double log1p(double x) { return m64::log1p(x); }
+    static __device__ __forceinline__ double exp(double x) { return m64::exp(x); }
+    static __device__ __forceinline__ double expm1(double x) { return m64::expm1(x); }
     static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
     static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
     static __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
