@@ -113,13 +113,16 @@ __device__ __forceinline__ Real psi_h(const Thermo<Real> &th, Real T, Real W)
     return drho_dp_T - drho_dT_p * dh_dp_T / (th.cp * W);
 }
 
-// resident CTAs per SM the FP32 property kernels ask the compiler to allow
-// for (a register cap; 0 leaves the choice to the compiler, as for FP64)
+// resident CTAs per SM the property kernels ask the compiler to allow for
+// (a register cap; 0 leaves the choice to the compiler)
 #ifndef PRK_FP32_MINB
 #define PRK_FP32_MINB 0
 #endif
+#ifndef PRK_FP64_MINB
+#define PRK_FP64_MINB 0
+#endif
 template <typename Real>
-constexpr int props_min_blocks() { return sizeof(Real) == 4 ? PRK_FP32_MINB : 0; }
+constexpr int props_min_blocks() { return sizeof(Real) == 4 ? PRK_FP32_MINB : PRK_FP64_MINB; }
 
 template <typename Real, typename RZ, int NS, bool KIJ>
 __global__ void __launch_bounds__(kBlock, props_min_blocks<Real>()) props_kernel(const __grid_constant__ PropsArgs<Real> a,
