@@ -56,8 +56,7 @@ ALGO_FP64_FLOPS_PER_CELL = {"props_fp64": 1698.6035400390624}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
 # / cells) of the same captures; a full launch moves this x its cells (the
 # surrogates: DRAM bytes per row of one fused-inference chunk launch)
-TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 108.3,
-                          "surrogate_bf16": 353.9, "surrogate_inverse_bf16": 446.4}
+TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 108.3}
 # surrogate: 2 x (13*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
@@ -70,7 +69,7 @@ TRANSPORT_CONFIDENCE = 0.02
 TRANSPORT_CONFIDENCE_INVERSE = 0.05
 
 # rows per surrogate inference chunk: all layers of a chunk run in one
-# persistent launch, activations in L2-resident rings
+# launch (CTA pairs with each 256-row block's activations in shared memory)
 SG_CHUNK = 1 << 22
 
 # Algorithmic bytes per cell of each path (N = 9 species): inputs + outputs
@@ -480,11 +479,11 @@ def run_ours(args):
         paths.append("surrogate_bf16")
         calls["surrogate_bf16"] = lambda: sg.infer(T32, p32, Y32, out=outsg, used_fallback=fb)
         n_chunks = (n + SG_CHUNK - 1) // SG_CHUNK
-        launches["surrogate_bf16"] = n_chunks * (1 + 1 + 1 + 1)   # prep, fused MLP, confidence test, fallback
+        launches["surrogate_bf16"] = n_chunks * (1 + 1 + 1 + 1)   # prep, MLP, confidence test, fallback
         # the inverse model: h*, p, Y -> T, rho, psi, mu, alpha, cp (the paper's arrangement)
         paths.append("surrogate_inverse_bf16")
         calls["surrogate_inverse_bf16"] = lambda: sgi.infer(hi32, p32, Y32, out=outsi, used_fallback=fbi)
-        launches["surrogate_inverse_bf16"] = n_chunks * (1 + 1 + 1 + 1)   # prep, fused MLP, transport test, fallback
+        launches["surrogate_inverse_bf16"] = n_chunks * (1 + 1 + 1 + 1)   # prep, MLP, transport test, fallback
     launches_per_step = sum(launches.values())
 
     def step(ev=None):

@@ -313,12 +313,15 @@ pr_status surrogate_loss_grad(sg_model *m, int64_t batch, const float *x, int64_
 pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p, const float *Y, int64_t ldY,
                           float *out, int64_t ldo, uint8_t *used_fallback, void *stream);
 
-/* Model options.  SG_OPT_FUSED_INFER (default 1 when available): run all
- * layers of an inference chunk in one persistent cooperative launch whose
+/* Model options.  SG_OPT_FUSED_INFER: run all layers of an inference chunk
+ * in one launch.  3 (the default for widths 256 and 512 when the device
+ * takes cluster launches): CTA pairs (clusters of two, tcgen05 pair MMA,
+ * M = 256) that take each block of 256 rows through every layer with its
+ * activations resident in shared memory, only the weights streaming from
+ * L2; 1 (the default otherwise): a persistent cooperative launch whose
  * activations stay in L2-sized rings (widths that are multiples of 256, up
- * to 1024, hidden_layers x width <= 4528).  1: 128 x 256 tiles, one CTA
- * each; 2: 256 x 256 tiles on CTA pairs (clusters of two, tcgen05 pair MMA,
- * each CTA holding half of every weight tile), falling back to 1 when the
+ * to 1024, hidden_layers x width <= 4528), 128 x 256 tiles, one CTA each;
+ * 2: the same with 256 x 256 tiles on CTA pairs, falling back to 1 when the
  * device refuses that launch; 0: one GEMM launch per layer.  All give
  * identical outputs.  PR_EINVAL for an unknown option or a value the model
  * cannot take. */
@@ -399,7 +402,8 @@ pr_status surrogate_set_option(sg_model *m, int option, int value);
 
 /* Current value of an option (host int *value).  For SG_OPT_FUSED_INFER it
  * is the kernel the next inference runs: 0 per-layer launches, 1 single
- * CTAs, 2 CTA pairs.  PR_EINVAL for an unknown option or a null pointer. */
+ * CTAs, 2 CTA pairs, 3 resident activations.  PR_EINVAL for an unknown
+ * option or a null pointer. */
 pr_status surrogate_get_option(const sg_model *m, int option, int *value);
 
 /* Box-Cox parameters of Bilger's mixture fraction in SG_MODE_BILGER (the

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "mlp_fused.cuh"
+#include "mlp_resident.cuh"
 #include "mlp_gemm.cuh"
 #include "pr_device.cuh"
 #include "pr_internal.h"
@@ -943,6 +944,64 @@ void fused_lag(int G, int ips, int &D, int &ring)
     ring = 2 * D + 4;
 }
 
+// The resident-activation kernel for width W (256 or 512).
+inline const void *resident_fn(int W)
+{
+    return W == 256 ? reinterpret_cast<const void *>(mlp_resident_kernel<256>)
+                    : reinterpret_cast<const void *>(mlp_resident_kernel<512>);
+}
+
+// CTA pairs of the resident-activation kernel the device holds at once (0:
+// none, or cluster launches unavailable).
+int resident_pairs(int L, int W)
+{
+    if (cudaFuncSetAttribute(resident_fn(W), cudaFuncAttributeMaxDynamicSharedMemorySize, ResCfg::kMaxSmem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * num_sms_current(), 1, 1);
+    cfg.blockDim = dim3(kResThreads, 1, 1);
+    cfg.dynamicSmemBytes = ResCfg::smem_bytes(L, W);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, resident_fn(W), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+// One launch of the resident-activation kernel: a pair per block of 256 rows,
+// at most `pairs` pairs (each walks its blocks in turn; pairs never wait on
+// one another, so no co-residency is needed).
+cudaError_t launch_resident(const ResidentArgs &ra, int pairs, cudaStream_t st)
+{
+    const int R = (ra.M + 255) / 256;
+    const int g = R < pairs ? R : pairs;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * g), 1, 1);
+    cfg.blockDim = dim3(kResThreads, 1, 1);
+    cfg.dynamicSmemBytes = ResCfg::smem_bytes(ra.L, ra.W);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return ra.W == 256 ? cudaLaunchKernelEx(&cfg, mlp_resident_kernel<256>, ra)
+                       : cudaLaunchKernelEx(&cfg, mlp_resident_kernel<512>, ra);
+}
+
 GemmArgs base_args(sg_model *m)
 {
     GemmArgs a;
@@ -1000,6 +1059,11 @@ static pr_status build_maps(sg_model *m)
             ok = ok && make_map(&m->tmp_w[0], d.wb[0], KIN, W, KIN, kFusedBN / 2);
             for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tmp_w[l], d.wb[l], W, W, W, kFusedBN / 2);
             ok = ok && make_map(&m->tmp_w[L], d.wb[L], W, NOP, W, kFusedOutBN / 2);
+        }
+        if (m->res_pairs > 0) {   // resident activations: each CTA of a pair loads half of every N-tile
+            ok = ok && make_map(&m->tmr_w[0], d.wb[0], KIN, W, KIN, (uint32_t)(W / 4));
+            for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tmr_w[l], d.wb[l], W, W, W, (uint32_t)(W / 4));
+            ok = ok && make_map(&m->tmr_w[L], d.wb[L], W, NOP, W, 8);
         }
         const int64_t rr = (int64_t)m->fused_ring_rows * 128;
         ok = ok && make_map_3d(&m->tmf_ring_ld, m->ring, W, rr, L, 128);
@@ -1139,8 +1203,9 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
         }
         alloc((void **)&m->ring, (size_t)L * m->fused_ring_rows * 128 * W * 2);
         alloc((void **)&m->d_done, (size_t)ceil_div(C, 128) * (L + 1) * 4);
+        m->res_pairs = ResCfg::supports(L, W) ? resident_pairs(L, W) : 0;
     }
-    m->fused_on = m->fused_ok;
+    m->fused_on = m->res_pairs > 0 ? 3 : m->fused_ok;   // resident activations where the shape allows
     alloc((void **)&d.hi[0], C * W * 2);
     alloc((void **)&d.hi[1], C * W * 2);
     alloc((void **)&m->d_list, C * 4);
@@ -1381,7 +1446,27 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
         prep_infer_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, used_fallback,
                                                                  m->d_flags, m->d_list, m->d_count);
         PR_CUDA_TRY(cudaGetLastError());
-        if (m->fused_on) {
+        if (m->fused_on == 3 && m->res_pairs > 0) {
+            // every layer in one launch, activations resident in shared memory
+            // (mlp_resident.cuh)
+            ResidentArgs ra;
+            memset(&ra, 0, sizeof(ra));
+            ra.tm_x = m->tm_xi;
+            for (int l = 0; l <= L; ++l) {
+                ra.tm_w[l] = m->tmr_w[l];
+                ra.bias[l] = d.master + d.lay[l].b_off;
+            }
+            ra.M = (int)mc; ra.L = L; ra.W = W;
+            ra.out6 = out + r0; ra.ld6 = ldo;
+            ra.out_mean = d.outstat; ra.out_std = d.outstat + NOUT_MAX;
+            ra.add_h = (d.mode != SG_MODE_FORWARD) ? nullptr : d.hig;
+            ra.log_mask = log_mask_of(d.mode, d.outputs);
+            ra.nout = d.nout;
+            ra.err = m->d_err;
+            ra.wait_cycles = m->wait_cycles > 0 ? m->wait_cycles : 4000000000LL;
+            ra.stall_test = m->stall_test;
+            PR_CUDA_TRY(launch_resident(ra, m->res_pairs, st));
+        } else if (m->fused_on) {
             // every layer in one cooperative launch (mlp_fused.cuh): single
             // CTAs, or CTA pairs when asked for and the device takes them
             bool pair = m->fused_on == 2 && m->fused_pair_ok;
@@ -1495,7 +1580,12 @@ pr_status surrogate_get_option(const sg_model *m, int option, int *value)
 {
     PR_CHECK_ARG(m != nullptr && value != nullptr, "surrogate_get_option: null argument");
     switch (option) {
-    case SG_OPT_FUSED_INFER: *value = !m->fused_on ? 0 : (m->fused_on == 2 && m->fused_pair_ok) ? 2 : 1; return PR_OK;
+    case SG_OPT_FUSED_INFER:
+        *value = !m->fused_on                            ? 0
+                 : (m->fused_on == 3 && m->res_pairs > 0) ? 3
+                 : (m->fused_on == 2 && m->fused_pair_ok) ? 2
+                                                          : 1;
+        return PR_OK;
     case SG_OPT_MODE: *value = m->dev.mode; return PR_OK;
     case SG_OPT_WAIT_LIMIT_KCYCLES: *value = (int)(m->wait_cycles / 1000); return PR_OK;
     case SG_OPT_TEST_STALL: *value = m->stall_test; return PR_OK;
@@ -1514,9 +1604,10 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
     PR_CHECK_ARG(m != nullptr, "surrogate_set_option: null model");
     switch (option) {
     case SG_OPT_FUSED_INFER:
-        PR_CHECK_ARG(value == 0 || ((value == 1 || value == 2) && m->fused_ok),
+        PR_CHECK_ARG(value == 0 || ((value == 1 || value == 2) && m->fused_ok) || (value == 3 && m->res_pairs > 0),
                      "surrogate_set_option: fused inference needs a width that is a multiple of 256, <= 1024, "
-                     "and its biases within shared memory");
+                     "and its biases within shared memory; resident activations need a width of 256 or 512 "
+                     "and cluster launches");
         m->fused_on = value;
         return PR_OK;
     case SG_OPT_WAIT_LIMIT_KCYCLES:

@@ -127,5 +127,9 @@ struct sg_model {
     uint32_t *d_done;
     CUtensorMap tmf_w[SG_MAX_HIDDEN + 1], tmf_ring_ld, tmf_ring_st;
     CUtensorMap tmp_w[SG_MAX_HIDDEN + 1];  // CTA pairs: half-height weight boxes
+    // resident-activation inference (mlp_resident.cuh): CTA pairs held at
+    // once (0: not available for this shape), weight boxes of W / 4 rows
+    int res_pairs;
+    CUtensorMap tmr_w[SG_MAX_HIDDEN + 1];
     std::vector<void *> allocs;
 };

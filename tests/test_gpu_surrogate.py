@@ -208,12 +208,14 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
 @pytest.mark.parametrize("width,layers,chunk,n", [(512, 4, 32768, 70000), (256, 2, 16384, 40961),
                                                    (512, 1, 1024, 300)])
 def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers, chunk, n):
-    """All layers of a chunk in one persistent launch (activation ring in L2,
-    cross-CTA arrival counters), with 128 x 256 tiles on single CTAs (the
-    default) or 256 x 256 tiles on CTA pairs, give the same bits as one launch
-    per layer: chunks longer than the ring (ring slots reused), a ragged last
-    chunk, an odd number of row blocks (the last pair's second half empty),
-    and a chunk shorter than the grid."""
+    """All layers of a chunk in one persistent launch -- activation ring in L2
+    with cross-CTA arrival counters, 128 x 256 tiles on single CTAs or 256 x
+    256 tiles on CTA pairs, or CTA pairs keeping each 256-row block's
+    activations in shared memory through all layers (the default) -- give the
+    same bits as one launch per layer: chunks longer than the ring (ring slots reused), a
+    ragged last chunk, an odd number of row blocks (the last pair's second
+    half empty), a chunk shorter than the grid, one hidden layer and width
+    256 (N-tiles of 128)."""
     import torch
     from paper_2312_04830_gb300 import binding
     sg = binding.Surrogate(ctx, width=width, hidden_layers=layers, max_batch=1024, infer_chunk=chunk, seed=21)
@@ -223,21 +225,22 @@ def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers
     T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=cuda)
     Td, pd, Yd = d(T), d(p), d(Y)
-    assert sg.fused_kind == "single"
+    assert sg.fused_kind == "resident"
     outs = []
-    for fused, kind in ((True, "single"), ("pair", "pair"), (False, "per-layer")):
+    kinds = ((True, "single"), ("pair", "pair"), ("resident", "resident"), (False, "per-layer"))
+    for fused, kind in kinds:
         sg.set_fused_infer(fused)
         assert sg.fused_kind == kind
         o, fb = sg.infer(Td, pd, Yd)
         sg.sync_status()
         outs.append(o.cpu().numpy())
-    assert np.array_equal(outs[0], outs[2], equal_nan=True)
-    assert np.array_equal(outs[1], outs[2], equal_nan=True)
+    for o in outs[:-1]:
+        assert np.array_equal(o, outs[-1], equal_nan=True)
     assert np.isfinite(outs[0]).mean() > 0.9
     sg.close()
 
 
-@pytest.mark.parametrize("kind", [True, "pair"])
+@pytest.mark.parametrize("kind", [True, "pair", "resident"])
 def test_fused_inference_wait_timeout_is_reported(ctx, orc, species, cuda, kind):
     """Failure detection of the persistent kernel (single CTAs and CTA pairs):
     with one arrival counter made unreachable and a short wait limit (20M
