@@ -69,7 +69,8 @@ struct ResidentArgs {
 };
 
 // Shared memory: the activation (128 x W BF16), the input tile (128 x 64
-// BF16), the stage ring, the barriers, the biases of every layer.
+// BF16), the stage ring, the output layer's weights when they fit (this CTA's
+// 8 rows x W, loaded once), the barriers, the biases of every layer.
 struct ResCfg {
     static constexpr int kMaxSmem = 232448;   // 227 KB opt-in per CTA
     static constexpr int STAGE = 16384;       // this CTA's half of a weight K-block (at most 128 x 64 BF16)
@@ -77,16 +78,21 @@ struct ResCfg {
     static constexpr int BAR_BYTES = 256;
     __host__ __device__ static int act_bytes(int W) { return 128 * W * 2; }
     __host__ __device__ static int bias_bytes(int L, int W) { return (L * W + kResOutBN) * 4; }
-    __host__ __device__ static int smem_bytes(int L, int W)
+    __host__ __device__ static int wout_bytes(int W) { return (W / 64) * 1024; }   // 8 rows x W BF16
+    __host__ __device__ static int smem_bytes(int L, int W, bool wo)
     {
-        return 1024 + act_bytes(W) + XBYTES + kResStages * STAGE + BAR_BYTES + bias_bytes(L, W);
+        return 1024 + act_bytes(W) + XBYTES + kResStages * STAGE + (wo ? wout_bytes(W) : 0) + BAR_BYTES +
+               bias_bytes(L, W);
     }
     // widths this kernel takes: two N-tiles of W / 2 columns fill at most the
     // 512 TMEM columns
     static bool supports(int L, int W)
     {
-        return (W == 256 || W == 512) && L >= 1 && L < kFusedMaxLayers && smem_bytes(L, W) <= kMaxSmem;
+        return (W == 256 || W == 512) && L >= 1 && L < kFusedMaxLayers && smem_bytes(L, W, false) <= kMaxSmem;
     }
+    // the output layer's weights stay in shared memory (else they stream
+    // through the stage ring like the others)
+    static bool wout_resident(int L, int W) { return smem_bytes(L, W, true) <= kMaxSmem; }
 };
 
 // Position in the stage ring: index and phase parity, advanced by increments
@@ -136,7 +142,8 @@ __device__ __forceinline__ void act_chunk(const uint32_t (&r)[16], const float *
 
 // The epilogue of one warp's NCOL columns of an N-tile: TMEM loads of 16
 // columns double-buffered, everything unrolled (column offsets are
-// immediates); rx as for act_chunk, for the first column.
+// immediates); rx as for act_chunk, for the first column.  (Loads of 32 or
+// all columns per wait measured slower: they spill at 96 registers.)
 template <int NCOL>
 __device__ __forceinline__ void act_columns(uint32_t taddr, const float *sb, uint32_t rx)
 {
@@ -153,7 +160,7 @@ __device__ __forceinline__ void act_columns(uint32_t taddr, const float *sb, uin
     }
 }
 
-template <int W>
+template <int W, bool WO>
 __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __grid_constant__ ResidentArgs a)
 {
     static_assert(W == 256 || W == 512, "resident activations: width 256 or 512");
@@ -166,7 +173,8 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
     uint8_t *act = smem;
     uint8_t *xbuf = smem + ResCfg::act_bytes(W);
     uint8_t *stage = xbuf + ResCfg::XBYTES;
-    uint64_t *full = reinterpret_cast<uint64_t *>(stage + S * ResCfg::STAGE);
+    uint8_t *wout = stage + S * ResCfg::STAGE;   // (WO) the output layer's weights, K-blocks of 8 x 64
+    uint64_t *full = reinterpret_cast<uint64_t *>(wout + (WO ? ResCfg::wout_bytes(W) : 0));
     uint64_t *empty = full + S;
     uint64_t *x_full = empty + S;     // input tile landed (both CTAs')
     uint64_t *x_empty = x_full + 1;   // input tile no longer read
@@ -175,7 +183,8 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
     uint64_t *epi_done = outf + 1;    // [2] (leader) activation half b written, accumulator b read
     uint64_t *out_done = epi_done + 2;   // (leader) output accumulator read
     uint64_t *drain = out_done + 1;      // (leader) every MMA issued has completed
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *w_full = drain + 1;        // (WO) the output layer's weights landed (both CTAs')
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(w_full + 1);
     float *sbias = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(full) + ResCfg::BAR_BYTES);   // [L W + 16]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -200,6 +209,7 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
         umma::mbar_init(&epi_done[1], 2);
         umma::mbar_init(out_done, 2);
         umma::mbar_init(drain, 1);
+        umma::mbar_init(w_full, 1);
         *tmem_slot = 0u;
         umma::fence_mbar_init();
         umma::tma_prefetch_desc(&a.tm_x);
@@ -241,8 +251,15 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
                 rp.next();
             };
             auto put_out = [&]() {
-                for (int k = 0; k < nkb; ++k) put(&a.tm_w[L], k * 64, (int)rank * 8, 2u * 8u * 128u);
+                if (!WO)
+                    for (int k = 0; k < nkb; ++k) put(&a.tm_w[L], k * 64, (int)rank * 8, 2u * 8u * 128u);
             };
+            if (WO && nr > 0) {   // the output layer's weights, once
+                if (leader) umma::mbar_arrive_expect_tx(w_full, 2u * (uint32_t)ResCfg::wout_bytes(W));
+                for (int k = 0; k < nkb; ++k)
+                    umma::tma_load_2d_pair(wout + k * 1024, &a.tm_w[L], umma::mapa_shared(umma::smem_u32(w_full), 0u),
+                                           k * 64, (int)rank * 8);
+            }
             for (int i = 0; i < nr && !fail; ++i) {
                 const int r = pair + i * npairs;
                 // the input tile, once the previous block's input layer has read it
@@ -276,6 +293,7 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
                 for (uint32_t k = (it_end > (uint32_t)S ? it_end - S : 0u); k < it_end; ++k)
                     if (!umma::mbar_wait(&full[k % S], (k / S) & 1u, 200000000LL)) fail = true;
                 if (nx > 0 && !umma::mbar_wait(x_full, (uint32_t)(nx - 1) & 1u, 200000000LL)) fail = true;
+                if (WO && nr > 0 && !umma::mbar_wait(w_full, 0u, 200000000LL)) fail = true;
             }
             if (fail) atomicExch(a.err, 1);
         }
@@ -289,6 +307,8 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
             const uint64_t d_act = umma::sdesc_kmajor_sw128(umma::smem_u32(act));
             const uint64_t d_x = umma::sdesc_kmajor_sw128(umma::smem_u32(xbuf));
             const uint64_t d_st = umma::sdesc_kmajor_sw128(umma::smem_u32(stage));
+            const uint64_t d_wo = umma::sdesc_kmajor_sw128(umma::smem_u32(wout));
+            uint32_t nwo = 0;
             auto wait_bar = [&](uint64_t *bar, uint32_t &n) {
                 if (!fail && !umma::mbar_wait(bar, n & 1u, wc)) fail = true;
                 ++n;
@@ -311,13 +331,22 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
                 for (int kk = 0; kk < 4; ++kk)
                     umma::mma_bf16_pair(d, da + 2 * kk, db + 2 * kk, id, (acc_in || kk > 0) ? 1u : 0u);
             };
-            auto output_layer = [&]() {   // both activation halves written (epi_done[0] waited before)
+            // both activation halves written (epi_done[0] waited before); with
+            // `next`, the next block's first epilogue may start once the first
+            // half of the activation has been read
+            auto output_layer = [&](bool next) {
                 wait_bar(&epi_done[1], ne1);
+                if (WO && nwo == 0) wait_bar(w_full, nwo);
                 for (int k = 0; k < nkb && !fail; ++k) {
-                    const uint64_t db = take();
-                    if (fail) break;
-                    kblock(acc1, d_act + (uint64_t)(k * kStageDesc), db, id_o, k > 0);
-                    give();
+                    if (WO) {
+                        kblock(acc1, d_act + (uint64_t)(k * kStageDesc), d_wo + (uint64_t)(k * 64), id_o, k > 0);
+                    } else {
+                        const uint64_t db = take();
+                        if (fail) break;
+                        kblock(acc1, d_act + (uint64_t)(k * kStageDesc), db, id_o, k > 0);
+                        give();
+                    }
+                    if (next && k == nkb / 2 - 1) umma::mma_commit_pair_mc(&hid[0], (uint16_t)0x3);
                 }
                 if (!fail) umma::mma_commit_pair_mc(outf, (uint16_t)0x3);
             };
@@ -328,9 +357,11 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
                 if (fail) break;
                 kblock(acc0, d_x, db, id_h, false);
                 give();
-                if (i > 0) output_layer();   // of the previous row block
+                if (i > 0)
+                    output_layer(true);   // of the previous row block
+                else
+                    umma::mma_commit_pair_mc(&hid[0], (uint16_t)0x3);
                 if (fail) break;
-                umma::mma_commit_pair_mc(&hid[0], (uint16_t)0x3);
                 if (i > 0) wait_bar(out_done, no);
                 db = take();
                 if (fail) break;
@@ -362,7 +393,7 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
             }
             if (nr > 0 && !fail) {
                 wait_bar(&epi_done[0], ne0);
-                output_layer();
+                output_layer(false);
             }
             // every MMA issued has completed before tensor memory is freed
             umma::mma_commit_pair_mc(drain, (uint16_t)0x1);

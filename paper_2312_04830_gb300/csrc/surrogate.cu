@@ -944,18 +944,22 @@ void fused_lag(int G, int ips, int &D, int &ring)
     ring = 2 * D + 4;
 }
 
-// The resident-activation kernel for width W (256 or 512).
-inline const void *resident_fn(int W)
+// The resident-activation kernel for width W (256 or 512) and this depth (the
+// output layer's weights resident in shared memory when they fit).
+inline const void *resident_fn(int L, int W)
 {
-    return W == 256 ? reinterpret_cast<const void *>(mlp_resident_kernel<256>)
-                    : reinterpret_cast<const void *>(mlp_resident_kernel<512>);
+    const bool wo = ResCfg::wout_resident(L, W);
+    if (W == 256) return wo ? reinterpret_cast<const void *>(mlp_resident_kernel<256, true>)
+                            : reinterpret_cast<const void *>(mlp_resident_kernel<256, false>);
+    return wo ? reinterpret_cast<const void *>(mlp_resident_kernel<512, true>)
+              : reinterpret_cast<const void *>(mlp_resident_kernel<512, false>);
 }
 
 // CTA pairs of the resident-activation kernel the device holds at once (0:
 // none, or cluster launches unavailable).
 int resident_pairs(int L, int W)
 {
-    if (cudaFuncSetAttribute(resident_fn(W), cudaFuncAttributeMaxDynamicSharedMemorySize, ResCfg::kMaxSmem) !=
+    if (cudaFuncSetAttribute(resident_fn(L, W), cudaFuncAttributeMaxDynamicSharedMemorySize, ResCfg::kMaxSmem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -968,11 +972,11 @@ int resident_pairs(int L, int W)
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(2 * num_sms_current(), 1, 1);
     cfg.blockDim = dim3(kResThreads, 1, 1);
-    cfg.dynamicSmemBytes = ResCfg::smem_bytes(L, W);
+    cfg.dynamicSmemBytes = ResCfg::smem_bytes(L, W, ResCfg::wout_resident(L, W));
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, resident_fn(W), &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&nc, resident_fn(L, W), &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -986,6 +990,7 @@ cudaError_t launch_resident(const ResidentArgs &ra, int pairs, cudaStream_t st)
 {
     const int R = (ra.M + 255) / 256;
     const int g = R < pairs ? R : pairs;
+    const bool wo = ResCfg::wout_resident(ra.L, ra.W);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -994,12 +999,15 @@ cudaError_t launch_resident(const ResidentArgs &ra, int pairs, cudaStream_t st)
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3((unsigned)(2 * g), 1, 1);
     cfg.blockDim = dim3(kResThreads, 1, 1);
-    cfg.dynamicSmemBytes = ResCfg::smem_bytes(ra.L, ra.W);
+    cfg.dynamicSmemBytes = ResCfg::smem_bytes(ra.L, ra.W, wo);
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return ra.W == 256 ? cudaLaunchKernelEx(&cfg, mlp_resident_kernel<256>, ra)
-                       : cudaLaunchKernelEx(&cfg, mlp_resident_kernel<512>, ra);
+    if (ra.W == 256)
+        return wo ? cudaLaunchKernelEx(&cfg, mlp_resident_kernel<256, true>, ra)
+                  : cudaLaunchKernelEx(&cfg, mlp_resident_kernel<256, false>, ra);
+    return wo ? cudaLaunchKernelEx(&cfg, mlp_resident_kernel<512, true>, ra)
+              : cudaLaunchKernelEx(&cfg, mlp_resident_kernel<512, false>, ra);
 }
 
 GemmArgs base_args(sg_model *m)

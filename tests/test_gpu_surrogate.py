@@ -206,7 +206,7 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
 
 
 @pytest.mark.parametrize("width,layers,chunk,n", [(512, 4, 32768, 70000), (256, 2, 16384, 40961),
-                                                   (512, 1, 1024, 300)])
+                                                   (512, 1, 1024, 300), (512, 6, 8192, 20000)])
 def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers, chunk, n):
     """All layers of a chunk in one persistent launch -- activation ring in L2
     with cross-CTA arrival counters, 128 x 256 tiles on single CTAs or 256 x
@@ -214,8 +214,9 @@ def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers
     activations in shared memory through all layers (the default) -- give the
     same bits as one launch per layer: chunks longer than the ring (ring slots reused), a
     ragged last chunk, an odd number of row blocks (the last pair's second
-    half empty), a chunk shorter than the grid, one hidden layer and width
-    256 (N-tiles of 128)."""
+    half empty), a chunk shorter than the grid, one hidden layer, width 256
+    (N-tiles of 128), and six hidden layers (the output layer's weights then
+    stream through the stage ring instead of staying in shared memory)."""
     import torch
     from paper_2312_04830_gb300 import binding
     sg = binding.Surrogate(ctx, width=width, hidden_layers=layers, max_batch=1024, infer_chunk=chunk, seed=21)
