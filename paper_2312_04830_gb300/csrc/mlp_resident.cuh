@@ -421,20 +421,31 @@ __global__ void __launch_bounds__(kResThreads, 1) mlp_resident_kernel(const __gr
             umma::tc_fence_after();
         };
         // warps 2..5 (one per lane quarter): de-standardised outputs of row block r
+        // (the per-row term and the first 8 outputs' bias, scale and shift are
+        // loaded before the wait; the rest is read after it)
         auto output_epilogue = [&](int r, bool signal) {
             const int m = r * 256 + (int)rank * 128 + row;
-            const float hadd = (a.add_h && m < a.M) ? __ldg(a.add_h + m) : 0.f;   // in flight during the wait
+            const float hadd = (a.add_h && m < a.M) ? __ldg(a.add_h + m) : 0.f;
+            const float *sb = sbias + L * W;
+            float ob[8], os[8], om[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                ob[jj] = sb[jj];
+                os[jj] = __ldg(a.out_std + jj);
+                om[jj] = __ldg(a.out_mean + jj);
+            }
             wait_bar(outf, nof);
             if (!fail) {
                 uint32_t rr[16];
                 umma::tmem_ld16(tmem + lanes + (uint32_t)BN, rr);
                 umma::tmem_ld_wait(rr);
                 if (m < a.M) {
-                    const float *sb = sbias + L * W;
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) {
                         if (jj >= a.nout) break;
-                        float qv = (__uint_as_float(rr[jj]) + sb[jj]) * __ldg(a.out_std + jj) + __ldg(a.out_mean + jj);
+                        float qv = jj < 8 ? (__uint_as_float(rr[jj]) + ob[jj & 7]) * os[jj & 7] + om[jj & 7]
+                                          : (__uint_as_float(rr[jj]) + sb[jj]) * __ldg(a.out_std + jj) +
+                                                __ldg(a.out_mean + jj);
                         if (jj == 2) qv += hadd;
                         a.out6[(long long)jj * a.ld6 + m] = ((a.log_mask >> jj) & 1) ? __expf(qv) : qv;
                     }
