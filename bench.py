@@ -55,8 +55,9 @@ FP64_FLOPS_PER_CELL = {"props_fp64": 1413.5, "newton_fp64": 1158.5, "species_fp6
 ALGO_FP64_FLOPS_PER_CELL = {"props_fp64": 1698.6035400390624}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum per launch
 # / cells) of the same captures; a full launch moves this x its cells (the
-# surrogates: DRAM bytes per row of one fused-inference chunk launch)
-TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 108.3}
+# forward surrogate: DRAM bytes per row of one resident-activation inference
+# launch over a 2 Mi-row chunk of the 128^3 field)
+TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 108.3, "surrogate_bf16": 151.8}
 # surrogate: 2 x (13*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
