@@ -369,20 +369,26 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * fallback like a cell outside the hull (flagged in used_fallback).  No effect
  * on the per-species networks. */
 #define SG_OPT_TRANSPORT_CONFIDENCE_PPM 8
-/* SG_OPT_OUTPUTS (the paper's per-species networks, Sec. 4.1): with
+/* SG_OPT_OUTPUTS (the paper's dedicated networks, Sec. 4.1): with
  * SG_MODE_INVERSE or SG_MODE_BILGER inputs, the network predicts
  *   SG_OUT_PROPS  (default) T, rho, psi, mu, alpha, cp;
  *   SG_OUT_DK     the 9 mixture-averaged diffusion coefficients D_k [m^2/s]
  *                 (pr_species_props; learned as logarithms);
- *   SG_OUT_HK     the 9 standard-state enthalpies h_k / (R T).
- * surrogate_infer then writes [9][ldo]; training targets y are [9][ldy] of
- * the same quantity; cells outside the hull take the FP64 inversion and the
- * FP64 per-species values at its T (with the context's correction table).
+ *   SG_OUT_HK     the 9 standard-state enthalpies h_k / (R T);
+ *   SG_OUT_SINGLE + j, j = 0..5: one of T, rho, psi, mu, alpha, cp alone
+ *                 (one dedicated network per property, as the paper trains
+ *                 them; learned as its logarithm).
+ * surrogate_infer then writes [n_out][ldo] (n_out = 9 for the per-species
+ * outputs, 1 for a single property); training targets y are [n_out][ldy] of
+ * the same quantities; cells outside the hull take the FP64 inversion and the
+ * FP64 values at its T (per-species: with the context's correction table;
+ * a single property other than T: the inversion starts from 1000 K).
  * Selecting outputs re-initialises the weights (set before fitting). */
 #define SG_OPT_OUTPUTS 7
 #define SG_OUT_PROPS 0
 #define SG_OUT_DK 1
 #define SG_OUT_HK 2
+#define SG_OUT_SINGLE 3
 #define SG_OPT_LOSS 5
 #define SG_LOSS_REL_MSE 0
 #define SG_LOSS_L1 1

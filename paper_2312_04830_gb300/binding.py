@@ -294,7 +294,9 @@ SG_OPT_MODE, SG_MODE_FORWARD, SG_MODE_INVERSE, SG_MODE_BILGER = 2, 0, 1, 2
 SG_OPT_WAIT_LIMIT_KCYCLES, SG_OPT_TEST_STALL = 3, 4
 SG_OPT_LOSS, SG_LOSS_REL_MSE, SG_LOSS_L1 = 5, 0, 1
 SG_OPT_CONFIDENCE_PPM = 6
-SG_OPT_OUTPUTS, SG_OUT_PROPS, SG_OUT_DK, SG_OUT_HK = 7, 0, 1, 2
+SG_OPT_OUTPUTS, SG_OUT_PROPS, SG_OUT_DK, SG_OUT_HK, SG_OUT_SINGLE = 7, 0, 1, 2, 3
+# the single-property networks, in the inverse model's output order
+SINGLE_OUTPUTS = ("T", "rho", "psi", "mu", "alpha", "cp")
 SG_OPT_TRANSPORT_CONFIDENCE_PPM = 8
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
@@ -466,12 +468,18 @@ class Surrogate:
 
     def set_outputs(self, kind: str):
         """'props' (the mode's six outputs), 'dk' (the 9 mixture-averaged
-        diffusion coefficients) or 'hk' (the 9 standard-state h_k / (R T));
-        per-species outputs need the inverse or Bilger mode.  Re-initialises
-        the weights."""
-        v = {"props": SG_OUT_PROPS, "dk": SG_OUT_DK, "hk": SG_OUT_HK}[kind]
+        diffusion coefficients), 'hk' (the 9 standard-state h_k / (R T)), or
+        one of 'T', 'rho', 'psi', 'mu', 'alpha', 'cp' (a dedicated network for
+        that property alone); all but 'props' need the inverse or Bilger mode.
+        Re-initialises the weights."""
+        if kind in SINGLE_OUTPUTS:
+            v, n = SG_OUT_SINGLE + SINGLE_OUTPUTS.index(kind), 1
+        else:
+            v = {"props": SG_OUT_PROPS, "dk": SG_OUT_DK, "hk": SG_OUT_HK}[kind]
+            n = N_OUT if v == SG_OUT_PROPS else 9
         check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_OUTPUTS, v), "surrogate_set_option")
-        self._n_out = N_OUT if v == SG_OUT_PROPS else 9
+        self._n_out = n
+        self.single_output = kind if kind in SINGLE_OUTPUTS else None
 
     def _pool(self, x, y):
         import torch

@@ -183,6 +183,7 @@ __host__ __device__ inline int log_mask_of(int mode, int outputs)
 {
     if (outputs == SG_OUT_DK) return kLogMaskDk;
     if (outputs == SG_OUT_HK) return 0;
+    if (outputs >= SG_OUT_SINGLE) return 1;   // one of the inverse model's six, all logarithms
     return (mode != SG_MODE_FORWARD) ? kLogMaskInverse : kLogMaskForward;
 }
 
@@ -191,7 +192,9 @@ __host__ __device__ inline int log_mask_of(int mode, int outputs)
 //     [log rho, Z, h - h_ig(T, Y), log cp, log mu, log lambda];
 //   inverse and Bilger models, y = [T, rho, psi, mu, alpha, cp]: the six logarithms;
 //   per-species outputs (inverse or Bilger inputs), y = D_k [9]: their logarithms,
-//   or y = h_k / (R T) [9] as they are.
+//   or y = h_k / (R T) [9] as they are;
+//   a single property of the inverse set (y = [one of T, rho, psi, mu, alpha, cp]):
+//   its logarithm.
 __device__ __forceinline__ void targets(const float *x, int64_t ldx, const float *y, int64_t ldy, int64_t i,
                                         const SgDev &d, float (&q)[NOUT_MAX])
 {
@@ -546,14 +549,15 @@ __global__ void __launch_bounds__(128) fallback_kernel(const int32_t *list, cons
 
 // FP64 Peng-Robinson fallback of the inverse model for the listed cells: the
 // safeguarded FP64 inversion T(h*, p, Y), started from the network's own T
-// (clamped to the bracket), then rho, psi, mu, alpha, cp at that T; NaN where
-// the inversion fails.
+// (clamped to the bracket; from 1000 K for a single-property network other than
+// T), then rho, psi, mu, alpha, cp at that T; NaN where the inversion fails.
+// sel < 0: all six outputs; sel = j: only property j, into output row 0.
 template <int NS, bool KIJ>
 __global__ void __launch_bounds__(128) fallback_inverse_kernel(const int32_t *list, const unsigned int *count,
                                                                int64_t r0, const float *H, const float *p,
                                                                const float *Y, int64_t ldY, float *out, int64_t ldo,
                                                                const SpeciesRec<double> *sp, const double *pair,
-                                                               const double *kij, int N, int flags)
+                                                               const double *kij, int N, int flags, int sel)
 {
     __shared__ SpeciesRec<double> s_sp[NS];
     __shared__ double s_pair[NS * NS];
@@ -574,7 +578,7 @@ __global__ void __launch_bounds__(128) fallback_inverse_kernel(const int32_t *li
         float o[6];
         for (int q = 0; q < 6; ++q) o[q] = __int_as_float(0x7fc00000);
         if (ok) {
-            double T0 = (double)out[i];   // the network's T
+            double T0 = (sel <= 0) ? (double)out[i] : 1000.0;   // the network's T
             if (!(T0 == T0)) T0 = 300.0;
             T0 = fmin(fmax(T0, prk::kTLo), prk::kTHi);
             double T, cpl;
@@ -596,8 +600,12 @@ __global__ void __launch_bounds__(128) fallback_inverse_kernel(const int32_t *li
                 }
             }
         }
+        if (sel >= 0) {
+            out[i] = o[sel < 6 ? sel : 0];
+        } else {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) out[(int64_t)q * ldo + i] = o[q];
+            for (int q = 0; q < 6; ++q) out[(int64_t)q * ldo + i] = o[q];
+        }
     }
 }
 
@@ -1545,7 +1553,8 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
         // FP64 Peng-Robinson for the cells outside the training hull (and the low-confidence ones)
         const int fb = ctx->num_sms * 4;
         const SpeciesRec<double> *sp64 = (const SpeciesRec<double> *)ctx->d_sp64;
-        if (d.outputs != SG_OUT_PROPS) {
+        const int sel = (d.outputs >= SG_OUT_SINGLE) ? d.outputs - SG_OUT_SINGLE : -1;
+        if (d.outputs == SG_OUT_DK || d.outputs == SG_OUT_HK) {
             if (ctx->has_kij)
                 fallback_species_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
                                                                      ldo, sp64, ctx->d_kij64, ctx->d_dtab64,
@@ -1560,11 +1569,11 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             if (ctx->has_kij)
                 fallback_inverse_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
                                                                      ldo, sp64, ctx->d_pair64, ctx->d_kij64,
-                                                                     ctx->n_species, ctx->flags);
+                                                                     ctx->n_species, ctx->flags, sel);
             else
                 fallback_inverse_kernel<9, false><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out,
                                                                       ldo, sp64, ctx->d_pair64, ctx->d_kij64,
-                                                                      ctx->n_species, ctx->flags);
+                                                                      ctx->n_species, ctx->flags, sel);
         } else if (ctx->has_kij)
             fallback_kernel<9, true><<<fb, 128, 0, st>>>(m->d_list, m->d_count, r0, T, p, Y, ldY, out, ldo,
                                                          (const SpeciesRec<double> *)ctx->d_sp64, ctx->d_pair64,
@@ -1626,13 +1635,13 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
         m->stall_test = value != 0;
         return PR_OK;
     case SG_OPT_OUTPUTS: {
-        PR_CHECK_ARG(value == SG_OUT_PROPS || value == SG_OUT_DK || value == SG_OUT_HK,
-                     "surrogate_set_option: bad outputs %d", value);
+        PR_CHECK_ARG(value >= SG_OUT_PROPS && value <= SG_OUT_SINGLE + 5, "surrogate_set_option: bad outputs %d", value);
         PR_CHECK_ARG(value == SG_OUT_PROPS || m->dev.mode != SG_MODE_FORWARD,
-                     "surrogate_set_option: per-species outputs need the inverse or Bilger inputs (h, p, Y)");
+                     "surrogate_set_option: per-species and single-property outputs need the inverse or Bilger "
+                     "inputs (h, p, Y)");
         SgDev &d = m->dev;
         d.outputs = value;
-        d.nout = (value == SG_OUT_PROPS) ? NOUT6 : m->ctx->n_species;
+        d.nout = (value == SG_OUT_PROPS) ? NOUT6 : (value >= SG_OUT_SINGLE) ? 1 : m->ctx->n_species;
         // the last layer's output count changes the exported parameter count;
         // start the weights afresh
         LayerLayout &LL = d.lay[d.hidden];
@@ -1664,7 +1673,7 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
         PR_CHECK_ARG(value != SG_MODE_BILGER || m->ctx->has_bilger,
                      "surrogate_set_option: SG_MODE_BILGER needs the context's element table (pr_set_bilger)");
         PR_CHECK_ARG(value != SG_MODE_FORWARD || m->dev.outputs == SG_OUT_PROPS,
-                     "surrogate_set_option: the forward model has no per-species outputs");
+                     "surrogate_set_option: the forward model has no per-species or single-property outputs");
         m->dev.mode = value;
         m->dev.bilger = m->ctx->d_bilger32;
         return PR_OK;

@@ -33,7 +33,7 @@ struct SgDev {
     float *norm;                            // SG_NORM_FLOATS
     float *outstat;                         // output mean[16] then std[16], gathered from norm
     int nout;                               // outputs of the model: 6, or 9 per-species ones
-    int outputs;                            // SG_OUT_PROPS, SG_OUT_DK or SG_OUT_HK
+    int outputs;                            // SG_OUT_PROPS, SG_OUT_DK, SG_OUT_HK or SG_OUT_SINGLE + j
     // training activations, batch-major [B][.] (the weight-gradient GEMMs read
     // them MN-major, so no transposed copies)
     __nv_bfloat16 *x0;

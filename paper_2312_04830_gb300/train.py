@@ -179,10 +179,14 @@ def evaluate_field_inverse(sg, ctx, grid, device):
     dil, _ = ctx.props(T64, torch.ones_like(p64), Y64, precision="fp64", outputs=("mu", "lambda"))
     out, fb = sg.infer(o8[2].float(), p64.float(), Y64.float())
     ref = torch.stack([T64, o8[0], o8[6], o8[4], o8[7], o8[3]])
+    names = INVERSE_OUT_NAMES
+    if out.shape[0] == 1:   # a dedicated single-property network
+        j = binding.SINGLE_OUTPUTS.index(sg.single_output)
+        ref, names = ref[j:j + 1], (INVERSE_OUT_NAMES[j],)
     ok = (st == 0) & torch.all(torch.isfinite(ref), dim=0)
     phys = ok & (o8[4] >= DILUTE_FLOOR * dil[4]) & (o8[5] >= DILUTE_FLOOR * dil[5])
     return {"cells": int(ok.sum()), "physical_cells": int(phys.sum()),
-            "physical": relative_rms(out[:, phys], ref[:, phys].float(), INVERSE_OUT_NAMES),
+            "physical": relative_rms(out[:, phys], ref[:, phys].float(), names),
             "fallback_fraction": float(fb.float().mean())}
 
 
@@ -269,8 +273,9 @@ def main():
     ap.add_argument("--model", choices=("forward", "inverse", "bilger"), default="forward",
                     help="T,p,Y -> properties; h,p,Y -> T and properties; or the same from h, p and Bilger's Z")
     ap.add_argument("--bc-shift", type=float, default=1e-3, help="Box-Cox shift of Bilger's Z")
-    ap.add_argument("--outputs", choices=("props", "dk", "hk"), default="props",
-                    help="inverse / Bilger models: the six properties, or the 9 D_k or h_k/(R T)")
+    ap.add_argument("--outputs", choices=("props", "dk", "hk") + binding.SINGLE_OUTPUTS, default="props",
+                    help="inverse / Bilger models: the six properties, the 9 D_k or h_k/(R T), "
+                         "or one property alone (a dedicated network)")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     ctx = binding.PropertyContext(W.species_table())
@@ -279,8 +284,13 @@ def main():
     if a.model == "forward":
         x, y = make_pool(ctx, a.pool, a.seed, dev, a.data, a.a2)
         xh, yh = make_pool(ctx, a.heldout, a.seed + 1, dev)
-    elif a.outputs != "props":
+    elif a.outputs in ("dk", "hk"):
         x, y = label_pool_species(ctx, *pool_states(a.pool, a.seed, a.data, a.a2), dev, a.outputs)
+        xh, yh = None, None
+    elif a.outputs != "props":   # one property of the inverse set
+        x, y = label_pool_inverse(ctx, *pool_states(a.pool, a.seed, a.data, a.a2), dev)
+        j = binding.SINGLE_OUTPUTS.index(a.outputs)
+        y = y[j:j + 1].contiguous()
         xh, yh = None, None
     else:
         x, y = label_pool_inverse(ctx, *pool_states(a.pool, a.seed, a.data, a.a2), dev)
@@ -292,7 +302,7 @@ def main():
         sg.set_mode(a.model)
     if a.outputs != "props":
         if a.model == "forward":
-            raise SystemExit("per-species outputs need --model inverse or bilger")
+            raise SystemExit("per-species and single-property outputs need --model inverse or bilger")
         sg.set_outputs(a.outputs)
     if a.model == "bilger":
         z = ctx.bilger_z(x[2:, :1 << 20].contiguous(), precision="fp32").double().cpu().numpy()
@@ -311,7 +321,7 @@ def main():
     if a.model == "forward":
         rep["heldout"] = evaluate(sg, xh, yh)
     if a.eval_field > 0:
-        if a.outputs != "props":
+        if a.outputs in ("dk", "hk"):
             rep["field"] = evaluate_field_species(sg, ctx, a.eval_field, dev, a.outputs)
         elif a.model == "forward":
             rep["field"] = evaluate_field(sg, ctx, a.eval_field, dev)

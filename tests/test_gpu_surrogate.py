@@ -928,3 +928,127 @@ def test_species_network_fallback_and_checkpoint(ctx, orc, species, cuda, tmp_pa
         sg2.set_mode("forward")                   # no per-species outputs for the forward model
     sg.close()
     sg2.close()
+
+
+# ----------------------------------------- dedicated single-property networks
+def make_pool_single(orc, species, n, seed, prop):
+    """Pool of a dedicated network for one property of the inverse set: x =
+    [h, p, Y], y = [that property] (float32)."""
+    from paper_2312_04830_gb300 import binding
+    x, y = make_pool_inverse(orc, species, n, seed)
+    j = binding.SINGLE_OUTPUTS.index(prop)
+    return x, np.ascontiguousarray(y[j:j + 1])
+
+
+@pytest.mark.parametrize("prop", ["T", "mu"])
+def test_single_property_network_matches_oracle_forward(ctx, orc, species, cuda, prop):
+    """One network per property, as the paper trains them (Sec. 4.1): the
+    inverse inputs, one output learned as its logarithm, through the default
+    tensor-core kernel, against the BF16-storage oracle MLP with the same
+    weights."""
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=1024, seed=61)
+    sg.set_mode("inverse")
+    sg.set_outputs(prop)
+    assert sg.num_params == 13 * 512 + 512 + 3 * (512 * 512 + 512) + 512 + 1
+    x, y = make_pool_single(orc, species, 6000, 62, prop)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    n = 2500
+    out, fb = sg.infer(to_dev(x[0, :n], cuda), to_dev(x[1, :n], cuda), to_dev(x[2:, :n], cuda))
+    sg.sync_status()
+    out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy()
+    assert out.shape == (1, n) and fb.sum() == 0
+    norm = sg.get_normalization().astype(np.float64)
+    mean, std = out_stats(norm, 1)
+    params = unflatten(sg.get_params(), [13, 512, 512, 512, 512, 1])
+    f = features_inverse(x[:, :n], species)
+    s_in = (f.T - norm[0:13]) / norm[13:26]
+    q = np.log(out)
+    s_gpu = (q.T - mean) / std
+    in_err = inverse_input_error(x[:, :n], species, f, norm)
+    out_err = 16 * MB.U32 * (np.abs(q.T) + np.abs(mean) + 1.0) / std
+    check_against_bf16_oracle("single " + prop, params, s_in, s_gpu, in_err, out_err)
+    sg.close()
+
+
+def test_single_property_network_gradients_match_oracle(ctx, orc, species, cuda):
+    """Training of a one-output network (mu): loss and every gradient against
+    the float64 oracle MLP (relative MSE on the standardised log mu)."""
+    from paper_2312_04830_gb300 import binding
+    width, layers, batch = 128, 2, 512
+    sg = binding.Surrogate(ctx, width=width, hidden_layers=layers, max_batch=batch, infer_chunk=1024, seed=63)
+    sg.set_mode("inverse")
+    sg.set_outputs("mu")
+    x, y = make_pool_single(orc, species, batch + 200, 64, "mu")
+    x, y = np.ascontiguousarray(x[:, :batch]), np.ascontiguousarray(y[:, :batch])
+    xd, yd = to_dev(x, cuda), to_dev(y, cuda)
+    sg.fit_normalization(xd, yd)
+    loss, grad = sg.loss_grad(xd, yd, batch)
+    sg.sync_status()
+    norm = sg.get_normalization().astype(np.float64)
+    mean, std = out_stats(norm, 1)
+    params = unflatten(sg.get_params(), [13] + [width] * layers + [1])
+    s_in = (features_inverse(x, species).T - norm[0:13]) / norm[13:26]
+    s_out = (np.log(y.astype(np.float64)).T - mean) / std
+    yhat, cache = omlp.forward(params, s_in, "tanh")
+    assert float(loss.item()) == pytest.approx(omlp.loss(yhat, s_out), rel=2e-2)
+    grads = omlp.backward(params, cache, yhat, s_out, "tanh")
+    g_gpu = grad.cpu().numpy().astype(np.float64)
+    off = 0
+    for li, (gW, gb) in enumerate(grads):
+        for name, go in (("W", gW.ravel()), ("b", gb)):
+            gg = g_gpu[off:off + go.size]
+            off += go.size
+            rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
+            cos = float(gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go)))
+            assert rel < 3e-2 and cos > 0.999, (li, name, rel, cos)
+    assert off == g_gpu.size
+    sg.close()
+
+
+@pytest.mark.parametrize("prop", ["T", "rho", "psi", "mu", "alpha", "cp"])
+def test_single_property_network_fallback_and_checkpoint(ctx, orc, species, cuda, tmp_path, prop):
+    """Cells outside the hull take the FP64 inversion and the FP64 value of the
+    network's property at its T: the oracle's T(h, p, Y) and property, rounded
+    to FP32 (the inversion starts from the network's value for T, from 1000 K
+    otherwise); a checkpoint restores the model; the forward mode refuses a
+    single-property network."""
+    from paper_2312_04830_gb300 import binding
+    j = binding.SINGLE_OUTPUTS.index(prop)
+    sg = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=512, seed=65)
+    sg.set_mode("inverse")
+    sg.set_outputs(prop)
+    x, y = make_pool_single(orc, species, 4000, 66, prop)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    T, p, Y = W.uniform_cells(400, seed=67)
+    T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
+    p[:200] = 2e7                                  # outside the pool's 10 MPa +- 5 %: out of the hull
+    o, _ = orc.props_ext(species, T, p, Y)
+    x32 = np.vstack([o[2], p, Y]).astype(np.float32)
+    args = [to_dev(x32[0], cuda), to_dev(x32[1], cuda), to_dev(x32[2:], cuda)]
+    out, fb = sg.infer(*args)
+    sg.sync_status()
+    out, fb = out.cpu().numpy().astype(np.float64), fb.cpu().numpy().astype(bool)
+    assert out.shape == (1, 400) and np.all(fb[:200])
+    x64 = x32.astype(np.float64)
+    To, sto, _ = orc.T_from_h(species, x64[0, :200], x64[1, :200], x64[2:, :200], np.full(200, 1000.0))
+    oo, sto2 = orc.props_ext(species, To, x64[1, :200], x64[2:, :200])
+    ref = np.vstack([To, oo[0], oo[6], oo[4], oo[7], oo[3]])[j]
+    m = (sto == 0) & (sto2 == 0)
+    assert m.sum() > 150
+    e = np.abs(out[0, :200][m] - ref[m]) / np.abs(ref[m])
+    print(prop, "fallback max rel err", e.max())
+    assert e.max() < 1e-6
+    path = tmp_path / f"single_{prop}.ckpt"
+    sg.save(path)
+    sg2 = binding.Surrogate(ctx, width=128, hidden_layers=2, max_batch=256, infer_chunk=512, seed=99)
+    sg2.set_mode("inverse")
+    sg2.set_outputs(prop)
+    sg2.load(path)
+    out2, _ = sg2.infer(*args)
+    sg2.sync_status()
+    assert np.array_equal(out2.cpu().numpy(), out.astype(np.float32), equal_nan=True)
+    with pytest.raises(binding.PrError):
+        sg2.set_mode("forward")
+    sg.close()
+    sg2.close()
