@@ -369,6 +369,11 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * fallback like a cell outside the hull (flagged in used_fallback).  No effect
  * on the per-species networks. */
 #define SG_OPT_TRANSPORT_CONFIDENCE_PPM 8
+/* SG_OPT_TIME_MLP: 1 records CUDA events on the call's stream around the MLP
+ * launch of every inference chunk (the one launch of a fused kernel, or the
+ * per-layer launches together) from now on, restarting the count; 0 stops.
+ * surrogate_mlp_time reads them.  Default 0. */
+#define SG_OPT_TIME_MLP 9
 /* SG_OPT_OUTPUTS (the paper's dedicated networks, Sec. 4.1): with
  * SG_MODE_INVERSE or SG_MODE_BILGER inputs, the network predicts
  *   SG_OUT_PROPS  (default) T, rho, psi, mu, alpha, cp;
@@ -421,6 +426,12 @@ pr_status surrogate_set_boxcox(sg_model *m, double lambda, double shift);
  * up waiting on one of its barriers since the last call (the flag is then
  * cleared). */
 pr_status surrogate_sync_status(sg_model *m);
+
+/* Device time of the MLP launches recorded since SG_OPT_TIME_MLP was set to 1
+ * or since the last call (host double *ms: the sum of the event intervals in
+ * milliseconds; host int64_t *launches: their number), then restarts the
+ * count.  Waits for the last recorded event.  PR_EINVAL for null arguments. */
+pr_status surrogate_mlp_time(sg_model *m, double *ms, int64_t *launches);
 
 /* Checkpoint (HOST file): weights, Adam moments, step count, normalisation. */
 pr_status surrogate_save(const sg_model *m, const char *path);

@@ -298,6 +298,7 @@ SG_OPT_OUTPUTS, SG_OUT_PROPS, SG_OUT_DK, SG_OUT_HK, SG_OUT_SINGLE = 7, 0, 1, 2, 
 # the single-property networks, in the inverse model's output order
 SINGLE_OUTPUTS = ("T", "rho", "psi", "mu", "alpha", "cp")
 SG_OPT_TRANSPORT_CONFIDENCE_PPM = 8
+SG_OPT_TIME_MLP = 9
 N_RAW, N_IN, N_OUT = 11, 13, 6   # raw inputs (T, p, Y_1..Y_9), network inputs, outputs
 
 
@@ -333,6 +334,8 @@ def _sg_lib():
         L.surrogate_set_boxcox.restype = i32
         L.surrogate_sync_status.argtypes = [vp]
         L.surrogate_sync_status.restype = i32
+        L.surrogate_mlp_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        L.surrogate_mlp_time.restype = i32
         L.surrogate_save.argtypes = [vp, ctypes.c_char_p]
         L.surrogate_save.restype = i32
         L.surrogate_load.argtypes = [vp, ctypes.c_char_p]
@@ -525,6 +528,18 @@ class Surrogate:
 
     def sync_status(self):
         check(_sg_lib().surrogate_sync_status(self.handle), "surrogate_sync_status")
+
+    def set_time_mlp(self, on: bool):
+        """Record CUDA events around the MLP launch of every inference chunk
+        from now on (restarting the count), or stop."""
+        check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_TIME_MLP, int(bool(on))), "surrogate_set_option")
+
+    def mlp_time(self):
+        """(milliseconds, launches) of the MLP launches recorded since
+        set_time_mlp(True) or the last call; restarts the count."""
+        ms, nl = ctypes.c_double(0.0), ctypes.c_int64(0)
+        check(_sg_lib().surrogate_mlp_time(self.handle, ctypes.byref(ms), ctypes.byref(nl)), "surrogate_mlp_time")
+        return ms.value, nl.value
 
     def save(self, path):
         check(_sg_lib().surrogate_save(self.handle, str(path).encode()), "surrogate_save")

@@ -1096,6 +1096,7 @@ static void free_model(sg_model *m)
 {
     if (!m) return;
     for (void *p : m->allocs) cudaFree(p);
+    for (cudaEvent_t e : m->tev) cudaEventDestroy(e);
     delete m;
 }
 
@@ -1440,6 +1441,21 @@ pr_status surrogate_loss_grad(sg_model *m, int64_t batch, const float *x, int64_
     return train_common(m, batch, batch, x, ldx, y, ldy, 0, 0.f, loss_out, grad_out, stream);
 }
 
+// The next (start, stop) event pair of SG_OPT_TIME_MLP, created on first use.
+static cudaError_t mlp_timer_pair(sg_model *m, cudaEvent_t &t0, cudaEvent_t &t1)
+{
+    while ((int)m->tev.size() < 2 * (m->tev_used + 1)) {
+        cudaEvent_t e;
+        const cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        m->tev.push_back(e);
+    }
+    t0 = m->tev[2 * m->tev_used];
+    t1 = m->tev[2 * m->tev_used + 1];
+    ++m->tev_used;
+    return cudaSuccess;
+}
+
 pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p, const float *Y, int64_t ldY,
                           float *out, int64_t ldo, uint8_t *used_fallback, void *stream)
 {
@@ -1462,6 +1478,11 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
         prep_infer_kernel<<<pb < 4096 ? pb : 4096, 256, 0, st>>>(d, r0, mc, T, p, Y, ldY, used_fallback,
                                                                  m->d_flags, m->d_list, m->d_count);
         PR_CUDA_TRY(cudaGetLastError());
+        cudaEvent_t tm0 = nullptr, tm1 = nullptr;
+        if (m->time_mlp) {
+            PR_CUDA_TRY(mlp_timer_pair(m, tm0, tm1));
+            PR_CUDA_TRY(cudaEventRecord(tm0, st));
+        }
         if (m->fused_on == 3 && m->res_pairs > 0) {
             // every layer in one launch, activations resident in shared memory
             // (mlp_resident.cuh)
@@ -1543,6 +1564,7 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             a.nout = d.nout;
             PR_CUDA_TRY((launch_gemm<16, kEpiOutPhys>(m->tm_hi[(L - 1) & 1], m->tm_w[L], a, mt, 1, 1, st)));
         }
+        if (m->time_mlp) PR_CUDA_TRY(cudaEventRecord(tm1, st));
         const float ctol = (d.mode == SG_MODE_FORWARD) ? m->conf_tol : 0.f;
         const float ttol = (d.outputs == SG_OUT_PROPS) ? m->tr_tol : 0.f;
         if (ctol > 0.f || ttol > 0.f) {
@@ -1610,6 +1632,7 @@ pr_status surrogate_get_option(const sg_model *m, int option, int *value)
     case SG_OPT_CONFIDENCE_PPM: *value = (int)(m->conf_tol * 1e6f + 0.5f); return PR_OK;
     case SG_OPT_TRANSPORT_CONFIDENCE_PPM: *value = (int)(m->tr_tol * 1e6f + 0.5f); return PR_OK;
     case SG_OPT_OUTPUTS: *value = m->dev.outputs; return PR_OK;
+    case SG_OPT_TIME_MLP: *value = m->time_mlp; return PR_OK;
     default: break;
     }
     PR_CHECK_ARG(false, "surrogate_get_option: unknown option %d", option);
@@ -1662,6 +1685,11 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
     case SG_OPT_TRANSPORT_CONFIDENCE_PPM:
         PR_CHECK_ARG(value >= 0, "surrogate_set_option: transport confidence tolerance must be >= 0");
         m->tr_tol = 1e-6f * (float)value;
+        return PR_OK;
+    case SG_OPT_TIME_MLP:
+        PR_CHECK_ARG(value == 0 || value == 1, "surrogate_set_option: SG_OPT_TIME_MLP takes 0 or 1");
+        m->time_mlp = value;
+        m->tev_used = 0;
         return PR_OK;
     case SG_OPT_LOSS:
         PR_CHECK_ARG(value == SG_LOSS_REL_MSE || value == SG_LOSS_L1, "surrogate_set_option: bad loss %d", value);
@@ -1775,6 +1803,22 @@ pr_status surrogate_load(sg_model *m, const char *path)
     launch_transpose_w(m->dev, 0);
     PR_CUDA_TRY(cudaDeviceSynchronize());
     m->step = step;
+    return PR_OK;
+}
+
+pr_status surrogate_mlp_time(sg_model *m, double *ms, int64_t *launches)
+{
+    PR_CHECK_ARG(m && ms && launches, "surrogate_mlp_time: null argument");
+    double t = 0.0;
+    if (m->tev_used > 0) PR_CUDA_TRY(cudaEventSynchronize(m->tev[2 * m->tev_used - 1]));
+    for (int k = 0; k < m->tev_used; ++k) {
+        float e = 0.f;
+        PR_CUDA_TRY(cudaEventElapsedTime(&e, m->tev[2 * k], m->tev[2 * k + 1]));
+        t += e;
+    }
+    *ms = t;
+    *launches = m->tev_used;
+    m->tev_used = 0;
     return PR_OK;
 }
 

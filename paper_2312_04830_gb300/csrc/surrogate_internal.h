@@ -132,4 +132,9 @@ struct sg_model {
     int res_pairs;
     CUtensorMap tmr_w[SG_MAX_HIDDEN + 1];
     std::vector<void *> allocs;
+    // SG_OPT_TIME_MLP: event pairs (start, stop) around the MLP launches,
+    // reused; the first 2 tev_used of them hold intervals not yet read
+    int time_mlp;
+    int tev_used;
+    std::vector<cudaEvent_t> tev;
 };

@@ -1052,3 +1052,35 @@ def test_single_property_network_fallback_and_checkpoint(ctx, orc, species, cuda
         sg2.set_mode("forward")
     sg.close()
     sg2.close()
+
+
+def test_mlp_launch_timing(ctx, orc, species, cuda):
+    """SG_OPT_TIME_MLP: CUDA events around each chunk's MLP launch; the count
+    is one interval per chunk and call, the read restarts it, the sum lies
+    within the calls' own device time, and switching it off records nothing."""
+    import torch
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=32768, seed=71)
+    x, y = make_pool(orc, species, 4000, seed=72)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    T, p, Y = W.uniform_cells(70000, seed=73)
+    T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=cuda)
+    Td, pd, Yd = d(T), d(p), d(Y)
+    sg.infer(Td, pd, Yd)                      # warm-up
+    torch.cuda.synchronize()
+    sg.set_time_mlp(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(2):
+        sg.infer(Td, pd, Yd)
+    b.record()
+    torch.cuda.synchronize()
+    ms, nl = sg.mlp_time()
+    assert nl == 2 * 3 and 0 < ms <= a.elapsed_time(b)
+    assert sg.mlp_time() == (0.0, 0)
+    sg.set_time_mlp(False)
+    sg.infer(Td, pd, Yd)
+    assert sg.mlp_time() == (0.0, 0)
+    sg.sync_status()
+    sg.close()
