@@ -1084,3 +1084,28 @@ def test_mlp_launch_timing(ctx, orc, species, cuda):
     assert sg.mlp_time() == (0.0, 0)
     sg.sync_status()
     sg.close()
+
+
+@pytest.mark.parametrize("chunk", [128, 1024])
+def test_resident_inference_small_calls(ctx, orc, species, cuda, chunk):
+    """The default kernel on calls of 1 to 257 rows (a pair whose second CTA has
+    no row, a last block of one row, a chunk shorter than a pair's 256 rows)
+    gives the per-layer launches' bits."""
+    import torch
+    from paper_2312_04830_gb300 import binding
+    sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=chunk, seed=81)
+    x, y = make_pool(orc, species, 4000, seed=82)
+    sg.fit_normalization(to_dev(x, cuda), to_dev(y, cuda))
+    assert sg.fused_kind == "resident"
+    T, p, Y = W.uniform_cells(257, seed=83)
+    T = 300.0 + (T - 100.0) * (2800.0 / 3400.0)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=cuda)
+    for n in (1, 2, 127, 128, 129, 255, 256, 257):
+        args = (d(T[:n]), d(p[:n]), d(Y[:, :n]))
+        sg.set_fused_infer("resident")
+        o_r, _ = sg.infer(*args)
+        sg.set_fused_infer(False)
+        o_l, _ = sg.infer(*args)
+        sg.sync_status()
+        assert np.array_equal(o_r.cpu().numpy(), o_l.cpu().numpy(), equal_nan=True), n
+    sg.close()
