@@ -348,6 +348,7 @@ struct Thermo {
     Real cv_ig_molar;     // ideal-gas molar cv [J/(mol K)]
     Real dpdT, dpdV;      // (dp/dT)_V [Pa/K], (dp/dV)_T [Pa mol/m^3], V molar
     int status;
+    int nroots;           // physical roots (Z > B) of the cubic at this state
 };
 
 // Mole-weighted NASA-7 coefficient sums of one range: A_j = sum_k x_k R a_j,k
@@ -399,6 +400,7 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
         const int nf = cubic_phys_roots<Real>(c2f, c1f, c0f, Bf, zf, &clear);
         if (nf == 1 && clear) {
             o.status = kOk;
+            o.nroots = 1;
             Zz = (RZ)zf[0];
             larg = (RZ)(Real(2.0 * kSqrt2) * Bf / (zf[0] + Real(1.0 - kSqrt2) * Bf));
             need_rz = false;
@@ -416,6 +418,7 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
         const RZ c0 = B * (B + M<RZ>::fma(B, B, -A));
         RZ zr[3];
         const int nr = cubic_phys_roots<RZ>(c2, c1, c0, B, zr);
+        o.nroots = nr;
         o.status = select_root<RZ>(zr, nr, A, B, Zz);
         if (o.status == kNoRoot) return;
         larg = RZ(2.0 * kSqrt2) * B / (Zz + RZ(1.0 - kSqrt2) * B);

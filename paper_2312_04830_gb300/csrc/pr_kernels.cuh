@@ -203,6 +203,69 @@ __device__ __noinline__ int eval_h(const Comp<Real, NS> &c, double T, Real p, co
     return kOk;
 }
 
+// The first FP64 evaluation of the inversion after the FP32 warm start, with
+// what the one-step acceptance below needs: the root count and the ideal-gas
+// molar cv.
+struct FirstEval {
+    int status;        // the thermodynamics' status (kOk, kAmbiguous or kNoRoot)
+    int nroots;        // physical roots of the cubic
+    double h, cp;      // J/kg, J/(kg K)
+    float cv_ig;       // ideal-gas molar cv [J/(mol K)]
+};
+
+template <typename Real, typename RZ, int NS, bool KIJ>
+__device__ __noinline__ FirstEval eval_h_first(const Comp<Real, NS> &c, double T, Real p, const SpeciesRec<Real> *sp,
+                                               const Real *kij, Real tmid_u)
+{
+    Thermo<Real> th;
+    thermo<Real, RZ, NS, KIJ>(c, (Real)T, p, sp, kij, th, tmid_u);
+    FirstEval f;
+    f.status = th.status;
+    f.nroots = th.status == kNoRoot ? 0 : th.nroots;
+    f.h = (double)th.h;
+    f.cp = (double)th.cp;
+    f.cv_ig = (float)th.cv_ig_molar;
+    return f;
+}
+
+// One-step acceptance of the FP64 inversion.  After the FP32 warm start, a
+// Newton step dT from T on a smooth branch of h(T) leaves an error
+// |e| <= (kappa / 2) (dT / T)^2 T, kappa = T |dcp/dT| / cp (Newton's
+// quadratic convergence).  The step T + dT is taken without a second FP64
+// evaluation when |dT| <= kAcceptStep T (e <= kappa 5e-13 T), the cubic has
+// a single physical root (no phase branch nearby), cp is below the
+// pseudo-boiling band (cp <= kPseudoCriticalCp x the ideal-gas cp, where
+// kappa stays O(10)), and no kink of h(T) -- a species' NASA-7 range switch
+// or the zero of its alpha factor 1 + kappa_k (1 - sqrt(T / Tc_k)) -- lies
+// within 10 |dT| + 1e-5 T of T (checked in FP32 from the FP32 tables).  Other
+// cells continue the safeguarded iteration from this evaluation.
+constexpr double kAcceptStep = 1e-6;
+
+template <int NS>
+__device__ __forceinline__ bool one_step_ok(const FirstEval &f, double T, double dT, double Wbar,
+                                            const SpeciesRec<float> *sp32, float tmid_u)
+{
+    constexpr double kPseudoCp = 3.0;   // as kPseudoCriticalCp below
+    if (f.status != kOk || f.nroots != 1 || !(f.cp > 0.0)) return false;
+    if (!(fabs(dT) <= kAcceptStep * T)) return false;
+    const double T1 = T + dT;
+    if (!(T1 > kTLo && T1 < kTHi)) return false;
+    if (!((float)f.cp * (float)Wbar <= (float)kPseudoCp * (f.cv_ig + (float)kR))) return false;
+    const float Tf = (float)T, margin = 10.f * fabsf((float)dT) + 1e-5f * Tf;
+    bool clear = true;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const float tm = tmid_u > 0.f ? tmid_u : sp32[k].T_mid;
+        clear = clear && fabsf(Tf - tm) > margin;
+        const float kq = sp32[k].kq;
+        if (kq > 0.f) {
+            const float r = (1.f + sp32[k].kappa) / kq;   // sqrt of the alpha factor's zero
+            clear = clear && fabsf(Tf - r * r) > margin;
+        }
+    }
+    return clear;
+}
+
 // h(T) and cp(T) in FP32 with FP32 arguments (the warm start's evaluations).
 template <int NS, bool KIJ>
 __device__ __noinline__ int eval_h_f32(const Comp<float, NS> &c, float T, float p, const SpeciesRec<float> *sp,
@@ -225,8 +288,9 @@ __device__ __noinline__ int eval_h_f32(const Comp<float, NS> &c, float T, float 
 // conversion.
 template <int NS, bool KIJ>
 __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, double T0, double hs, double p,
-                                               const SpeciesRec<float> *sp, const float *kij, float tmid_u)
+                                               const SpeciesRec<float> *sp, const float *kij, float tmid_u, bool &ok)
 {
+    ok = false;
     Comp<float, NS> c;
 #pragma unroll
     for (int k = 0; k < NS; ++k) c.x[k] = (float)c64.x[k];
@@ -242,7 +306,10 @@ __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, doub
         if (!(Tn > (float)kTLo && Tn < (float)kTHi)) return T0;
         const bool done = fabsf(Tn - T) <= 1e-5f * Tn;
         T = Tn;
-        if (done) return (double)T;
+        if (done) {
+            ok = true;
+            return (double)T;
+        }
     }
     return T0;
 }
@@ -256,7 +323,8 @@ __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, doub
 template <typename Real, typename RZ, int NS, bool KIJ>
 __device__ __forceinline__ int newton_solve(const Comp<Real, NS> &c, double hs, Real p, double T,
                                             const SpeciesRec<Real> *sp, const Real *kij, Real tmid_u, int max_iter,
-                                            double rtol, double jump_tol, double &Tres, int &iters, double &cp_last)
+                                            double rtol, double jump_tol, double &Tres, int &iters, double &cp_last,
+                                            bool first_given = false, double h0 = 0.0, double cp0 = 0.0)
 {
     double lo = kTLo, hi = kTHi;
     bool lo_done = false, hi_done = false;   // endpoint h evaluated (range checked)
@@ -266,9 +334,11 @@ __device__ __forceinline__ int newton_solve(const Comp<Real, NS> &c, double hs, 
     cp_last = 0.0;
 #pragma unroll 1
     for (it = 1; it <= max_iter; ++it) {
-        double h, cp;
-        int e = eval_h<Real, RZ, NS, KIJ>(c, T, p, sp, kij, tmid_u, h, cp);
-        if (e) { st = e; Tres = T; break; }
+        double h = h0, cp = cp0;   // the first evaluation, when the caller made it
+        if (it > 1 || !first_given) {
+            int e = eval_h<Real, RZ, NS, KIJ>(c, T, p, sp, kij, tmid_u, h, cp);
+            if (e) { st = e; Tres = T; break; }
+        }
         cp_last = cp;
         const double f = h - hs;
         if (fabs(f) <= rtol * fmax(fabs(hs), fabs(cp) * T)) { st = kOk; Tres = T; break; }
@@ -348,6 +418,94 @@ __device__ __forceinline__ bool comp_fp64_of_fp32(Comp<double, NS> &c, const flo
 // (and the near-critical region), where the mixed inversion re-solves in FP64.
 constexpr double kPseudoCriticalCp = 3.0;
 
+// The FP64 inversion with the FP32 warm start: every cell first tries the
+// one-step acceptance (one FP64 evaluation); the others -- and cells whose
+// warm start failed -- go into a block-wide queue with that evaluation, and
+// whenever the queue holds a block's worth, all threads of the block finish
+// those cells by the safeguarded iteration together, so its longer iterations
+// run in full warps instead of holding back warps whose other cells are done.
+template <int NS, bool KIJ>
+__device__ __forceinline__ void newton_fp64_queued(const NewtonArgs<double> &a, const Smem<double, NS, KIJ> &s,
+                                                   const Smem<float, NS, KIJ> &s32, int64_t stride, double rtol,
+                                                   double jump_tol)
+{
+    __shared__ int q_n;
+    __shared__ int64_t q_i[2 * kBlock];
+    __shared__ double q_T[2 * kBlock], q_h[2 * kBlock], q_cp[2 * kBlock];
+    __shared__ unsigned char q_first[2 * kBlock];
+    if (threadIdx.x == 0) q_n = 0;
+    __syncthreads();
+    // a queued cell through the safeguarded iteration (from its first
+    // evaluation when it has one)
+    auto finish = [&](int e) {
+        const int64_t i = q_i[e];
+        Comp<double, NS> c;
+        load_comp<double, NS>(c, a.Y, a.ldY, i, a.N, s.sp);
+        double Tres, cp_last;
+        int it;
+        const int st = newton_solve<double, double, NS, KIJ>(c, (double)__ldg(a.hstar + i), __ldg(a.p + i), q_T[e],
+                                                             s.sp, s.kij, a.tmid_u, a.max_iter, rtol, jump_tol, Tres,
+                                                             it, cp_last, q_first[e] != 0, q_h[e], q_cp[e]);
+        a.Tout[i] = Tres;
+        a.status[i] = st;
+        if (a.iters) a.iters[i] = it;
+    };
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        if (i < a.n) {
+            const double hs = __ldg(a.hstar + i);
+            const double p = __ldg(a.p + i);
+            const double Tg = __ldg(a.Tg + i);
+            Comp<double, NS> c;
+            bool ok = load_comp<double, NS>(c, a.Y, a.ldY, i, a.N, s.sp);
+            ok = ok && isfinite(hs) && isfinite(Tg) && (p > 0.0) && isfinite(p);
+            if (!ok) {
+                a.Tout[i] = nan("");
+                a.status[i] = kBadInput;
+                if (a.iters) a.iters[i] = 0;
+            } else {
+                bool wok;
+                const double T = warm_start_fp32<NS, KIJ>(c, fmin(fmax(Tg, kTLo), kTHi), hs, p, s32.sp, s32.kij,
+                                                          (float)a.tmid_u, wok);
+                bool accepted = false, first = false;
+                double h0 = 0.0, cp0 = 0.0;
+                if (wok) {
+                    const FirstEval f = eval_h_first<double, double, NS, KIJ>(c, T, p, s.sp, s.kij, a.tmid_u);
+                    if (f.status != kNoRoot) {
+                        const double dT = (f.cp > 0.0) ? -(f.h - hs) / f.cp : 0.0;
+                        if (one_step_ok<NS>(f, T, dT, c.Wbar, s32.sp, (float)a.tmid_u)) {
+                            a.Tout[i] = T + dT;
+                            a.status[i] = kOk;
+                            if (a.iters) a.iters[i] = 1;
+                            accepted = true;
+                        } else {
+                            first = true;
+                            h0 = f.h;
+                            cp0 = f.cp;
+                        }
+                    }
+                }
+                if (!accepted) {   // the safeguarded iteration, in a full batch of the block
+                    const int e = atomicAdd(&q_n, 1);
+                    q_i[e] = i;
+                    q_T[e] = T;
+                    q_h[e] = h0;
+                    q_cp[e] = cp0;
+                    q_first[e] = first ? 1 : 0;
+                }
+            }
+        }
+        __syncthreads();
+        while (q_n >= (int)blockDim.x) {
+            finish(q_n - (int)blockDim.x + (int)threadIdx.x);
+            __syncthreads();
+            if (threadIdx.x == 0) q_n -= (int)blockDim.x;
+            __syncthreads();
+        }
+    }
+    if ((int)threadIdx.x < q_n) finish((int)threadIdx.x);
+}
+
 template <typename Real, typename RZ, int NS, bool KIJ>
 __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a)
 {
@@ -366,6 +524,12 @@ __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a
     const double rtol = (sizeof(Real) == 4) ? fmax(a.rtol, 2e-6) : a.rtol;
     const double jump_tol = (sizeof(Real) == 4) ? 2e-5 : 1e-6;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if constexpr (kFp64) {
+        if (warm) {
+            newton_fp64_queued<NS, KIJ>(a, s, s32[0], stride, rtol, jump_tol);
+            return;
+        }
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         const double hs = (double)__ldg(a.hstar + i);
         const Real p = __ldg(a.p + i);
@@ -377,9 +541,6 @@ __global__ void __launch_bounds__(kBlock) newton_kernel(const NewtonArgs<Real> a
         double Tres = nan("");
         if (ok) {
             double T = fmin(fmax(Tg, kTLo), kTHi);
-            if constexpr (kFp64) {
-                if (warm) T = warm_start_fp32<NS, KIJ>(c, T, hs, (double)p, s32[0].sp, s32[0].kij, (float)a.tmid_u);
-            }
             double cp_last;
             st = newton_solve<Real, RZ, NS, KIJ>(c, hs, p, T, s.sp, s.kij, (Real)a.tmid_u, a.max_iter, rtol, jump_tol,
                                                  Tres, it, cp_last);

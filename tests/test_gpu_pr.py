@@ -235,6 +235,66 @@ def test_reduced_precision_error_budget(ctx, orc, species, cuda, precision):
         assert s["p99"] < 1e-3, (name, s)
 
 
+def test_fp64_inversion_one_step_acceptance(ctx, orc, species, cuda):
+    """The FP64 inversion takes the first FP64 Newton step after the FP32
+    warm start without a second evaluation only on smooth single-root states
+    away from the pseudo-boiling band and from the kinks of h(T): on O2 and
+    CH4 across their pseudo-boiling temperatures at 10 MPa, on cells next to
+    the NASA-7 range switch (1000 K) and on ordinary uniform cells, T equals
+    the oracle's inversion and the true T to 1e-10 (within 0.1 mK of the
+    range switch, where the fits' small step in h gives h(T) = h* two roots,
+    the GPU's T solves h(T) = h* to 1e-12); band cells (cp > 3.3 x the
+    ideal-gas cp) and cells within 5 mK of 1000 K take two or more FP64
+    evaluations, and most ordinary cells take one."""
+    import torch
+    rng = np.random.default_rng(37)
+    n = 6144
+    k_o2, k_ch4 = W.SPECIES.index("O2"), W.SPECIES.index("CH4")
+    Y = np.zeros((9, n))
+    T = np.empty(n)
+    Y[k_o2, :2048] = 1.0
+    T[:2048] = rng.uniform(140.0, 200.0, 2048)                 # O2 across its pseudo-boiling band
+    Y[k_ch4, 2048:4096] = 1.0
+    T[2048:4096] = rng.uniform(190.0, 280.0, 2048)             # CH4
+    Tu, pu, Yu = W.uniform_cells(2048, seed=38)                 # ordinary cells, a few at the range switch
+    T[4096:], Y[:, 4096:] = Tu, Yu
+    T[4096:4352] = 1000.0 + rng.uniform(-0.005, 0.005, 256)
+    p = np.full(n, 10e6)
+    p[4096:] = pu
+    hs, sts = orc.props(species, T, p, Y)
+    guess = T * (1 + rng.uniform(-0.05, 0.05, n))
+    To, sto, _ = orc.T_from_h(species, hs[2], p, Y, guess)
+    d64 = lambda a: to_dev(a, torch.float64, cuda)
+    Tg, stg, itg = ctx.T_from_h(d64(hs[2]), d64(p), d64(Y), d64(guess))
+    Tg, stg, itg = Tg.cpu().numpy(), stg.cpu().numpy(), itg.cpu().numpy()
+    ok = (sto == 0) & (sts == 0)
+    assert ok.sum() > 6000
+    assert np.all(stg[ok] == 0)
+    # the NASA-7 fits do not meet exactly at their range switch: h(T) drops by
+    # ~0.01 J/kg across 1000 K here, so h(T) = h* has a root on either side
+    # within ~1e-5 K of it; there the GPU's T must solve h(T) = h*, whichever
+    # root it found, and elsewhere it must equal the oracle's root
+    near = np.abs(T - 1000.0) < 1e-4
+    far = ok & ~near
+    np.testing.assert_allclose(Tg[far], To[far], rtol=1e-10)
+    np.testing.assert_allclose(Tg[far], T[far], rtol=1e-10)
+    hn, stn = orc.props(species, Tg[ok & near], p[ok & near], Y[:, ok & near])
+    assert np.all(stn == 0)
+    assert np.all(np.abs(hn[2] - hs[2][ok & near]) <= 1e-12 * np.abs(hs[2][ok & near]))
+    cp = hs[3]
+    dT = 1e-3 * T
+    ratio = cp / ((orc.h_ideal(species, T + dT, Y) - orc.h_ideal(species, T - dT, Y)) / (2 * dT))
+    band = ok & (ratio > 3.3)
+    kink = ok & (np.abs(T - 1000.0) < 0.005)
+    plain = ok & (np.arange(n) >= 4352)
+    print("one-step acceptance: band cells %d (min evaluations %d), range-switch cells %d (min %d), "
+          "ordinary cells accepted %.3f" % (band.sum(), itg[band].min(), kink.sum(), itg[kink].min(),
+                                            float((itg[plain] == 1).mean())))
+    assert band.sum() > 200 and np.all(itg[band] >= 2)
+    assert kink.sum() > 200 and np.all(itg[kink] >= 2)
+    assert (itg[plain] == 1).mean() > 0.8
+
+
 def test_mixed_inversion_fp64_in_pseudo_boiling_band(ctx, orc, species, cuda):
     """The mixed inversion re-solves in FP64 the cells whose cp exceeds three
     times the ideal-gas cp (the pseudo-boiling band near the pseudo-critical
