@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = FP64_PEAK_NOMINAL_TFLOPS
 # FP64 flops per cell the FP64 kernels execute, from ncu instruction counts
 # (2 x DFMA + DADD + DMUL per launch / cells) of one launch on the 128^3
 # flame-vortex field; reported beside the algorithmic count as kernel_flops
-FP64_FLOPS_PER_CELL = {"props_fp64": 1413.5, "newton_fp64": 1158.5, "species_fp64": 4117.0}
+FP64_FLOPS_PER_CELL = {"props_fp64": 1413.5, "newton_fp64": 626.7, "species_fp64": 4117.0}
 # Algorithmic FP64 work per cell of the forward property path, from the
 # oracle's operation counter on the 256^3 flame-vortex field (oracle/count_ops.py,
 # whose record is oracle/op_counts_flame_vortex_256.json): the method's
@@ -57,7 +57,7 @@ ALGO_FP64_FLOPS_PER_CELL = {"props_fp64": 1698.6035400390624}
 # / cells) of the same captures; a full launch moves this x its cells (the
 # forward surrogate: DRAM bytes per row of one resident-activation inference
 # launch over a 2 Mi-row chunk of the 128^3 field)
-TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 108.3, "surrogate_bf16": 151.8}
+TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 123.1, "surrogate_bf16": 151.8}
 # surrogate: 2 x (13*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
