@@ -295,6 +295,43 @@ def test_fp64_inversion_one_step_acceptance(ctx, orc, species, cuda):
     assert (itg[plain] == 1).mean() > 0.8
 
 
+@pytest.mark.parametrize("n,band_frac", [(1, 1.0), (31, 0.5), (255, 1.0), (256, 1.0), (257, 0.3), (1000, 1.0),
+                                         (4099, 0.2)])
+def test_T_from_h_fp64_ragged_sizes(ctx, orc, species, cuda, n, band_frac):
+    """The FP64 inversion on ragged sizes, with a share of pseudo-boiling
+    cells (O2 at 10 MPa between 150 and 175 K, which take the full
+    iteration after the first FP64 evaluation) mixed among ordinary cells,
+    up to all of them: every cell's T equals the oracle's inversion and the
+    true T to 1e-10, whether it finished after one evaluation, in a full batch
+    of its block or in the block's last, partial batch."""
+    import torch
+    rng = np.random.default_rng(500 + n)
+    T, p, Y = W.uniform_cells(n, seed=600 + n)
+    band = rng.random(n) < band_frac
+    k_o2 = W.SPECIES.index("O2")
+    Y[:, band] = 0.0
+    Y[k_o2, band] = 1.0
+    T[band] = rng.uniform(150.0, 175.0, int(band.sum()))
+    p[band] = 10e6
+    hs, sts = orc.props(species, T, p, Y)
+    guess = T * (1 + rng.uniform(-0.05, 0.05, n))
+    To, sto, _ = orc.T_from_h(species, hs[2], p, Y, guess)
+    d64 = lambda a: to_dev(a, torch.float64, cuda)
+    Tg, stg, itg = ctx.T_from_h(d64(hs[2]), d64(p), d64(Y), d64(guess))
+    Tg, stg, itg = Tg.cpu().numpy(), stg.cpu().numpy(), itg.cpu().numpy()
+    ok = (sto == 0) & (sts == 0) & (np.abs(T - 1000.0) > 1e-4)   # off the NASA-7 range switch's two roots
+    assert ok.sum() >= 0.95 * n
+    assert np.all(stg[ok] == 0)
+    np.testing.assert_allclose(Tg[ok], To[ok], rtol=1e-10)
+    np.testing.assert_allclose(Tg[ok], T[ok], rtol=1e-10)
+    # cells well inside the band (cp > 3.3 x the ideal-gas cp) never stop
+    # after one evaluation
+    dT = 1e-3 * T
+    ratio = hs[3] / ((orc.h_ideal(species, T + dT, Y) - orc.h_ideal(species, T - dT, Y)) / (2 * dT))
+    inside = ok & band & (ratio > 3.3)
+    assert np.all(itg[inside] >= 2)
+
+
 def test_mixed_inversion_fp64_in_pseudo_boiling_band(ctx, orc, species, cuda):
     """The mixed inversion re-solves in FP64 the cells whose cp exceeds three
     times the ideal-gas cp (the pseudo-boiling band near the pseudo-critical
