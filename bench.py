@@ -58,6 +58,11 @@ ALGO_FP64_FLOPS_PER_CELL = {"props_fp64": 1698.6035400390624}
 # forward surrogate: DRAM bytes per row of one resident-activation inference
 # launch over a 2 Mi-row chunk of the 128^3 field)
 TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 123.1, "surrogate_bf16": 151.8}
+# Instructions per cell the FP32 property kernel issues (ncu smsp__inst_executed.sum
+# x 32 / cells, one full launch on the 128^3 flame-vortex field): the kernel is
+# issue-bound, so its roofline is the issue rate, one warp instruction per
+# clock per scheduler, 4 schedulers per SM
+ISSUED_INSTR_PER_CELL = {"props_fp32": 1244.0}
 # surrogate: 2 x (13*512 + 3*512^2 + 512*6) algorithmic flops per cell (4 x 512 hidden)
 def mlp_flops_per_cell(width=512, layers=4, n_in=13, n_out=6):
     return 2.0 * (n_in * width + (layers - 1) * width * width + width * n_out)
@@ -671,6 +676,13 @@ def run_ours(args):
                       else "executed (ncu DFMA, DADD, DMUL counts)",
                       "kernel_flops_per_cell": FP64_FLOPS_PER_CELL[nm],
                       "kernel_fp64_frac": FP64_FLOPS_PER_CELL[nm] * n / sec / 1e12 / FP64_PEAK_TFLOPS})
+        if nm in ISSUED_INSTR_PER_CELL:
+            mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz")
+            if mhz:
+                issue_peak = 4 * torch.cuda.get_device_properties(dev).multi_processor_count * 32 * mhz * 1e6
+                ir = ISSUED_INSTR_PER_CELL[nm] * n / sec
+                r.update({"issued_instr_per_cell": ISSUED_INSTR_PER_CELL[nm], "thread_instr_per_s": ir,
+                          "issue_frac": ir / issue_peak})
         if nm in ("surrogate_bf16", "surrogate_inverse_bf16"):
             ff = fb_frac if nm == "surrogate_bf16" else float(fbi.float().mean())
             tf = mlp_flops_per_cell() * n * (1.0 - ff) / sec / 1e12
