@@ -172,7 +172,8 @@ __device__ __forceinline__ bool load_comp(Comp<Real, NS> &c, const Real *__restr
 }
 
 // ------------------------------------------------------- a_m(T) and derivatives
-template <typename Real, int NS, bool KIJ>
+// (D2 = false: the second derivative is not needed and left at 0)
+template <typename Real, int NS, bool KIJ, bool D2 = true>
 __device__ __forceinline__ void mix_a(const Comp<Real, NS> &c, Real T, const SpeciesRec<Real> *sp,
                                       const Real *kij1m, Real &am, Real &dam, Real &d2am)
 {
@@ -190,11 +191,11 @@ __device__ __forceinline__ void mix_a(const Comp<Real, NS> &c, Real T, const Spe
             S0 = M<Real>::fma(xg, u, S0);              // x sqrt(ac) |u|
             const Real xgq = xg * sp[k].kq;
             S1 = M<Real>::fma(xgq, h1, S1);
-            S2 = M<Real>::fma(xgq, h2, S2);
+            if constexpr (D2) S2 = M<Real>::fma(xgq, h2, S2);
         }
         am = S0 * S0;
         dam = Real(2) * S0 * S1;
-        d2am = Real(2) * M<Real>::fma(S0, S2, S1 * S1);
+        d2am = D2 ? Real(2) * M<Real>::fma(S0, S2, S1 * S1) : Real(0);
     } else {
         // O(N^2) with (1 - k_ij) weights; per-species terms recomputed in the
         // inner loop instead of being held in N-long register arrays
@@ -217,7 +218,7 @@ __device__ __forceinline__ void mix_a(const Comp<Real, NS> &c, Real T, const Spe
             }
             a0 = M<Real>::fma(ri, t0, a0);
             a1 = M<Real>::fma(Real(2) * dri, t0, a1);
-            a2 = M<Real>::fma(Real(2), M<Real>::fma(d2ri, t0, dri * t1), a2);
+            if constexpr (D2) a2 = M<Real>::fma(Real(2), M<Real>::fma(d2ri, t0, dri * t1), a2);
         }
         am = a0;
         dam = a1;
@@ -371,12 +372,14 @@ __device__ __forceinline__ void nasa_sums(const Comp<Real, NS> &c, const Species
 // tmid_u > 0: every species switches NASA-7 range at tmid_u, so the ideal-gas
 // sums are taken over mole-weighted coefficients (one range test per cell,
 // one polynomial each for cp and h); otherwise species by species.
-template <typename Real, typename RZ, int NS, bool KIJ>
+// CP = false: Z, h and the ideal-gas cv only (cp, the density and the
+// pressure derivatives are left at 0).
+template <typename Real, typename RZ, int NS, bool KIJ, bool CP = true>
 __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, const SpeciesRec<Real> *sp,
                                        const Real *kij1m, Thermo<Real> &o, Real tmid_u = Real(0))
 {
     Real am, dam, d2am;
-    mix_a<Real, NS, KIJ>(c, T, sp, kij1m, am, dam, d2am);
+    mix_a<Real, NS, KIJ, CP>(c, T, sp, kij1m, am, dam, d2am);
     const Real bm = c.bm;
     const Real RT = Real(kR) * T;
     RZ Zz;
@@ -458,6 +461,16 @@ __device__ __forceinline__ void thermo(const Comp<Real, NS> &c, Real T, Real p, 
     const Real Z = (Real)Zz;
     const Real Lr = M<Real>::log1p((Real)larg);
     const Real h_dep = M<Real>::fma(RT, (Real)(Zz - RZ(1)), M<Real>::fma(T, dam, -am) * inv2s2b * Lr);
+    if constexpr (!CP) {
+        o.Z = Z;
+        o.rho_mol = 0;
+        o.h = (h_ig + h_dep) * iW;
+        o.cp = 0;
+        o.cv_ig_molar = cp_ig - Real(kR);
+        o.dpdT = 0;
+        o.dpdV = 0;
+        return;
+    }
     const Real cv_dep = T * d2am * inv2s2b * Lr;
     const Real ZRT = Z * RT;
     const Real rzp = Real(1) / (ZRT * p);

@@ -203,13 +203,15 @@ __device__ __noinline__ int eval_h(const Comp<Real, NS> &c, double T, Real p, co
     return kOk;
 }
 
-// The first FP64 evaluation of the inversion after the FP32 warm start, with
-// what the one-step acceptance below needs: the root count and the ideal-gas
-// molar cv.
+// The first FP64 evaluation of the inversion after the FP32 warm start: h,
+// and what the one-step acceptance below needs, the root count and the
+// ideal-gas molar cv.  cp is not evaluated in FP64 here: the step and the
+// acceptance take the FP32 cp at the same T (the warm start's), whose
+// relative error (~1e-6) moves a step of at most 1e-6 T by ~1e-12 T.
 struct FirstEval {
     int status;        // the thermodynamics' status (kOk, kAmbiguous or kNoRoot)
     int nroots;        // physical roots of the cubic
-    double h, cp;      // J/kg, J/(kg K)
+    double h, cp;      // J/kg; J/(kg K), set by the caller
     float cv_ig;       // ideal-gas molar cv [J/(mol K)]
 };
 
@@ -218,12 +220,12 @@ __device__ __noinline__ FirstEval eval_h_first(const Comp<Real, NS> &c, double T
                                                const Real *kij, Real tmid_u)
 {
     Thermo<Real> th;
-    thermo<Real, RZ, NS, KIJ>(c, (Real)T, p, sp, kij, th, tmid_u);
+    thermo<Real, RZ, NS, KIJ, false>(c, (Real)T, p, sp, kij, th, tmid_u);
     FirstEval f;
     f.status = th.status;
     f.nroots = th.status == kNoRoot ? 0 : th.nroots;
     f.h = (double)th.h;
-    f.cp = (double)th.cp;
+    f.cp = 0.0;
     f.cv_ig = (float)th.cv_ig_molar;
     return f;
 }
@@ -231,8 +233,9 @@ __device__ __noinline__ FirstEval eval_h_first(const Comp<Real, NS> &c, double T
 // One-step acceptance of the FP64 inversion.  After the FP32 warm start, a
 // Newton step dT from T on a smooth branch of h(T) leaves an error
 // |e| <= (kappa / 2) (dT / T)^2 T, kappa = T |dcp/dT| / cp (Newton's
-// quadratic convergence).  The step T + dT is taken without a second FP64
-// evaluation when |dT| <= kAcceptStep T (e <= kappa 5e-13 T), the cubic has
+// quadratic convergence), plus |dT| times the relative error of the cp it
+// divides by (the FP32 cp: ~1e-6).  The step T + dT is taken without a second
+// FP64 evaluation when |dT| <= kAcceptStep T (e <= kappa 5e-13 T + 1e-12 T), the cubic has
 // a single physical root (no phase branch nearby), cp is below the
 // pseudo-boiling band (cp <= kPseudoCriticalCp x the ideal-gas cp, where
 // kappa stays O(10)), and no kink of h(T) -- a species' NASA-7 range switch
@@ -285,12 +288,15 @@ __device__ __noinline__ int eval_h_f32(const Comp<float, NS> &c, float T, float 
 // FP64 iteration then starts from T0 as it would without a warm start).  The
 // update runs in FP32 as well (h* rounded to FP32 moves the root by less than
 // the FP32 enthalpy's own error), so the FP64 pipe only does the final
-// conversion.
+// conversion.  cp_end: the FP32 cp at the returned root (0 if that
+// evaluation fails), for the first FP64 step.
 template <int NS, bool KIJ>
 __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, double T0, double hs, double p,
-                                               const SpeciesRec<float> *sp, const float *kij, float tmid_u, bool &ok)
+                                               const SpeciesRec<float> *sp, const float *kij, float tmid_u, bool &ok,
+                                               float &cp_end)
 {
     ok = false;
+    cp_end = 0.f;
     Comp<float, NS> c;
 #pragma unroll
     for (int k = 0; k < NS; ++k) c.x[k] = (float)c64.x[k];
@@ -308,6 +314,8 @@ __device__ __noinline__ double warm_start_fp32(const Comp<double, NS> &c64, doub
         T = Tn;
         if (done) {
             ok = true;
+            float he, cpe;
+            if (!eval_h_f32<NS, KIJ>(c, T, pf, sp, kij, tmid_u, he, cpe) && cpe > 0.f) cp_end = cpe;
             return (double)T;
         }
     }
@@ -465,12 +473,14 @@ __device__ __forceinline__ void newton_fp64_queued(const NewtonArgs<double> &a, 
                 if (a.iters) a.iters[i] = 0;
             } else {
                 bool wok;
+                float cp32;
                 const double T = warm_start_fp32<NS, KIJ>(c, fmin(fmax(Tg, kTLo), kTHi), hs, p, s32.sp, s32.kij,
-                                                          (float)a.tmid_u, wok);
+                                                          (float)a.tmid_u, wok, cp32);
                 bool accepted = false, first = false;
                 double h0 = 0.0, cp0 = 0.0;
-                if (wok) {
-                    const FirstEval f = eval_h_first<double, double, NS, KIJ>(c, T, p, s.sp, s.kij, a.tmid_u);
+                if (wok && cp32 > 0.f) {
+                    FirstEval f = eval_h_first<double, double, NS, KIJ>(c, T, p, s.sp, s.kij, a.tmid_u);
+                    f.cp = (double)cp32;
                     if (f.status != kNoRoot) {
                         const double dT = (f.cp > 0.0) ? -(f.h - hs) / f.cp : 0.0;
                         if (one_step_ok<NS>(f, T, dT, c.Wbar, s32.sp, (float)a.tmid_u)) {
