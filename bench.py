@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = FP64_PEAK_NOMINAL_TFLOPS
 # FP64 flops per cell the FP64 kernels execute, from ncu instruction counts
 # (2 x DFMA + DADD + DMUL per launch / cells) of one launch on the 128^3
 # flame-vortex field; reported beside the algorithmic count as kernel_flops
-FP64_FLOPS_PER_CELL = {"props_fp64": 1413.5, "newton_fp64": 626.7, "species_fp64": 4117.0}
+FP64_FLOPS_PER_CELL = {"props_fp64": 1413.5, "newton_fp64": 520.6, "species_fp64": 4117.0}
 # Algorithmic FP64 work per cell of the forward property path, from the
 # oracle's operation counter on the 256^3 flame-vortex field (oracle/count_ops.py,
 # whose record is oracle/op_counts_flame_vortex_256.json): the method's
@@ -57,7 +57,7 @@ ALGO_FP64_FLOPS_PER_CELL = {"props_fp64": 1698.6035400390624}
 # / cells) of the same captures; a full launch moves this x its cells (the
 # forward surrogate: DRAM bytes per row of one resident-activation inference
 # launch over a 2 Mi-row chunk of the 128^3 field)
-TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 123.1, "surrogate_bf16": 151.8}
+TRAFFIC_BYTES_PER_CELL = {"props_fp64": 124.6, "newton_fp64": 125.4, "surrogate_bf16": 151.8}
 # Instructions per cell the FP32 property kernel issues (ncu smsp__inst_executed.sum
 # x 32 / cells, one full launch on the 128^3 flame-vortex field): the kernel is
 # issue-bound, so its roofline is the issue rate, one warp instruction per
