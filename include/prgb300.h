@@ -322,8 +322,11 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
  * activations stay in L2-sized rings (widths that are multiples of 256, up
  * to 1024, hidden_layers x width <= 4528), 128 x 256 tiles, one CTA each;
  * 2: the same with 256 x 256 tiles on CTA pairs, falling back to 1 when the
- * device refuses that launch; 0: one GEMM launch per layer.  All give
- * identical outputs.  PR_EINVAL for an unknown option or a value the model
+ * device refuses that launch; 4 (widths 256 and 512, cluster launches): CTA
+ * pairs whose activations alternate from layer to layer between tensor
+ * memory (read as the next layer's MMA A operand) and shared memory, in
+ * N-tiles of 128; 0: one GEMM launch per layer.  All give identical
+ * outputs.  PR_EINVAL for an unknown option or a value the model
  * cannot take. */
 #define SG_OPT_FUSED_INFER 1
 /* SG_OPT_MODE: SG_MODE_FORWARD (default) or SG_MODE_INVERSE, the paper's own

@@ -379,8 +379,9 @@ class Surrogate:
         block's activations in shared memory through all layers; True:
         activation rings in L2, 128 x 256 tiles, one CTA each; 'pair': the
         same with 256 x 256 tiles on CTA pairs), or one launch per layer
-        (False)."""
-        v = {"pair": 2, "resident": 3}.get(on, None) if isinstance(on, str) else int(bool(on))
+        (False); 'pingpong': CTA pairs whose activations alternate between
+        tensor memory and shared memory from layer to layer."""
+        v = {"pair": 2, "resident": 3, "pingpong": 4}.get(on, None) if isinstance(on, str) else int(bool(on))
         if v is None:
             raise ValueError(f"unknown fused-inference kind {on!r}")
         check(_sg_lib().surrogate_set_option(self.handle, SG_OPT_FUSED_INFER, v), "surrogate_set_option")
@@ -388,15 +389,15 @@ class Surrogate:
     def get_option(self, option: int) -> int:
         """Current value of a model option (SG_OPT_*); for SG_OPT_FUSED_INFER
         the kernel the next inference runs: 0 per layer, 1 single CTAs, 2
-        CTA pairs, 3 resident activations."""
+        CTA pairs, 3 resident activations, 4 alternating activations."""
         v = ctypes.c_int(0)
         check(_sg_lib().surrogate_get_option(self.handle, int(option), ctypes.byref(v)), "surrogate_get_option")
         return v.value
 
     @property
     def fused_kind(self) -> str:
-        """'resident', 'pair', 'single' or 'per-layer': the inference kernel in use."""
-        return {0: "per-layer", 1: "single", 2: "pair", 3: "resident"}[self.get_option(SG_OPT_FUSED_INFER)]
+        """'pingpong', 'resident', 'pair', 'single' or 'per-layer': the inference kernel in use."""
+        return {0: "per-layer", 1: "single", 2: "pair", 3: "resident", 4: "pingpong"}[self.get_option(SG_OPT_FUSED_INFER)]
 
     def set_loss(self, kind: str):
         """Training loss: 'mse' (relative MSE on the standardised targets, the

@@ -27,6 +27,7 @@
 
 #include "mlp_fused.cuh"
 #include "mlp_resident.cuh"
+#include "mlp_pingpong.cuh"
 #include "mlp_gemm.cuh"
 #include "pr_device.cuh"
 #include "pr_internal.h"
@@ -991,6 +992,68 @@ int resident_pairs(int L, int W)
     return nc;
 }
 
+inline const void *pingpong_fn(int L, int W)
+{
+    const bool wo = PPCfg::wout_resident(L, W);
+    if (W == 256) return wo ? reinterpret_cast<const void *>(mlp_pingpong_kernel<256, true>)
+                            : reinterpret_cast<const void *>(mlp_pingpong_kernel<256, false>);
+    return wo ? reinterpret_cast<const void *>(mlp_pingpong_kernel<512, true>)
+              : reinterpret_cast<const void *>(mlp_pingpong_kernel<512, false>);
+}
+
+// CTA pairs of the alternating-activation kernel the device holds at once
+// (0: none, or cluster launches unavailable).
+int pingpong_pairs(int L, int W)
+{
+    if (cudaFuncSetAttribute(pingpong_fn(L, W), cudaFuncAttributeMaxDynamicSharedMemorySize, PPCfg::kMaxSmem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * num_sms_current(), 1, 1);
+    cfg.blockDim = dim3(kPPThreads, 1, 1);
+    cfg.dynamicSmemBytes = PPCfg::smem_bytes(L, W, PPCfg::wout_resident(L, W));
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, pingpong_fn(L, W), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+// One launch of the alternating-activation kernel (as launch_resident).
+cudaError_t launch_pingpong(const ResidentArgs &ra, int pairs, cudaStream_t st)
+{
+    const int R = (ra.M + 255) / 256;
+    const int g = R < pairs ? R : pairs;
+    const bool wo = PPCfg::wout_resident(ra.L, ra.W);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * g), 1, 1);
+    cfg.blockDim = dim3(kPPThreads, 1, 1);
+    cfg.dynamicSmemBytes = PPCfg::smem_bytes(ra.L, ra.W, wo);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (ra.W == 256)
+        return wo ? cudaLaunchKernelEx(&cfg, mlp_pingpong_kernel<256, true>, ra)
+                  : cudaLaunchKernelEx(&cfg, mlp_pingpong_kernel<256, false>, ra);
+    return wo ? cudaLaunchKernelEx(&cfg, mlp_pingpong_kernel<512, true>, ra)
+              : cudaLaunchKernelEx(&cfg, mlp_pingpong_kernel<512, false>, ra);
+}
+
 // One launch of the resident-activation kernel: a pair per block of 256 rows,
 // at most `pairs` pairs (each walks its blocks in turn; pairs never wait on
 // one another, so no co-residency is needed).
@@ -1080,6 +1143,11 @@ static pr_status build_maps(sg_model *m)
             ok = ok && make_map(&m->tmr_w[0], d.wb[0], KIN, W, KIN, (uint32_t)(W / 4));
             for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tmr_w[l], d.wb[l], W, W, W, (uint32_t)(W / 4));
             ok = ok && make_map(&m->tmr_w[L], d.wb[L], W, NOP, W, 8);
+        }
+        if (m->pp_pairs > 0) {   // alternating activations: a CTA's 64 rows of every 128-row N-tile
+            ok = ok && make_map(&m->tmq_w[0], d.wb[0], KIN, W, KIN, (uint32_t)(kPPBN / 2));
+            for (int l = 1; l < L; ++l) ok = ok && make_map(&m->tmq_w[l], d.wb[l], W, W, W, (uint32_t)(kPPBN / 2));
+            ok = ok && make_map(&m->tmq_w[L], d.wb[L], W, NOP, W, 8);
         }
         const int64_t rr = (int64_t)m->fused_ring_rows * 128;
         ok = ok && make_map_3d(&m->tmf_ring_ld, m->ring, W, rr, L, 128);
@@ -1221,6 +1289,7 @@ pr_status surrogate_create(pr_ctx *ctx, const sg_config *cfg, uint64_t seed, sg_
         alloc((void **)&m->ring, (size_t)L * m->fused_ring_rows * 128 * W * 2);
         alloc((void **)&m->d_done, (size_t)ceil_div(C, 128) * (L + 1) * 4);
         m->res_pairs = ResCfg::supports(L, W) ? resident_pairs(L, W) : 0;
+        m->pp_pairs = PPCfg::supports(L, W) ? pingpong_pairs(L, W) : 0;
     }
     m->fused_on = m->res_pairs > 0 ? 3 : m->fused_ok;   // resident activations where the shape allows
     alloc((void **)&d.hi[0], C * W * 2);
@@ -1483,14 +1552,16 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             PR_CUDA_TRY(mlp_timer_pair(m, tm0, tm1));
             PR_CUDA_TRY(cudaEventRecord(tm0, st));
         }
-        if (m->fused_on == 3 && m->res_pairs > 0) {
+        if ((m->fused_on == 3 && m->res_pairs > 0) || (m->fused_on == 4 && m->pp_pairs > 0)) {
             // every layer in one launch, activations resident in shared memory
-            // (mlp_resident.cuh)
+            // (mlp_resident.cuh), or alternating between tensor and shared
+            // memory (mlp_pingpong.cuh)
+            const bool pp = m->fused_on == 4;
             ResidentArgs ra;
             memset(&ra, 0, sizeof(ra));
             ra.tm_x = m->tm_xi;
             for (int l = 0; l <= L; ++l) {
-                ra.tm_w[l] = m->tmr_w[l];
+                ra.tm_w[l] = pp ? m->tmq_w[l] : m->tmr_w[l];
                 ra.bias[l] = d.master + d.lay[l].b_off;
             }
             ra.M = (int)mc; ra.L = L; ra.W = W;
@@ -1502,7 +1573,8 @@ pr_status surrogate_infer(sg_model *m, int64_t n, const float *T, const float *p
             ra.err = m->d_err;
             ra.wait_cycles = m->wait_cycles > 0 ? m->wait_cycles : 4000000000LL;
             ra.stall_test = m->stall_test;
-            PR_CUDA_TRY(launch_resident(ra, m->res_pairs, st));
+            if (pp) PR_CUDA_TRY(launch_pingpong(ra, m->pp_pairs, st));
+            else PR_CUDA_TRY(launch_resident(ra, m->res_pairs, st));
         } else if (m->fused_on) {
             // every layer in one cooperative launch (mlp_fused.cuh): single
             // CTAs, or CTA pairs when asked for and the device takes them
@@ -1621,6 +1693,7 @@ pr_status surrogate_get_option(const sg_model *m, int option, int *value)
     switch (option) {
     case SG_OPT_FUSED_INFER:
         *value = !m->fused_on                            ? 0
+                 : (m->fused_on == 4 && m->pp_pairs > 0)  ? 4
                  : (m->fused_on == 3 && m->res_pairs > 0) ? 3
                  : (m->fused_on == 2 && m->fused_pair_ok) ? 2
                                                           : 1;
@@ -1644,7 +1717,8 @@ pr_status surrogate_set_option(sg_model *m, int option, int value)
     PR_CHECK_ARG(m != nullptr, "surrogate_set_option: null model");
     switch (option) {
     case SG_OPT_FUSED_INFER:
-        PR_CHECK_ARG(value == 0 || ((value == 1 || value == 2) && m->fused_ok) || (value == 3 && m->res_pairs > 0),
+        PR_CHECK_ARG(value == 0 || ((value == 1 || value == 2) && m->fused_ok) || (value == 3 && m->res_pairs > 0) ||
+                         (value == 4 && m->pp_pairs > 0),
                      "surrogate_set_option: fused inference needs a width that is a multiple of 256, <= 1024, "
                      "and its biases within shared memory; resident activations need a width of 256 or 512 "
                      "and cluster launches");

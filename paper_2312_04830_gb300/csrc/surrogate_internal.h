@@ -131,6 +131,11 @@ struct sg_model {
     // once (0: not available for this shape), weight boxes of W / 4 rows
     int res_pairs;
     CUtensorMap tmr_w[SG_MAX_HIDDEN + 1];
+    // activations alternating between tensor and shared memory
+    // (mlp_pingpong.cuh): CTA pairs the device holds at once, and the weight
+    // maps (boxes of 64 rows: a CTA's half of a 128-row N-tile)
+    int pp_pairs;
+    CUtensorMap tmq_w[SG_MAX_HIDDEN + 1];
     std::vector<void *> allocs;
     // SG_OPT_TIME_MLP: event pairs (start, stop) around the MLP launches,
     // reused; the first 2 tev_used of them hold intervals not yet read

@@ -210,9 +210,10 @@ def test_inference_matches_oracle_forward(ctx, orc, species, cuda):
 def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers, chunk, n):
     """All layers of a chunk in one persistent launch -- activation ring in L2
     with cross-CTA arrival counters, 128 x 256 tiles on single CTAs or 256 x
-    256 tiles on CTA pairs, or CTA pairs keeping each 256-row block's
-    activations in shared memory through all layers (the default) -- give the
-    same bits as one launch per layer: chunks longer than the ring (ring slots reused), a
+    256 tiles on CTA pairs, CTA pairs keeping each 256-row block's
+    activations in shared memory through all layers (the default), or CTA
+    pairs alternating them between tensor memory (the next layer's A operand)
+    and shared memory -- give the same bits as one launch per layer: chunks longer than the ring (ring slots reused), a
     ragged last chunk, an odd number of row blocks (the last pair's second
     half empty), a chunk shorter than the grid, one hidden layer, width 256
     (N-tiles of 128), and six hidden layers (the output layer's weights then
@@ -228,7 +229,8 @@ def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers
     Td, pd, Yd = d(T), d(p), d(Y)
     assert sg.fused_kind == "resident"
     outs = []
-    kinds = ((True, "single"), ("pair", "pair"), ("resident", "resident"), (False, "per-layer"))
+    kinds = ((True, "single"), ("pair", "pair"), ("resident", "resident"), ("pingpong", "pingpong"),
+             (False, "per-layer"))
     for fused, kind in kinds:
         sg.set_fused_infer(fused)
         assert sg.fused_kind == kind
@@ -1088,9 +1090,9 @@ def test_mlp_launch_timing(ctx, orc, species, cuda):
 
 @pytest.mark.parametrize("chunk", [128, 1024])
 def test_resident_inference_small_calls(ctx, orc, species, cuda, chunk):
-    """The default kernel on calls of 1 to 257 rows (a pair whose second CTA has
-    no row, a last block of one row, a chunk shorter than a pair's 256 rows)
-    gives the per-layer launches' bits."""
+    """The default kernel and the alternating-activation kernel on calls of 1
+    to 257 rows (a pair whose second CTA has no row, a last block of one row, a
+    chunk shorter than a pair's 256 rows) give the per-layer launches' bits."""
     import torch
     from paper_2312_04830_gb300 import binding
     sg = binding.Surrogate(ctx, width=512, hidden_layers=4, max_batch=1024, infer_chunk=chunk, seed=81)
@@ -1102,10 +1104,11 @@ def test_resident_inference_small_calls(ctx, orc, species, cuda, chunk):
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=cuda)
     for n in (1, 2, 127, 128, 129, 255, 256, 257):
         args = (d(T[:n]), d(p[:n]), d(Y[:, :n]))
-        sg.set_fused_infer("resident")
-        o_r, _ = sg.infer(*args)
         sg.set_fused_infer(False)
         o_l, _ = sg.infer(*args)
-        sg.sync_status()
-        assert np.array_equal(o_r.cpu().numpy(), o_l.cpu().numpy(), equal_nan=True), n
+        for kind in ("resident", "pingpong"):
+            sg.set_fused_infer(kind)
+            o_r, _ = sg.infer(*args)
+            sg.sync_status()
+            assert np.array_equal(o_r.cpu().numpy(), o_l.cpu().numpy(), equal_nan=True), (kind, n)
     sg.close()
