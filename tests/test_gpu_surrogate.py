@@ -243,10 +243,12 @@ def test_fused_inference_equals_layerwise(ctx, orc, species, cuda, width, layers
     sg.close()
 
 
-@pytest.mark.parametrize("kind", [True, "pair", "resident"])
+@pytest.mark.parametrize("kind", [True, "pair", "resident", "pingpong"])
 def test_fused_inference_wait_timeout_is_reported(ctx, orc, species, cuda, kind):
-    """Failure detection of the persistent kernel (single CTAs and CTA pairs):
-    with one arrival counter made unreachable and a short wait limit (20M
+    """Failure detection of the persistent kernels (single CTAs, CTA pairs,
+    resident and alternating activations): with one wait made unreachable
+    (an arrival counter, or an epilogue the MMA issuer waits for that never
+    comes) and a short wait limit (20M
     cycles, ~10 ms), the waits run out, the kernel finishes, the host gets
     PR_ETIMEOUT, and the context stays usable: the next launches give the
     per-layer result bit for bit."""
