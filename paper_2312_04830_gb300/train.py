@@ -5,7 +5,7 @@ uniform cells and half noisy flame-sheet states, labelled by the FP64
 Peng-Robinson path (`pr_props`); states with non-physical outcomes dropped
 (the paper's data constraints, Sec. 4.2); batches of 65536 drawn from the pool;
 Adam with a cosine-decayed learning rate; error measured on held-out states
-against the FP64 PR path, the surrogate's judge.
+against the FP64 PR path.
 
     python -m paper_2312_04830_gb300.train --pool 67108864 --epochs 20 --save sg.ckpt
 
