@@ -25,9 +25,12 @@
 // every MMA issued before), and the MMAs that last read that buffer (the
 // layer before, or the previous block's) were issued earlier.
 //
-// Weights: each CTA loads its 64 rows of a 128-row N-tile, one K-block of 64
-// at a time (8 KB stages, eight of them); the output layer's 8 rows per CTA
-// stay in shared memory when they fit.  Every wait is bounded; a failed wait
+// Weights: each CTA loads its 64 rows of a 128-row N-tile, two K-blocks of 64
+// per stage (16 KB stages, four of them: one barrier poll, fence and commit
+// of the MMA issuer per eight MMAs, which hides that bookkeeping behind the
+// 128-column MMAs; the input layer's stage holds two N-tiles' single
+// K-blocks); the output layer's 8 rows per CTA stay in shared memory when
+// they fit.  Every wait is bounded; a failed wait
 // sets the error flag, the roles stop, and the epilogue warps keep their trip
 // counts so their named barrier always completes.
 #pragma once
@@ -39,8 +42,9 @@ namespace mlp {
 constexpr int kPPEpiWarps = 16;                      // four per TMEM lane quarter
 constexpr int kPPThreads = 64 + 32 * kPPEpiWarps;    // producer, MMA issuer, epilogue
 constexpr int kPPBN = 128;                           // N-tile width
-constexpr int kPPStages = 8;
-constexpr int kPPStage = 8192;                       // this CTA's 64 rows x 64 K of a weight N-tile
+constexpr int kPPStages = 4;
+constexpr int kPPStage = 16384;                      // two halves of this CTA's 64 rows x 64 K of a weight N-tile
+constexpr int kPPHalf = 8192;
 constexpr uint32_t kPPAccCol = 256;                  // first accumulator column
 
 // Shared memory: the activation (128 x W BF16), the input tile (128 x 64
@@ -178,17 +182,19 @@ __global__ void __launch_bounds__(kPPThreads, 1) mlp_pingpong_kernel(const __gri
         if (lane == 0) {
             PPRing rp;
             uint32_t it = 0, nx = 0;
-            const uint32_t wbytes = 2u * 64u * 128u;   // the pair's halves of a weight K-block
+            const uint32_t wbytes = 2u * 2u * 64u * 128u;   // both CTAs' two K-blocks of a stage
             const int hrow = (int)rank * (kPPBN / 2);
-            auto put = [&](const CUtensorMap *tm, int c0, int c1, uint32_t bytes) {
+            // one stage: the boxes at (k0, r0) and (k1, r1) in its two halves
+            auto put = [&](const CUtensorMap *tm, int k0, int r0, int k1, int r1, uint32_t bytes) {
                 if (fail) return;
                 if (it >= (uint32_t)S && !umma::mbar_wait(&empty[rp.s], rp.ph ^ 1u, wc)) {
                     fail = true;
                     return;
                 }
                 if (leader) umma::mbar_arrive_expect_tx(&full[rp.s], bytes);
-                umma::tma_load_2d_pair(stage + rp.s * kPPStage, tm, umma::mapa_shared(umma::smem_u32(&full[rp.s]), 0u),
-                                       c0, c1);
+                const uint32_t bar = umma::mapa_shared(umma::smem_u32(&full[rp.s]), 0u);
+                umma::tma_load_2d_pair(stage + rp.s * kPPStage, tm, bar, k0, r0);
+                umma::tma_load_2d_pair(stage + rp.s * kPPStage + kPPHalf, tm, bar, k1, r1);
                 ++it;
                 rp.next();
             };
@@ -208,12 +214,14 @@ __global__ void __launch_bounds__(kPPThreads, 1) mlp_pingpong_kernel(const __gri
                 umma::tma_load_2d_pair(xbuf, &a.tm_x, umma::mapa_shared(umma::smem_u32(x_full), 0u), 0,
                                        r * 256 + (int)rank * 128);
                 ++nx;
-                for (int j = 0; j < NT; ++j) put(&a.tm_w[0], 0, j * kPPBN + hrow, wbytes);
+                for (int j = 0; j < NT; j += 2) put(&a.tm_w[0], 0, j * kPPBN + hrow, 0, (j + 1) * kPPBN + hrow, wbytes);
                 for (int l = 1; l < L; ++l)
                     for (int j = 0; j < NT; ++j)
-                        for (int k = 0; k < nkb; ++k) put(&a.tm_w[l], k * 64, j * kPPBN + hrow, wbytes);
+                        for (int k = 0; k < nkb; k += 2)
+                            put(&a.tm_w[l], k * 64, j * kPPBN + hrow, (k + 1) * 64, j * kPPBN + hrow, wbytes);
                 if (!WO)
-                    for (int k = 0; k < nkb; ++k) put(&a.tm_w[L], k * 64, (int)rank * 8, 2u * 8u * 128u);
+                    for (int k = 0; k < nkb; k += 2)
+                        put(&a.tm_w[L], k * 64, (int)rank * 8, (k + 1) * 64, (int)rank * 8, 2u * 2u * 8u * 128u);
             }
             const uint32_t it_end = it;
             for (int j = 0; j < S && !fail; ++j) {
@@ -281,20 +289,27 @@ __global__ void __launch_bounds__(kPPThreads, 1) mlp_pingpong_kernel(const __gri
                     ++nwo;
                     umma::tc_fence_after();
                 }
+                const uint32_t id = output ? id_o : id_h;
 #pragma unroll 1
-                for (int k = 0; k < nkb && !fail; ++k) {
-                    if (first_of_layer && (k & 1) == 0) wait_ev(prev_first + (uint32_t)(k >> 1));
+                for (int k = 0; k < nkb && !fail; k += 2) {   // two K-blocks per stage
+                    if (first_of_layer) wait_ev(prev_first + (uint32_t)(k >> 1));
                     if (fail) break;
-                    uint64_t db;
+                    uint64_t db0, db1;
                     if (output && WO) {
-                        db = d_wo + (uint64_t)(k * 64);
+                        db0 = d_wo + (uint64_t)(k * 64);
+                        db1 = db0 + 64;
                     } else {
-                        db = take();
+                        db0 = take();
                         if (fail) break;
+                        db1 = db0 + (uint64_t)(kPPHalf >> 4);
                     }
-                    const uint32_t id = output ? id_o : id_h;
-                    if (fromT) kblock_t(d, actT + 32u * (uint32_t)k, db, id, k > 0);
-                    else kblock_s(d, d_act + (uint64_t)(k * kBlkDesc), db, id, k > 0);
+                    if (fromT) {
+                        kblock_t(d, actT + 32u * (uint32_t)k, db0, id, k > 0);
+                        kblock_t(d, actT + 32u * (uint32_t)(k + 1), db1, id, true);
+                    } else {
+                        kblock_s(d, d_act + (uint64_t)(k * kBlkDesc), db0, id, k > 0);
+                        kblock_s(d, d_act + (uint64_t)((k + 1) * kBlkDesc), db1, id, true);
+                    }
                     if (!(output && WO)) give();
                 }
                 if (!fail) umma::mma_commit_pair_mc(&afull[g & 1u], (uint16_t)0x3);
@@ -304,15 +319,19 @@ __global__ void __launch_bounds__(kPPThreads, 1) mlp_pingpong_kernel(const __gri
                 if (!fail && !umma::mbar_wait(x_full, nxf & 1u, wc)) fail = true;
                 ++nxf;
                 umma::tc_fence_after();
-                // input layer: K = 64 from the input tile
-                for (int j = 0; j < NT && !fail; ++j) {
-                    if (g >= 2) wait_ev(g - 2);
+                // input layer: K = 64 from the input tile, two N-tiles per stage
+                for (int j = 0; j < NT && !fail; j += 2) {
                     const uint64_t db = take();
                     if (fail) break;
-                    kblock_s(acc0 + (g & 1u) * kPPBN, d_x, db, id_h, false);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (g >= 2) wait_ev(g - 2);
+                        if (fail) break;
+                        kblock_s(acc0 + (g & 1u) * kPPBN, d_x, db + (uint64_t)(h * (kPPHalf >> 4)), id_h, false);
+                        umma::mma_commit_pair_mc(&afull[g & 1u], (uint16_t)0x3);
+                        ++g;
+                    }
                     give();
-                    umma::mma_commit_pair_mc(&afull[g & 1u], (uint16_t)0x3);
-                    ++g;
                 }
                 if (fail) break;
                 umma::mma_commit_pair_mc(x_empty, (uint16_t)0x3);
