@@ -416,7 +416,8 @@ pr_status surrogate_set_option(sg_model *m, int option, int value);
 
 /* Current value of an option (host int *value).  For SG_OPT_FUSED_INFER it
  * is the kernel the next inference runs: 0 per-layer launches, 1 single
- * CTAs, 2 CTA pairs, 3 resident activations.  PR_EINVAL for an unknown
+ * CTAs, 2 CTA pairs, 3 resident activations, 4 activations alternating
+ * between tensor and shared memory.  PR_EINVAL for an unknown
  * option or a null pointer. */
 pr_status surrogate_get_option(const sg_model *m, int option, int *value);
 
